@@ -1,0 +1,285 @@
+"""Seeded synthetic problem generators (meshes, masks, loads, G_c fields).
+
+This module holds no arithmetic of the crack-element method itself: it only
+describes problems -- structured Q4 grid sizes, which elements are active,
+which edges are loaded and by what time law, which elements are pre-cracked,
+and the per-element critical energy release rate G_c.  Both the CUDA library
+binding and the CPU oracle read the same ``Problem``.
+
+Numbering (also stated in ``include/cem.h``):
+  node (i, j)      -> j*(nx+1) + i
+  element (i, j)   -> j*nx + i
+  horizontal edge (i, j), nodes (i,j)-(i+1,j), 0 <= j <= ny -> j*nx + i
+  vertical edge (i, j),   nodes (i,j)-(i,j+1), 0 <= j < ny  -> nx*(ny+1) + j*(nx+1) + i
+  element local edges: 0 bottom, 1 right, 2 top, 3 left.
+
+Workloads (materials from the paper's Sec. 4.2 Neumann branching example:
+E = 32 GPa, nu = 0.2, rho = 2450 kg/m^3, G_c = 3 J/m^2):
+  * ``notched_plate``: 0.1 x 0.04 m plate, pre-notch along mid-height from
+    the left edge, constant normal traction on top and bottom (Sec. 4.2).
+  * ``fragmentation``: square plate with a central hole under an internal
+    pressure pulse (shape of the Sec. 4.4 law) or an outward edge velocity,
+    Weibull G_c field.
+  * ``batch_specimens``: notched plates of random size, notch and traction.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+TRACTION, PRESSURE, VELOCITY = 0, 1, 2
+LAW_CONST, LAW_RAMP, LAW_RAMP_EXP = 0, 1, 2
+SCOPE_NBHD, SCOPE_GLOBAL, SCOPE_TIPS = 0, 1, 2
+
+
+# ----------------------------------------------------------------- Philox
+_M0, _M1 = 0xD2511F53, 0xCD9E8D57
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+_MASK = 0xFFFFFFFF
+
+
+def philox4x32_10(counter: np.ndarray, key) -> np.ndarray:
+    """Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), vectorised.
+
+    counter: (n, 4) uint32 array; key: two uint32 words.  Returns (n, 4) uint32.
+    """
+    c = np.asarray(counter, dtype=np.uint64).reshape(-1, 4).copy()
+    k0, k1 = np.uint64(int(key[0]) & _MASK), np.uint64(int(key[1]) & _MASK)
+    m0, m1, mask = np.uint64(_M0), np.uint64(_M1), np.uint64(_MASK)
+    for r in range(10):
+        if r:
+            k0 = np.uint64((int(k0) + _W0) & _MASK)
+            k1 = np.uint64((int(k1) + _W1) & _MASK)
+        p0 = m0 * c[:, 0]
+        p1 = m1 * c[:, 2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        n0 = hi1 ^ c[:, 1] ^ k0
+        n2 = hi0 ^ c[:, 3] ^ k1
+        c = np.stack([n0, lo1, n2, lo0], axis=1)
+    return c.astype(np.uint32)
+
+
+def uniform01(n: int, seed: int, stream: int = 0) -> np.ndarray:
+    """n uniforms in (0, 1): U_e = (x_e + 0.5) / 2^32, x_e = first Philox word
+    of counter (e, stream, 0, 0) under key (seed, 0)."""
+    ctr = np.zeros((n, 4), dtype=np.uint64)
+    ctr[:, 0] = np.arange(n, dtype=np.uint64)
+    ctr[:, 1] = stream
+    x = philox4x32_10(ctr, (seed, 0))[:, 0].astype(np.float64)
+    return (x + 0.5) / 4294967296.0
+
+
+def weibull_gc(n: int, mean: float, shape: float, seed: int) -> np.ndarray:
+    """Per-element G_c = lam * (-ln U)^(1/k), lam = mean / Gamma(1 + 1/k), FP32."""
+    lam = mean / math.gamma(1.0 + 1.0 / shape)
+    u = uniform01(n, seed)
+    return (lam * (-np.log(u)) ** (1.0 / shape)).astype(np.float32)
+
+
+# ---------------------------------------------------------------- records
+@dataclass
+class Material:
+    E: float = 32e9
+    nu: float = 0.2
+    rho: float = 2450.0
+    gc_uniform: float = 3.0
+    plane_strain: bool = True
+    gamma: float = 1.0
+    gamma_mode: int = 0
+    scope: int = SCOPE_NBHD
+
+
+@dataclass
+class BC:
+    kind: int
+    items: np.ndarray
+    comp_mask: int = 0
+    law: int = LAW_CONST
+    a0: float = 0.0
+    t0: float = 0.0
+    tau: float = 0.0
+
+
+@dataclass
+class Problem:
+    name: str
+    nx: int
+    ny: int
+    hx: float
+    hy: float
+    material: Material = field(default_factory=Material)
+    active: Optional[np.ndarray] = None      # uint8 per element, None = all
+    gc: Optional[np.ndarray] = None          # float32 per element, None = uniform
+    bcs: List[BC] = field(default_factory=list)
+    precracks: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.int32))
+    dt_factor: float = 0.5
+    dt: Optional[float] = None
+    steps: int = 0
+    energy_every: int = 0
+    phantom_cap: int = 4096
+    crack_cap: int = 4096
+
+    @property
+    def n_nodes(self):
+        return (self.nx + 1) * (self.ny + 1)
+
+    @property
+    def n_elems(self):
+        return self.nx * self.ny
+
+    @property
+    def n_active(self):
+        return self.n_elems if self.active is None else int(np.count_nonzero(self.active))
+
+
+# ---------------------------------------------------------------- topology
+def h_edge(nx, i, j):
+    return j * nx + i
+
+
+def v_edge(nx, ny, i, j):
+    return nx * (ny + 1) + j * (nx + 1) + i
+
+
+def node_id(nx, i, j):
+    return j * (nx + 1) + i
+
+
+def boundary_edges(nx, ny, side):
+    """Edge ids of one side of the outer rectangle: 'bottom', 'top', 'left', 'right'."""
+    if side == "bottom":
+        return np.array([h_edge(nx, i, 0) for i in range(nx)], np.int32)
+    if side == "top":
+        return np.array([h_edge(nx, i, ny) for i in range(nx)], np.int32)
+    if side == "left":
+        return np.array([v_edge(nx, ny, 0, j) for j in range(ny)], np.int32)
+    if side == "right":
+        return np.array([v_edge(nx, ny, nx, j) for j in range(ny)], np.int32)
+    raise ValueError(side)
+
+
+def boundary_nodes(nx, ny, side):
+    if side == "bottom":
+        return np.array([node_id(nx, i, 0) for i in range(nx + 1)], np.int32)
+    if side == "top":
+        return np.array([node_id(nx, i, ny) for i in range(nx + 1)], np.int32)
+    if side == "left":
+        return np.array([node_id(nx, 0, j) for j in range(ny + 1)], np.int32)
+    if side == "right":
+        return np.array([node_id(nx, nx, j) for j in range(ny + 1)], np.int32)
+    raise ValueError(side)
+
+
+def interface_edges(nx, ny, active):
+    """Edges between an active and an inactive element (the rim of a hole)."""
+    act = np.asarray(active, bool).reshape(ny, nx)
+    out = []
+    # horizontal edges 1..ny-1 separate rows j-1 and j
+    for j in range(1, ny):
+        diff = act[j - 1, :] != act[j, :]
+        for i in np.nonzero(diff)[0]:
+            out.append(h_edge(nx, int(i), j))
+    for j in range(ny):
+        diff = act[j, :-1] != act[j, 1:]
+        for i in np.nonzero(diff)[0]:
+            out.append(v_edge(nx, ny, int(i) + 1, j))
+    return np.array(sorted(out), np.int32)
+
+
+# ---------------------------------------------------------------- workloads
+def notched_plate(nx=100, ny=40, lx=0.1, ly=0.04, notch_len=0.05, traction=1e6,
+                  steps=2000, material: Optional[Material] = None, name=None,
+                  dt_factor=0.5, energy_every=0, phantom_cap=None, crack_cap=None):
+    """Pre-notched plate under constant opposite normal tractions on the top
+    and bottom edges (Sec. 4.2 setting).  The notch runs from the left edge
+    through the element row just below mid-height (mid-height is a node
+    line), as a row of pattern-II pre-cracks from left to right edge points."""
+    hx, hy = lx / nx, ly / ny
+    jn = ny // 2 - 1
+    nn = int(round(notch_len / hx))
+    pre = np.array([[jn * nx + i, 3, 1] for i in range(nn)], np.int32).reshape(-1, 3)
+    bcs = [BC(TRACTION, boundary_edges(nx, ny, "top"), 2, LAW_CONST, +traction),
+           BC(TRACTION, boundary_edges(nx, ny, "bottom"), 2, LAW_CONST, -traction)]
+    ne = nx * ny
+    return Problem(name=name or f"notched_plate_{nx}x{ny}", nx=nx, ny=ny, hx=hx, hy=hy,
+                   material=material or Material(), bcs=bcs, precracks=pre, steps=steps,
+                   dt_factor=dt_factor, energy_every=energy_every,
+                   phantom_cap=phantom_cap or max(4096, ne // 4),
+                   crack_cap=crack_cap or max(4096, ne // 4))
+
+
+def hole_mask(n, L, r):
+    """Element inactive iff its centroid lies strictly within r of the centre."""
+    h = L / n
+    c = (np.arange(n) + 0.5) * h - 0.5 * L
+    X, Y = np.meshgrid(c, c)
+    return (X * X + Y * Y >= r * r).astype(np.uint8).reshape(-1)
+
+
+def fragmentation(n=2048, L=0.1, r=0.005, mode="neumann", p0=50e6, v0=2.0, seed=2509,
+                  gc_mean=3.0, gc_shape=10.0, steps=None, t_end=60e-6,
+                  material: Optional[Material] = None, energy_every=0, name=None,
+                  phantom_cap=None, crack_cap=None):
+    """Square plate with a central hole; Weibull G_c; internal pressure pulse
+    p(t) = p0 t/t0 (t <= t0), p0 exp(-(t-t0)/tau) after, t0 = 1 us,
+    tau = 100 us (Sec. 4.4 law shape) or outward edge velocity ramped over
+    t0 = 1 us (Sec. 4.1 ramp shape)."""
+    h = L / n
+    active = hole_mask(n, L, r)
+    gc = weibull_gc(n * n, gc_mean, gc_shape, seed)
+    mat = material or Material()
+    if mode == "neumann":
+        bcs = [BC(PRESSURE, interface_edges(n, n, active), 0, LAW_RAMP_EXP, p0, 1e-6, 100e-6)]
+    elif mode == "dirichlet":
+        bcs = [BC(VELOCITY, boundary_nodes(n, n, "left"), 1, LAW_RAMP, -v0, 1e-6),
+               BC(VELOCITY, boundary_nodes(n, n, "right"), 1, LAW_RAMP, +v0, 1e-6),
+               BC(VELOCITY, boundary_nodes(n, n, "bottom"), 2, LAW_RAMP, -v0, 1e-6),
+               BC(VELOCITY, boundary_nodes(n, n, "top"), 2, LAW_RAMP, +v0, 1e-6)]
+    else:
+        raise ValueError(mode)
+    ne = n * n
+    prob = Problem(name=name or f"fragmentation_{n}x{n}_{mode}", nx=n, ny=n, hx=h, hy=h,
+                   material=mat, active=active, gc=gc, bcs=bcs, energy_every=energy_every,
+                   phantom_cap=phantom_cap or max(8192, ne // 16),
+                   crack_cap=crack_cap or max(8192, ne // 16))
+    if steps is None:
+        steps = int(math.ceil(t_end / estimate_dt(prob)))
+    prob.steps = steps
+    return prob
+
+
+def estimate_dt(prob: Problem) -> float:
+    """Half the plane-strain CFL limit, for sizing step counts only."""
+    m = prob.material
+    E, nu, rho = m.E, m.nu, m.rho
+    cd = math.sqrt(E * (1 - nu) / (rho * (1 + nu) * (1 - 2 * nu)))
+    return prob.dt_factor * min(prob.hx, prob.hy) / cd
+
+
+def batch_specimens(count=64, seed=1827, t_end=80e-6, smin=1.0, smax=4.0):
+    """Notched plates with s ~ U(smin, smax): nx = round(100 s), ny = round(40 s),
+    notch length ~ U(30, 60) mm, traction ~ U(0.5, 3) MPa, each run to t_end."""
+    u = np.stack([uniform01(count, seed, stream=q) for q in range(3)], axis=1)
+    out = []
+    for b in range(count):
+        s = smin + (smax - smin) * u[b, 0]
+        nx, ny = int(round(100 * s)), int(round(40 * s))
+        notch = 0.030 + 0.030 * u[b, 1]
+        trac = 0.5e6 + 2.5e6 * u[b, 2]
+        p = notched_plate(nx=nx, ny=ny, notch_len=notch, traction=trac, steps=0,
+                          name=f"specimen_{b}")
+        p.steps = int(math.ceil(t_end / estimate_dt(p)))
+        out.append(p)
+    return out
+
+
+CONFIGS = {
+    "notched_plate_100x40": lambda: notched_plate(100, 40, steps=2000),
+    "notched_plate_400x160": lambda: notched_plate(400, 160, steps=int(math.ceil(80e-6 / estimate_dt(notched_plate(400, 160, steps=0))))),
+    "fragmentation_2048_neumann": lambda: fragmentation(2048, mode="neumann"),
+    "fragmentation_2048_dirichlet": lambda: fragmentation(2048, mode="dirichlet"),
+}
