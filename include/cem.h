@@ -1,0 +1,231 @@
+/*
+ * cem.h -- C ABI of the GB300-native explicit MCT-2D-CEM time step.
+ *
+ * Method: the Multiple Crack-tips Tracking two-dimensional Crack Element Model
+ * (arXiv 2509.01827).  One explicit step of a structured bilinear
+ * quadrilateral (Q4) mesh is
+ *   (1) ES-FEM strain at the edge midpoints, plane stress/strain sigma = D eps,
+ *       internal force of intact elements and of split-element pieces
+ *       (Sec. 2.1, Eqs. 1, 2, 4, 6);
+ *   (2) a deterministic node gather, then the central-difference update with
+ *       lumped mass and Neumann / Dirichlet loads (Sec. 2 "explicit
+ *       formulation"; load laws of Secs. 4.1, 4.3, 4.4; equivalent nodal forces
+ *       of tractions, Sec. 4.3);
+ *   (3) multi-tip crack tracking: every free-surface edge point evaluates the
+ *       energy release rate G of its candidate paths (Sec. 2.2), applies the
+ *       Q4 cracking conditions, and the largest G in its neighbourhood splits
+ *       its element (Sec. 3); the device-side surface/tip list grows and
+ *       shrinks by stream compaction.
+ * All of it runs in this library's own CUDA kernels for sm_103a.
+ *
+ * Numbering (structured nx * ny mesh, element size hx * hy, unit thickness):
+ *   node (i,j), 0<=i<=nx, 0<=j<=ny         id = j*(nx+1) + i, X = (i*hx, j*hy)
+ *   element (i,j), 0<=i<nx, 0<=j<ny        id = j*nx + i
+ *   element local nodes (counter-clockwise) 0:(i,j) 1:(i+1,j) 2:(i+1,j+1) 3:(i,j+1)
+ *   element local edges 0 bottom, 1 right, 2 top, 3 left; edge k joins local
+ *   nodes k and (k+1)%4 and its quadrature point is its midpoint
+ *   horizontal edge (i,j), nodes (i,j)-(i+1,j), 0<=j<=ny: id = j*nx + i
+ *   vertical edge (i,j),   nodes (i,j)-(i,j+1), 0<=j<ny:  id = nx*(ny+1) + j*(nx+1) + i
+ *   Real nodes are [0, (nx+1)(ny+1)); phantom nodes of split elements follow.
+ *
+ * Conventions:
+ *   - Every input array is copied during the call; the caller keeps ownership.
+ *   - The library owns its device state.  It allocates it with the caller's
+ *     allocator callbacks when given (e.g. PyTorch's caching allocator), else
+ *     with cudaMallocAsync on the handle's stream.
+ *   - Functions return a cem_status; nothing throws across the ABI;
+ *     cem_last_error() returns the message of the last failure on a handle.
+ *   - A handle is used by one host thread at a time.  All device work goes to
+ *     the stream given in the descriptor (NULL = the legacy default stream).
+ *   - Floating-point state is SI: metres, seconds, pascals, kilograms.
+ */
+#ifndef CEM_H
+#define CEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cem_handle cem_handle; /* opaque, library-owned */
+
+typedef enum {
+  CEM_OK = 0,
+  CEM_ERR_ARG = -1,       /* invalid argument (message says which) */
+  CEM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  CEM_ERR_CAPACITY = -3,  /* a phantom/crack/list/winner capacity was exceeded */
+  CEM_ERR_NONFINITE = -4, /* a displacement or velocity became NaN or Inf */
+  CEM_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  CEM_ERR_STATE = -6      /* call out of order (e.g. stepping before material) */
+} cem_status;
+
+typedef enum { CEM_FP64 = 0, CEM_FP32_MIXED = 1 } cem_precision;
+
+typedef enum { CEM_TRACTION = 0, CEM_PRESSURE = 1, CEM_VELOCITY = 2 } cem_bc_kind;
+typedef enum { CEM_LAW_CONST = 0, CEM_LAW_RAMP = 1, CEM_LAW_RAMP_EXP = 2 } cem_law;
+typedef enum { CEM_SCOPE_NBHD = 0, CEM_SCOPE_GLOBAL = 1, CEM_SCOPE_TIPS = 2 } cem_scope;
+typedef enum { CEM_GAMMA_LITERAL = 0, CEM_GAMMA_RATIO = 1 } cem_gamma_mode;
+
+typedef void *(*cem_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*cem_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+  int nx, ny;                        /* elements along x and y, >= 1 */
+  double hx, hy;                     /* element size (m), > 0 */
+  const unsigned char *elem_active;  /* [nx*ny], 0 = hole; NULL = all active */
+  int n_precracks;                   /* split at t = 0, in the given order, */
+  const int *precrack;               /* [3*n]: (element, entry edge, exit edge) */
+  int phantom_capacity;              /* max phantom nodes; 0 = nx*ny/4 + 4096 */
+  int crack_capacity;                /* max split elements; 0 = nx*ny/4 + 4096 */
+  int list_capacity;                 /* max surface-list entries; 0 = automatic */
+  int precision;                     /* cem_precision */
+  double dt_factor;                  /* dt = dt_factor * min(hx,hy) / c_d (0 -> 0.5) */
+  double dt;                         /* > 0 overrides dt_factor */
+  int energy_every;                  /* record energies every K steps (0 = never) */
+  void *cuda_stream;                 /* cudaStream_t, NULL = legacy default stream */
+  int device;                        /* CUDA device ordinal */
+  cem_alloc_fn alloc;                /* optional device allocator */
+  cem_free_fn free;                  /* required when alloc is given */
+  void *alloc_ctx;
+} cem_mesh_desc;
+
+/* Builds the structured mesh and its device state (one bulk host-to-device
+ * copy).  Pre-cracks are applied by cem_set_material, which fixes the masses.
+ * Errors: CEM_ERR_ARG (sizes, capacities, pre-crack triples), CEM_ERR_CUDA. */
+cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out);
+
+/* Linear elastic material (E > 0, -1 < nu < 0.5, rho > 0), per-element
+ * critical energy release rate G_c (gc_per_elem[nx*ny], FP32, or NULL for
+ * gc_uniform), plane strain (1) or plane stress (0), the split ratio gamma
+ * of the Q4 cracking conditions (Sec. 2.2) with gamma_mode
+ * CEM_GAMMA_LITERAL (G_p > gamma (G_p - G_q)) or CEM_GAMMA_RATIO
+ * (G_p > gamma G_q), and the tracking scope (Sec. 3): CEM_SCOPE_NBHD (a
+ * proposal wins if its (G, -edge id) is the largest among proposals whose
+ * elements share a node with its own), CEM_SCOPE_GLOBAL (one winner per
+ * step) or CEM_SCOPE_TIPS (only crack fronts propose).  Computes lumped
+ * masses, the time step, then applies the descriptor's pre-cracks.  Call
+ * once, before cem_set_bc / cem_step.  Errors: CEM_ERR_ARG, CEM_ERR_STATE
+ * (called twice), CEM_ERR_CAPACITY (pre-cracks exceed capacities). */
+cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
+                            const float *gc_per_elem, double gc_uniform,
+                            int plane_strain, double gamma, int gamma_mode,
+                            int mct_scope);
+
+/* Adds a load.  CEM_TRACTION: items are boundary edge ids; each node of an
+ * edge of length L receives L/2 * a0 along x (comp_mask bit 0) and/or y
+ * (bit 1).  CEM_PRESSURE: boundary edge ids; pressure a0 pushes into the
+ * material along the inward normal.  CEM_VELOCITY: node ids; the masked
+ * velocity components are prescribed as law(t) * a0.  Time law:
+ * CEM_LAW_CONST 1; CEM_LAW_RAMP t/t0 then 1 (Secs. 4.1, 4.3);
+ * CEM_LAW_RAMP_EXP t/t0 then exp(-(t-t0)/tau) (Sec. 4.4).  All Neumann loads
+ * share one law, all Dirichlet loads share one law.  Loads act on real
+ * nodes only.  Errors: CEM_ERR_ARG (not a boundary edge, bad node, law
+ * mismatch), CEM_ERR_STATE (after the first step). */
+cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items,
+                      int comp_mask, int law, double a0, double t0, double tau);
+
+/* Which field cem_set_fields / cem_get_fields move.  Node fields are FP64
+ * arrays over all nodes (real then phantom): x block then y block. */
+typedef enum {
+  CEM_FIELD_U = 0,       /* double[2 * n_nodes_total] */
+  CEM_FIELD_V = 1,       /* double[2 * n_nodes_total] */
+  CEM_FIELD_MASS = 2,    /* double[n_nodes_total] (get only) */
+  CEM_FIELD_STATE = 3,   /* uint8[nx*ny]: 0 intact, 1 split, 2 inactive (get only) */
+  CEM_FIELD_ENERGY = 4,  /* double[7 * n_energy]: step, t, KE, SE, W_ext, W_dir, U_d */
+  CEM_FIELD_GC = 5       /* float[nx*ny] (get only) */
+} cem_field;
+
+/* Sets initial u or v of all current nodes before the first step.
+ * data is host memory (on_device = 0) or a device pointer (1); n_bytes must
+ * equal the field size.  Errors: CEM_ERR_ARG, CEM_ERR_STATE. */
+cem_status cem_set_fields(cem_handle *h, int which, const void *data,
+                          long n_bytes, int on_device);
+
+/* Advances n explicit steps on the handle's stream (CUDA-graph replays) and
+ * synchronises once at the end to read the device status word.  Returns the
+ * first device error: CEM_ERR_CAPACITY, CEM_ERR_NONFINITE; or CEM_ERR_STATE
+ * before cem_set_material. */
+cem_status cem_step(cem_handle *h, int n);
+
+/* Copies a field into out (host, or device pointer when on_device = 1).
+ * n_bytes must be at least the field size (see cem_get_counts). */
+cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes,
+                          int on_device);
+
+typedef struct {
+  long n_nodes;      /* real nodes */
+  long n_phantoms;   /* phantom nodes */
+  long n_elems;
+  long n_active;     /* active elements */
+  long n_cracked;    /* split elements (pre-cracks included) */
+  long n_surface;    /* free-surface edge points */
+  long n_tips;       /* surface points on a cut edge (crack fronts) */
+  long n_energy;     /* energy records */
+  long step;         /* steps taken */
+  double dt;         /* time step (s) */
+  double t;          /* step * dt */
+} cem_counts;
+
+cem_status cem_get_counts(cem_handle *h, cem_counts *out);
+
+/* A crack front: a surface edge point on a cut edge whose other element is
+ * intact (the element "ahead").  Sorted by edge id. */
+typedef struct {
+  int edge_id;       /* edge id of the tip point */
+  int ahead_elem;    /* intact element ahead of it */
+  double x, y;       /* reference coordinates of the edge midpoint (m) */
+  double G_last;     /* largest candidate G at the last evaluation (J/m^2) */
+  int birth_step;    /* step at which the cut reached this edge (-1: pre-crack) */
+  int parent;        /* the split element behind the tip */
+} cem_tip;
+
+cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out);
+
+/* One split element.  node[p][a] is the node used by piece p at local node
+ * a (a real node id or a phantom id); Ap are the piece areas; ud is the
+ * energy dissipated by this split (G_c * segment length; 0 for pre-cracks). */
+typedef struct {
+  int elem, ka, kb, step;
+  int node[2][4];
+  double Ap[2];
+  double ud;
+} cem_crack;
+
+/* Split elements sorted by element id. */
+cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out);
+
+/* One phantom node: its id, the real node it duplicates, the element and
+ * local node that created it, and its users (element, piece, local node),
+ * sorted by element; unused slots are -1. */
+typedef struct {
+  int id, owner, creator_elem, creator_local, n_users;
+  int users[4][3];
+} cem_phantom;
+
+/* Phantoms in id order. */
+cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out);
+
+/* Free-surface edge points sorted by edge id: edge, ahead element, tip flag. */
+cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip,
+                           int cap, int *n_out);
+
+/* Testing hook for the tracking bookkeeping: runs the selection and split
+ * (Sec. 3) on caller-given proposals (surface edge id, its ahead element,
+ * chosen exit edge, G) without a mechanics step.  Errors: CEM_ERR_ARG when a
+ * proposal is not a surface point of its element. */
+cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge,
+                                     const int *elem, const int *k,
+                                     const double *G);
+
+/* Message of the last failure on h (or of the last failed create when h is
+ * NULL).  Valid until the next call on h. */
+const char *cem_last_error(const cem_handle *h);
+
+/* Frees the device state and the handle. */
+void cem_mesh_destroy(cem_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

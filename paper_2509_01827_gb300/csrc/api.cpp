@@ -1,0 +1,834 @@
+// api.cpp -- host runtime behind the C ABI of include/cem.h.
+//
+// Owns the device state of one structured mesh, builds the problem on the
+// host (loads, masses via a kernel, pre-cracks via the tracking kernel),
+// captures one CUDA graph per (displacement buffer, energy-record) variant of
+// the explicit step, and replays them.  Host arithmetic that must agree with
+// the definition bit for bit (D matrix, time step, equivalent nodal forces,
+// load factors) is compiled with -ffp-contract=off.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cem.h"
+#include "cem_internal.h"
+
+using namespace cem;
+
+struct cem_handle {
+  DevState d{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  cem_alloc_fn alloc = nullptr;
+  cem_free_fn free_fn = nullptr;
+  void *ctx = nullptr;
+  std::vector<void *> blocks;
+  int nx = 0, ny = 0;
+  double hx = 0, hy = 0;
+  std::vector<uint8_t> active;
+  std::vector<int> precracks;
+  double dt_factor = 0.5, dt_explicit = 0.0;
+  bool material = false;
+  // loads (host mirrors, uploaded on change)
+  std::vector<double> Fx, Fy, Vx, Vy;
+  std::vector<uint8_t> nflag;
+  bool neu_set = false, dir_set = false;
+  int neu_law = 0, dir_law = 0;
+  double neu_t0 = 0, neu_tau = 0, dir_t0 = 0, dir_tau = 0;
+  int cur = 0;
+  long step = 0;
+  int energy_every = 0;
+  cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][energy]
+  Counters *h_cnt = nullptr;  // pinned
+  bool own_stream = false;
+  void *scratch = nullptr;     // reusable device scratch for getters
+  size_t scratch_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+cem_status fail(cem_handle *h, cem_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_create_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(h, expr)                                                               \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return fail((h), CEM_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(_e)); \
+  } while (0)
+
+void *dalloc(cem_handle *h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, h->ctx);
+  } else if (cudaMallocAsync(&p, bytes, h->st) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    h->blocks.push_back(p);
+    if (cudaMemsetAsync(p, 0, bytes, h->st) != cudaSuccess) return nullptr;
+  }
+  return p;
+}
+
+// Device scratch reused by getters; grows geometrically.
+void *scratch(cem_handle *h, size_t bytes) {
+  if (bytes <= h->scratch_bytes) return h->scratch;
+  size_t want = std::max(bytes, 2 * h->scratch_bytes);
+  void *p = dalloc(h, want);
+  if (!p) return nullptr;
+  h->scratch = p;
+  h->scratch_bytes = want;
+  return p;
+}
+
+template <class T>
+bool dalloc_n(cem_handle *h, T *&p, size_t n) {
+  p = (T *)dalloc(h, n * sizeof(T));
+  return p != nullptr;
+}
+
+double law_eval(int law, double t, double t0, double tau) {
+  if (law == CEM_LAW_CONST) return 1.0;
+  if (t <= t0) return t / t0;
+  if (law == CEM_LAW_RAMP) return 1.0;
+  return exp(-(t - t0) / tau);
+}
+
+void edge_sides_host(const cem_handle *h, int g, int &lo, int &hi) {
+  int nx = h->nx, ny = h->ny, nh = nx * (ny + 1);
+  if (g < nh) {
+    int j = g / nx, i = g % nx;
+    lo = j > 0 ? (j - 1) * nx + i : -1;
+    hi = j < ny ? j * nx + i : -1;
+  } else {
+    int gg = g - nh, j = gg / (nx + 1), i = gg % (nx + 1);
+    lo = i > 0 ? j * nx + i - 1 : -1;
+    hi = i < nx ? j * nx + i : -1;
+  }
+}
+
+void edge_nodes_host(const cem_handle *h, int g, int &n1, int &n2) {
+  int nx = h->nx, ny = h->ny, nh = nx * (ny + 1), r = nx + 1;
+  if (g < nh) {
+    int j = g / nx, i = g % nx;
+    n1 = j * r + i; n2 = j * r + i + 1;
+  } else {
+    int gg = g - nh, j = gg / r, i = gg % r;
+    n1 = j * r + i; n2 = (j + 1) * r + i;
+  }
+}
+
+int local_edge_host(const cem_handle *h, int e, int g) {
+  int nx = h->nx, ny = h->ny, nh = nx * (ny + 1);
+  int i = e % nx, j = e / nx;
+  if (g == j * nx + i) return 0;
+  if (g == nh + j * (nx + 1) + i + 1) return 1;
+  if (g == (j + 1) * nx + i) return 2;
+  if (g == nh + j * (nx + 1) + i) return 3;
+  return -1;
+}
+
+cem_status sync_status(cem_handle *h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int s = h->h_cnt->status;
+  if (s & STAT_CAPACITY)
+    return fail(h, CEM_ERR_CAPACITY,
+                "capacity exceeded (phantoms %d/%d, cracks %d/%d, list %d/%d, proposals cap %d)",
+                h->h_cnt->n_ph, h->d.ph_cap, h->h_cnt->n_ck, h->d.ck_cap, h->h_cnt->n_S,
+                h->d.list_cap, h->d.prop_cap);
+  if (s & STAT_NONFINITE) return fail(h, CEM_ERR_NONFINITE, "non-finite displacement or velocity");
+  if (s & STAT_TIMEOUT) return fail(h, CEM_ERR_TIMEOUT, "device wait timed out");
+  return CEM_OK;
+}
+
+cem_status upload_loads(cem_handle *h) {
+  size_t nn = (size_t)h->d.g.nn;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.Fx, h->Fx.data(), nn * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.Fy, h->Fy.data(), nn * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.Vx, h->Vx.data(), nn * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.Vy, h->Vy.data(), nn * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.nflag, h->nflag.data(), nn, cudaMemcpyHostToDevice, h->st));
+  std::vector<int> bc;
+  for (size_t N = 0; N < nn; ++N)
+    if (h->nflag[N]) bc.push_back((int)N);
+  if (!bc.empty())
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.bc_nodes, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice, h->st));
+  h->d.n_bc = (int)bc.size();
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+void drop_graphs(cem_handle *h) {
+  for (auto &row : h->graphs)
+    for (auto &g : row)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// Enqueues one explicit step (buffers cur -> cur^1) on the stream.
+cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy) {
+  const DevState &d = h->d;
+  cudaError_t e;
+  if (energy && (e = launch_energy_pre(d, h->st)) != cudaSuccess) return e;
+  if (d.precision == CEM_FP32_MIXED) e = launch_step_fp32(d, cur, first, energy, h->st);
+  else e = launch_step_fp64(d, cur, first, energy, h->st);
+  if (e != cudaSuccess) return e;
+  if (energy && (e = launch_energy_post(d, energy_parts_needed(d), h->st)) != cudaSuccess) return e;
+  return launch_track(d, cur ^ 1, TRACK_STEP, h->st);
+}
+
+cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
+  if (!h->graphs[cur][energy]) {
+    cudaGraph_t g;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(h, cur, false, energy != 0);
+    cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
+    if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
+  }
+  *out = h->graphs[cur][energy];
+  return CEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cem_last_error(const cem_handle *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
+  if (!desc || !out) return fail(nullptr, CEM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (desc->nx < 1 || desc->ny < 1 || !(desc->hx > 0) || !(desc->hy > 0))
+    return fail(nullptr, CEM_ERR_ARG, "bad mesh size");
+  long ne = (long)desc->nx * desc->ny, nn = (long)(desc->nx + 1) * (desc->ny + 1);
+  if (ne > (1L << 27)) return fail(nullptr, CEM_ERR_ARG, "mesh too large (max 2^27 elements)");
+  if (desc->precision != CEM_FP64 && desc->precision != CEM_FP32_MIXED)
+    return fail(nullptr, CEM_ERR_ARG, "bad precision");
+  if (desc->alloc && !desc->free) return fail(nullptr, CEM_ERR_ARG, "alloc without free");
+  if (desc->n_precracks < 0 || (desc->n_precracks > 0 && !desc->precrack))
+    return fail(nullptr, CEM_ERR_ARG, "bad pre-crack list");
+  cem_handle *h = new (std::nothrow) cem_handle();
+  if (!h) return fail(nullptr, CEM_ERR_ARG, "out of host memory");
+  h->device = desc->device;
+  h->st = (cudaStream_t)desc->cuda_stream;
+  h->alloc = desc->alloc;
+  h->free_fn = desc->free;
+  h->ctx = desc->alloc_ctx;
+  h->nx = desc->nx; h->ny = desc->ny; h->hx = desc->hx; h->hy = desc->hy;
+  h->dt_factor = desc->dt_factor > 0 ? desc->dt_factor : 0.5;
+  h->dt_explicit = desc->dt;
+  h->energy_every = desc->energy_every > 0 ? desc->energy_every : 0;
+  h->active.assign((size_t)ne, 1);
+  if (desc->elem_active)
+    for (long e = 0; e < ne; ++e) h->active[e] = desc->elem_active[e] != 0;
+  for (int q = 0; q < desc->n_precracks; ++q) {
+    int e = desc->precrack[3 * q], ka = desc->precrack[3 * q + 1], kb = desc->precrack[3 * q + 2];
+    if (e < 0 || e >= ne || !h->active[e] || ka < 0 || ka > 3 || kb < 0 || kb > 3 || ka == kb) {
+      delete h;
+      return fail(nullptr, CEM_ERR_ARG, "bad pre-crack triple %d", q);
+    }
+    for (int r = 0; r < q; ++r)
+      if (desc->precrack[3 * r] == e) {
+        delete h;
+        return fail(nullptr, CEM_ERR_ARG, "element %d pre-cracked twice", e);
+      }
+    h->precracks.insert(h->precracks.end(), {e, ka, kb});
+  }
+  cudaError_t ce = cudaSetDevice(h->device);
+  if (ce == cudaSuccess && !h->st) {
+    // graphs cannot be captured on the legacy default stream: use our own
+    ce = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    h->own_stream = ce == cudaSuccess;
+  }
+  if (ce != cudaSuccess) {
+    delete h;
+    return fail(nullptr, CEM_ERR_CUDA, "device set-up: %s", cudaGetErrorString(ce));
+  }
+  DevState &d = h->d;
+  d.g.nx = desc->nx; d.g.ny = desc->ny; d.g.nn = (int)nn; d.g.ne = (int)ne;
+  d.g.nh = desc->nx * (desc->ny + 1);
+  d.g.ned = d.g.nh + (desc->nx + 1) * desc->ny;
+  d.g.hx = desc->hx; d.g.hy = desc->hy; d.g.A = desc->hx * desc->hy;
+  d.g.rx = 1.0 / desc->hx; d.g.rxh = d.g.rx * 0.5;
+  d.g.ry = 1.0 / desc->hy; d.g.ryh = d.g.ry * 0.5;
+  d.precision = desc->precision;
+  d.ph_cap = desc->phantom_capacity > 0 ? desc->phantom_capacity : (int)(ne / 4 + 4096);
+  d.ck_cap = desc->crack_capacity > 0 ? desc->crack_capacity : (int)(ne / 4 + 4096);
+  long rim = 0;
+  for (int g = 0; g < d.g.ned; ++g) {
+    int lo, hi;
+    edge_sides_host(h, g, lo, hi);
+    bool alo = lo >= 0 && h->active[lo], ahi = hi >= 0 && h->active[hi];
+    rim += alo != ahi;
+  }
+  long lc = desc->list_capacity > 0 ? desc->list_capacity
+                                    : 2 * (rim + 4L * d.ck_cap) + 8192;
+  if (lc > (1L << 30)) lc = 1L << 30;
+  d.list_cap = (int)lc;
+  d.prop_cap = 8192;
+  d.ncap = d.g.nn + d.ph_cap;
+  d.lam_cap = 4096;
+  d.rec_cap = 65536;
+  size_t nc = (size_t)d.ncap, nec = (size_t)ne;
+  bool ok = true;
+  if (d.precision == CEM_FP64) {
+    for (int b = 0; b < 2; ++b) ok = ok && dalloc_n(h, d.ux[b], nc) && dalloc_n(h, d.uy[b], nc);
+    ok = ok && dalloc_n(h, d.vx, nc) && dalloc_n(h, d.vy, nc) && dalloc_n(h, d.pf, (size_t)d.ck_cap * 16);
+  } else {
+    for (int b = 0; b < 2; ++b)
+      ok = ok && dalloc_n(h, d.uxh[b], nc) && dalloc_n(h, d.uxl[b], nc) &&
+           dalloc_n(h, d.uyh[b], nc) && dalloc_n(h, d.uyl[b], nc);
+    ok = ok && dalloc_n(h, d.vxf, nc) && dalloc_n(h, d.vyf, nc) && dalloc_n(h, d.minvf, nc) &&
+         dalloc_n(h, d.pff, (size_t)d.ck_cap * 16);
+  }
+  ok = ok && dalloc_n(h, d.m, nc) && dalloc_n(h, d.minv, nc) && dalloc_n(h, d.Wn, nc) &&
+       dalloc_n(h, d.Wd, nc) && dalloc_n(h, d.nflag, (size_t)nn) && dalloc_n(h, d.Fx, (size_t)nn) &&
+       dalloc_n(h, d.Fy, (size_t)nn) && dalloc_n(h, d.Vx, (size_t)nn) && dalloc_n(h, d.Vy, (size_t)nn) &&
+       dalloc_n(h, d.bc_nodes, (size_t)nn) && dalloc_n(h, d.estate, nec) &&
+       dalloc_n(h, d.crack_of, nec) && dalloc_n(h, d.gc, nec) &&
+       dalloc_n(h, d.ck_elem, (size_t)d.ck_cap) && dalloc_n(h, d.ck_info, (size_t)d.ck_cap) &&
+       dalloc_n(h, d.ck_node, (size_t)d.ck_cap * 8) && dalloc_n(h, d.ck_Ap, (size_t)d.ck_cap * 2) &&
+       dalloc_n(h, d.ck_ud, (size_t)d.ck_cap) && dalloc_n(h, d.ck_step, (size_t)d.ck_cap) &&
+       dalloc_n(h, d.ph_owner, (size_t)d.ph_cap) && dalloc_n(h, d.ph_creator, (size_t)d.ph_cap) &&
+       dalloc_n(h, d.ph_nuser, (size_t)d.ph_cap) && dalloc_n(h, d.ph_users, (size_t)d.ph_cap * 4) &&
+       dalloc_n(h, d.S, (size_t)d.list_cap) && dalloc_n(h, d.S_info, (size_t)d.list_cap) &&
+       dalloc_n(h, d.S_G, (size_t)d.list_cap) && dalloc_n(h, d.spos, (size_t)d.g.ned) &&
+       dalloc_n(h, d.pr_key, (size_t)d.prop_cap) && dalloc_n(h, d.pr_edge, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.pr_k, (size_t)d.prop_cap) && dalloc_n(h, d.pr_G, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.cnt, 1) && dalloc_n(h, d.lamN, (size_t)d.lam_cap) &&
+       dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
+  d.e_part_cap = energy_parts_needed(d);
+  ok = ok && dalloc_n(h, d.e_part, (size_t)d.e_part_cap * 2);
+  if (!ok || cudaHostAlloc((void **)&h->h_cnt, sizeof(Counters), cudaHostAllocDefault) != cudaSuccess) {
+    g_create_error = "device allocation failed";
+    cem_mesh_destroy(h);
+    return CEM_ERR_CUDA;
+  }
+  // element states and crack map
+  std::vector<uint8_t> st((size_t)ne);
+  for (long e = 0; e < ne; ++e) st[e] = h->active[e] ? ST_INTACT : ST_OUT;
+  std::vector<int> minus1(std::max((size_t)ne, (size_t)d.g.ned), -1);
+  if (cudaMemcpyAsync(d.estate, st.data(), nec, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(d.crack_of, minus1.data(), nec * 4, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(d.spos, minus1.data(), (size_t)d.g.ned * 4, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess) {
+    g_create_error = "initial upload failed";
+    cem_mesh_destroy(h);
+    return CEM_ERR_CUDA;
+  }
+  h->Fx.assign((size_t)nn, 0.0); h->Fy.assign((size_t)nn, 0.0);
+  h->Vx.assign((size_t)nn, 0.0); h->Vy.assign((size_t)nn, 0.0);
+  h->nflag.assign((size_t)nn, 0);
+  *out = h;
+  return CEM_OK;
+}
+
+void cem_mesh_destroy(cem_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  drop_graphs(h);
+  if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+  for (void *p : h->blocks) {
+    if (h->free_fn) h->free_fn(p, h->ctx);
+    else cudaFreeAsync(p, h->st);
+  }
+  if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+  if (h->h_cnt) cudaFreeHost(h->h_cnt);
+  if (h->own_stream) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
+                            const float *gc_per_elem, double gc_uniform, int plane_strain,
+                            double gamma, int gamma_mode, int mct_scope) {
+  if (!h) return CEM_ERR_ARG;
+  if (h->material) return fail(h, CEM_ERR_STATE, "material already set");
+  if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(rho > 0)) return fail(h, CEM_ERR_ARG, "bad material");
+  if (mct_scope < 0 || mct_scope > 2 || gamma_mode < 0 || gamma_mode > 1)
+    return fail(h, CEM_ERR_ARG, "bad scope or gamma mode");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  Mat &m = h->d.mat;
+  if (plane_strain) {
+    double c = E / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    m.D11 = c * (1.0 - nu);
+    m.D12 = c * nu;
+    m.D33 = c * (1.0 - 2.0 * nu) * 0.5;
+  } else {
+    double c = E / (1.0 - nu * nu);
+    m.D11 = c;
+    m.D12 = c * nu;
+    m.D33 = c * (1.0 - nu) * 0.5;
+  }
+  m.D11f = (float)m.D11; m.D12f = (float)m.D12; m.D33f = (float)m.D33;
+  m.rho = rho; m.gamma = gamma; m.gamma_mode = gamma_mode; m.scope = mct_scope;
+  if (h->dt_explicit > 0) {
+    m.dt = h->dt_explicit;
+  } else {
+    double cd;
+    if (plane_strain) cd = sqrt((E * (1.0 - nu)) / (rho * ((1.0 + nu) * (1.0 - 2.0 * nu))));
+    else cd = sqrt(E / (rho * (1.0 - nu * nu)));
+    double hmin = h->hx < h->hy ? h->hx : h->hy;
+    m.dt = h->dt_factor * hmin / cd;
+  }
+  const DevState &d = h->d;
+  std::vector<float> gc((size_t)d.g.ne);
+  for (int e = 0; e < d.g.ne; ++e) gc[e] = gc_per_elem ? gc_per_elem[e] : (float)gc_uniform;
+  CUDA_TRY(h, cudaMemcpyAsync(d.gc, gc.data(), gc.size() * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_init_masses(d, h->st));
+  if (d.precision == CEM_FP32_MIXED) {
+    // minvf follows minv
+    std::vector<double> mi((size_t)d.g.nn);
+    CUDA_TRY(h, cudaMemcpyAsync(mi.data(), d.minv, mi.size() * 8, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    std::vector<float> mf(mi.size());
+    for (size_t q = 0; q < mi.size(); ++q) mf[q] = (float)mi[q];
+    CUDA_TRY(h, cudaMemcpyAsync(d.minvf, mf.data(), mf.size() * 4, cudaMemcpyHostToDevice, h->st));
+  }
+  // pre-cracks, one at a time in the given order (the same split routine)
+  for (size_t q = 0; q < h->precracks.size(); q += 3) {
+    int e = h->precracks[q], ka = h->precracks[q + 1], kb = h->precracks[q + 2];
+    int i = e % h->nx, j = e / h->nx, nh = h->nx * (h->ny + 1);
+    int edge = ka == 0 ? j * h->nx + i : ka == 1 ? nh + j * (h->nx + 1) + i + 1
+             : ka == 2 ? (j + 1) * h->nx + i : nh + j * (h->nx + 1) + i;
+    int key = e * 4 + ka;
+    double G = 0.0;
+    int one = 1;
+    CUDA_TRY(h, cudaMemcpyAsync(d.pr_key, &key, 4, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d.pr_edge, &edge, 4, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d.pr_k, &kb, 4, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d.pr_G, &G, 8, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->n_prop, &one, 4, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, launch_track(d, h->cur, TRACK_PRECRACK, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  }
+  CUDA_TRY(h, launch_build_surface(d, h->st));
+  h->material = true;
+  return sync_status(h);
+}
+
+cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items, int comp_mask,
+                      int law, double a0, double t0, double tau) {
+  if (!h) return CEM_ERR_ARG;
+  if (h->step != 0) return fail(h, CEM_ERR_STATE, "loads must be set before the first step");
+  if (n_items < 0 || (n_items > 0 && !items)) return fail(h, CEM_ERR_ARG, "bad items");
+  if (law < 0 || law > 2) return fail(h, CEM_ERR_ARG, "bad law");
+  if (law != CEM_LAW_CONST && !(t0 > 0)) return fail(h, CEM_ERR_ARG, "t0 must be > 0");
+  if (law == CEM_LAW_RAMP_EXP && !(tau > 0)) return fail(h, CEM_ERR_ARG, "tau must be > 0");
+  const int nh = h->nx * (h->ny + 1), ned = nh + (h->nx + 1) * h->ny;
+  const int nn = (h->nx + 1) * (h->ny + 1);
+  if (kind == CEM_TRACTION || kind == CEM_PRESSURE) {
+    if (h->neu_set && (h->neu_law != law || h->neu_t0 != t0 || h->neu_tau != tau))
+      return fail(h, CEM_ERR_ARG, "all Neumann loads share one time law");
+    for (int q = 0; q < n_items; ++q) {
+      int g = items[q], lo, hi;
+      if (g < 0 || g >= ned) return fail(h, CEM_ERR_ARG, "edge %d is not a boundary edge", g);
+      edge_sides_host(h, g, lo, hi);
+      bool alo = lo >= 0 && h->active[lo], ahi = hi >= 0 && h->active[hi];
+      if (alo == ahi) return fail(h, CEM_ERR_ARG, "edge %d is not a boundary edge", g);
+    }
+    std::vector<int> sorted(items, items + n_items);
+    std::sort(sorted.begin(), sorted.end());
+    for (int g : sorted) {
+      int lo, hi, n1, n2;
+      edge_sides_host(h, g, lo, hi);
+      bool alo = lo >= 0 && h->active[lo];
+      bool horiz = g < nh;
+      double sgn = alo ? 1.0 : -1.0;  // outward normal of the material side
+      double ox = horiz ? 0.0 : sgn, oy = horiz ? sgn : 0.0;
+      double L = horiz ? h->hx : h->hy;
+      double tx, ty;
+      if (kind == CEM_TRACTION) {
+        tx = (comp_mask & 1) ? a0 : 0.0;
+        ty = (comp_mask & 2) ? a0 : 0.0;
+      } else {
+        tx = -a0 * ox;
+        ty = -a0 * oy;
+      }
+      double half = 0.5 * L;
+      edge_nodes_host(h, g, n1, n2);
+      h->Fx[n1] = h->Fx[n1] + half * tx; h->Fy[n1] = h->Fy[n1] + half * ty;
+      h->Fx[n2] = h->Fx[n2] + half * tx; h->Fy[n2] = h->Fy[n2] + half * ty;
+      h->nflag[n1] |= NF_LOADED;
+      h->nflag[n2] |= NF_LOADED;
+    }
+    h->neu_set = true; h->neu_law = law; h->neu_t0 = t0; h->neu_tau = tau;
+  } else if (kind == CEM_VELOCITY) {
+    if (h->dir_set && (h->dir_law != law || h->dir_t0 != t0 || h->dir_tau != tau))
+      return fail(h, CEM_ERR_ARG, "all Dirichlet loads share one time law");
+    if ((comp_mask & 3) == 0) return fail(h, CEM_ERR_ARG, "empty component mask");
+    for (int q = 0; q < n_items; ++q)
+      if (items[q] < 0 || items[q] >= nn) return fail(h, CEM_ERR_ARG, "bad node %d", items[q]);
+    for (int q = 0; q < n_items; ++q) {
+      int N = items[q];
+      if (comp_mask & 1) { h->nflag[N] |= NF_DIRX; h->Vx[N] = a0; }
+      if (comp_mask & 2) { h->nflag[N] |= NF_DIRY; h->Vy[N] = a0; }
+    }
+    h->dir_set = true; h->dir_law = law; h->dir_t0 = t0; h->dir_tau = tau;
+  } else {
+    return fail(h, CEM_ERR_ARG, "bad load kind");
+  }
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  return upload_loads(h);
+}
+
+cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_bytes, int on_device) {
+  if (!h || !data) return CEM_ERR_ARG;
+  if (h->step != 0) return fail(h, CEM_ERR_STATE, "fields can only be set before the first step");
+  if (which != CEM_FIELD_U && which != CEM_FIELD_V) return fail(h, CEM_ERR_ARG, "field not settable");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  long n = h->d.g.nn + h->h_cnt->n_ph;
+  if (n_bytes != 16 * n) return fail(h, CEM_ERR_ARG, "expected %ld bytes", 16 * n);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const DevState &d = h->d;
+  if (d.precision == CEM_FP64) {
+    double *dx = which == CEM_FIELD_U ? d.ux[h->cur] : d.vx;
+    double *dy = which == CEM_FIELD_U ? d.uy[h->cur] : d.vy;
+    CUDA_TRY(h, cudaMemcpyAsync(dx, data, n * 8, kind, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(dy, (const char *)data + n * 8, n * 8, kind, h->st));
+  } else {
+    double *tmp = (double *)scratch(h, (size_t)n * 16);
+    if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+    CUDA_TRY(h, cudaMemcpyAsync(tmp, data, n * 16, kind, h->st));
+    if (which == CEM_FIELD_U)
+      CUDA_TRY(h, launch_fp64_to_fp32(d, h->cur, tmp, tmp + n, nullptr, nullptr, (int)n, h->st));
+    else
+      CUDA_TRY(h, launch_fp64_to_fp32(d, h->cur, nullptr, nullptr, tmp, tmp + n, (int)n, h->st));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+cem_status cem_step(cem_handle *h, int n) {
+  if (!h) return CEM_ERR_ARG;
+  if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
+  if (n < 0) return fail(h, CEM_ERR_ARG, "negative step count");
+  if (n == 0) return CEM_OK;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  const DevState &d = h->d;
+  const double dt = d.mat.dt;
+  std::vector<double> lamN(d.lam_cap), lamD(d.lam_cap);
+  int done = 0;
+  while (done < n) {
+    int chunk = std::min(n - done, d.lam_cap);
+    for (int q = 0; q < chunk; ++q) {
+      long s = h->step + q;
+      lamN[q] = h->neu_set ? law_eval(h->neu_law, (double)s * dt, h->neu_t0, h->neu_tau) : 0.0;
+      lamD[q] = h->dir_set ? law_eval(h->dir_law, ((double)s + 0.5) * dt, h->dir_t0, h->dir_tau) : 0.0;
+    }
+    int base = (int)h->step;
+    CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN.data(), chunk * 8, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD.data(), chunk * 8, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &base, 4, cudaMemcpyHostToDevice, h->st));
+    // the table must be consumed before the host buffers change
+    for (int q = 0; q < chunk; ++q) {
+      bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
+      if (h->step == 0) {
+        CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
+      } else {
+        cudaGraphExec_t gx;
+        cem_status rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
+        if (rc != CEM_OK) return rc;
+        CUDA_TRY(h, cudaGraphLaunch(gx, h->st));
+      }
+      h->cur ^= 1;
+      h->step += 1;
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    done += chunk;
+  }
+  CUDA_TRY(h, launch_check_finite(d, h->cur, h->st));
+  return sync_status(h);
+}
+
+cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
+  if (!h || !out) return CEM_ERR_ARG;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const Counters c = *h->h_cnt;
+  out->n_nodes = h->d.g.nn;
+  out->n_phantoms = c.n_ph;
+  out->n_elems = h->d.g.ne;
+  long act = 0;
+  for (uint8_t a : h->active) act += a;
+  out->n_active = act;
+  out->n_cracked = c.n_ck;
+  out->n_energy = c.n_rec;
+  out->step = c.step;
+  out->dt = h->d.mat.dt;
+  out->t = (double)c.step * h->d.mat.dt;
+  out->n_surface = 0;
+  out->n_tips = 0;
+  if (c.n_S > 0) {
+    int *tmp = (int *)scratch(h, (size_t)c.n_S * 12);
+    if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+    CUDA_TRY(h, launch_surface_info(h->d, tmp, h->st));
+    std::vector<int> v((size_t)c.n_S * 3);
+    CUDA_TRY(h, cudaMemcpyAsync(v.data(), tmp, v.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (int i = 0; i < c.n_S; ++i)
+      if (v[3 * i] >= 0) { out->n_surface++; out->n_tips += v[3 * i + 2]; }
+  }
+  return CEM_OK;
+}
+
+cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int on_device) {
+  if (!h || !out) return CEM_ERR_ARG;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const DevState &d = h->d;
+  long n = d.g.nn + h->h_cnt->n_ph;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  long need;
+  switch (which) {
+    case CEM_FIELD_U:
+    case CEM_FIELD_V: need = 16 * n; break;
+    case CEM_FIELD_MASS: need = 8 * n; break;
+    case CEM_FIELD_STATE: need = d.g.ne; break;
+    case CEM_FIELD_ENERGY: need = 56L * h->h_cnt->n_rec; break;
+    case CEM_FIELD_GC: need = 4L * d.g.ne; break;
+    default: return fail(h, CEM_ERR_ARG, "unknown field %d", which);
+  }
+  if (n_bytes < need) return fail(h, CEM_ERR_ARG, "buffer too small: need %ld bytes", need);
+  char *o = (char *)out;
+  if (which == CEM_FIELD_U || which == CEM_FIELD_V) {
+    if (d.precision == CEM_FP64) {
+      const double *sx = which == CEM_FIELD_U ? d.ux[h->cur] : d.vx;
+      const double *sy = which == CEM_FIELD_U ? d.uy[h->cur] : d.vy;
+      CUDA_TRY(h, cudaMemcpyAsync(o, sx, n * 8, kind, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(o + n * 8, sy, n * 8, kind, h->st));
+    } else {
+      double *tmp = (double *)scratch(h, (size_t)n * 16);
+      if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+      if (which == CEM_FIELD_U)
+        CUDA_TRY(h, launch_fp32_to_fp64(d, h->cur, tmp, tmp + n, nullptr, nullptr, (int)n, h->st));
+      else
+        CUDA_TRY(h, launch_fp32_to_fp64(d, h->cur, nullptr, nullptr, tmp, tmp + n, (int)n, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(o, tmp, n * 16, kind, h->st));
+    }
+  } else if (which == CEM_FIELD_MASS) {
+    CUDA_TRY(h, cudaMemcpyAsync(o, d.m, n * 8, kind, h->st));
+  } else if (which == CEM_FIELD_STATE) {
+    CUDA_TRY(h, cudaMemcpyAsync(o, d.estate, d.g.ne, kind, h->st));
+  } else if (which == CEM_FIELD_ENERGY) {
+    if (need) CUDA_TRY(h, cudaMemcpyAsync(o, d.erec, need, kind, h->st));
+  } else {
+    CUDA_TRY(h, cudaMemcpyAsync(o, d.gc, need, kind, h->st));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out) {
+  if (!h || !n_out) return CEM_ERR_ARG;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int n = h->h_cnt->n_ck;
+  *n_out = n;
+  if (!out || n == 0) return CEM_OK;
+  if (cap < n) return fail(h, CEM_ERR_ARG, "need room for %d cracks", n);
+  const DevState &d = h->d;
+  std::vector<int> el(n), info(n), nodes((size_t)n * 8), stp(n);
+  std::vector<double> Ap((size_t)n * 2), ud(n);
+  CUDA_TRY(h, cudaMemcpyAsync(el.data(), d.ck_elem, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(info.data(), d.ck_info, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(nodes.data(), d.ck_node, n * 32, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(stp.data(), d.ck_step, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(Ap.data(), d.ck_Ap, n * 16, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(ud.data(), d.ck_ud, n * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  std::vector<int> order(n);
+  for (int q = 0; q < n; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return el[a] < el[b]; });
+  for (int r = 0; r < n; ++r) {
+    int q = order[r];
+    cem_crack &c = out[r];
+    c.elem = el[q];
+    c.ka = info[q] & 3;
+    c.kb = (info[q] >> 2) & 3;
+    c.step = stp[q];
+    for (int p = 0; p < 2; ++p)
+      for (int a = 0; a < 4; ++a) c.node[p][a] = nodes[(size_t)q * 8 + p * 4 + a];
+    c.Ap[0] = Ap[2 * q];
+    c.Ap[1] = Ap[2 * q + 1];
+    c.ud = ud[q];
+  }
+  return CEM_OK;
+}
+
+cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out) {
+  if (!h || !n_out) return CEM_ERR_ARG;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int n = h->h_cnt->n_ph;
+  *n_out = n;
+  if (!out || n == 0) return CEM_OK;
+  if (cap < n) return fail(h, CEM_ERR_ARG, "need room for %d phantoms", n);
+  const DevState &d = h->d;
+  std::vector<int> own(n), cr(n), nu(n), us((size_t)n * 4);
+  CUDA_TRY(h, cudaMemcpyAsync(own.data(), d.ph_owner, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(cr.data(), d.ph_creator, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(nu.data(), d.ph_nuser, n * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(us.data(), d.ph_users, n * 16, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  for (int q = 0; q < n; ++q) {
+    cem_phantom &p = out[q];
+    p.id = d.g.nn + q;
+    p.owner = own[q];
+    p.creator_elem = cr[q] >> 2;
+    p.creator_local = cr[q] & 3;
+    p.n_users = nu[q];
+    for (int u = 0; u < 4; ++u) {
+      int code = us[(size_t)q * 4 + u];
+      bool used = u < nu[q];
+      p.users[u][0] = used ? code >> 3 : -1;
+      p.users[u][1] = used ? (code >> 2) & 1 : -1;
+      p.users[u][2] = used ? code & 3 : -1;
+    }
+  }
+  return CEM_OK;
+}
+
+static cem_status surface_rows(cem_handle *h, std::vector<int> &rows) {
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int n = h->h_cnt->n_S;
+  rows.clear();
+  if (n == 0) return CEM_OK;
+  int *tmp = (int *)scratch(h, (size_t)n * 12);
+  if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+  CUDA_TRY(h, launch_surface_info(h->d, tmp, h->st));
+  std::vector<int> v((size_t)n * 3);
+  CUDA_TRY(h, cudaMemcpyAsync(v.data(), tmp, v.size() * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i)
+    if (v[3 * i] >= 0) idx.push_back(i);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return v[3 * a] < v[3 * b]; });
+  for (int i : idx) rows.insert(rows.end(), {v[3 * i], v[3 * i + 1], v[3 * i + 2], i});
+  return CEM_OK;
+}
+
+cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip, int cap, int *n_out) {
+  if (!h || !n_out) return CEM_ERR_ARG;
+  std::vector<int> rows;
+  cem_status rc = surface_rows(h, rows);
+  if (rc != CEM_OK) return rc;
+  int n = (int)(rows.size() / 4);
+  *n_out = n;
+  if (n > cap && (edge || ahead || is_tip)) return fail(h, CEM_ERR_ARG, "need room for %d points", n);
+  for (int q = 0; q < n && q < cap; ++q) {
+    if (edge) edge[q] = rows[4 * q];
+    if (ahead) ahead[q] = rows[4 * q + 1] >> 2;
+    if (is_tip) is_tip[q] = rows[4 * q + 2];
+  }
+  return CEM_OK;
+}
+
+cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out) {
+  if (!h || !n_out) return CEM_ERR_ARG;
+  std::vector<int> rows;
+  cem_status rc = surface_rows(h, rows);
+  if (rc != CEM_OK) return rc;
+  const DevState &d = h->d;
+  int nS = h->h_cnt->n_S, nck = h->h_cnt->n_ck;
+  std::vector<double> SG(nS > 0 ? nS : 1);
+  std::vector<int> crack_of((size_t)d.g.ne), stp(nck > 0 ? nck : 1);
+  if (nS) CUDA_TRY(h, cudaMemcpyAsync(SG.data(), d.S_G, (size_t)nS * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(crack_of.data(), d.crack_of, crack_of.size() * 4, cudaMemcpyDeviceToHost, h->st));
+  if (nck) CUDA_TRY(h, cudaMemcpyAsync(stp.data(), d.ck_step, (size_t)nck * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int n = 0;
+  for (size_t q = 0; q < rows.size(); q += 4) {
+    if (!rows[q + 2]) continue;
+    if (out && n < cap) {
+      int g = rows[q], info = rows[q + 1], e = info >> 2, k0 = info & 3;
+      int nh = h->nx * (h->ny + 1), i = e % h->nx, j = e / h->nx;
+      int f = k0 == 0 ? e - h->nx : k0 == 1 ? e + 1 : k0 == 2 ? e + h->nx : e - 1;
+      cem_tip &t = out[n];
+      t.edge_id = g;
+      t.ahead_elem = e;
+      if (g < nh) {
+        int jj = g / h->nx, ii = g % h->nx;
+        t.x = (ii + 0.5) * h->hx; t.y = jj * h->hy;
+      } else {
+        int gg = g - nh, jj = gg / (h->nx + 1), ii = gg % (h->nx + 1);
+        t.x = ii * h->hx; t.y = (jj + 0.5) * h->hy;
+      }
+      (void)i; (void)j;
+      t.G_last = SG[rows[q + 3]];
+      t.parent = f;
+      int c = crack_of[f];
+      t.birth_step = c >= 0 ? stp[c] : -1;
+    }
+    ++n;
+  }
+  *n_out = n;
+  if (out && n > cap) return fail(h, CEM_ERR_ARG, "need room for %d tips", n);
+  return CEM_OK;
+}
+
+cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge, const int *elem,
+                                     const int *k, const double *G) {
+  if (!h) return CEM_ERR_ARG;
+  if (!h->material) return fail(h, CEM_ERR_STATE, "material first");
+  if (n < 0 || n > h->d.prop_cap) return fail(h, CEM_ERR_ARG, "bad proposal count");
+  if (n == 0) return CEM_OK;
+  std::vector<int> key(n);
+  for (int q = 0; q < n; ++q) {
+    if (elem[q] < 0 || elem[q] >= h->d.g.ne || k[q] < 0 || k[q] > 3)
+      return fail(h, CEM_ERR_ARG, "proposal %d is not a surface point of its element", q);
+    int k0 = local_edge_host(h, elem[q], edge[q]);
+    if (k0 < 0 || k0 == k[q]) return fail(h, CEM_ERR_ARG, "proposal %d is not a surface point of its element", q);
+    key[q] = elem[q] * 4 + k0;
+  }
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  const DevState &d = h->d;
+  CUDA_TRY(h, cudaMemcpyAsync(d.pr_key, key.data(), n * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.pr_edge, edge, n * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.pr_k, k, n * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.pr_G, G, n * 8, cudaMemcpyHostToDevice, h->st));
+  int zero = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->n_prop, &n, 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->pad[0], &zero, 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  CUDA_TRY(h, launch_track(d, h->cur, TRACK_DEBUG, h->st));
+  cem_status rc = sync_status(h);
+  if (rc != CEM_OK) return rc;
+  if (h->h_cnt->pad[0]) return fail(h, CEM_ERR_ARG, "a proposal is not a surface point of its element");
+  return CEM_OK;
+}
+
+}  // extern "C"

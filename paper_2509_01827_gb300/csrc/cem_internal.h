@@ -1,0 +1,134 @@
+// cem_internal.h -- device state and kernel entry points of libcem (not part
+// of the public ABI; see include/cem.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cem {
+
+enum : int { ST_INTACT = 0, ST_CRACKED = 1, ST_OUT = 2 };
+
+// node flags
+enum : uint8_t { NF_LOADED = 1, NF_DIRX = 2, NF_DIRY = 4 };
+
+// device status bits
+enum : int { STAT_CAPACITY = 1, STAT_NONFINITE = 2, STAT_TIMEOUT = 4 };
+
+// Counters live in device memory so that captured graphs can be replayed.
+struct Counters {
+  int n_ph;       // phantom nodes in use
+  int n_ck;       // split elements in use
+  int n_S;        // surface-list length (including tombstones)
+  int n_dead;     // tombstones in the surface list
+  int n_prop;     // proposals of the current step
+  int status;     // STAT_* bits
+  int step;       // steps taken
+  int lam_base;   // first step of the uploaded load-factor table
+  int n_rec;      // energy records written
+  int n_win_last; // winners of the last step (diagnostic)
+  int pad[6];
+};
+
+struct Geo {
+  int nx, ny, nn, ne, nh, ned;
+  double hx, hy, A;
+  double rx, rxh, ry, ryh; // 1/hx, 0.5/hx, 1/hy, 0.5/hy
+};
+
+struct Mat {
+  double D11, D12, D33, rho, gamma, dt;
+  int gamma_mode, scope;
+  float D11f, D12f, D33f;
+};
+
+// Surface-list entry payload: packed (ahead element * 4 + local edge k0).
+struct DevState {
+  Geo g;
+  Mat mat;
+  int precision;
+  int ph_cap, ck_cap, list_cap, prop_cap, ncap;
+  int lam_cap;
+
+  // node arrays over ncap = nn + ph_cap; FP64 mode
+  double *ux[2], *uy[2];
+  double *vx, *vy;
+  // FP32-mixed mode: displacement as float hi + lo, velocity float
+  float *uxh[2], *uxl[2], *uyh[2], *uyl[2];
+  float *vxf, *vyf, *minvf;
+  double *m, *minv;
+  double *Wn, *Wd;
+  uint8_t *nflag;        // [nn]
+  double *Fx, *Fy;       // [nn] Neumann load at unit load factor
+  double *Vx, *Vy;       // [nn] prescribed velocity at unit load factor
+  int *bc_nodes;         // nodes with a load or a prescribed velocity
+  int n_bc;
+
+  // elements
+  uint8_t *estate;       // [ne]
+  int *crack_of;         // [ne]
+  float *gc;             // [ne]
+
+  // split-element table [ck_cap]
+  int *ck_elem;
+  int *ck_info;          // ka | kb << 2 | side(a) << (4 + a)
+  int *ck_node;          // [ck_cap * 8], piece p local a at p*4+a
+  double *ck_Ap;         // [ck_cap * 2]
+  double *ck_ud;
+  int *ck_step;
+  double *pf;            // [ck_cap * 16] piece nodal forces (FP64 mode)
+  float *pff;            // [ck_cap * 16] piece nodal forces (FP32 mode)
+
+  // phantoms [ph_cap]
+  int *ph_owner;
+  int *ph_creator;       // e * 4 + a
+  int *ph_nuser;
+  int *ph_users;         // [ph_cap * 4], (e << 3) | (p << 2) | a, sorted by e
+
+  // surface list [list_cap]
+  int *S;                // edge id or -1 (tombstone)
+  int *S_info;           // ahead * 4 + k0
+  double *S_G;           // largest candidate G at the last evaluation
+  int *spos;             // [ned] position in S or -1
+
+  // proposals of the current step [prop_cap]
+  int *pr_key;           // ahead * 4 + k0
+  int *pr_edge;
+  int *pr_k;
+  double *pr_G;
+
+  Counters *cnt;
+  double *lamN, *lamD;   // [lam_cap] load factors of steps lam_base + i
+
+  // energy
+  double *e_part;        // per-block partial sums
+  int e_part_cap;
+  double *erec;          // [rec_cap * 7]
+  int rec_cap;
+};
+
+// ------------------------------------------------------------------ launch
+// All launchers enqueue on `st` and return cudaGetLastError().
+cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
+cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
+                             cudaStream_t st);
+cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
+                             cudaStream_t st);
+cudaError_t launch_track(const DevState &d, int cur_next, int mode, cudaStream_t st);
+cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
+cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);
+cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);
+cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st);
+cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st);
+cudaError_t launch_check_finite(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *uy,
+                                double *vx, double *vy, int n, cudaStream_t st);
+cudaError_t launch_fp64_to_fp32(const DevState &d, int cur, const double *ux,
+                                const double *uy, const double *vx, const double *vy,
+                                int n, cudaStream_t st);
+int energy_parts_needed(const DevState &d);
+
+// track modes
+enum : int { TRACK_STEP = 0, TRACK_PRECRACK = 1, TRACK_DEBUG = 2 };
+
+}  // namespace cem

@@ -1,0 +1,163 @@
+// energy.cu -- FP64 energy records, finiteness check and precision
+// conversions (compiled with -fmad=false).
+//
+// An energy record at step n holds KE of the mid-step velocity
+// vbar^n = (v^{n-1/2} + v^{n+1/2}) / 2, the strain energy of u^n (each
+// element or piece owns A_p/4 of each of its edge points), the external and
+// prescribed-velocity work done before step n, and the dissipated energy
+// U_d = sum of G_c * segment length over the splits made before step n.
+// Per-block partial sums are added in a fixed order, so records are
+// reproducible run to run.
+#include <cuda_runtime.h>
+
+#include "cem_internal.h"
+
+namespace cem {
+
+namespace {
+
+constexpr int TB = 1024;
+
+__device__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(TB) k_energy_pre(DevState d) {
+  Counters *c = d.cnt;
+  int rec = c->n_rec;
+  if (rec >= d.rec_cap) {
+    if (threadIdx.x == 0) atomicOr(&c->status, STAT_CAPACITY);
+    return;
+  }
+  double wn = 0.0, wd = 0.0, ud = 0.0;
+  for (int q = threadIdx.x; q < d.n_bc; q += TB) {
+    int N = d.bc_nodes[q];
+    wn += d.Wn[N];
+    wd += d.Wd[N];
+  }
+  int nck = c->n_ck;
+  for (int q = threadIdx.x; q < nck; q += TB) ud += d.ck_ud[q];
+  wn = block_sum(wn);
+  wd = block_sum(wd);
+  ud = block_sum(ud);
+  if (threadIdx.x == 0) {
+    double *r = d.erec + (size_t)rec * 7;
+    r[0] = (double)c->step;
+    r[1] = (double)c->step * d.mat.dt;
+    r[4] = wn;
+    r[5] = wd;
+    r[6] = ud;
+  }
+}
+
+__global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
+  Counters *c = d.cnt;
+  int rec = c->n_rec;
+  if (rec >= d.rec_cap) return;
+  double ke = 0.0, se = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += TB) {
+    ke += d.e_part[2 * q];
+    se += d.e_part[2 * q + 1];
+  }
+  ke = block_sum(ke);
+  se = block_sum(se);
+  if (threadIdx.x == 0) {
+    double *r = d.erec + (size_t)rec * 7;
+    r[2] = ke;
+    r[3] = se;
+    c->n_rec = rec + 1;
+  }
+}
+
+__global__ void k_check_finite(DevState d, int cur) {
+  int n = d.g.nn + d.cnt->n_ph;
+  bool bad = false;
+  for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
+    double a, b, v, w;
+    if (d.precision == 1) {
+      a = (double)d.uxh[cur][N] + (double)d.uxl[cur][N];
+      b = (double)d.uyh[cur][N] + (double)d.uyl[cur][N];
+      v = d.vxf[N];
+      w = d.vyf[N];
+    } else {
+      a = d.ux[cur][N]; b = d.uy[cur][N]; v = d.vx[N]; w = d.vy[N];
+    }
+    if (!isfinite(a) || !isfinite(b) || !isfinite(v) || !isfinite(w)) bad = true;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&d.cnt->status, STAT_NONFINITE);
+}
+
+__global__ void k_f32_to_f64(DevState d, int cur, double *ux, double *uy, double *vx, double *vy,
+                             int n) {
+  for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
+    if (ux) ux[N] = (double)d.uxh[cur][N] + (double)d.uxl[cur][N];
+    if (uy) uy[N] = (double)d.uyh[cur][N] + (double)d.uyl[cur][N];
+    if (vx) vx[N] = (double)d.vxf[N];
+    if (vy) vy[N] = (double)d.vyf[N];
+  }
+}
+
+__global__ void k_f64_to_f32(DevState d, int cur, const double *ux, const double *uy,
+                             const double *vx, const double *vy, int n) {
+  for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
+    if (ux) {
+      float h = (float)ux[N];
+      d.uxh[cur][N] = h;
+      d.uxl[cur][N] = (float)(ux[N] - (double)h);
+    }
+    if (uy) {
+      float h = (float)uy[N];
+      d.uyh[cur][N] = h;
+      d.uyl[cur][N] = (float)(uy[N] - (double)h);
+    }
+    if (vx) d.vxf[N] = (float)vx[N];
+    if (vy) d.vyf[N] = (float)vy[N];
+  }
+}
+
+int grid_for(int n, int block, int maxb) {
+  int b = (n + block - 1) / block;
+  return b < 1 ? 1 : (b > maxb ? maxb : b);
+}
+
+}  // namespace
+
+cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st) {
+  k_energy_pre<<<1, TB, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st) {
+  k_energy_post<<<1, TB, 0, st>>>(d, nparts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const DevState &d, int cur, cudaStream_t st) {
+  k_check_finite<<<grid_for(d.ncap, 256, 1216), 256, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *uy, double *vx,
+                                double *vy, int n, cudaStream_t st) {
+  k_f32_to_f64<<<grid_for(n, 256, 1216), 256, 0, st>>>(d, cur, ux, uy, vx, vy, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_to_fp32(const DevState &d, int cur, const double *ux, const double *uy,
+                                const double *vx, const double *vy, int n, cudaStream_t st) {
+  k_f64_to_f32<<<grid_for(n, 256, 1216), 256, 0, st>>>(d, cur, ux, uy, vx, vy, n);
+  return cudaGetLastError();
+}
+
+}  // namespace cem
