@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit MCT-2D-CEM step on one or more GB300s.
+
+Workload (default): the 2048 x 2048 Q4 fragmentation plate -- 0.1 m square,
+central hole of radius 5 mm, 50 MPa internal pressure pulse, Weibull G_c
+(mean 3 J/m^2, shape 10, seed 2509) -- run from t = 0.  A "step" is one
+whole explicit step: piece forces, tile update of every real node, phantom
+update, surface evaluation, multi-tip tracking, and an energy record every
+50 steps.  Metric: element-updates/s = active elements * steps / time.
+
+--impl ours (default): the CUDA library; value from CUDA events around the
+  timed steps (graph replays), roofline of the dominant kernel from a
+  profiled window of the same run, oracle CPU baseline on a bounded sample.
+--impl reference: the CPU oracle as it stands (the only reference this
+  method has), timed on a bounded sample on this host.
+Multi-GPU (torchrun): one independent replica per GPU (the path does not
+shard across GPUs); value = all ranks' element-updates / max rank time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "element-updates/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def make_problem(workload):
+    from paper_2509_01827_gb300 import inputs
+    if workload == "fragmentation_2048_neumann":
+        p = inputs.fragmentation(2048, mode="neumann", p0=50e6, seed=2509)
+    elif workload == "fragmentation_2048_dirichlet":
+        p = inputs.fragmentation(2048, mode="dirichlet", v0=2.0, seed=2509)
+    elif workload == "notched_plate_400x160":
+        p = inputs.CONFIGS["notched_plate_400x160"]()
+    else:
+        raise SystemExit(f"unknown workload {workload}")
+    p.energy_every = 50
+    return p
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 10:
+                continue
+            if self.uuid and self.uuid not in c[1]:
+                continue
+            rows.append(c)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle
+def time_oracle(prob, budget_s=15.0, max_steps=60):
+    """The CPU oracle as it stands, single thread, on a bounded sample of the
+    workload: the first steps of the same run."""
+    from oracle.oracle import from_problem
+    t0 = time.perf_counter()
+    s = from_problem(prob)
+    setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t1
+    n = int(max(1, min(max_steps, budget_s / max(one, 1e-6)))) if one < budget_s else 0
+    t2 = time.perf_counter()
+    if n:
+        s.step(n)
+    rest = time.perf_counter() - t2
+    steps = n + 1
+    el = time.perf_counter() - t1
+    del rest
+    value = prob.n_active * steps / el
+    return {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"first {steps} steps of the {prob.nx}x{prob.ny} run "
+                      f"({prob.n_active} active elements), FP64, single thread; "
+                      f"set-up {setup:.1f}s not timed", "seconds": round(el, 3)}
+
+
+# ------------------------------------------------------------------ ours
+def bytes_per_update(precision):
+    """Algorithmic bytes of the tile kernel per (real node, element) pair."""
+    if precision == "fp32":
+        # u hi+lo read+write 32, v read+write 16, 1/m 4, node flag 1, element state 1
+        return 54.0
+    # u read+write 32, v read+write 32, 1/m 8, node flag 1, element state 1
+    return 74.0
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2509_01827_gb300 import build as _build
+    from paper_2509_01827_gb300.cem import CEM_FP32_MIXED, CEM_FP64, Solver
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    prec = CEM_FP32_MIXED if args.precision == "fp32" else CEM_FP64
+    prob = make_problem(args.workload)
+    sol = Solver(prob, precision=prec, device=dev)
+    stream = sol._stream
+    nact = prob.n_active
+    # warm-up (also builds the CUDA graphs)
+    sol.step(args.warmup)
+    torch.cuda.synchronize()
+    c0 = sol.counts()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sol.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    time.sleep(0.2)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    c1 = sol.counts()
+    launches = c1["kernel_launches"] - c0["kernel_launches"]
+    value = world * nact * args.steps / (ms * 1e-3)
+
+    # per-kernel device time over a profiled window of the same run
+    nprof = max(1, min(args.profile_steps, 4000))
+    prof = sol.profile_steps(nprof)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or HBM_FALLBACK_GBS
+    bpu = bytes_per_update(args.precision)
+    units = prob.n_nodes  # one tile-kernel launch updates every real node once
+    bytes_launch = units * bpu
+    main_ms = prof["main"] / nprof
+    achieved = bytes_launch / (main_ms * 1e-3) / 1e9
+    share = prof["main"] / prof["total"] if prof["total"] > 0 else None
+
+    # end to end through the C ABI: one cem_step(1) per step from the host,
+    # load factors uploaded from pinned host memory and the status word read
+    # back every step
+    ne2e = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        sol.step(1)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * nact * ne2e / e2e_s
+
+    companion = None
+    if args.companion and rank == 0 and world == 1:
+        other = CEM_FP64 if prec == CEM_FP32_MIXED else CEM_FP32_MIXED
+        s2 = Solver(make_problem(args.workload), precision=other, device=dev)
+        s2.step(args.warmup)
+        torch.cuda.synchronize()
+        n2 = args.companion_steps
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s2._stream)
+        s2.step(n2)
+        f1.record(s2._stream)
+        torch.cuda.synchronize()
+        companion = {"precision": "fp64" if other == CEM_FP64 else "fp32",
+                     "value": nact * n2 / (f0.elapsed_time(f1) * 1e-3), "unit": METRIC,
+                     "steps": n2, "warmup": args.warmup}
+        s2.close()
+
+    counts = sol.counts()
+    sol.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "mesh": f"{prob.nx}x{prob.ny} Q4",
+                   "active_elements": nact, "nodes": prob.n_nodes,
+                   "precision": "fp32-mixed (FP32 element math, compensated FP32 displacement)"
+                   if args.precision == "fp32" else "fp64",
+                   "energy_every": prob.energy_every,
+                   "l2": f"inputs larger than L2: state {bpu * prob.n_nodes / 1e6:.0f} MB > 129 MB",
+                   "parallelism": f"replicas x{world}",
+                   "cracked_elements_end": counts["n_cracked"], "tips_end": counts["n_tips"],
+                   "t_end_us": counts["t"] * 1e6},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": args.traffic,
+                     "kernel": "tile update (k_main)", "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": main_ms, "share_of_step": share,
+                     "profiled_steps": nprof, "per_kernel_ms": prof},
+        "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 20,
+                "d2h_bytes_per_step": 64, "steps": ne2e,
+                "how": "one cem_step(1) call per step from the host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if args.precision == "fp64":
+        line["roofline"]["note"] = ("the FP64 tile kernel is bound by the FP64 pipe, "
+                                    "not by HBM")
+    if companion:
+        line["companion"] = companion
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(make_problem(args.workload), args.cpu_budget)
+    return line
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    prob = make_problem(args.workload)
+    per = []
+    for _ in range(args.warmup):
+        pass
+    t_all = time.perf_counter()
+    for _ in range(max(1, args.steps_reference)):
+        per.append(time_oracle(prob, args.cpu_budget / max(1, args.steps_reference)))
+    wall = time.perf_counter() - t_all
+    vals = [p["value"] for p in per]
+    value = float(np.median(vals))
+    cb = dict(per[-1])
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "mesh": f"{prob.nx}x{prob.ny} Q4",
+                       "active_elements": prob.n_active},
+            "cpu_baseline": cb, "wall_s": wall,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="fragmentation_2048_neumann")
+    ap.add_argument("--profile-steps", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--companion", type=int, default=1)
+    ap.add_argument("--companion-steps", type=int, default=100)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--steps-reference", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the tile kernel, when known")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, rank, world)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

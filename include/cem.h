@@ -36,7 +36,9 @@
  *   - Functions return a cem_status; nothing throws across the ABI;
  *     cem_last_error() returns the message of the last failure on a handle.
  *   - A handle is used by one host thread at a time.  All device work goes to
- *     the stream given in the descriptor (NULL = the legacy default stream).
+ *     the stream given in the descriptor; with NULL the library creates its
+ *     own non-blocking stream (graphs cannot be captured on the legacy
+ *     default stream).
  *   - Floating-point state is SI: metres, seconds, pascals, kilograms.
  */
 #ifndef CEM_H
@@ -83,7 +85,7 @@ typedef struct {
   double dt_factor;                  /* dt = dt_factor * min(hx,hy) / c_d (0 -> 0.5) */
   double dt;                         /* > 0 overrides dt_factor */
   int energy_every;                  /* record energies every K steps (0 = never) */
-  void *cuda_stream;                 /* cudaStream_t, NULL = legacy default stream */
+  void *cuda_stream;                 /* cudaStream_t, NULL = a stream of the library's own */
   int device;                        /* CUDA device ordinal */
   cem_alloc_fn alloc;                /* optional device allocator */
   cem_free_fn free;                  /* required when alloc is given */
@@ -165,6 +167,9 @@ typedef struct {
   long step;         /* steps taken */
   double dt;         /* time step (s) */
   double t;          /* step * dt */
+  long kernel_launches; /* kernels this handle has enqueued (graph nodes included) */
+  long last_proposals;  /* proposals evaluated in the last step */
+  long last_winners;    /* splits made in the last step */
 } cem_counts;
 
 cem_status cem_get_counts(cem_handle *h, cem_counts *out);
@@ -209,6 +214,13 @@ cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out
 /* Free-surface edge points sorted by edge id: edge, ahead element, tip flag. */
 cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip,
                            int cap, int *n_out);
+
+/* Profiling: advances n steps like cem_step but with direct kernel launches
+ * bracketed by CUDA events on the handle's stream, and returns device
+ * milliseconds in ms[8]: [0] all n steps (first event to last), [1] piece
+ * forces, [2] tile update of real nodes, [3] phantom update, [4] surface
+ * evaluation, [5] tracking, [6] energy records, [7] number of kernels. */
+cem_status cem_profile_steps(cem_handle *h, int n, double *ms);
 
 /* Testing hook for the tracking bookkeeping: runs the selection and split
  * (Sec. 3) on caller-given proposals (surface edge id, its ahead element,

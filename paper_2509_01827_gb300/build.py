@@ -23,9 +23,10 @@ UNITS = [
     ("track.cu", ["-fmad=false"]),
     ("energy.cu", ["-fmad=false"]),
     ("step_fp32.cu", []),
+    ("eval_fp32.cu", ["-fmad=false"]),
     ("api.cpp", []),
 ]
-HEADERS = ["cem_internal.h", "q4_fp64.cuh"]
+HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh"]
 
 
 def _stale(obj, deps):

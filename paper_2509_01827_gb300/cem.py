@@ -41,7 +41,8 @@ class cem_counts(C.Structure):
     _fields_ = [("n_nodes", C.c_long), ("n_phantoms", C.c_long), ("n_elems", C.c_long),
                 ("n_active", C.c_long), ("n_cracked", C.c_long), ("n_surface", C.c_long),
                 ("n_tips", C.c_long), ("n_energy", C.c_long), ("step", C.c_long),
-                ("dt", C.c_double), ("t", C.c_double)]
+                ("dt", C.c_double), ("t", C.c_double), ("kernel_launches", C.c_long),
+                ("last_proposals", C.c_long), ("last_winners", C.c_long)]
 
 
 class cem_tip(C.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "cem_get_phantoms": (C.c_int, [_h, C.POINTER(cem_phantom), C.c_int, _ip]),
     "cem_get_surface": (C.c_int, [_h, _ip, _ip, _ip, C.c_int, _ip]),
     "cem_debug_apply_proposals": (C.c_int, [_h, C.c_int, _ip, _ip, _ip, _dp]),
+    "cem_profile_steps": (C.c_int, [_h, C.c_int, _dp]),
     "cem_last_error": (C.c_char_p, [_h]),
     "cem_mesh_destroy": (None, [_h]),
 }
@@ -210,6 +212,13 @@ def cem_debug_apply_proposals(h, edge, elem, k, G):
     g = np.ascontiguousarray(G, np.float64)
     _chk(h, lib().cem_debug_apply_proposals(h, len(e), _p(e, _ip), _p(el, _ip), _p(kk, _ip),
                                             _p(g, _dp)))
+
+
+def cem_profile_steps(h, n):
+    ms = np.zeros(8)
+    _chk(h, lib().cem_profile_steps(h, int(n), _p(ms, _dp)))
+    keys = ["total", "pieces", "main", "phantom", "eval", "track", "energy", "kernels"]
+    return dict(zip(keys, ms.tolist()))
 
 
 def cem_mesh_destroy(h):
@@ -378,6 +387,9 @@ class Solver:
 
     def tips(self):
         return cem_get_crack_tips(self.h, self.counts()["n_tips"])
+
+    def profile_steps(self, n):
+        return cem_profile_steps(self.h, n)
 
     def debug_apply_proposals(self, edge, elem, k, G):
         cem_debug_apply_proposals(self.h, edge, elem, k, G)

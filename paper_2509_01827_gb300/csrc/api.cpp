@@ -47,7 +47,9 @@ struct cem_handle {
   int energy_every = 0;
   cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][energy]
   Counters *h_cnt = nullptr;  // pinned
+  double *h_lam = nullptr;    // pinned staging of the load-factor table
   bool own_stream = false;
+  long launches = 0;           // kernels enqueued (graph replays count their nodes)
   void *scratch = nullptr;     // reusable device scratch for getters
   size_t scratch_bytes = 0;
   std::string err;
@@ -185,16 +187,46 @@ void drop_graphs(cem_handle *h) {
       if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
-// Enqueues one explicit step (buffers cur -> cur^1) on the stream.
-cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy) {
+int kernels_in_step(bool energy) { return kStepKernels + 1 + (energy ? 2 : 0); }
+
+// Enqueues one explicit step (buffers cur -> cur^1) on the stream.  With
+// marks (profiling) events are recorded after the energy prologue, after
+// each step kernel, after the energy epilogue and after tracking:
+// marks[0..6].
+cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
+                         cudaEvent_t *marks = nullptr) {
   const DevState &d = h->d;
   cudaError_t e;
   if (energy && (e = launch_energy_pre(d, h->st)) != cudaSuccess) return e;
-  if (d.precision == CEM_FP32_MIXED) e = launch_step_fp32(d, cur, first, energy, h->st);
-  else e = launch_step_fp64(d, cur, first, energy, h->st);
+  if (marks) cudaEventRecord(marks[0], h->st);
+  if (d.precision == CEM_FP32_MIXED) e = launch_step_fp32(d, cur, first, energy, h->st, marks ? marks + 1 : nullptr);
+  else e = launch_step_fp64(d, cur, first, energy, h->st, marks ? marks + 1 : nullptr);
   if (e != cudaSuccess) return e;
+  if (marks) cudaEventRecord(marks[4], h->st);
   if (energy && (e = launch_energy_post(d, energy_parts_needed(d), h->st)) != cudaSuccess) return e;
-  return launch_track(d, cur ^ 1, TRACK_STEP, h->st);
+  if (marks) cudaEventRecord(marks[5], h->st);
+  e = launch_track(d, cur ^ 1, TRACK_STEP, h->st);
+  if (marks) cudaEventRecord(marks[6], h->st);
+  return e;
+}
+
+// Load factors of steps [h->step, h->step + chunk) into the device table.
+cem_status upload_load_factors(cem_handle *h, int chunk) {
+  const DevState &d = h->d;
+  const double dt = d.mat.dt;
+  double *lamN = h->h_lam, *lamD = h->h_lam + d.lam_cap;
+  for (int q = 0; q < chunk; ++q) {
+    long s = h->step + q;
+    lamN[q] = h->neu_set ? law_eval(h->neu_law, (double)s * dt, h->neu_t0, h->neu_tau) : 0.0;
+    lamD[q] = h->dir_set ? law_eval(h->dir_law, ((double)s + 0.5) * dt, h->dir_t0, h->dir_tau) : 0.0;
+  }
+  int base = (int)h->step;
+  h->h_cnt->lam_base = base;
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN, chunk * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD, chunk * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &h->h_cnt->lam_base, 4, cudaMemcpyHostToDevice, h->st));
+  // the pinned staging is reused only after the stream has been synchronised
+  return CEM_OK;
 }
 
 cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
@@ -277,6 +309,27 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
   d.g.hx = desc->hx; d.g.hy = desc->hy; d.g.A = desc->hx * desc->hy;
   d.g.rx = 1.0 / desc->hx; d.g.rxh = d.g.rx * 0.5;
   d.g.ry = 1.0 / desc->hy; d.g.ryh = d.g.ry * 0.5;
+  d.g.rxf = (float)d.g.rx; d.g.ryf = (float)d.g.ry; d.g.qAf = (float)(d.g.A * 0.25);
+  {
+    // reference edge vectors and candidate-path normals for the FP32 mode
+    const double XN[4] = {-1, 1, 1, -1}, EN[4] = {-1, -1, 1, 1};
+    const double XG[4] = {0, 1, 0, -1}, EG[4] = {-1, 0, 1, 0};
+    for (int k0 = 0; k0 < 4; ++k0) {
+      double DX = (XN[(k0 + 1) % 4] - XN[k0]) * (0.5 * desc->hx);
+      double DY = (EN[(k0 + 1) % 4] - EN[k0]) * (0.5 * desc->hy);
+      d.g.DXf[k0] = (float)DX;
+      d.g.DYf[k0] = (float)DY;
+      for (int k = 0; k < 4; ++k) {
+        if (k == k0) { d.g.nxf[k0][k] = d.g.nyf[k0][k] = 0.f; continue; }
+        double sx = (XG[k] - XG[k0]) * (0.5 * desc->hx), sy = (EG[k] - EG[k0]) * (0.5 * desc->hy);
+        double rx = -sy, ry = sx;
+        if (rx * DX + ry * DY < 0.0) { rx = -rx; ry = -ry; }
+        double len = sqrt(sx * sx + sy * sy);
+        d.g.nxf[k0][k] = (float)(rx / len);
+        d.g.nyf[k0][k] = (float)(ry / len);
+      }
+    }
+  }
   d.precision = desc->precision;
   d.ph_cap = desc->phantom_capacity > 0 ? desc->phantom_capacity : (int)(ne / 4 + 4096);
   d.ck_cap = desc->crack_capacity > 0 ? desc->crack_capacity : (int)(ne / 4 + 4096);
@@ -301,10 +354,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
     for (int b = 0; b < 2; ++b) ok = ok && dalloc_n(h, d.ux[b], nc) && dalloc_n(h, d.uy[b], nc);
     ok = ok && dalloc_n(h, d.vx, nc) && dalloc_n(h, d.vy, nc) && dalloc_n(h, d.pf, (size_t)d.ck_cap * 16);
   } else {
-    for (int b = 0; b < 2; ++b)
-      ok = ok && dalloc_n(h, d.uxh[b], nc) && dalloc_n(h, d.uxl[b], nc) &&
-           dalloc_n(h, d.uyh[b], nc) && dalloc_n(h, d.uyl[b], nc);
-    ok = ok && dalloc_n(h, d.vxf, nc) && dalloc_n(h, d.vyf, nc) && dalloc_n(h, d.minvf, nc) &&
+    for (int b = 0; b < 2; ++b) ok = ok && dalloc_n(h, d.u4[b], nc);
+    ok = ok && dalloc_n(h, d.v2, nc) && dalloc_n(h, d.minvf, nc) &&
          dalloc_n(h, d.pff, (size_t)d.ck_cap * 16);
   }
   ok = ok && dalloc_n(h, d.m, nc) && dalloc_n(h, d.minv, nc) && dalloc_n(h, d.Wn, nc) &&
@@ -325,7 +376,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
   d.e_part_cap = energy_parts_needed(d);
   ok = ok && dalloc_n(h, d.e_part, (size_t)d.e_part_cap * 2);
-  if (!ok || cudaHostAlloc((void **)&h->h_cnt, sizeof(Counters), cudaHostAllocDefault) != cudaSuccess) {
+  if (!ok || cudaHostAlloc((void **)&h->h_cnt, sizeof(Counters), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void **)&h->h_lam, 2 * sizeof(double) * d.lam_cap, cudaHostAllocDefault) != cudaSuccess) {
     g_create_error = "device allocation failed";
     cem_mesh_destroy(h);
     return CEM_ERR_CUDA;
@@ -360,6 +412,7 @@ void cem_mesh_destroy(cem_handle *h) {
   }
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
+  if (h->h_lam) cudaFreeHost(h->h_lam);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
 }
@@ -396,6 +449,7 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
     double hmin = h->hx < h->hy ? h->hx : h->hy;
     m.dt = h->dt_factor * hmin / cd;
   }
+  m.dtf = (float)m.dt;
   const DevState &d = h->d;
   std::vector<float> gc((size_t)d.g.ne);
   for (int e = 0; e < d.g.ne; ++e) gc[e] = gc_per_elem ? gc_per_elem[e] : (float)gc_uniform;
@@ -533,31 +587,22 @@ cem_status cem_step(cem_handle *h, int n) {
   if (n == 0) return CEM_OK;
   CUDA_TRY(h, cudaSetDevice(h->device));
   const DevState &d = h->d;
-  const double dt = d.mat.dt;
-  std::vector<double> lamN(d.lam_cap), lamD(d.lam_cap);
   int done = 0;
   while (done < n) {
     int chunk = std::min(n - done, d.lam_cap);
-    for (int q = 0; q < chunk; ++q) {
-      long s = h->step + q;
-      lamN[q] = h->neu_set ? law_eval(h->neu_law, (double)s * dt, h->neu_t0, h->neu_tau) : 0.0;
-      lamD[q] = h->dir_set ? law_eval(h->dir_law, ((double)s + 0.5) * dt, h->dir_t0, h->dir_tau) : 0.0;
-    }
-    int base = (int)h->step;
-    CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN.data(), chunk * 8, cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD.data(), chunk * 8, cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &base, 4, cudaMemcpyHostToDevice, h->st));
-    // the table must be consumed before the host buffers change
+    cem_status rc = upload_load_factors(h, chunk);
+    if (rc != CEM_OK) return rc;
     for (int q = 0; q < chunk; ++q) {
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
         CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
       } else {
         cudaGraphExec_t gx;
-        cem_status rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
+        rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
         if (rc != CEM_OK) return rc;
         CUDA_TRY(h, cudaGraphLaunch(gx, h->st));
       }
+      h->launches += kernels_in_step(energy);
       h->cur ^= 1;
       h->step += 1;
     }
@@ -565,6 +610,54 @@ cem_status cem_step(cem_handle *h, int n) {
     done += chunk;
   }
   CUDA_TRY(h, launch_check_finite(d, h->cur, h->st));
+  h->launches += 1;
+  return sync_status(h);
+}
+
+cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
+  if (!h || !ms) return CEM_ERR_ARG;
+  if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
+  if (n < 1 || n > h->d.lam_cap) return fail(h, CEM_ERR_ARG, "1 <= n <= %d", h->d.lam_cap);
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  for (int q = 0; q < 8; ++q) ms[q] = 0.0;
+  cem_status rc = upload_load_factors(h, n);
+  if (rc != CEM_OK) return rc;
+  const int M = 8;  // events per step: start + 7 marks
+  std::vector<cudaEvent_t> ev((size_t)n * M);
+  for (auto &e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+  long kernels = 0;
+  cudaError_t err = cudaSuccess;
+  for (int q = 0; q < n && err == cudaSuccess; ++q) {
+    bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
+    cudaEventRecord(ev[(size_t)q * M], h->st);
+    err = enqueue_step(h, h->cur, h->step == 0, energy, &ev[(size_t)q * M + 1]);
+    kernels += kernels_in_step(energy);
+    h->cur ^= 1;
+    h->step += 1;
+  }
+  cudaError_t es = cudaStreamSynchronize(h->st);
+  if (err == cudaSuccess && es == cudaSuccess) {
+    float t;
+    cudaEventElapsedTime(&t, ev[0], ev[(size_t)(n - 1) * M + 7]);
+    ms[0] = t;
+    for (int q = 0; q < n; ++q) {
+      cudaEvent_t *e = &ev[(size_t)q * M];
+      float a, b, c, dd, f, g, k;
+      cudaEventElapsedTime(&a, e[0], e[1]);  // energy prologue
+      cudaEventElapsedTime(&b, e[1], e[2]);  // pieces
+      cudaEventElapsedTime(&c, e[2], e[3]);  // tile update
+      cudaEventElapsedTime(&dd, e[3], e[4]); // phantoms
+      cudaEventElapsedTime(&f, e[4], e[5]);  // evaluation
+      cudaEventElapsedTime(&g, e[5], e[6]);  // energy epilogue
+      cudaEventElapsedTime(&k, e[6], e[7]);  // tracking
+      ms[1] += b; ms[2] += c; ms[3] += dd; ms[4] += f; ms[5] += k; ms[6] += a + g;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return fail(h, CEM_ERR_CUDA, "profiled step: %s", cudaGetErrorString(err));
+  if (es != cudaSuccess) return fail(h, CEM_ERR_CUDA, "profiled step sync: %s", cudaGetErrorString(es));
+  ms[7] = (double)kernels;
+  h->launches += kernels;
   return sync_status(h);
 }
 
@@ -585,6 +678,9 @@ cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
   out->step = c.step;
   out->dt = h->d.mat.dt;
   out->t = (double)c.step * h->d.mat.dt;
+  out->kernel_launches = h->launches;
+  out->last_proposals = c.n_prop_last;
+  out->last_winners = c.n_win_last;
   out->n_surface = 0;
   out->n_tips = 0;
   if (c.n_S > 0) {

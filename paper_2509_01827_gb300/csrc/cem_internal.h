@@ -27,19 +27,24 @@ struct Counters {
   int lam_base;   // first step of the uploaded load-factor table
   int n_rec;      // energy records written
   int n_win_last; // winners of the last step (diagnostic)
-  int pad[6];
+  int n_prop_last; // proposals of the last step (diagnostic)
+  int pad[5];
 };
 
 struct Geo {
   int nx, ny, nn, ne, nh, ned;
   double hx, hy, A;
   double rx, rxh, ry, ryh; // 1/hx, 0.5/hx, 1/hy, 0.5/hy
+  // FP32 copies for the FP32-mixed kernels (no FP64 work on the hot path)
+  float rxf, ryf, qAf;     // 1/hx, 1/hy, A/4
+  float DXf[4], DYf[4];    // reference vector X_N2 - X_N1 of local edge k
+  float nxf[4][4], nyf[4][4];  // unit normal of candidate path k0 -> k
 };
 
 struct Mat {
   double D11, D12, D33, rho, gamma, dt;
   int gamma_mode, scope;
-  float D11f, D12f, D33f;
+  float D11f, D12f, D33f, dtf;
 };
 
 // Surface-list entry payload: packed (ahead element * 4 + local edge k0).
@@ -53,9 +58,11 @@ struct DevState {
   // node arrays over ncap = nn + ph_cap; FP64 mode
   double *ux[2], *uy[2];
   double *vx, *vy;
-  // FP32-mixed mode: displacement as float hi + lo, velocity float
-  float *uxh[2], *uxl[2], *uyh[2], *uyl[2];
-  float *vxf, *vyf, *minvf;
+  // FP32-mixed mode, one record per node: displacement as compensated
+  // float pairs (x.hi, x.lo, y.hi, y.lo) and velocity (x, y)
+  float4 *u4[2];
+  float2 *v2;
+  float *minvf;
   double *m, *minv;
   double *Wn, *Wd;
   uint8_t *nflag;        // [nn]
@@ -110,10 +117,14 @@ struct DevState {
 // ------------------------------------------------------------------ launch
 // All launchers enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
+// The step launchers enqueue four kernels (pieces, tile update of real nodes,
+// phantoms, surface evaluation); when marks is given they record marks[0..2]
+// after the first three of them (profiling).
+constexpr int kStepKernels = 4;
 cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st);
+                             cudaStream_t st, cudaEvent_t *marks = nullptr);
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st);
+                             cudaStream_t st, cudaEvent_t *marks = nullptr);
 cudaError_t launch_track(const DevState &d, int cur_next, int mode, cudaStream_t st);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);

@@ -86,10 +86,12 @@ __global__ void k_check_finite(DevState d, int cur) {
   for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
     double a, b, v, w;
     if (d.precision == 1) {
-      a = (double)d.uxh[cur][N] + (double)d.uxl[cur][N];
-      b = (double)d.uyh[cur][N] + (double)d.uyl[cur][N];
-      v = d.vxf[N];
-      w = d.vyf[N];
+      const float4 U = d.u4[cur][N];
+      const float2 V = d.v2[N];
+      a = (double)U.x + (double)U.y;
+      b = (double)U.z + (double)U.w;
+      v = V.x;
+      w = V.y;
     } else {
       a = d.ux[cur][N]; b = d.uy[cur][N]; v = d.vx[N]; w = d.vy[N];
     }
@@ -101,28 +103,32 @@ __global__ void k_check_finite(DevState d, int cur) {
 __global__ void k_f32_to_f64(DevState d, int cur, double *ux, double *uy, double *vx, double *vy,
                              int n) {
   for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
-    if (ux) ux[N] = (double)d.uxh[cur][N] + (double)d.uxl[cur][N];
-    if (uy) uy[N] = (double)d.uyh[cur][N] + (double)d.uyl[cur][N];
-    if (vx) vx[N] = (double)d.vxf[N];
-    if (vy) vy[N] = (double)d.vyf[N];
+    const float4 U = d.u4[cur][N];
+    const float2 V = d.v2[N];
+    if (ux) ux[N] = (double)U.x + (double)U.y;
+    if (uy) uy[N] = (double)U.z + (double)U.w;
+    if (vx) vx[N] = (double)V.x;
+    if (vy) vy[N] = (double)V.y;
   }
 }
 
 __global__ void k_f64_to_f32(DevState d, int cur, const double *ux, const double *uy,
                              const double *vx, const double *vy, int n) {
   for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
+    float4 U = d.u4[cur][N];
+    float2 V = d.v2[N];
     if (ux) {
-      float h = (float)ux[N];
-      d.uxh[cur][N] = h;
-      d.uxl[cur][N] = (float)(ux[N] - (double)h);
+      U.x = (float)ux[N];
+      U.y = (float)(ux[N] - (double)U.x);
     }
     if (uy) {
-      float h = (float)uy[N];
-      d.uyh[cur][N] = h;
-      d.uyl[cur][N] = (float)(uy[N] - (double)h);
+      U.z = (float)uy[N];
+      U.w = (float)(uy[N] - (double)U.z);
     }
-    if (vx) d.vxf[N] = (float)vx[N];
-    if (vy) d.vyf[N] = (float)vy[N];
+    if (vx) V.x = (float)vx[N];
+    if (vy) V.y = (float)vy[N];
+    d.u4[cur][N] = U;
+    d.v2[N] = V;
   }
 }
 

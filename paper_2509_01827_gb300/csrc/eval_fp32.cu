@@ -1,0 +1,142 @@
+// eval_fp32.cu -- surface-point evaluation of the FP32-mixed mode
+// (compiled with -fmad=false so that its FP64 re-check uses the same
+// operation order as the FP64 mode).
+//
+// Each free-surface point computes the energy release rate of its three
+// candidate paths (Sec. 2.2) in FP32 from the compensated displacement.  If
+// any candidate lies within 1e-3 of G_c (|G/G_c - 1| < 1e-3) the point is
+// re-evaluated in FP64, so that the threshold decision is the FP64 one.  The
+// Q4 cracking rule then runs on the (FP64-widened) values and proposals are
+// appended with a warp ballot.
+#include <cuda_runtime.h>
+
+#include "cem_internal.h"
+#include "eval_common.cuh"
+#include "q4_fp64.cuh"
+
+namespace cem {
+
+namespace {
+
+__device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl) {
+  return (bh - ah) + (bl - al);
+}
+
+// Own FP32 strain of intact element e at its edge k (Eq. 4 at the edge point).
+__device__ void own_strain32(const DevState &d, const U32x2 &U, int e, int k, float eps[3]) {
+  const Geo &g = d.g;
+  float xh[4], xl[4], yh[4], yl[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 q = U.u[elem_node(g, e, a)];
+    xh[a] = q.x; xl[a] = q.y; yh[a] = q.z; yl[a] = q.w;
+  }
+  const float rx = g.rxf, ry = g.ryf, hx2 = 0.5f * rx, hy2 = 0.5f * ry;
+  float au = df_diff(xh[0], xl[0], xh[1], xl[1]), bu = df_diff(xh[3], xl[3], xh[2], xl[2]);
+  float cu = df_diff(xh[0], xl[0], xh[3], xl[3]), eu = df_diff(xh[1], xl[1], xh[2], xl[2]);
+  float av = df_diff(yh[0], yl[0], yh[1], yl[1]), bv = df_diff(yh[3], yl[3], yh[2], yl[2]);
+  float cv = df_diff(yh[0], yl[0], yh[3], yl[3]), ev = df_diff(yh[1], yl[1], yh[2], yl[2]);
+  switch (k) {
+    case 0: eps[0] = rx * au; eps[1] = hy2 * (cv + ev); eps[2] = hy2 * (cu + eu) + rx * av; break;
+    case 1: eps[0] = hx2 * (au + bu); eps[1] = ry * ev; eps[2] = ry * eu + hx2 * (av + bv); break;
+    case 2: eps[0] = rx * bu; eps[1] = hy2 * (cv + ev); eps[2] = hy2 * (cu + eu) + rx * bv; break;
+    default: eps[0] = hx2 * (au + bu); eps[1] = ry * cv; eps[2] = ry * cu + hx2 * (av + bv); break;
+  }
+}
+
+__device__ void used_stress32(const DevState &d, const U32x2 &U, int e, int k, float s[3]) {
+  float e1[3];
+  own_strain32(d, U, e, k, e1);
+  int f = elem_neighbor(d.g, e, k);
+  if (estatus(d, f) == ST_INTACT) {
+    float e2[3];
+    own_strain32(d, U, f, (k + 2) & 3, e2);
+    for (int c = 0; c < 3; ++c) e1[c] = 0.5f * (e1[c] + e2[c]);
+  }
+  const Mat &m = d.mat;
+  s[0] = m.D11f * e1[0] + m.D12f * e1[1];
+  s[1] = m.D12f * e1[0] + m.D11f * e1[1];
+  s[2] = m.D33f * e1[2];
+}
+
+__device__ void eval_G32(const DevState &d, const U32x2 &U, int e, int k0, float G[4]) {
+  const Geo &g = d.g;
+  int N1 = elem_node(g, e, k0), N2 = elem_node(g, e, (k0 + 1) & 3);
+  const float DX = g.DXf[k0], DY = g.DYf[k0];
+  const float4 P1 = U.u[N1], P2 = U.u[N2];
+  float dux = df_diff(P1.x, P1.y, P2.x, P2.y);
+  float duy = df_diff(P1.z, P1.w, P2.z, P2.w);
+  // |x_N2 - x_N1|^2 - |X_N2 - X_N1|^2 without cancellation
+  float stretch = 2.f * (DX * dux + DY * duy) + (dux * dux + duy * duy);
+  float H = stretch > 0.f ? 1.f : 0.f;
+  float ddx = dux * H, ddy = duy * H;
+  for (int k = 0; k < 4; ++k) {
+    if (k == k0) { G[k] = -1.f; continue; }
+    const float nx = g.nxf[k0][k], ny = g.nyf[k0][k];
+    float s[3];
+    used_stress32(d, U, e, k, s);
+    float tx = s[0] * nx + s[2] * ny;
+    float ty = s[2] * nx + s[1] * ny;
+    G[k] = 0.5f * (ddx * tx + ddy * ty);
+  }
+}
+
+// FP64 re-evaluation, out of line so that its FP64 instructions are not
+// predicated into every surface point's FP32 evaluation.
+__device__ __noinline__ void recheck64(const DevState &d, const float4 *u, int e, int k0,
+                                       double *G) {
+  const U32x2 U{u};
+  eval_G64(d, U, e, k0, G);
+}
+
+__global__ void k_eval32(DevState d, int cur) {
+  const int n = d.cnt->n_S;
+  const U32x2 U{d.u4[cur]};
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    int i = base + threadIdx.x;
+    bool has = false;
+    int key = 0, edge = 0, kk = -1;
+    double Gk = 0.0;
+    if (i < n) {
+      edge = d.S[i];
+      if (edge >= 0) {
+        key = d.S_info[i];
+        int e = key >> 2, k0 = key & 3;
+        if (d.mat.scope != 2 || is_tip_edge(d, e, k0)) {
+          float G32[4];
+          eval_G32(d, U, e, k0, G32);
+          float gc = d.gc[e];
+          bool near = false;
+          for (int k = 0; k < 4; ++k)
+            if (k != k0 && fabsf(G32[k] / gc - 1.f) < 1e-3f) near = true;
+          double G[4];
+          if (near) {
+            recheck64(d, d.u4[cur], e, k0, G);  // FP64 re-check near the threshold
+          } else {
+            for (int k = 0; k < 4; ++k) G[k] = (double)G32[k];
+          }
+          double gm = -1.0;
+          for (int k = 0; k < 4; ++k) gm = fmax(gm, G[k]);
+          d.S_G[i] = gm;
+          kk = q4_rule(d, e, k0, G);
+          if (kk >= 0) { has = true; Gk = G[kk]; }
+        }
+      }
+    }
+    append_proposal(d, has, key, edge, kk, Gk);
+  }
+}
+
+int grid_for(int n, int block, int maxb) {
+  int b = (n + block - 1) / block;
+  return b < 1 ? 1 : (b > maxb ? maxb : b);
+}
+
+}  // namespace
+
+cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st) {
+  k_eval32<<<grid_for(d.list_cap, 256, 1216), 256, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+}  // namespace cem

@@ -1,13 +1,598 @@
-// step_fp32.cu -- FP32-mixed explicit step (placeholder until the FP32 tile
-// kernel lands: the FP64 path is the parity reference).
+// step_fp32.cu -- FP32-mixed explicit step: FP32 element arithmetic,
+// displacement kept as a compensated pair of floats (hi + lo, ~48-bit
+// mantissa) and advanced with an error-free two-sum, FP64 energy sums.
+//
+// k_main32 is the bandwidth-bound kernel of the method: one pass over every
+// real node per step.  For each node it forms the strains at the midpoints of
+// the 12 edges around it from node differences (Eq. 4 at the edge points):
+// along an edge the tangential derivative is the difference of its two
+// nodes, across it the normal derivative of each side is the sum of that
+// side's two across-edge differences; with two intact neighbours the two
+// sides are averaged (Eqs. 1-2 with equal areas), otherwise each intact side
+// keeps its own strain; sigma = D eps per side (zero for split or missing
+// sides); the node force is B^T sigma A/4 (Eq. 6) summed over those edges
+// and sides, plus the forces of split-element pieces; then the
+// central-difference update.
 #include <cuda_runtime.h>
 
 #include "cem_internal.h"
+#include "q4_fp64.cuh"
 
 namespace cem {
 
-cudaError_t launch_step_fp32(const DevState &, int, bool, bool, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+
+__device__ __forceinline__ void block_sum2(double a, double b, double *out) {
+  __shared__ double wa[32], wb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;  // 1-D or 2-D blocks
+  int lane = t & 31, w = t >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) { wa[w] = a; wb[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    a = lane < nw ? wa[lane] : 0.0;
+    b = lane < nw ? wb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { out[0] = a; out[1] = b; }
+  }
+}
+
+// (hi, lo) += x with an error-free transformation (Knuth two-sum) and
+// renormalisation, so the pair keeps about 48 significant bits.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
+  float s = __fadd_rn(hi, x);
+  float bb = __fsub_rn(s, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  float l = __fadd_rn(lo, err);
+  float h = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h, s));
+  hi = h;
+}
+
+__device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl) {
+  return (bh - ah) + (bl - al);  // (b - a)
+}
+
+struct Stress3 {
+  float xx, yy, xy;
+};
+
+__device__ __forceinline__ Stress3 stress32(const Mat &m, float exx, float eyy, float gxy) {
+  Stress3 s;
+  s.xx = fmaf(m.D11f, exx, m.D12f * eyy);
+  s.yy = fmaf(m.D12f, exx, m.D11f * eyy);
+  s.xy = m.D33f * gxy;
+  return s;
+}
+
+
+// Central-difference update of a node that carries a load, a prescribed
+// velocity, or whose kinetic energy is recorded this step.  Kept out of line:
+// if it were inlined, the compiler could predicate its FP64 instructions into
+// the update of every node, and on this GPU the FP64 pipe is 1/64 of FP32.
+__device__ __noinline__ double update_special(const DevState &d, int N, int cur, int first,
+                                              float fx, float fy, float4 U, float2 vo, float minv,
+                                              int nf, int energy) {
+  const int idx = d.cnt->step - d.cnt->lam_base;
+  const double lamN = d.lamN[idx], lamD = d.lamD[idx];
+  const float dt = d.mat.dtf;
+  const float dtv = first ? 0.5f * dt : dt;
+  float fex = 0.f, fey = 0.f;
+  if (nf & NF_LOADED) {
+    fex = (float)(lamN * d.Fx[N]);
+    fey = (float)(lamN * d.Fy[N]);
+  }
+  const float vxo = vo.x, vyo = vo.y;
+  float vxn = fmaf(dtv, (fex - fx) * minv, vxo);
+  float vyn = fmaf(dtv, (fey - fy) * minv, vyo);
+  if (nf & NF_DIRX) vxn = (float)(lamD * d.Vx[N]);
+  if (nf & NF_DIRY) vyn = (float)(lamD * d.Vy[N]);
+  const double vbx = first ? (double)vxo : 0.5 * ((double)vxo + (double)vxn);
+  const double vby = first ? (double)vyo : 0.5 * ((double)vyo + (double)vyn);
+  const double dtd = d.mat.dt;
+  if (nf & NF_LOADED) d.Wn[N] += dtd * ((double)fex * vbx + (double)fey * vby);
+  if (nf & (NF_DIRX | NF_DIRY)) {
+    const double m = d.m[N];
+    const double dv = first ? 0.5 * dtd : dtd;
+    const double Rx = m * (((double)vxn - (double)vxo) / dv) - ((double)fex - (double)fx);
+    const double Ry = m * (((double)vyn - (double)vyo) / dv) - ((double)fey - (double)fy);
+    double w = 0.0;
+    if (nf & NF_DIRX) w += Rx * vbx;
+    if (nf & NF_DIRY) w += Ry * vby;
+    d.Wd[N] += dtd * w;
+  }
+  d.v2[N] = make_float2(vxn, vyn);
+  df_add(U.x, U.y, dt * vxn);
+  df_add(U.z, U.w, dt * vyn);
+  d.u4[cur ^ 1][N] = U;
+  return energy ? 0.5 * (d.m[N] * (vbx * vbx + vby * vby)) : 0.0;
+}
+
+// Update of a node without loads: FP32 only.
+__device__ __forceinline__ void update_plain(const DevState &d, int N, int cur, float dtv,
+                                             float dt, float fx, float fy, float4 U, float2 vo,
+                                             float minv) {
+  const float vxn = fmaf(dtv, -fx * minv, vo.x);
+  const float vyn = fmaf(dtv, -fy * minv, vo.y);
+  d.v2[N] = make_float2(vxn, vyn);
+  df_add(U.x, U.y, dt * vxn);
+  df_add(U.z, U.w, dt * vyn);
+  d.u4[cur ^ 1][N] = U;
+}
+
+// ------------------------------------------------------------------ pieces
+// Piece forces of split elements: own strain at each edge point, FP32.
+__global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
+  const int n = 2 * d.cnt->n_ck;
+  const Geo &g = d.g;
+  const float rx = g.rxf, ry = g.ryf;
+  const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
+  double se = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int c = t >> 1, p = t & 1;
+    float xh[4], xl[4], yh[4], yl[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float4 U = d.u4[cur][d.ck_node[c * 8 + p * 4 + a]];
+      xh[a] = U.x; xl[a] = U.y; yh[a] = U.z; yl[a] = U.w;
+    }
+    // edge differences: a = u1-u0 (bottom), b = u2-u3 (top), c = u3-u0 (left), e = u2-u1 (right)
+    float au = df_diff(xh[0], xl[0], xh[1], xl[1]), bu = df_diff(xh[3], xl[3], xh[2], xl[2]);
+    float cu = df_diff(xh[0], xl[0], xh[3], xl[3]), eu = df_diff(xh[1], xl[1], xh[2], xl[2]);
+    float av = df_diff(yh[0], yl[0], yh[1], yl[1]), bv = df_diff(yh[3], yl[3], yh[2], yl[2]);
+    float cv = df_diff(yh[0], yl[0], yh[3], yl[3]), ev = df_diff(yh[1], yl[1], yh[2], yl[2]);
+    // strains at edge points 0..3 (Eq. 4 at the edge midpoints)
+    float ex[4], ey[4], gx[4];
+    ex[0] = rx * au;          ey[0] = hy2 * (cv + ev); gx[0] = fmaf(hy2, cu + eu, rx * av);
+    ex[1] = hx2 * (au + bu);  ey[1] = ry * ev;         gx[1] = fmaf(ry, eu, hx2 * (av + bv));
+    ex[2] = rx * bu;          ey[2] = hy2 * (cv + ev); gx[2] = fmaf(hy2, cu + eu, rx * bv);
+    ex[3] = hx2 * (au + bu);  ey[3] = ry * cv;         gx[3] = fmaf(ry, cu, hx2 * (av + bv));
+    Stress3 s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] = stress32(d.mat, ex[k], ey[k], gx[k]);
+    const float qA = (float)(d.ck_Ap[c * 2 + p] * 0.25);
+    float f[8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float cx = dxn(k, a) * hx2, cy = dyn(k, a) * hy2;
+        sx = fmaf(cx, s[k].xx, fmaf(cy, s[k].xy, sx));
+        sy = fmaf(cy, s[k].yy, fmaf(cx, s[k].xy, sy));
+      }
+      f[2 * a] = sx * qA;
+      f[2 * a + 1] = sy * qA;
+    }
+    float *o = d.pff + c * 16 + p * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o[q] = f[q];
+    if (energy) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        acc += 0.5 * (double)qA *
+               ((double)ex[k] * s[k].xx + (double)ey[k] * s[k].yy + (double)gx[k] * s[k].xy);
+      se += acc;
+    }
+  }
+  if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + blockIdx.x));
+}
+
+// -------------------------------------------------------------- main tile
+// One CTA of 32 x 8 threads owns a tile of TX x TY = 32 x 16 real nodes
+// (two rows per thread).  Shared memory holds, with a two-node halo:
+//   sU  displacement pairs (x.hi, x.lo, y.hi, y.lo) of nodes [i0-2, i0+TX+1] x [j0-2, j0+TY+1]
+//   sD  node differences D(i,j) = (ux(i+1,j)-ux(i,j), uy(i+1,j)-uy(i,j),
+//       ux(i,j+1)-ux(i,j), uy(i,j+1)-uy(i,j)) of nodes [i0-2, i0+TX] x [j0-2, j0+TY],
+//       formed from the pairs as (hi_b - hi_a) + (lo_b - lo_a)
+//   sH  stresses (xx, yy, xy) used by the element above (.a) and below (.b)
+//       horizontal edges h(i,j), i in [i0-1, i0+TX), j in [j0-1, j0+TY]
+//   sV  the same for the element right (.a) and left (.b) of vertical edges
+//       v(i,j), i in [i0-1, i0+TX], j in [j0-1, j0+TY)
+// sU is dead once sD is formed and shares its storage with sH.
+constexpr int TX = 32, TY = 16, BX = 32, BY = 8;
+constexpr int UXn = TX + 4, UYn = TY + 4;
+constexpr int DXn = TX + 3, DYn = TY + 3;
+constexpr int EXn = TX + 3, EYn = TY + 3;
+constexpr int HXn = TX + 1, HYn = TY + 2;
+constexpr int VXn = TX + 2, VYn = TY + 1;
+
+struct SmemA {
+  float4 U[UYn][UXn];
+};
+struct SmemB {
+  float4 Ha[HYn][HXn], Hb[HYn][HXn];
+};
+union SmemMain {
+  SmemA a;
+  SmemB b;
+};
+struct SmemFastH {  // intact tiles: one stress per edge, as (xx, xy) and (yy, xy)
+  float2 P[HYn][HXn], Q[HYn][HXn];
+};
+struct SmemFastV {
+  float2 P[VYn][VXn], Q[VYn][VXn];
+};
+union SmemV {
+  struct {
+    float4 a[VYn][VXn], b[VYn][VXn];
+  } gen;
+  SmemFastV fast;
+};
+struct SmemTile {  // > 48 KB: dynamic shared memory
+  union {
+    SmemMain ab;
+    SmemFastH fh;
+  } u1;
+  float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
+  SmemV v;
+  uint8_t st[EYn][EXn];
+};
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int first) {
+  extern __shared__ float4 smem_dyn[];
+  SmemTile &T = *reinterpret_cast<SmemTile *>(smem_dyn);
+  float4 (*sU)[UXn] = T.u1.ab.a.U;
+  float4 (*sHa)[HXn] = T.u1.ab.b.Ha, (*sHb)[HXn] = T.u1.ab.b.Hb;
+  float2 (*fHP)[HXn] = T.u1.fh.P, (*fHQ)[HXn] = T.u1.fh.Q;
+  float2 (*sDx)[DXn] = T.Dx, (*sDy)[DXn] = T.Dy;
+  float4 (*sVa)[VXn] = T.v.gen.a, (*sVb)[VXn] = T.v.gen.b;
+  float2 (*fVP)[VXn] = T.v.fast.P, (*fVQ)[VXn] = T.v.fast.Q;
+  uint8_t (*sst)[EXn] = T.st;
+
+  const Geo &g = d.g;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int stride = g.nx + 1;
+  const float4 *__restrict__ u4 = d.u4[cur];
+
+  // own nodes (i, j0+ty) and (i, j0+ty+8): issue their loads first
+  const int i = i0 + tx;
+  float2 own_v[2];
+  float own_mi[2];
+  int own_nf[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + ty + r * BY;
+    if (i <= g.nx && j <= g.ny) {
+      const int N = j * stride + i;
+      own_v[r] = d.v2[N];
+      own_mi[r] = d.minvf[N];
+      own_nf[r] = d.nflag[N];
+    } else {
+      own_v[r] = make_float2(0.f, 0.f);
+      own_mi[r] = 0.f;
+      own_nf[r] = 0;
+    }
+  }
+  // stage displacements and element states: every load is issued before
+  // any shared store, so the block waits for one memory latency, not six
+  const int tid0 = tx + ty * BX;
+  constexpr int NU = (UXn * UYn + BX * BY - 1) / (BX * BY);
+  constexpr int NE = (EXn * EYn + BX * BY - 1) / (BX * BY);
+  float4 ureg[NU];
+  int sreg[NE];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int q = tid0 + k * BX * BY;
+    const int ly = q / UXn, lx = q - ly * UXn;
+    const int jj = j0 - 2 + ly, ii = i0 - 2 + lx;
+    ureg[k] = (q < UXn * UYn && jj >= 0 && jj <= g.ny && ii >= 0 && ii <= g.nx)
+                  ? u4[jj * stride + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    const int q = tid0 + k * BX * BY;
+    const int ly = q / EXn, lx = q - ly * EXn;
+    const int jj = j0 - 2 + ly, ii = i0 - 2 + lx;
+    sreg[k] = (q < EXn * EYn && jj >= 0 && jj < g.ny && ii >= 0 && ii < g.nx)
+                  ? (int)d.estate[jj * g.nx + ii] : (int)ST_OUT;
+  }
+  int any_open = 0;  // some element of the halo is not intact
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int q = tid0 + k * BX * BY;
+    if (q < UXn * UYn) sU[q / UXn][q % UXn] = ureg[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    const int q = tid0 + k * BX * BY;
+    if (q < EXn * EYn) {
+      sst[q / EXn][q % EXn] = (uint8_t)sreg[k];
+      any_open |= sreg[k] != ST_INTACT;
+    }
+  }
+  const bool general = __syncthreads_or(any_open) != 0;
+  // own displacement pairs, needed by the update after sU is overwritten
+  float4 own_u[2];
+  own_u[0] = sU[ty + 2][tx + 2];
+  own_u[1] = sU[ty + BY + 2][tx + 2];
+  const int tid = tx + ty * BX;
+  constexpr int NTH = BX * BY;
+  for (int q = tid; q < DXn * DYn; q += NTH) {
+    const int ly = q / DXn, lx = q - ly * DXn;
+    const float4 U0 = sU[ly][lx], Ux = sU[ly][lx + 1], Uy = sU[ly + 1][lx];
+    sDx[ly][lx] = make_float2((Ux.x - U0.x) + (Ux.y - U0.y), (Ux.z - U0.z) + (Ux.w - U0.w));
+    sDy[ly][lx] = make_float2((Uy.x - U0.x) + (Uy.y - U0.y), (Uy.z - U0.z) + (Uy.w - U0.w));
+  }
+  __syncthreads();
+
+  const Mat &m = d.mat;
+  const float rx = g.rxf, ry = g.ryf;
+  const float hx2 = 0.5f * rx, hy2 = 0.5f * ry, hx4 = 0.25f * rx, hy4 = 0.25f * ry;
+  const float qA = g.qAf;
+  double se = 0.0;
+
+  if (!general) {
+    // every element around the tile is intact: smoothed strain on every
+    // edge, one stress per edge (stored in the .a arrays)
+    for (int q = tid; q < HXn * HYn; q += NTH) {
+      {
+        const int ly = q / HXn, lx = q - ly * HXn;
+        const float2 X0 = sDx[ly + 1][lx + 1];
+        const float2 Y0 = sDy[ly + 1][lx + 1], Y1 = sDy[ly + 1][lx + 2];
+        const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];
+        const float exx = rx * X0.x;
+        const float eyy = hy4 * ((Y0.y + Y1.y) + (Z0.y + Z1.y));
+        const float gxy = fmaf(hy4, (Y0.x + Y1.x) + (Z0.x + Z1.x), rx * X0.y);
+        const Stress3 st = stress32(m, exx, eyy, gxy);
+        fHP[ly][lx] = make_float2(st.xx, st.xy);
+        fHQ[ly][lx] = make_float2(st.yy, st.xy);
+        if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
+          se += (double)qA * (double)(exx * st.xx + eyy * st.yy + gxy * st.xy);
+      }
+    }
+    for (int q = tid; q < VXn * VYn; q += NTH) {
+      {
+        const int ly = q / VXn, lx = q - ly * VXn;
+        const float2 Y0 = sDy[ly + 1][lx + 1];
+        const float2 X0 = sDx[ly + 1][lx + 1], X1 = sDx[ly + 2][lx + 1];
+        const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];
+        const float exx = hx4 * ((X0.x + X1.x) + (W0.x + W1.x));
+        const float eyy = ry * Y0.y;
+        const float gxy = fmaf(hx4, (X0.y + X1.y) + (W0.y + W1.y), ry * Y0.x);
+        const Stress3 st = stress32(m, exx, eyy, gxy);
+        fVP[ly][lx] = make_float2(st.xx, st.xy);
+        fVQ[ly][lx] = make_float2(st.yy, st.xy);
+        if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
+          se += (double)qA * (double)(exx * st.xx + eyy * st.yy + gxy * st.xy);
+      }
+    }
+  } else {
+    // horizontal edges h(ii,jj), ii = i0-1+lx, jj = j0-1+ly:
+    // below element (ii, jj-1) = sst[ly][lx+1], above (ii, jj) = sst[ly+1][lx+1]
+    for (int q = tid; q < HXn * HYn; q += NTH) {
+      {
+        const int ly = q / HXn, lx = q - ly * HXn;
+        const int sb = sst[ly][lx + 1], sa = sst[ly + 1][lx + 1];
+        float4 Ta = make_float4(0.f, 0.f, 0.f, 0.f), Tb = Ta;
+        if (sa == ST_INTACT || sb == ST_INTACT) {
+          const float2 X0 = sDx[ly + 1][lx + 1];                        // (ii,jj)
+          const float2 Y0 = sDy[ly + 1][lx + 1], Y1 = sDy[ly + 1][lx + 2];  // (ii,jj), (ii+1,jj)
+          const float exx = rx * X0.x, cdv = rx * X0.y;
+          float eyy, gxy, w;
+          if (sa == ST_INTACT && sb == ST_INTACT) {
+            const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];      // (ii,jj-1), (ii+1,jj-1)
+            eyy = hy4 * ((Y0.y + Y1.y) + (Z0.y + Z1.y));
+            gxy = fmaf(hy4, (Y0.x + Y1.x) + (Z0.x + Z1.x), cdv);
+            w = 1.f;
+          } else if (sa == ST_INTACT) {
+            eyy = hy2 * (Y0.y + Y1.y);
+            gxy = fmaf(hy2, Y0.x + Y1.x, cdv);
+            w = 0.5f;
+          } else {
+            const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];
+            eyy = hy2 * (Z0.y + Z1.y);
+            gxy = fmaf(hy2, Z0.x + Z1.x, cdv);
+            w = 0.5f;
+          }
+          const Stress3 s = stress32(m, exx, eyy, gxy);
+          const float4 S = make_float4(s.xx, s.yy, s.xy, 0.f);
+          if (sa == ST_INTACT) Ta = S;
+          if (sb == ST_INTACT) Tb = S;
+          if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
+            se += (double)qA * (double)(w * (exx * s.xx + eyy * s.yy + gxy * s.xy));
+        }
+        sHa[ly][lx] = Ta;
+        sHb[ly][lx] = Tb;
+      }
+    }
+    // vertical edges v(ii,jj), ii = i0-1+lx, jj = j0-1+ly:
+    // left element (ii-1, jj) = sst[ly+1][lx], right (ii, jj) = sst[ly+1][lx+1]
+    for (int q = tid; q < VXn * VYn; q += NTH) {
+      {
+        const int ly = q / VXn, lx = q - ly * VXn;
+        const int sl = sst[ly + 1][lx], sr = sst[ly + 1][lx + 1];
+        float4 Ta = make_float4(0.f, 0.f, 0.f, 0.f), Tb = Ta;
+        if (sl == ST_INTACT || sr == ST_INTACT) {
+          const float2 Y0 = sDy[ly + 1][lx + 1];                        // (ii,jj)
+          const float2 X0 = sDx[ly + 1][lx + 1], X1 = sDx[ly + 2][lx + 1];  // (ii,jj), (ii,jj+1)
+          const float eyy = ry * Y0.y, cdu = ry * Y0.x;
+          float exx, gxy, w;
+          if (sl == ST_INTACT && sr == ST_INTACT) {
+            const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];      // (ii-1,jj), (ii-1,jj+1)
+            exx = hx4 * ((X0.x + X1.x) + (W0.x + W1.x));
+            gxy = fmaf(hx4, (X0.y + X1.y) + (W0.y + W1.y), cdu);
+            w = 1.f;
+          } else if (sr == ST_INTACT) {
+            exx = hx2 * (X0.x + X1.x);
+            gxy = fmaf(hx2, X0.y + X1.y, cdu);
+            w = 0.5f;
+          } else {
+            const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];
+            exx = hx2 * (W0.x + W1.x);
+            gxy = fmaf(hx2, W0.y + W1.y, cdu);
+            w = 0.5f;
+          }
+          const Stress3 s = stress32(m, exx, eyy, gxy);
+          const float4 S = make_float4(s.xx, s.yy, s.xy, 0.f);
+          if (sr == ST_INTACT) Ta = S;
+          if (sl == ST_INTACT) Tb = S;
+          if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
+            se += (double)qA * (double)(w * (exx * s.xx + eyy * s.yy + gxy * s.xy));
+        }
+        sVa[ly][lx] = Ta;
+        sVb[ly][lx] = Tb;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+
+  double ke = 0.0;
+  const float dt = m.dtf;
+  const float dtv = first ? 0.5f * dt : dt;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + ty + r * BY;
+    if (i > g.nx || j > g.ny) continue;
+    // edge arrays: edge (i', j') at [j' - (j0-1)][i' - (i0-1)]
+    const int ci = tx + 1, cj = ty + r * BY + 1;
+    float fx, fy;
+    if (!general) {
+      // one stress per edge: the two sides of every edge carry the same sigma
+      // (xx, xy) of h(i-1,j), h(i,j); (yy, xy) of the rows above / below
+      const float2 H1 = fHP[cj][ci - 1], H2 = fHP[cj][ci];
+      const float2 Hu0 = fHQ[cj + 1][ci - 1], Hu1 = fHQ[cj + 1][ci];
+      const float2 Hd0 = fHQ[cj - 1][ci - 1], Hd1 = fHQ[cj - 1][ci];
+      // (yy, xy) of v(i,j-1), v(i,j); (xx, xy) of the columns left / right
+      const float2 V1 = fVQ[cj - 1][ci], V2 = fVQ[cj][ci];
+      const float2 Vl0 = fVP[cj - 1][ci - 1], Vl1 = fVP[cj][ci - 1];
+      const float2 Vr0 = fVP[cj - 1][ci + 1], Vr1 = fVP[cj][ci + 1];
+      fx = (2.f * rx) * (H1.x - H2.x) + hy2 * ((Hd0.y + Hd1.y) - (Hu0.y + Hu1.y)) +
+           (2.f * ry) * (V1.y - V2.y) + hx2 * ((Vl0.x + Vl1.x) - (Vr0.x + Vr1.x));
+      fy = (2.f * rx) * (H1.y - H2.y) + hy2 * ((Hd0.x + Hd1.x) - (Hu0.x + Hu1.x)) +
+           (2.f * ry) * (V1.x - V2.x) + hx2 * ((Vl0.y + Vl1.y) - (Vr0.y + Vr1.y));
+    } else {
+          const float4 A1 = sHa[cj][ci - 1], B1 = sHb[cj][ci - 1];  // h(i-1, j): N right node
+      const float4 A2 = sHa[cj][ci], B2 = sHb[cj][ci];          // h(i, j):   N left node
+      fx = rx * ((A1.x + B1.x) - (A2.x + B2.x)) + hy2 * ((B1.z - A1.z) + (B2.z - A2.z));
+      fy = rx * ((A1.z + B1.z) - (A2.z + B2.z)) + hy2 * ((B1.y - A1.y) + (B2.y - A2.y));
+      // h(i-1, j+1), h(i, j+1): N is a lower node of their below element;
+      // h(i-1, j-1), h(i, j-1): N is an upper node of their above element
+      const float4 Bu0 = sHb[cj + 1][ci - 1], Bu1 = sHb[cj + 1][ci];
+      const float4 Ad0 = sHa[cj - 1][ci - 1], Ad1 = sHa[cj - 1][ci];
+      fx += hy2 * ((Ad0.z + Ad1.z) - (Bu0.z + Bu1.z));
+      fy += hy2 * ((Ad0.y + Ad1.y) - (Bu0.y + Bu1.y));
+      // v(i, j-1): N top node; v(i, j): N bottom node (a = right, b = left)
+      const float4 R1 = sVa[cj - 1][ci], L1 = sVb[cj - 1][ci];
+      const float4 R2 = sVa[cj][ci], L2 = sVb[cj][ci];
+      fx += ry * ((R1.z + L1.z) - (R2.z + L2.z)) + hx2 * ((L1.x - R1.x) + (L2.x - R2.x));
+      fy += ry * ((R1.y + L1.y) - (R2.y + L2.y)) + hx2 * ((L1.z - R1.z) + (L2.z - R2.z));
+      // v(i-1, j-1), v(i-1, j): N is a right node of their right element;
+      // v(i+1, j-1), v(i+1, j): N is a left node of their left element
+      const float4 Rl0 = sVa[cj - 1][ci - 1], Rl1 = sVa[cj][ci - 1];
+      const float4 Lr0 = sVb[cj - 1][ci + 1], Lr1 = sVb[cj][ci + 1];
+      fx += hx2 * ((Rl0.x + Rl1.x) - (Lr0.x + Lr1.x));
+      fy += hx2 * ((Rl0.z + Rl1.z) - (Lr0.z + Lr1.z));
+    }
+    fx *= qA;
+    fy *= qA;
+    // pieces of split neighbours in increasing element id; element states at
+    // [ej - (j0-2)][ei - (i0-2)]
+    const int ey0 = j - 1 - (j0 - 2), ex0 = i - 1 - (i0 - 2);
+    const int s00 = sst[ey0][ex0], s01 = sst[ey0][ex0 + 1], s10 = sst[ey0 + 1][ex0],
+              s11 = sst[ey0 + 1][ex0 + 1];
+    if (general && ((s00 | s01 | s10 | s11) & ST_CRACKED)) {
+      const int sts[4] = {s00, s01, s10, s11};
+      const int dei[4] = {-1, 0, -1, 0}, dej[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (sts[k] == ST_CRACKED) {
+          const int c = d.crack_of[(j + dej[k]) * g.nx + i + dei[k]];
+          const int side = (d.ck_info[c] >> (4 + la[k])) & 1;
+          fx += d.pff[c * 16 + side * 8 + 2 * la[k]];
+          fy += d.pff[c * 16 + side * 8 + 2 * la[k] + 1];
+        }
+      }
+    }
+    const int N = j * stride + i;
+    if (ENERGY || own_nf[r])
+      ke += update_special(d, N, cur, first, fx, fy, own_u[r], own_v[r], own_mi[r], own_nf[r],
+                           ENERGY ? 1 : 0);
+    else
+      update_plain(d, N, cur, dtv, dt, fx, fy, own_u[r], own_v[r], own_mi[r]);
+  }
+  if (ENERGY) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum2(ke, se, d.e_part + 2 * b);
+  }
+}
+
+// ---------------------------------------------------------------- phantoms
+__global__ void k_phantom32(DevState d, int cur, int first, int energy, int part_off) {
+  const int n = d.cnt->n_ph;
+  double ke = 0.0;
+  const float dt = d.mat.dtf;
+  const float dtv = first ? 0.5f * dt : dt;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int N = d.g.nn + t;
+    int nu = d.ph_nuser[t];
+    float fx = 0.f, fy = 0.f;
+    for (int q = 0; q < nu; ++q) {
+      int u = d.ph_users[t * 4 + q];
+      int e = u >> 3, p = (u >> 2) & 1, a = u & 3;
+      int c = d.crack_of[e];
+      fx += d.pff[c * 16 + p * 8 + 2 * a];
+      fy += d.pff[c * 16 + p * 8 + 2 * a + 1];
+    }
+    if (energy)
+      ke += update_special(d, N, cur, first, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N], 0, 1);
+    else
+      update_plain(d, N, cur, dtv, dt, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N]);
+  }
+  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + blockIdx.x));
+}
+
+int grid_for(int n, int block, int maxb) {
+  int b = (n + block - 1) / block;
+  return b < 1 ? 1 : (b > maxb ? maxb : b);
+}
+
+}  // namespace
+
+cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st);
+
+int tiles_fp32(const DevState &d) {
+  return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + TY - 1) / TY);
+}
+
+int energy_parts_fp32(const DevState &d) { return tiles_fp32(d) + 2 * 304 + 8; }
+
+cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
+                             cudaStream_t st, cudaEvent_t *marks) {
+  const dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
+  const dim3 block(BX, BY);
+  const int tiles = grid.x * grid.y;  // energy partials of the tiles come first
+  int gp = grid_for(2 * d.ck_cap, 256, 304);
+  int gph = grid_for(d.ph_cap, 256, 304);
+  k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+  if (marks) cudaEventRecord(marks[0], st);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_main32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SmemTile));
+    cudaFuncSetAttribute(k_main32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SmemTile));
+    attr = true;
+  }
+  if (energy) k_main32<true><<<grid, block, sizeof(SmemTile), st>>>(d, cur, first ? 1 : 0);
+  else k_main32<false><<<grid, block, sizeof(SmemTile), st>>>(d, cur, first ? 1 : 0);
+  if (marks) cudaEventRecord(marks[1], st);
+  k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+  if (marks) cudaEventRecord(marks[2], st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_eval32(d, cur, st);
 }
 
 }  // namespace cem

@@ -16,6 +16,7 @@
 
 #include "cem_internal.h"
 #include "q4_fp64.cuh"
+#include "eval_common.cuh"
 
 namespace cem {
 
@@ -317,125 +318,9 @@ __global__ void k_phantom64(DevState d, int cur, int first, int energy, int part
   if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + blockIdx.x));
 }
 
-// ------------------------------------------------------------- evaluation
-
-// Own strain of intact element e at its edge k from the global displacement.
-__device__ __forceinline__ void own_strain(const DevState &d, const double *ux, const double *uy,
-                                           int e, int k, double eps[3]) {
-  double u[4], v[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int N = elem_node(d.g, e, a);
-    u[a] = ux[N];
-    v[a] = uy[N];
-  }
-  strain64_rt(d.g, k, u, v, eps);
-}
-
-// Stress used by intact element e at its edge k (smoothed with an intact
-// neighbour, own strain otherwise) -- identical arithmetic to k_main64.
-__device__ void used_stress(const DevState &d, const double *ux, const double *uy, int e, int k,
-                            double s[3]) {
-  double eo[3];
-  own_strain(d, ux, uy, e, k, eo);
-  int f = elem_neighbor(d.g, e, k);
-  if (estatus(d, f) == ST_INTACT) {
-    double ef[3], ep[3];
-    own_strain(d, ux, uy, f, (k + 2) & 3, ef);
-    const double *p1 = e < f ? eo : ef;
-    const double *p2 = e < f ? ef : eo;
-    for (int c = 0; c < 3; ++c) ep[c] = 0.5 * p1[c] + 0.5 * p2[c];
-    stress64(d.mat, ep, s);
-  } else {
-    stress64(d.mat, eo, s);
-  }
-}
-
-__device__ bool is_tip_edge(const DevState &d, int e, int k0) {
-  int f = elem_neighbor(d.g, e, k0);
-  if (estatus(d, f) != ST_CRACKED) return false;
-  int info = d.ck_info[d.crack_of[f]];
-  int kf = (k0 + 2) & 3;
-  return (info & 3) == kf || ((info >> 2) & 3) == kf;
-}
-
-// Energy release rates of the three candidate paths of surface point
-// (e, k0) -- Sec. 2.2 -- in FP64 from the displacement ux/uy.
-__device__ void eval_G64(const DevState &d, const double *ux, const double *uy, int e, int k0,
-                         double G[4]) {
-  const Geo &g = d.g;
-  int N1 = elem_node(g, e, k0), N2 = elem_node(g, e, (k0 + 1) & 3);
-  double DX = (xi_n((k0 + 1) & 3) - xi_n(k0)) * (0.5 * g.hx);
-  double DY = (eta_n((k0 + 1) & 3) - eta_n(k0)) * (0.5 * g.hy);
-  double dux = ux[N2] - ux[N1];
-  double duy = uy[N2] - uy[N1];
-  double dx = DX + dux, dy = DY + duy;
-  double cur2 = dx * dx + dy * dy;
-  double ref2 = DX * DX + DY * DY;
-  double H = cur2 > ref2 ? 1.0 : 0.0;
-  double ddx = dux * H, ddy = duy * H;
-  double x0 = (xi_g(k0) + 1.0) * (0.5 * g.hx), y0 = (eta_g(k0) + 1.0) * (0.5 * g.hy);
-  for (int k = 0; k < 4; ++k) {
-    if (k == k0) { G[k] = -1.0; continue; }
-    double xk = (xi_g(k) + 1.0) * (0.5 * g.hx), yk = (eta_g(k) + 1.0) * (0.5 * g.hy);
-    double sx = xk - x0, sy = yk - y0;
-    double rx = -sy, ry = sx;
-    if (rx * DX + ry * DY < 0.0) { rx = -rx; ry = -ry; }
-    double len = sqrt(sx * sx + sy * sy);
-    double nx = rx / len, ny = ry / len;
-    double s[3];
-    used_stress(d, ux, uy, e, k, s);
-    double tx = s[0] * nx + s[2] * ny;
-    double ty = s[2] * nx + s[1] * ny;
-    G[k] = 0.5 * (ddx * tx + ddy * ty);
-  }
-}
-
-// Q4 cracking conditions with the split ratio gamma (Sec. 2.2).
-__device__ int q4_rule(const DevState &d, int e, int k0, const double G[4]) {
-  double gc = (double)d.gc[e];
-  int best = -1, ncand = 0;
-  for (int k = 0; k < 4; ++k) {
-    if (k == k0 || !(G[k] > gc)) continue;
-    ++ncand;
-    if (best < 0 || G[k] > G[best]) best = k;
-  }
-  if (ncand == 0) return -1;
-  for (int q = 0; q < 4; ++q) {
-    if (q == k0 || q == best || !(G[q] > gc)) continue;
-    bool ok = d.mat.gamma_mode == 0 ? (G[best] > d.mat.gamma * (G[best] - G[q]))
-                                    : (G[best] > d.mat.gamma * G[q]);
-    if (!ok) return -1;
-  }
-  return best;
-}
-
-// Warp-aggregated append of a proposal (ballot + popc).
-__device__ __forceinline__ void append_proposal(const DevState &d, bool has, int key, int edge,
-                                                int k, double G) {
-  unsigned mask = __ballot_sync(0xffffffffu, has);
-  if (!mask) return;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(mask) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(&d.cnt->n_prop, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (has) {
-    int pos = base + __popc(mask & ((1u << lane) - 1));
-    if (pos < d.prop_cap) {
-      d.pr_key[pos] = key;
-      d.pr_edge[pos] = edge;
-      d.pr_k[pos] = k;
-      d.pr_G[pos] = G;
-    } else {
-      atomicOr(&d.cnt->status, STAT_CAPACITY);
-    }
-  }
-}
-
 __global__ void k_eval64(DevState d, int cur) {
   const int n = d.cnt->n_S;
-  const double *ux = d.ux[cur], *uy = d.uy[cur];
+  const U64 U{d.ux[cur], d.uy[cur]};
   // whole warps iterate together so that the ballot sees every lane
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     int i = base + threadIdx.x;
@@ -449,7 +334,7 @@ __global__ void k_eval64(DevState d, int cur) {
         int e = key >> 2, k0 = key & 3;
         if (d.mat.scope != 2 || is_tip_edge(d, e, k0)) {
           double G[4];
-          eval_G64(d, ux, uy, e, k0, G);
+          eval_G64(d, U, e, k0, G);
           double gm = -1.0;
           for (int k = 0; k < 4; ++k) gm = fmax(gm, G[k]);
           d.S_G[i] = gm;
@@ -486,7 +371,10 @@ int grid_for(int n, int block, int maxb) {
 
 }  // namespace
 
+int energy_parts_fp32(const DevState &d);
+
 int energy_parts_needed(const DevState &d) {
+  if (d.precision == 1) return energy_parts_fp32(d);
   int tiles = ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + TY - 1) / TY);
   return tiles + 2 * 304 + 8;
 }
@@ -497,14 +385,17 @@ cudaError_t launch_init_masses(const DevState &d, cudaStream_t st) {
 }
 
 cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t *marks) {
   dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
   int tiles = grid.x * grid.y;
   int gp = grid_for(2 * d.ck_cap, 256, 304);
   int gph = grid_for(d.ph_cap, 256, 304);
   k_pieces64<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+  if (marks) cudaEventRecord(marks[0], st);
   k_main64<<<grid, NT, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0);
+  if (marks) cudaEventRecord(marks[1], st);
   k_phantom64<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+  if (marks) cudaEventRecord(marks[2], st);
   k_eval64<<<grid_for(d.list_cap, 256, 1216), 256, 0, st>>>(d, cur);
   return cudaGetLastError();
 }

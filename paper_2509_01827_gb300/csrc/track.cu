@@ -31,6 +31,7 @@ namespace {
 
 constexpr int TB = 1024;           // threads of the tracking CTA
 constexpr int SORT_CAP = 8192;     // proposals per step (power of two)
+constexpr int WB = TB / 8;         // winners split per batch (eight threads each)
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of v over the block; returns the prefix, *total = sum.
@@ -100,165 +101,55 @@ __device__ void set_mass(const DevState &d, int N, double m) {
   if (d.precision == 1) d.minvf[N] = (float)mi;
 }
 
-struct SplitPlan {
-  int e, ka, kb;
-  int side[4];
-  int n4[4];
-  int reuse[4];  // phantom reused for local node a, or -1
-  double alpha[2];
-};
-
-__device__ void plan_split(const DevState &d, int e, int ka, int kb, SplitPlan &sp) {
+// Phantom of local node a of element e that the split (entry ka, exit kb)
+// reuses: the one held by the cracked neighbour across a cut edge of e that
+// contains the node, if that edge is cut in the neighbour too (first such
+// edge in increasing local edge index); -1 when a new phantom is needed.
+__device__ int reuse_lookup(const DevState &d, int e, int ka, int kb, int a) {
   const Geo &g = d.g;
-  sp.e = e; sp.ka = ka; sp.kb = kb;
-  double pax = xi_g(ka), pay = eta_g(ka), pbx = xi_g(kb), pby = eta_g(kb);
-  for (int a = 0; a < 4; ++a) {
-    double cross = (pbx - pax) * (eta_n(a) - pay) - (pby - pay) * (xi_n(a) - pax);
-    sp.side[a] = cross > 0.0 ? 0 : 1;
-    sp.n4[a] = elem_node(g, e, a);
+  const int k1 = (a + 3) & 3, k2 = a;
+  const int kk[2] = {k1 < k2 ? k1 : k2, k1 < k2 ? k2 : k1};
+  const int N = elem_node(g, e, a);
+  for (int q = 0; q < 2; ++q) {
+    const int k = kk[q];
+    if (k != ka && k != kb) continue;
+    const int f = elem_neighbor(g, e, k);
+    if (estatus(d, f) != ST_CRACKED) continue;
+    const int cf = d.crack_of[f];
+    const int inf = d.ck_info[cf];
+    const int kf = (k + 2) & 3;
+    if ((inf & 3) != kf && ((inf >> 2) & 3) != kf) continue;
+    int af = -1;
+    for (int b = 0; b < 4; ++b)
+      if (elem_node(g, f, b) == N) af = b;
+    const int sf = (inf >> (4 + af)) & 1;
+    return d.ck_node[cf * 8 + (1 - sf) * 4 + af];
   }
-  // shoelace area fractions in natural coordinates (reference square area 4)
+  return -1;
+}
+
+// Area fractions of the two pieces by the shoelace formula in natural
+// coordinates (the reference square has area 4).
+__device__ void area_fractions(int ka, int kb, const int side[4], double alpha[2]) {
   for (int p = 0; p < 2; ++p) {
     double px[6], py[6];
     int nv = 0;
     for (int w = 0; w < 8; ++w) {
       if ((w & 1) == 0) {
-        int a = w >> 1;
-        if (sp.side[a] == p) { px[nv] = xi_n(a); py[nv] = eta_n(a); ++nv; }
+        const int a = w >> 1;
+        if (side[a] == p) { px[nv] = xi_n(a); py[nv] = eta_n(a); ++nv; }
       } else {
-        int k = w >> 1;
+        const int k = w >> 1;
         if (k == ka || k == kb) { px[nv] = xi_g(k); py[nv] = eta_g(k); ++nv; }
       }
     }
     double twice = 0.0;
     for (int v = 0; v < nv; ++v) {
-      int w = (v + 1) % nv;
+      const int w = (v + 1) % nv;
       twice = twice + (px[v] * py[w] - px[w] * py[v]);
     }
-    sp.alpha[p] = fabs(twice) * 0.5 / 4.0;
+    alpha[p] = fabs(twice) * 0.5 / 4.0;
   }
-  // phantoms to reuse from a cracked neighbour across a shared cut edge
-  for (int a = 0; a < 4; ++a) {
-    sp.reuse[a] = -1;
-    int k1 = (a + 3) & 3, k2 = a;
-    int kk[2] = {k1 < k2 ? k1 : k2, k1 < k2 ? k2 : k1};
-    for (int q = 0; q < 2 && sp.reuse[a] < 0; ++q) {
-      int k = kk[q];
-      if (k != ka && k != kb) continue;
-      int f = elem_neighbor(g, e, k);
-      if (estatus(d, f) != ST_CRACKED) continue;
-      int cf = d.crack_of[f];
-      int inf = d.ck_info[cf];
-      int kf = (k + 2) & 3;
-      if ((inf & 3) != kf && ((inf >> 2) & 3) != kf) continue;
-      int af = -1;
-      for (int b = 0; b < 4; ++b)
-        if (elem_node(g, f, b) == sp.n4[a]) af = b;
-      int sf = (inf >> (4 + af)) & 1;
-      sp.reuse[a] = d.ck_node[cf * 8 + (1 - sf) * 4 + af];
-    }
-  }
-}
-
-__device__ int count_new(const SplitPlan &sp) {
-  int c = 0;
-  for (int a = 0; a < 4; ++a) c += sp.reuse[a] < 0;
-  return c;
-}
-
-// Writes the split of one winner (crack slot c, first new phantom id ph0).
-__device__ bool apply_split(const DevState &d, const SplitPlan &sp, int c, int ph0, int cur_next,
-                            int step, bool precrack) {
-  const Geo &g = d.g;
-  const int e = sp.e;
-  int node[2][4];
-  double mold[4];
-  int nextp = ph0;
-  for (int a = 0; a < 4; ++a) {
-    node[sp.side[a]][a] = sp.n4[a];
-    int p = 1 - sp.side[a];
-    int P = sp.reuse[a];
-    if (P < 0) {
-      P = nextp++;
-      int t = P - g.nn, N = sp.n4[a];
-      d.ph_owner[t] = N;
-      d.ph_creator[t] = e * 4 + a;
-      d.ph_nuser[t] = 0;
-      d.Wn[P] = 0.0;
-      d.Wd[P] = 0.0;
-      if (d.precision == 1) {
-        d.uxh[cur_next][P] = d.uxh[cur_next][N]; d.uxl[cur_next][P] = d.uxl[cur_next][N];
-        d.uyh[cur_next][P] = d.uyh[cur_next][N]; d.uyl[cur_next][P] = d.uyl[cur_next][N];
-        d.vxf[P] = d.vxf[N]; d.vyf[P] = d.vyf[N];
-      } else {
-        d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
-        d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
-      }
-      mold[a] = -1.0;
-    } else {
-      mold[a] = d.m[P];
-    }
-    node[p][a] = P;
-  }
-  int info = sp.ka | (sp.kb << 2);
-  for (int a = 0; a < 4; ++a) info |= sp.side[a] << (4 + a);
-  d.ck_elem[c] = e;
-  d.ck_info[c] = info;
-  for (int p = 0; p < 2; ++p)
-    for (int a = 0; a < 4; ++a) d.ck_node[c * 8 + p * 4 + a] = node[p][a];
-  d.ck_Ap[c * 2] = sp.alpha[0] * g.A;
-  d.ck_Ap[c * 2 + 1] = sp.alpha[1] * g.A;
-  d.ck_step[c] = precrack ? -1 : step;
-  if (precrack) {
-    d.ck_ud[c] = 0.0;
-  } else {
-    double xa = (xi_g(sp.ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(sp.ka) + 1.0) * (0.5 * g.hy);
-    double xb = (xi_g(sp.kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(sp.kb) + 1.0) * (0.5 * g.hy);
-    double sx = xb - xa, sy = yb - ya;
-    double L = sqrt(sx * sx + sy * sy);
-    d.ck_ud[c] = (double)d.gc[e] * L;
-  }
-  d.crack_of[e] = c;
-  d.estate[e] = ST_CRACKED;
-  // users of the phantoms, kept sorted by element id
-  bool ok = true;
-  for (int a = 0; a < 4; ++a) {
-    int p = 1 - sp.side[a];
-    int t = node[p][a] - g.nn;
-    int nu = d.ph_nuser[t];
-    if (nu >= 4) { ok = false; continue; }
-    int q = nu;
-    int code = (e << 3) | (p << 2) | a;
-    while (q > 0 && (d.ph_users[t * 4 + q - 1] >> 3) > e) {
-      d.ph_users[t * 4 + q] = d.ph_users[t * 4 + q - 1];
-      --q;
-    }
-    d.ph_users[t * 4 + q] = code;
-    d.ph_nuser[t] = nu + 1;
-  }
-  // masses touched by the split
-  for (int a = 0; a < 4; ++a) set_mass(d, sp.n4[a], mass_real(d, sp.n4[a]));
-  for (int a = 0; a < 4; ++a) {
-    int p = 1 - sp.side[a];
-    int P = node[p][a];
-    double mnew = mass_phantom(d, P);
-    if (mold[a] >= 0.0) {
-      // momentum-conserving merge of the mass moved from the real node
-      double dm = d.mat.rho * (sp.alpha[p] * g.A) * 0.25;
-      int N = sp.n4[a];
-      if (d.precision == 1) {
-        double vx = ((mold[a] * (double)d.vxf[P]) + dm * (double)d.vxf[N]) / mnew;
-        double vy = ((mold[a] * (double)d.vyf[P]) + dm * (double)d.vyf[N]) / mnew;
-        d.vxf[P] = (float)vx;
-        d.vyf[P] = (float)vy;
-      } else {
-        d.vx[P] = (mold[a] * d.vx[P] + dm * d.vx[N]) / mnew;
-        d.vy[P] = (mold[a] * d.vy[P] + dm * d.vy[N]) / mnew;
-      }
-    }
-    set_mass(d, P, mnew);
-  }
-  return ok;
 }
 
 // Sorted proposals live in shared memory as (key << 32 | index).
@@ -430,69 +321,188 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
     const int nwin = s_nwin;
     const int step = cnt->step;
 
-    // ---- split winners in increasing element id, 1024 at a time
-    for (int base = 0; base < nwin; base += TB) {
-      int w = base + tid;
-      bool act = w < nwin && !s_stop;
-      SplitPlan sp;
-      int nnew = 0;
-      if (act) {
-        int i = swin[w];
-        int idx = (int)(sk[i] & 0xffffffffu);
-        int key = (int)(sk[i] >> 32);
-        plan_split(d, key >> 2, key & 3, d.pr_k[idx], sp);
-        nnew = count_new(sp);
+    // ---- split winners in increasing element id, WB at a time with eight
+    //      threads per winner (lanes 0-3: local nodes, 4-7: their phantoms),
+    //      so that each phase's chain of dependent loads stays short
+    __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_n4[WB][4], b_reuse[WB][4];
+    __shared__ int b_node[WB][2][4], b_c[WB], b_ph0[WB];
+    __shared__ double b_alpha[WB][2], b_mold[WB][4];
+    __shared__ int s_fits;
+    const int lane = tid & 7, wl = tid >> 3;  // winner slot in the batch
+    for (int base = 0; base < nwin; base += WB) {
+      const int nb = nwin - base < WB ? nwin - base : WB;
+      const bool act = wl < nb && !s_stop;
+      // phase 1: plan
+      if (act && lane == 0) {
+        const int i = swin[base + wl];
+        const int idx = (int)(sk[i] & 0xffffffffu);
+        const int key = (int)(sk[i] >> 32);
+        b_e[wl] = key >> 2;
+        b_ka[wl] = key & 3;
+        b_kb[wl] = d.pr_k[idx];
       }
+      __syncthreads();
+      if (act && lane < 4) {
+        const int e = b_e[wl], ka = b_ka[wl], kb = b_kb[wl], a = lane;
+        const double pax = xi_g(ka), pay = eta_g(ka), pbx = xi_g(kb), pby = eta_g(kb);
+        const double cross = (pbx - pax) * (eta_n(a) - pay) - (pby - pay) * (xi_n(a) - pax);
+        b_side[wl][a] = cross > 0.0 ? 0 : 1;
+        b_n4[wl][a] = elem_node(g, e, a);
+        b_reuse[wl][a] = reuse_lookup(d, e, ka, kb, a);
+      }
+      __syncthreads();
+      if (act && lane == 4) {
+        int side[4];
+        for (int a = 0; a < 4; ++a) side[a] = b_side[wl][a];
+        area_fractions(b_ka[wl], b_kb[wl], side, b_alpha[wl]);
+      }
+      // phase 2: crack slots and phantom ids in winner order
+      int nnew = 0;
+      if (act && lane == 0)
+        for (int a = 0; a < 4; ++a) nnew += b_reuse[wl][a] < 0;
       int tot_new;
-      int pre_new = block_exscan(act ? nnew : 0, &tot_new);
-      int nact = nwin - base < TB ? nwin - base : TB;
-      bool fits = !s_stop && s_nph + tot_new <= d.ph_cap && s_nck + nact <= d.ck_cap;
-      bool ok = true;
-      if (act && fits)
-        ok = apply_split(d, sp, s_nck + (w - base), g.nn + s_nph + pre_new, cur_next, step,
-                         mode == TRACK_PRECRACK);
-      if (act && !ok) atomicOr(&cnt->status, STAT_CAPACITY);
-      // surface list: appends and tombstones
-      int napp = 0;
-      int app_edge[4], app_info[4];
-      if (act && fits) {
-        for (int k = 0; k < 4; ++k) {
-          int ed = elem_edge(g, sp.e, k);
-          int f = elem_neighbor(g, sp.e, k);
-          if (estatus(d, f) == ST_INTACT) {
-            app_edge[napp] = ed;
-            app_info[napp] = f * 4 + ((k + 2) & 3);
-            ++napp;
+      const int pre_new = block_exscan(nnew, &tot_new);
+      if (tid == 0)
+        s_fits = !s_stop && s_nph + tot_new <= d.ph_cap && s_nck + nb <= d.ck_cap;
+      if (act && lane == 0) {
+        b_c[wl] = s_nck + wl;
+        b_ph0[wl] = g.nn + s_nph + pre_new;
+      }
+      __syncthreads();
+      const bool go = act && s_fits;
+      // phase 3: phantoms (new ones copy the real node's state) and the record
+      if (go && lane < 4) {
+        const int a = lane, sd = b_side[wl][a], N = b_n4[wl][a];
+        b_node[wl][sd][a] = N;
+        int P = b_reuse[wl][a];
+        if (P < 0) {
+          int rank = 0;
+          for (int q = 0; q < a; ++q) rank += b_reuse[wl][q] < 0;
+          P = b_ph0[wl] + rank;
+          const int t = P - g.nn;
+          d.ph_owner[t] = N;
+          d.ph_creator[t] = b_e[wl] * 4 + a;
+          d.ph_nuser[t] = 0;
+          d.Wn[P] = 0.0;
+          d.Wd[P] = 0.0;
+          if (d.precision == 1) {
+            d.u4[cur_next][P] = d.u4[cur_next][N];
+            d.v2[P] = d.v2[N];
           } else {
-            int pos = d.spos[ed];
-            if (pos >= 0) {
-              d.S[pos] = -1;
-              d.spos[ed] = -1;
-              atomicAdd(&s_dead, 1);
-            }
+            d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
+            d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
+          }
+          b_mold[wl][a] = -1.0;
+        } else {
+          b_mold[wl][a] = d.m[P];
+        }
+        b_node[wl][1 - sd][a] = P;
+      }
+      if (go && lane == 4) {
+        const int e = b_e[wl], c = b_c[wl], ka = b_ka[wl], kb = b_kb[wl];
+        int info = ka | (kb << 2);
+        for (int a = 0; a < 4; ++a) info |= b_side[wl][a] << (4 + a);
+        d.ck_elem[c] = e;
+        d.ck_info[c] = info;
+        d.ck_Ap[c * 2] = b_alpha[wl][0] * g.A;
+        d.ck_Ap[c * 2 + 1] = b_alpha[wl][1] * g.A;
+        d.ck_step[c] = mode == TRACK_PRECRACK ? -1 : step;
+        if (mode == TRACK_PRECRACK) {
+          d.ck_ud[c] = 0.0;
+        } else {
+          const double xa = (xi_g(ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(ka) + 1.0) * (0.5 * g.hy);
+          const double xb = (xi_g(kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(kb) + 1.0) * (0.5 * g.hy);
+          const double sx = xb - xa, sy = yb - ya;
+          const double L = sqrt(sx * sx + sy * sy);
+          d.ck_ud[c] = (double)d.gc[e] * L;
+        }
+        d.crack_of[e] = c;
+        d.estate[e] = ST_CRACKED;
+      }
+      __syncthreads();
+      // phase 4: node lists of the pieces and the phantoms' users
+      if (go && lane < 4) {
+        const int a = lane, c = b_c[wl], e = b_e[wl];
+        d.ck_node[c * 8 + a] = b_node[wl][0][a];
+        d.ck_node[c * 8 + 4 + a] = b_node[wl][1][a];
+        const int p = 1 - b_side[wl][a];
+        const int t = b_node[wl][p][a] - g.nn;
+        const int nu = d.ph_nuser[t];
+        if (nu >= 4) {
+          atomicOr(&cnt->status, STAT_CAPACITY);
+        } else {
+          int q = nu;
+          while (q > 0 && (d.ph_users[t * 4 + q - 1] >> 3) > e) {
+            d.ph_users[t * 4 + q] = d.ph_users[t * 4 + q - 1];
+            --q;
+          }
+          d.ph_users[t * 4 + q] = (e << 3) | (p << 2) | a;
+          d.ph_nuser[t] = nu + 1;
+        }
+      }
+      __syncthreads();
+      // phase 5: masses of the four real nodes (lanes 0-3) and of their
+      // phantoms (lanes 4-7, momentum-conserving merge into shared ones)
+      if (go && lane < 4) {
+        const int N = b_n4[wl][lane];
+        set_mass(d, N, mass_real(d, N));
+      } else if (go) {
+        const int a = lane - 4, p = 1 - b_side[wl][a];
+        const int P = b_node[wl][p][a];
+        const double mnew = mass_phantom(d, P);
+        const double mold = b_mold[wl][a];
+        if (mold >= 0.0) {
+          const double dm = d.mat.rho * (b_alpha[wl][p] * g.A) * 0.25;
+          const int N = b_n4[wl][a];
+          if (d.precision == 1) {
+            const float2 vp = d.v2[P], vn = d.v2[N];
+            const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
+            const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
+            d.v2[P] = make_float2((float)vx, (float)vy);
+          } else {
+            d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
+            d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
+          }
+        }
+        set_mass(d, P, mnew);
+      }
+      // phase 6: surface list -- lanes 0-3 look at edge k = lane
+      int app = 0, app_edge = 0, app_info = 0;
+      if (go && lane < 4) {
+        const int e = b_e[wl], k = lane;
+        const int ed = elem_edge(g, e, k);
+        const int f = elem_neighbor(g, e, k);
+        if (estatus(d, f) == ST_INTACT) {
+          app = 1;
+          app_edge = ed;
+          app_info = f * 4 + ((k + 2) & 3);
+        } else {
+          const int pos = d.spos[ed];
+          if (pos >= 0) {
+            d.S[pos] = -1;
+            d.spos[ed] = -1;
+            atomicAdd(&s_dead, 1);
           }
         }
       }
       int tot_app;
-      int pre_app = block_exscan(napp, &tot_app);
-      bool lfits = s_nS + tot_app <= d.list_cap;
-      if (act && fits && lfits) {
-        for (int q = 0; q < napp; ++q) {
-          int dst = s_nS + pre_app + q;
-          d.S[dst] = app_edge[q];
-          d.S_info[dst] = app_info[q];
-          d.S_G[dst] = 0.0;
-          d.spos[app_edge[q]] = dst;
-        }
+      const int pre_app = block_exscan(app, &tot_app);
+      const bool lfits = s_nS + tot_app <= d.list_cap;
+      if (app && lfits) {
+        const int dst = s_nS + pre_app;
+        d.S[dst] = app_edge;
+        d.S_info[dst] = app_info;
+        d.S_G[dst] = 0.0;
+        d.spos[app_edge] = dst;
       }
       __syncthreads();
       if (tid == 0) {
-        if (!fits || !lfits) {
+        if (!s_fits || !lfits) {
           s_stop = 1;
           atomicOr(&cnt->status, STAT_CAPACITY);
         } else {
           s_nph += tot_new;
-          s_nck += nact;
+          s_nck += nb;
           s_nS += tot_app;
         }
       }
@@ -515,6 +525,7 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
   }
   __syncthreads();
   if (tid == 0) {
+    cnt->n_prop_last = cnt->n_prop;
     cnt->n_prop = 0;
     if (mode == TRACK_STEP) cnt->step = cnt->step + 1;
   }
