@@ -49,6 +49,7 @@ struct cem_handle {
   Counters *h_cnt = nullptr;  // pinned
   double *h_lam = nullptr;    // pinned staging of the load-factor table
   bool own_stream = false;
+  StepStreams ss{};           // fork/join streams and events of one step
   long launches = 0;           // kernels enqueued (graph replays count their nodes)
   void *scratch = nullptr;     // reusable device scratch for getters
   size_t scratch_bytes = 0;
@@ -199,8 +200,8 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
   cudaError_t e;
   if (energy && (e = launch_energy_pre(d, h->st)) != cudaSuccess) return e;
   if (marks) cudaEventRecord(marks[0], h->st);
-  if (d.precision == CEM_FP32_MIXED) e = launch_step_fp32(d, cur, first, energy, h->st, marks ? marks + 1 : nullptr);
-  else e = launch_step_fp64(d, cur, first, energy, h->st, marks ? marks + 1 : nullptr);
+  if (d.precision == CEM_FP32_MIXED) e = launch_step_fp32(d, cur, first, energy, h->ss, marks ? marks + 1 : nullptr);
+  else e = launch_step_fp64(d, cur, first, energy, h->ss, marks ? marks + 1 : nullptr);
   if (e != cudaSuccess) return e;
   if (marks) cudaEventRecord(marks[4], h->st);
   if (energy && (e = launch_energy_post(d, energy_parts_needed(d), h->st)) != cudaSuccess) return e;
@@ -298,6 +299,12 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
     ce = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
     h->own_stream = ce == cudaSuccess;
   }
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->ss.aux1, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->ss.aux2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.join1, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.join2, cudaEventDisableTiming);
+  h->ss.main = h->st;
   if (ce != cudaSuccess) {
     delete h;
     return fail(nullptr, CEM_ERR_CUDA, "device set-up: %s", cudaGetErrorString(ce));
@@ -413,6 +420,11 @@ void cem_mesh_destroy(cem_handle *h) {
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->h_lam) cudaFreeHost(h->h_lam);
+  if (h->ss.aux1) cudaStreamDestroy(h->ss.aux1);
+  if (h->ss.aux2) cudaStreamDestroy(h->ss.aux2);
+  if (h->ss.fork) cudaEventDestroy(h->ss.fork);
+  if (h->ss.join1) cudaEventDestroy(h->ss.join1);
+  if (h->ss.join2) cudaEventDestroy(h->ss.join2);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
 }

@@ -117,14 +117,21 @@ struct DevState {
 // ------------------------------------------------------------------ launch
 // All launchers enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
-// The step launchers enqueue four kernels (pieces, tile update of real nodes,
-// phantoms, surface evaluation); when marks is given they record marks[0..2]
-// after the first three of them (profiling).
+// Streams of one step.  The piece forces run first on `main`; then the tile
+// update of real nodes (main), the phantom update (aux1, needs only the piece
+// forces) and the surface evaluation (aux2, reads only the previous state)
+// run concurrently and join back into `main`.  With marks (profiling) the
+// kernels run one after the other on `main` and marks[0..2] are recorded
+// after the first three.
+struct StepStreams {
+  cudaStream_t main, aux1, aux2;
+  cudaEvent_t fork, join1, join2;
+};
 constexpr int kStepKernels = 4;
 cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st, cudaEvent_t *marks = nullptr);
+                             const StepStreams &ss, cudaEvent_t *marks = nullptr);
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st, cudaEvent_t *marks = nullptr);
+                             const StepStreams &ss, cudaEvent_t *marks = nullptr);
 cudaError_t launch_track(const DevState &d, int cur_next, int mode, cudaStream_t st);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);

@@ -569,14 +569,12 @@ int tiles_fp32(const DevState &d) {
 int energy_parts_fp32(const DevState &d) { return tiles_fp32(d) + 2 * 304 + 8; }
 
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st, cudaEvent_t *marks) {
+                             const StepStreams &ss, cudaEvent_t *marks) {
   const dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
   const dim3 block(BX, BY);
   const int tiles = grid.x * grid.y;  // energy partials of the tiles come first
   int gp = grid_for(2 * d.ck_cap, 256, 304);
   int gph = grid_for(d.ph_cap, 256, 304);
-  k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
-  if (marks) cudaEventRecord(marks[0], st);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_main32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -585,14 +583,36 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
                          (int)sizeof(SmemTile));
     attr = true;
   }
-  if (energy) k_main32<true><<<grid, block, sizeof(SmemTile), st>>>(d, cur, first ? 1 : 0);
-  else k_main32<false><<<grid, block, sizeof(SmemTile), st>>>(d, cur, first ? 1 : 0);
-  if (marks) cudaEventRecord(marks[1], st);
-  k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
-  if (marks) cudaEventRecord(marks[2], st);
-  cudaError_t e = cudaGetLastError();
+  cudaStream_t st = ss.main;
+  auto main_kernel = [&](cudaStream_t s) {
+    if (energy) k_main32<true><<<grid, block, sizeof(SmemTile), s>>>(d, cur, first ? 1 : 0);
+    else k_main32<false><<<grid, block, sizeof(SmemTile), s>>>(d, cur, first ? 1 : 0);
+  };
+  if (marks) {
+    k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+    cudaEventRecord(marks[0], st);
+    main_kernel(st);
+    cudaEventRecord(marks[1], st);
+    k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+    cudaEventRecord(marks[2], st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_eval32(d, cur, st);
+  }
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  cudaError_t e = launch_eval32(d, cur, ss.aux2);
   if (e != cudaSuccess) return e;
-  return launch_eval32(d, cur, st);
+  k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+  main_kernel(st);
+  cudaEventRecord(ss.join1, ss.aux1);
+  cudaEventRecord(ss.join2, ss.aux2);
+  cudaStreamWaitEvent(st, ss.join1, 0);
+  cudaStreamWaitEvent(st, ss.join2, 0);
+  return cudaGetLastError();
 }
 
 }  // namespace cem

@@ -385,18 +385,35 @@ cudaError_t launch_init_masses(const DevState &d, cudaStream_t st) {
 }
 
 cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
-                             cudaStream_t st, cudaEvent_t *marks) {
+                             const StepStreams &ss, cudaEvent_t *marks) {
   dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
   int tiles = grid.x * grid.y;
   int gp = grid_for(2 * d.ck_cap, 256, 304);
   int gph = grid_for(d.ph_cap, 256, 304);
+  const int ge = grid_for(d.list_cap, 256, 1216);
+  cudaStream_t st = ss.main;
+  if (marks) {
+    k_pieces64<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+    cudaEventRecord(marks[0], st);
+    k_main64<<<grid, NT, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0);
+    cudaEventRecord(marks[1], st);
+    k_phantom64<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+    cudaEventRecord(marks[2], st);
+    k_eval64<<<ge, 256, 0, st>>>(d, cur);
+    return cudaGetLastError();
+  }
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  k_eval64<<<ge, 256, 0, ss.aux2>>>(d, cur);
   k_pieces64<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
-  if (marks) cudaEventRecord(marks[0], st);
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_phantom64<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
   k_main64<<<grid, NT, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0);
-  if (marks) cudaEventRecord(marks[1], st);
-  k_phantom64<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
-  if (marks) cudaEventRecord(marks[2], st);
-  k_eval64<<<grid_for(d.list_cap, 256, 1216), 256, 0, st>>>(d, cur);
+  cudaEventRecord(ss.join1, ss.aux1);
+  cudaEventRecord(ss.join2, ss.aux2);
+  cudaStreamWaitEvent(st, ss.join1, 0);
+  cudaStreamWaitEvent(st, ss.join2, 0);
   return cudaGetLastError();
 }
 
