@@ -215,11 +215,12 @@ cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out
 cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip,
                            int cap, int *n_out);
 
-/* Profiling: advances n steps like cem_step but with direct kernel launches
- * bracketed by CUDA events on the handle's stream, and returns device
- * milliseconds in ms[8]: [0] all n steps (first event to last), [1] piece
- * forces, [2] tile update of real nodes, [3] phantom update, [4] surface
- * evaluation, [5] tracking, [6] energy records, [7] number of kernels. */
+/* Profiling: advances n steps like cem_step but with direct kernel launches,
+ * one after the other, bracketed by CUDA events on the handle's stream, and
+ * returns device milliseconds in ms[9]: [0] all n steps (first event to
+ * last), [1] piece forces, [2] tile update of real nodes, [3] phantom
+ * update, [4] surface evaluation, [5] tracking selection, [6] energy
+ * records, [7] number of kernels, [8] split writes. */
 cem_status cem_profile_steps(cem_handle *h, int n, double *ms);
 
 /* Testing hook for the tracking bookkeeping: runs the selection and split

@@ -215,9 +215,9 @@ def cem_debug_apply_proposals(h, edge, elem, k, G):
 
 
 def cem_profile_steps(h, n):
-    ms = np.zeros(8)
+    ms = np.zeros(9)
     _chk(h, lib().cem_profile_steps(h, int(n), _p(ms, _dp)))
-    keys = ["total", "pieces", "main", "phantom", "eval", "track", "energy", "kernels"]
+    keys = ["total", "pieces", "main", "phantom", "eval", "select", "energy", "kernels", "apply"]
     return dict(zip(keys, ms.tolist()))
 
 

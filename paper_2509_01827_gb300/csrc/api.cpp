@@ -188,12 +188,12 @@ void drop_graphs(cem_handle *h) {
       if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
-int kernels_in_step(bool energy) { return kStepKernels + 1 + (energy ? 2 : 0); }
+int kernels_in_step(bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
 
 // Enqueues one explicit step (buffers cur -> cur^1) on the stream.  With
 // marks (profiling) events are recorded after the energy prologue, after
-// each step kernel, after the energy epilogue and after tracking:
-// marks[0..6].
+// each step kernel, after the energy epilogue, after the tracking selection
+// and after the split writes: marks[0..7].
 cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
                          cudaEvent_t *marks = nullptr) {
   const DevState &d = h->d;
@@ -205,9 +205,14 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
   if (e != cudaSuccess) return e;
   if (marks) cudaEventRecord(marks[4], h->st);
   if (energy && (e = launch_energy_post(d, energy_parts_needed(d), h->st)) != cudaSuccess) return e;
-  if (marks) cudaEventRecord(marks[5], h->st);
-  e = launch_track(d, cur ^ 1, TRACK_STEP, h->st);
-  if (marks) cudaEventRecord(marks[6], h->st);
+  if (marks) {
+    cudaEventRecord(marks[5], h->st);
+    e = launch_select(d, TRACK_STEP, h->st);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(marks[6], h->st);
+  }
+  e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st);
+  if (marks) cudaEventRecord(marks[7], h->st);
   return e;
 }
 
@@ -379,6 +384,10 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.S_G, (size_t)d.list_cap) && dalloc_n(h, d.spos, (size_t)d.g.ned) &&
        dalloc_n(h, d.pr_key, (size_t)d.prop_cap) && dalloc_n(h, d.pr_edge, (size_t)d.prop_cap) &&
        dalloc_n(h, d.pr_k, (size_t)d.prop_cap) && dalloc_n(h, d.pr_G, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.pl_e, (size_t)d.prop_cap) && dalloc_n(h, d.pl_info, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.pl_reuse, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_tomb, (size_t)d.prop_cap * 4) &&
+       dalloc_n(h, d.pl_c, (size_t)d.prop_cap) && dalloc_n(h, d.pl_ph0, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.pl_app0, (size_t)d.prop_cap) && dalloc_n(h, d.pl_alpha, (size_t)d.prop_cap * 2) &&
        dalloc_n(h, d.cnt, 1) && dalloc_n(h, d.lamN, (size_t)d.lam_cap) &&
        dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
   d.e_part_cap = energy_parts_needed(d);
@@ -490,7 +499,8 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
     CUDA_TRY(h, cudaMemcpyAsync(d.pr_k, &kb, 4, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(h, cudaMemcpyAsync(d.pr_G, &G, 8, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->n_prop, &one, 4, cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(h, launch_track(d, h->cur, TRACK_PRECRACK, h->st));
+    CUDA_TRY(h, launch_select(d, TRACK_PRECRACK, h->st));
+    CUDA_TRY(h, launch_apply(d, h->cur, TRACK_PRECRACK, h->st));
     CUDA_TRY(h, cudaStreamSynchronize(h->st));
   }
   CUDA_TRY(h, launch_build_surface(d, h->st));
@@ -631,10 +641,10 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
   if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
   if (n < 1 || n > h->d.lam_cap) return fail(h, CEM_ERR_ARG, "1 <= n <= %d", h->d.lam_cap);
   CUDA_TRY(h, cudaSetDevice(h->device));
-  for (int q = 0; q < 8; ++q) ms[q] = 0.0;
+  for (int q = 0; q < 9; ++q) ms[q] = 0.0;
   cem_status rc = upload_load_factors(h, n);
   if (rc != CEM_OK) return rc;
-  const int M = 8;  // events per step: start + 7 marks
+  const int M = 9;  // events per step: start + 8 marks
   std::vector<cudaEvent_t> ev((size_t)n * M);
   for (auto &e : ev) CUDA_TRY(h, cudaEventCreate(&e));
   long kernels = 0;
@@ -650,19 +660,20 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
   cudaError_t es = cudaStreamSynchronize(h->st);
   if (err == cudaSuccess && es == cudaSuccess) {
     float t;
-    cudaEventElapsedTime(&t, ev[0], ev[(size_t)(n - 1) * M + 7]);
+    cudaEventElapsedTime(&t, ev[0], ev[(size_t)(n - 1) * M + 8]);
     ms[0] = t;
     for (int q = 0; q < n; ++q) {
       cudaEvent_t *e = &ev[(size_t)q * M];
-      float a, b, c, dd, f, g, k;
+      float a, b, c, dd, f, g, k, w;
       cudaEventElapsedTime(&a, e[0], e[1]);  // energy prologue
       cudaEventElapsedTime(&b, e[1], e[2]);  // pieces
       cudaEventElapsedTime(&c, e[2], e[3]);  // tile update
       cudaEventElapsedTime(&dd, e[3], e[4]); // phantoms
       cudaEventElapsedTime(&f, e[4], e[5]);  // evaluation
       cudaEventElapsedTime(&g, e[5], e[6]);  // energy epilogue
-      cudaEventElapsedTime(&k, e[6], e[7]);  // tracking
-      ms[1] += b; ms[2] += c; ms[3] += dd; ms[4] += f; ms[5] += k; ms[6] += a + g;
+      cudaEventElapsedTime(&k, e[6], e[7]);  // tracking selection
+      cudaEventElapsedTime(&w, e[7], e[8]);  // split writes
+      ms[1] += b; ms[2] += c; ms[3] += dd; ms[4] += f; ms[5] += k; ms[6] += a + g; ms[8] += w;
     }
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -932,7 +943,8 @@ cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge, cons
   CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->n_prop, &n, 4, cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->pad[0], &zero, 4, cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  CUDA_TRY(h, launch_track(d, h->cur, TRACK_DEBUG, h->st));
+  CUDA_TRY(h, launch_select(d, TRACK_DEBUG, h->st));
+  CUDA_TRY(h, launch_apply(d, h->cur, TRACK_DEBUG, h->st));
   cem_status rc = sync_status(h);
   if (rc != CEM_OK) return rc;
   if (h->h_cnt->pad[0]) return fail(h, CEM_ERR_ARG, "a proposal is not a surface point of its element");

@@ -28,7 +28,9 @@ struct Counters {
   int n_rec;      // energy records written
   int n_win_last; // winners of the last step (diagnostic)
   int n_prop_last; // proposals of the last step (diagnostic)
-  int pad[5];
+  // planned by the selection kernel, committed by the apply kernel
+  int pend_nwin, pend_nph, pend_nck, pend_nS, pend_dead;
+  int pad[3];
 };
 
 struct Geo {
@@ -104,6 +106,16 @@ struct DevState {
   int *pr_k;
   double *pr_G;
 
+  // split plans of the current step [prop_cap], in increasing element id
+  int *pl_e;
+  int *pl_info;          // ka | kb << 2 | side(a) << (4+a) | append(k) << (8+k)
+  int *pl_reuse;         // [4] phantom reused for local node a, or -1
+  int *pl_tomb;          // [4] surface-list position to tombstone for edge k, or -1
+  int *pl_c;             // split-table slot
+  int *pl_ph0;           // first new phantom id
+  int *pl_app0;          // first surface-list position of its appended edges
+  double *pl_alpha;      // [2] piece area fractions
+
   Counters *cnt;
   double *lamN, *lamD;   // [lam_cap] load factors of steps lam_base + i
 
@@ -119,10 +131,11 @@ struct DevState {
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
 // Streams of one step.  The piece forces run first on `main`; then the tile
 // update of real nodes (main), the phantom update (aux1, needs only the piece
-// forces) and the surface evaluation (aux2, reads only the previous state)
-// run concurrently and join back into `main`.  With marks (profiling) the
-// kernels run one after the other on `main` and marks[0..2] are recorded
-// after the first three.
+// forces) and the surface evaluation followed by the tracking selection
+// (aux2, read only the previous state) run concurrently and join back into
+// `main`, where the split writes follow.  With marks (profiling) the four
+// step kernels run one after the other on `main`, marks[0..2] are recorded
+// after the first three, and the caller launches selection and writes.
 struct StepStreams {
   cudaStream_t main, aux1, aux2;
   cudaEvent_t fork, join1, join2;
@@ -132,7 +145,10 @@ cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy
                              const StepStreams &ss, cudaEvent_t *marks = nullptr);
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
                              const StepStreams &ss, cudaEvent_t *marks = nullptr);
-cudaError_t launch_track(const DevState &d, int cur_next, int mode, cudaStream_t st);
+// Tracking: selection and planning (one CTA; may run concurrently with the
+// node updates) then the split writes (many CTAs; after the node updates).
+cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st);
+cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);
 cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);

@@ -603,6 +603,8 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
   cudaError_t e = launch_eval32(d, cur, ss.aux2);
   if (e != cudaSuccess) return e;
+  e = launch_select(d, TRACK_STEP, ss.aux2);
+  if (e != cudaSuccess) return e;
   k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux1, ss.fork, 0);

@@ -405,6 +405,7 @@ cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
   k_eval64<<<ge, 256, 0, ss.aux2>>>(d, cur);
+  launch_select(d, TRACK_STEP, ss.aux2);
   k_pieces64<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux1, ss.fork, 0);

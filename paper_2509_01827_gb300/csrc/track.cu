@@ -2,23 +2,27 @@
 // (compiled with -fmad=false: the split's masses, momentum merge and
 // dissipated energy follow the FP64 expression order of the definition).
 //
-// k_track runs as ONE cooperative CTA per step.  It
-//   1. sorts the step's proposals by (ahead element, local edge) with a
-//      bitonic sort in shared memory (the warp-ballot append of k_eval is
-//      unordered; the sort makes everything after it deterministic);
-//   2. selects winners (Sec. 3): a proposal wins if its key (G, -edge id)
-//      is the strict maximum among proposals whose ahead elements share a
-//      node with its own (binary searches over the three neighbouring rows),
-//      or the single global maximum, or -- pre-cracks -- unconditionally;
-//   3. splits each winner (in increasing element id) along the segment
-//      between the midpoints of its entry and exit edges into two
-//      phantom-node pieces (crack patterns I and II, Fig. 2-3), sharing a
-//      phantom with the cracked neighbour across a cut edge, recomputes the
-//      lumped masses it touches, merges momentum into shared phantoms and
-//      records U_d = G_c * segment length;
-//   4. updates the device-side surface list: tombstones edges that lost their
-//      intact element, appends edges that gained one, and compacts the list
-//      with warp ballots when half of it is dead.
+// Each step's tracking is two kernels.  k_select (one CTA) runs on the
+// evaluation stream, concurrently with the node updates, and
+//   1. compacts the surface list with warp ballots when half of it is dead;
+//   2. sorts the step's proposals by (ahead element, local edge) with a
+//      bitonic sort in shared memory (the warp-ballot append of the
+//      evaluation is unordered; the sort makes everything after it
+//      deterministic);
+//   3. selects winners (Sec. 3): a proposal wins if its key (G, -edge id) is
+//      the strict maximum among proposals whose ahead elements share a node
+//      with its own (binary searches over the three neighbouring rows), or
+//      the single global maximum, or -- pre-cracks -- unconditionally;
+//   4. plans each winner's split (eight threads per winner): sides of the
+//      segment between the entry and exit edge midpoints (crack patterns I
+//      and II, Fig. 2-3), phantoms shared with a cracked neighbour across a
+//      cut edge, area fractions, split-table slot, phantom ids and
+//      surface-list positions by prefix sums in increasing element id.
+// k_apply (many CTAs, eight threads per winner) runs after the node updates:
+// it writes the split records, creates phantoms (copies of u^{n+1},
+// v^{n+1/2}), recomputes the lumped masses it touches, merges momentum into
+// shared phantoms, records U_d = G_c * segment length, tombstones and
+// appends surface-list entries, and commits the counters.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,34 +67,56 @@ __device__ int block_exscan(int v, int *total) {
   return pre;
 }
 
+// Lumped mass of real node N: every element around it (in increasing id)
+// gives rho A_p / 4 of the piece that holds N (the whole area if intact).
+// Loads are issued level by level for the four elements, the sum keeps the
+// canonical order.
 __device__ double mass_real(const DevState &d, int N) {
   const Geo &g = d.g;
-  int r = g.nx + 1, i = N % r, j = N / r;
+  const int r = g.nx + 1, i = N % r, j = N / r;
   const int di[4] = {-1, 0, -1, 0}, dj[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
-  double acc = 0.0;
+  int e[4], st[4], c[4];
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    int ei = i + di[q], ej = j + dj[q];
-    if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
-    int e = ej * g.nx + ei, st = d.estate[e];
-    if (st == ST_INTACT) {
-      acc = acc + d.mat.rho * g.A * 0.25;
-    } else if (st == ST_CRACKED) {
-      int c = d.crack_of[e];
-      int side = (d.ck_info[c] >> (4 + la[q])) & 1;
-      acc = acc + d.mat.rho * d.ck_Ap[c * 2 + side] * 0.25;
+    const int ei = i + di[q], ej = j + dj[q];
+    e[q] = (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) ? -1 : ej * g.nx + ei;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) st[q] = e[q] < 0 ? ST_OUT : (int)d.estate[e[q]];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c[q] = st[q] == ST_CRACKED ? d.crack_of[e[q]] : -1;
+  double Ap[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Ap[q] = g.A;
+    if (c[q] >= 0) {
+      const int side = (d.ck_info[c[q]] >> (4 + la[q])) & 1;
+      Ap[q] = d.ck_Ap[c[q] * 2 + side];
     }
   }
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (st[q] != ST_OUT) acc = acc + d.mat.rho * Ap[q] * 0.25;
   return acc;
 }
 
+// Lumped mass of phantom P: its users (sorted by element) give rho A_p / 4.
 __device__ double mass_phantom(const DevState &d, int P) {
-  int t = P - d.g.nn;
+  const int t = P - d.g.nn;
+  const int nu = d.ph_nuser[t];
+  int u[4], c[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = q < nu ? d.ph_users[t * 4 + q] : -1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c[q] = u[q] >= 0 ? d.crack_of[u[q] >> 3] : -1;
+  double Ap[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Ap[q] = c[q] >= 0 ? d.ck_Ap[c[q] * 2 + ((u[q] >> 2) & 1)] : 0.0;
   double acc = 0.0;
-  for (int q = 0; q < d.ph_nuser[t]; ++q) {
-    int u = d.ph_users[t * 4 + q];
-    int c = d.crack_of[u >> 3];
-    acc = acc + d.mat.rho * d.ck_Ap[c * 2 + ((u >> 2) & 1)] * 0.25;
-  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q < nu) acc = acc + d.mat.rho * Ap[q] * 0.25;
   return acc;
 }
 
@@ -203,14 +229,26 @@ __device__ void compact_surface(const DevState &d) {
   }
 }
 
-__global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode) {
+// Selection and planning (one CTA).  Reads the step's proposals and the
+// current crack state, never writes it: the node-update kernels may run
+// concurrently.  Produces, for each winner in increasing element id, its
+// split plan (sides, phantoms to reuse, area fractions, split-table slot,
+// first new phantom id, surface-list appends and tombstones) and the
+// counters the apply kernel commits.
+__global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
   extern __shared__ unsigned long long smem[];
   unsigned long long *sk = smem;                    // [SORT_CAP]
   int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP]
-  __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead;
+  __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done;
+  __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_reuse[WB][4], b_app[WB],
+      b_tomb[WB][4];
   Counters *cnt = d.cnt;
   const Geo &g = d.g;
   const int tid = threadIdx.x;
+  // stable compaction of the surface list when half of it is dead (the
+  // evaluation of this step has finished; nothing else reads the list now)
+  if (mode == TRACK_STEP && cnt->n_dead > 1024 && 2 * cnt->n_dead > cnt->n_S) compact_surface(d);
+  __syncthreads();
   if (tid == 0) {
     int n = cnt->n_prop;
     if (n > d.prop_cap) n = d.prop_cap;
@@ -221,6 +259,7 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
     s_nck = cnt->n_ck;
     s_nS = cnt->n_S;
     s_dead = 0;
+    s_done = 0;
   }
   __syncthreads();
   const int n = s_n;
@@ -259,7 +298,6 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
         __syncthreads();
       }
     }
-    // number of valid sorted entries
     __shared__ int s_valid;
     if (tid == 0) s_valid = 0;
     __syncthreads();
@@ -270,7 +308,6 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
 
     // ---- winners
     if (mode != TRACK_PRECRACK && d.mat.scope == 1) {
-      // global: the single largest (G, -edge)
       if (tid == 0) {
         int best = -1;
         for (int i = 0; i < nv; ++i) {
@@ -319,20 +356,12 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
       }
     }
     const int nwin = s_nwin;
-    const int step = cnt->step;
 
-    // ---- split winners in increasing element id, WB at a time with eight
-    //      threads per winner (lanes 0-3: local nodes, 4-7: their phantoms),
-    //      so that each phase's chain of dependent loads stays short
-    __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_n4[WB][4], b_reuse[WB][4];
-    __shared__ int b_node[WB][2][4], b_c[WB], b_ph0[WB];
-    __shared__ double b_alpha[WB][2], b_mold[WB][4];
-    __shared__ int s_fits;
-    const int lane = tid & 7, wl = tid >> 3;  // winner slot in the batch
+    // ---- plan the splits, WB winners at a time, eight threads each
+    const int lane = tid & 7, wl = tid >> 3;
     for (int base = 0; base < nwin; base += WB) {
       const int nb = nwin - base < WB ? nwin - base : WB;
       const bool act = wl < nb && !s_stop;
-      // phase 1: plan
       if (act && lane == 0) {
         const int i = swin[base + wl];
         const int idx = (int)(sk[i] & 0xffffffffu);
@@ -340,193 +369,239 @@ __global__ void __launch_bounds__(TB) k_track(DevState d, int cur_next, int mode
         b_e[wl] = key >> 2;
         b_ka[wl] = key & 3;
         b_kb[wl] = d.pr_k[idx];
+        b_app[wl] = 0;
       }
       __syncthreads();
       if (act && lane < 4) {
+        // local node a: side and the phantom to reuse
         const int e = b_e[wl], ka = b_ka[wl], kb = b_kb[wl], a = lane;
         const double pax = xi_g(ka), pay = eta_g(ka), pbx = xi_g(kb), pby = eta_g(kb);
         const double cross = (pbx - pax) * (eta_n(a) - pay) - (pby - pay) * (xi_n(a) - pax);
         b_side[wl][a] = cross > 0.0 ? 0 : 1;
-        b_n4[wl][a] = elem_node(g, e, a);
         b_reuse[wl][a] = reuse_lookup(d, e, ka, kb, a);
-      }
-      __syncthreads();
-      if (act && lane == 4) {
-        int side[4];
-        for (int a = 0; a < 4; ++a) side[a] = b_side[wl][a];
-        area_fractions(b_ka[wl], b_kb[wl], side, b_alpha[wl]);
-      }
-      // phase 2: crack slots and phantom ids in winner order
-      int nnew = 0;
-      if (act && lane == 0)
-        for (int a = 0; a < 4; ++a) nnew += b_reuse[wl][a] < 0;
-      int tot_new;
-      const int pre_new = block_exscan(nnew, &tot_new);
-      if (tid == 0)
-        s_fits = !s_stop && s_nph + tot_new <= d.ph_cap && s_nck + nb <= d.ck_cap;
-      if (act && lane == 0) {
-        b_c[wl] = s_nck + wl;
-        b_ph0[wl] = g.nn + s_nph + pre_new;
-      }
-      __syncthreads();
-      const bool go = act && s_fits;
-      // phase 3: phantoms (new ones copy the real node's state) and the record
-      if (go && lane < 4) {
-        const int a = lane, sd = b_side[wl][a], N = b_n4[wl][a];
-        b_node[wl][sd][a] = N;
-        int P = b_reuse[wl][a];
-        if (P < 0) {
-          int rank = 0;
-          for (int q = 0; q < a; ++q) rank += b_reuse[wl][q] < 0;
-          P = b_ph0[wl] + rank;
-          const int t = P - g.nn;
-          d.ph_owner[t] = N;
-          d.ph_creator[t] = b_e[wl] * 4 + a;
-          d.ph_nuser[t] = 0;
-          d.Wn[P] = 0.0;
-          d.Wd[P] = 0.0;
-          if (d.precision == 1) {
-            d.u4[cur_next][P] = d.u4[cur_next][N];
-            d.v2[P] = d.v2[N];
-          } else {
-            d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
-            d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
-          }
-          b_mold[wl][a] = -1.0;
-        } else {
-          b_mold[wl][a] = d.m[P];
-        }
-        b_node[wl][1 - sd][a] = P;
-      }
-      if (go && lane == 4) {
-        const int e = b_e[wl], c = b_c[wl], ka = b_ka[wl], kb = b_kb[wl];
-        int info = ka | (kb << 2);
-        for (int a = 0; a < 4; ++a) info |= b_side[wl][a] << (4 + a);
-        d.ck_elem[c] = e;
-        d.ck_info[c] = info;
-        d.ck_Ap[c * 2] = b_alpha[wl][0] * g.A;
-        d.ck_Ap[c * 2 + 1] = b_alpha[wl][1] * g.A;
-        d.ck_step[c] = mode == TRACK_PRECRACK ? -1 : step;
-        if (mode == TRACK_PRECRACK) {
-          d.ck_ud[c] = 0.0;
-        } else {
-          const double xa = (xi_g(ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(ka) + 1.0) * (0.5 * g.hy);
-          const double xb = (xi_g(kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(kb) + 1.0) * (0.5 * g.hy);
-          const double sx = xb - xa, sy = yb - ya;
-          const double L = sqrt(sx * sx + sy * sy);
-          d.ck_ud[c] = (double)d.gc[e] * L;
-        }
-        d.crack_of[e] = c;
-        d.estate[e] = ST_CRACKED;
-      }
-      __syncthreads();
-      // phase 4: node lists of the pieces and the phantoms' users
-      if (go && lane < 4) {
-        const int a = lane, c = b_c[wl], e = b_e[wl];
-        d.ck_node[c * 8 + a] = b_node[wl][0][a];
-        d.ck_node[c * 8 + 4 + a] = b_node[wl][1][a];
-        const int p = 1 - b_side[wl][a];
-        const int t = b_node[wl][p][a] - g.nn;
-        const int nu = d.ph_nuser[t];
-        if (nu >= 4) {
-          atomicOr(&cnt->status, STAT_CAPACITY);
-        } else {
-          int q = nu;
-          while (q > 0 && (d.ph_users[t * 4 + q - 1] >> 3) > e) {
-            d.ph_users[t * 4 + q] = d.ph_users[t * 4 + q - 1];
-            --q;
-          }
-          d.ph_users[t * 4 + q] = (e << 3) | (p << 2) | a;
-          d.ph_nuser[t] = nu + 1;
-        }
-      }
-      __syncthreads();
-      // phase 5: masses of the four real nodes (lanes 0-3) and of their
-      // phantoms (lanes 4-7, momentum-conserving merge into shared ones)
-      if (go && lane < 4) {
-        const int N = b_n4[wl][lane];
-        set_mass(d, N, mass_real(d, N));
-      } else if (go) {
-        const int a = lane - 4, p = 1 - b_side[wl][a];
-        const int P = b_node[wl][p][a];
-        const double mnew = mass_phantom(d, P);
-        const double mold = b_mold[wl][a];
-        if (mold >= 0.0) {
-          const double dm = d.mat.rho * (b_alpha[wl][p] * g.A) * 0.25;
-          const int N = b_n4[wl][a];
-          if (d.precision == 1) {
-            const float2 vp = d.v2[P], vn = d.v2[N];
-            const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
-            const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
-            d.v2[P] = make_float2((float)vx, (float)vy);
-          } else {
-            d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
-            d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
-          }
-        }
-        set_mass(d, P, mnew);
-      }
-      // phase 6: surface list -- lanes 0-3 look at edge k = lane
-      int app = 0, app_edge = 0, app_info = 0;
-      if (go && lane < 4) {
-        const int e = b_e[wl], k = lane;
-        const int ed = elem_edge(g, e, k);
+      } else if (act) {
+        // local edge k: appended to the surface list if the element across
+        // it is intact, else its current entry (if any) becomes a tombstone
+        const int e = b_e[wl], k = lane - 4;
         const int f = elem_neighbor(g, e, k);
+        b_tomb[wl][k] = -1;
         if (estatus(d, f) == ST_INTACT) {
-          app = 1;
-          app_edge = ed;
-          app_info = f * 4 + ((k + 2) & 3);
+          atomicOr(&b_app[wl], 1 << k);
         } else {
-          const int pos = d.spos[ed];
-          if (pos >= 0) {
-            d.S[pos] = -1;
-            d.spos[ed] = -1;
-            atomicAdd(&s_dead, 1);
-          }
+          b_tomb[wl][k] = d.spos[elem_edge(g, e, k)];
         }
       }
-      int tot_app;
-      const int pre_app = block_exscan(app, &tot_app);
-      const bool lfits = s_nS + tot_app <= d.list_cap;
-      if (app && lfits) {
-        const int dst = s_nS + pre_app;
-        d.S[dst] = app_edge;
-        d.S_info[dst] = app_info;
-        d.S_G[dst] = 0.0;
-        d.spos[app_edge] = dst;
-      }
       __syncthreads();
+      int nnew = 0, napp = 0, ndead = 0;
+      if (act && lane == 0) {
+        for (int a = 0; a < 4; ++a) {
+          nnew += b_reuse[wl][a] < 0;
+          ndead += b_tomb[wl][a] >= 0;
+        }
+        napp = __popc(b_app[wl]);
+      }
+      int tot_new, tot_app;
+      const int pre_new = block_exscan(nnew, &tot_new);
+      const int pre_app = block_exscan(napp, &tot_app);
       if (tid == 0) {
-        if (!s_fits || !lfits) {
+        const bool fits = !s_stop && s_nph + tot_new <= d.ph_cap && s_nck + nb <= d.ck_cap &&
+                          s_nS + tot_app <= d.list_cap;
+        if (!fits) {
           s_stop = 1;
           atomicOr(&cnt->status, STAT_CAPACITY);
-        } else {
-          s_nph += tot_new;
-          s_nck += nb;
-          s_nS += tot_app;
         }
       }
       __syncthreads();
-    }
-    if (tid == 0) {
-      cnt->n_ph = s_nph;
-      cnt->n_ck = s_nck;
-      cnt->n_S = s_nS;
-      cnt->n_dead += s_dead;
-      cnt->n_win_last = nwin;
-    }
-    __syncthreads();
-    if (cnt->n_dead > 1024 && 2 * cnt->n_dead > cnt->n_S) {
+      if (act && lane == 0 && !s_stop) {
+        const int w = base + wl;
+        int side[4];
+        for (int a = 0; a < 4; ++a) side[a] = b_side[wl][a];
+        double alpha[2];
+        area_fractions(b_ka[wl], b_kb[wl], side, alpha);
+        int info = b_ka[wl] | (b_kb[wl] << 2) | (b_app[wl] << 8);
+        for (int a = 0; a < 4; ++a) info |= side[a] << (4 + a);
+        d.pl_e[w] = b_e[wl];
+        d.pl_info[w] = info;
+        for (int a = 0; a < 4; ++a) {
+          d.pl_reuse[w * 4 + a] = b_reuse[wl][a];
+          d.pl_tomb[w * 4 + a] = b_tomb[wl][a];
+        }
+        d.pl_alpha[w * 2] = alpha[0];
+        d.pl_alpha[w * 2 + 1] = alpha[1];
+        d.pl_c[w] = s_nck + wl;
+        d.pl_ph0[w] = g.nn + s_nph + pre_new;
+        d.pl_app0[w] = s_nS + pre_app;
+      }
+      if (act && lane == 0 && !s_stop) atomicAdd(&s_dead, ndead);
       __syncthreads();
-      compact_surface(d);
+      if (tid == 0 && !s_stop) {
+        s_nph += tot_new;
+        s_nck += nb;
+        s_nS += tot_app;
+        s_done = base + nb;
+      }
+      __syncthreads();
     }
-  } else if (tid == 0) {
-    cnt->n_win_last = 0;
   }
   __syncthreads();
   if (tid == 0) {
+    cnt->pend_nwin = s_done;
+    cnt->pend_nph = s_nph;
+    cnt->pend_nck = s_nck;
+    cnt->pend_nS = s_nS;
+    cnt->pend_dead = s_dead;
     cnt->n_prop_last = cnt->n_prop;
     cnt->n_prop = 0;
+  }
+}
+
+// Split writes: eight threads per planned winner (lanes 0-3: local nodes,
+// 4-7: their phantoms / the split record), winners in parallel.  Runs after
+// the node updates of the step, so new phantoms copy u^{n+1} and v^{n+1/2}.
+__global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+  Counters *cnt = d.cnt;
+  const Geo &g = d.g;
+  const int nw = cnt->pend_nwin;
+  const int step = cnt->step;
+  const int lane32 = threadIdx.x & 31, lane = lane32 & 7, grp = lane32 >> 3;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int wb = warp * 4; wb < nw; wb += nwarps * 4) {
+    const int w = wb + grp;
+    const bool act = w < nw;
+    int e = 0, info = 0, c = 0, sd = 0, a = lane & 3, P = -1, N = 0;
+    double mold = -1.0;
+    if (act) {
+      e = d.pl_e[w];
+      info = d.pl_info[w];
+      c = d.pl_c[w];
+      sd = (info >> (4 + a)) & 1;
+      N = elem_node(g, e, a);
+    }
+    // phase A: phantoms and node lists (lanes 0-3); the split record (lane 4)
+    if (act && lane < 4) {
+      P = d.pl_reuse[w * 4 + a];
+      if (P < 0) {
+        int rank = 0;
+        for (int q = 0; q < a; ++q) rank += d.pl_reuse[w * 4 + q] < 0;
+        P = d.pl_ph0[w] + rank;
+        const int t = P - g.nn;
+        d.ph_owner[t] = N;
+        d.ph_creator[t] = e * 4 + a;
+        d.ph_nuser[t] = 0;
+        d.Wn[P] = 0.0;
+        d.Wd[P] = 0.0;
+        if (d.precision == 1) {
+          d.u4[cur_next][P] = d.u4[cur_next][N];
+          d.v2[P] = d.v2[N];
+        } else {
+          d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
+          d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
+        }
+      } else {
+        mold = d.m[P];
+      }
+      d.ck_node[c * 8 + sd * 4 + a] = N;
+      d.ck_node[c * 8 + (1 - sd) * 4 + a] = P;
+    } else if (act && lane == 4) {
+      const int ka = info & 3, kb = (info >> 2) & 3;
+      d.ck_elem[c] = e;
+      d.ck_info[c] = info & 0xff;
+      d.ck_Ap[c * 2] = d.pl_alpha[w * 2] * g.A;
+      d.ck_Ap[c * 2 + 1] = d.pl_alpha[w * 2 + 1] * g.A;
+      d.ck_step[c] = mode == TRACK_PRECRACK ? -1 : step;
+      if (mode == TRACK_PRECRACK) {
+        d.ck_ud[c] = 0.0;
+      } else {
+        const double xa = (xi_g(ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(ka) + 1.0) * (0.5 * g.hy);
+        const double xb = (xi_g(kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(kb) + 1.0) * (0.5 * g.hy);
+        const double sx = xb - xa, sy = yb - ya;
+        const double L = sqrt(sx * sx + sy * sy);
+        d.ck_ud[c] = (double)d.gc[e] * L;
+      }
+      d.crack_of[e] = c;
+      d.estate[e] = ST_CRACKED;
+    }
+    __syncwarp();
+    // phase B: users of the phantoms, kept sorted by element id
+    if (act && lane < 4) {
+      const int p = 1 - sd;
+      const int t = P - g.nn;
+      const int nu = d.ph_nuser[t];
+      if (nu >= 4) {
+        atomicOr(&cnt->status, STAT_CAPACITY);
+      } else {
+        int us[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) us[q] = q < nu ? d.ph_users[t * 4 + q] : 0x7fffffff;
+        const int code = (e << 3) | (p << 2) | a;
+        int out[4], o = 0;
+        bool placed = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!placed && (q >= nu || (us[q] >> 3) > e)) {
+            if (o < 4) out[o] = code;
+            ++o;
+            placed = true;
+          }
+          if (q < nu && o < 4) { out[o] = us[q]; ++o; }
+        }
+        if (!placed && o < 4) out[o] = code;
+        for (int q = 0; q <= nu; ++q) d.ph_users[t * 4 + q] = out[q];
+        d.ph_nuser[t] = nu + 1;
+      }
+    }
+    __syncwarp();
+    // phase C: masses of the real nodes (lanes 0-3) and their phantoms
+    // (lanes 4-7, momentum-conserving merge into a reused phantom)
+    const int Pn = __shfl_sync(0xffffffffu, P, (lane32 & ~7) | a);
+    const double mo = __shfl_sync(0xffffffffu, mold, (lane32 & ~7) | a);
+    if (act && lane < 4) {
+      set_mass(d, N, mass_real(d, N));
+    } else if (act) {
+      const int p = 1 - sd;
+      const double mnew = mass_phantom(d, Pn);
+      if (mo >= 0.0) {
+        const double dm = d.mat.rho * (d.pl_alpha[w * 2 + p] * g.A) * 0.25;
+        if (d.precision == 1) {
+          const float2 vp = d.v2[Pn], vn = d.v2[N];
+          const double vx = ((mo * (double)vp.x) + dm * (double)vn.x) / mnew;
+          const double vy = ((mo * (double)vp.y) + dm * (double)vn.y) / mnew;
+          d.v2[Pn] = make_float2((float)vx, (float)vy);
+        } else {
+          d.vx[Pn] = (mo * d.vx[Pn] + dm * d.vx[N]) / mnew;
+          d.vy[Pn] = (mo * d.vy[Pn] + dm * d.vy[N]) / mnew;
+        }
+      }
+      set_mass(d, Pn, mnew);
+    }
+    // phase D: surface list -- lanes 0-3 handle local edge k = lane
+    if (act && lane < 4) {
+      const int k = lane;
+      const int ed = elem_edge(g, e, k);
+      const int app = (info >> 8) & 15;
+      if ((app >> k) & 1) {
+        const int dst = d.pl_app0[w] + __popc(app & ((1 << k) - 1));
+        const int f = elem_neighbor(g, e, k);
+        d.S[dst] = ed;
+        d.S_info[dst] = f * 4 + ((k + 2) & 3);
+        d.S_G[dst] = 0.0;
+        d.spos[ed] = dst;
+      } else {
+        const int pos = d.pl_tomb[w * 4 + k];
+        if (pos >= 0) {
+          d.S[pos] = -1;
+          d.spos[ed] = -1;
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cnt->n_ph = cnt->pend_nph;
+    cnt->n_ck = cnt->pend_nck;
+    cnt->n_S = cnt->pend_nS;
+    cnt->n_dead += cnt->pend_dead;
+    cnt->n_win_last = nw;
     if (mode == TRACK_STEP) cnt->step = cnt->step + 1;
   }
 }
@@ -585,16 +660,21 @@ __global__ void k_surface_info(DevState d, int *out3) {
 
 }  // namespace
 
-cudaError_t launch_track(const DevState &d, int cur_next, int mode, cudaStream_t st) {
+cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
   size_t sm = SORT_CAP * sizeof(unsigned long long) + SORT_CAP * sizeof(int);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_track, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_track<<<1, TB, sm, st>>>(d, cur_next, mode);
+  k_select<<<1, TB, sm, st>>>(d, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st) {
+  k_apply<<<64, 256, 0, st>>>(d, cur_next, mode);
   return cudaGetLastError();
 }
 
