@@ -231,6 +231,52 @@ cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge,
                                      const int *elem, const int *k,
                                      const double *G);
 
+/* Allocation-free energy check.  The paper has no counterpart: this is a
+ * library convenience for callers that cannot allocate device memory, such
+ * as a host application whose device memory is all handed to its own
+ * fixed-size arena, or a monitor that samples energies while other streams
+ * are busy and must not call cudaMalloc / cudaFree (cudaFree synchronises the
+ * device).  It allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *
+ * Computes, for one state of an uncracked nx * ny mesh (holes allowed), the
+ * kinetic energy 1/2 sum m_N |v_N|^2 with row-sum lumped masses and the
+ * ES-FEM strain energy (each active element owns A/4 of each of its four
+ * edge points; an edge point shared with an active element uses the mean of
+ * the two elements' strains), the same quantities as KE and SE of an energy
+ * record of cem_step for a mesh without splits.  Only the grouping of the
+ * partial sums differs, so the two agree to rounding.
+ *
+ * Arguments (all pointers are device memory of the calling thread's current
+ * device; the caller owns them): elem_active uint8[nx*ny] (0 = hole) or NULL;
+ * u and v double[2*(nx+1)*(ny+1)] (x block then y block, node id
+ * j*(nx+1)+i); out double[2] receives KE then SE.  E, nu, rho, plane_strain
+ * as in cem_set_material.  cuda_stream is a cudaStream_t (NULL = the legacy
+ * default stream); the call only enqueues work, so read out after the stream
+ * is synchronised.  err (host, may be NULL) receives a message of at most
+ * err_len bytes on failure.
+ *
+ * Scratch and its limit: one (KE, SE) pair per node row in a fixed device
+ * array of 2 * (CEM_NOALLOC_MAX_NY + 1) doubles (256 KiB + 16 B), which every
+ * device that loads the library holds until the process exits.  Meshes with
+ * ny > CEM_NOALLOC_MAX_NY are rejected with CEM_ERR_ARG.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.  All
+ * calls on a device share the array: calls whose work overlaps on the GPU
+ * (different streams or host threads without an order between them) race
+ * and corrupt each other's results, so order them.  Nothing in the array
+ * has to start at zero: each call writes every slot it reads.
+ *
+ * Errors: CEM_ERR_ARG (sizes, material, a missing pointer or one that is not
+ * device memory of the current device), CEM_ERR_CUDA (no device, symbol
+ * lookup or launch failure). */
+#define CEM_NOALLOC_MAX_NY 16384
+cem_status cem_state_energy_noalloc(int nx, int ny, double hx, double hy,
+                                    const unsigned char *elem_active, double E,
+                                    double nu, double rho, int plane_strain,
+                                    const double *u, const double *v, double *out,
+                                    void *cuda_stream, char *err, int err_len);
+
 /* Message of the last failure on h (or of the last failed create when h is
  * NULL).  Valid until the next call on h. */
 const char *cem_last_error(const cem_handle *h);

@@ -24,6 +24,7 @@ UNITS = [
     ("energy.cu", ["-fmad=false"]),
     ("step_fp32.cu", []),
     ("eval_fp32.cu", ["-fmad=false"]),
+    ("state_energy_noalloc.cu", ["-fmad=false"]),
     ("api.cpp", []),
 ]
 HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh"]

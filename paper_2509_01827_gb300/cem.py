@@ -84,6 +84,10 @@ SIGNATURES = {
     "cem_get_surface": (C.c_int, [_h, _ip, _ip, _ip, C.c_int, _ip]),
     "cem_debug_apply_proposals": (C.c_int, [_h, C.c_int, _ip, _ip, _ip, _dp]),
     "cem_profile_steps": (C.c_int, [_h, C.c_int, _dp]),
+    "cem_state_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_void_p,
+                                           C.c_double, C.c_double, C.c_double, C.c_int,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_char_p, C.c_int]),
     "cem_last_error": (C.c_char_p, [_h]),
     "cem_mesh_destroy": (None, [_h]),
 }
@@ -219,6 +223,21 @@ def cem_profile_steps(h, n):
     _chk(h, lib().cem_profile_steps(h, int(n), _p(ms, _dp)))
     keys = ["total", "pieces", "main", "phantom", "eval", "select", "energy", "kernels", "apply"]
     return dict(zip(keys, ms.tolist()))
+
+
+def cem_state_energy_noalloc(nx, ny, hx, hy, elem_active_ptr, E, nu, rho, plane_strain,
+                             u_ptr, v_ptr, out_ptr, stream_ptr=0):
+    """Allocation-free energy check on device pointers (integers): enqueues
+    KE and SE of one uncracked state into out_ptr (double[2]) on the stream.
+    For callers that cannot allocate device memory; the library's scratch is a
+    fixed device array, so calls that overlap on the GPU must be ordered."""
+    err = C.create_string_buffer(256)
+    rc = lib().cem_state_energy_noalloc(int(nx), int(ny), float(hx), float(hy),
+                                        elem_active_ptr or None, float(E), float(nu), float(rho),
+                                        int(bool(plane_strain)), u_ptr, v_ptr, out_ptr,
+                                        stream_ptr or None, err, len(err))
+    if rc != CEM_OK:
+        raise CemError(rc, err.value.decode())
 
 
 def cem_mesh_destroy(h):
