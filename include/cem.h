@@ -231,6 +231,45 @@ cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge,
                                      const int *elem, const int *k,
                                      const double *G);
 
+/* Batched stepping of many independent meshes (specimen sweeps): every
+ * member advances by exactly the step defined above (Secs. 2-3); the batch
+ * only changes how the work is launched.  One launch per kernel kind covers
+ * all members (persistent grids walking lists of (member, tile or block)
+ * items, one CUDA graph per step), so small meshes no longer pay one set of
+ * launches each.
+ *
+ * cem_batch_create: members[n] are mesh handles with their material (and
+ * loads) set, on one device, with the same precision, energy_every and
+ * current step.  step_end[n] (host, may be NULL = no limit) is the step
+ * count at which each member stops; cem_step(batch, k) advances every member
+ * by k steps or up to its limit.  cuda_stream as in cem_mesh_desc.  While
+ * in the batch a member cannot be stepped, loaded or given fields on its
+ * own; its getters work as usual and read its state.  Members must outlive
+ * the batch (destroy the batch first); destroying a member detaches it and
+ * the batch then refuses to step.  The batch's own device memory (states
+ * and work lists, a few KB per member) comes from member 0's allocator.
+ * On a batch handle cem_get_counts returns sums over the members (step =
+ * batch step, dt = t = 0); the other getters return CEM_ERR_STATE.
+ * Errors: CEM_ERR_ARG (mismatched members), CEM_ERR_STATE (member without
+ * material or already in a batch), CEM_ERR_CUDA.  cem_step on a batch also
+ * returns the first member error, naming the member in the message. */
+cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_end,
+                            void *cuda_stream, cem_handle **out);
+
+/* Launch configuration of a batch: tile_rows (8 or 16) is the height of the
+ * FP32 tile update's tiles (32 nodes wide; the FP64 tiles are fixed at
+ * 32 x 8), grid_main the persistent grid of the tile update (1 .. 64 x SMs).
+ * Results do not depend on it in FP64; in FP32 the grouping of some sums
+ * changes with the tile height (last-bit differences).  Default 16, 3 x SMs. */
+cem_status cem_batch_set_config(cem_handle *batch, int tile_rows, int grid_main);
+
+/* Autotuner: times steps_per_candidate real steps (after one untimed step)
+ * for each candidate configuration -- tile heights {16, 8} (FP32 only) x
+ * grids {1, 2, 3, 4} x SMs -- keeps the fastest and returns it.  The timed
+ * steps advance the simulation like cem_step. */
+cem_status cem_batch_autotune(cem_handle *batch, int steps_per_candidate, int *tile_rows,
+                              int *grid_main);
+
 /* Allocation-free energy check.  The paper has no counterpart: this is a
  * library convenience for callers that cannot allocate device memory, such
  * as a host application whose device memory is all handed to its own

@@ -84,6 +84,10 @@ SIGNATURES = {
     "cem_get_surface": (C.c_int, [_h, _ip, _ip, _ip, C.c_int, _ip]),
     "cem_debug_apply_proposals": (C.c_int, [_h, C.c_int, _ip, _ip, _ip, _dp]),
     "cem_profile_steps": (C.c_int, [_h, C.c_int, _dp]),
+    "cem_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_long),
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cem_batch_set_config": (C.c_int, [_h, C.c_int, C.c_int]),
+    "cem_batch_autotune": (C.c_int, [_h, C.c_int, _ip, _ip]),
     "cem_state_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, C.c_void_p,
                                            C.c_double, C.c_double, C.c_double, C.c_int,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -223,6 +227,27 @@ def cem_profile_steps(h, n):
     _chk(h, lib().cem_profile_steps(h, int(n), _p(ms, _dp)))
     keys = ["total", "pieces", "main", "phantom", "eval", "select", "energy", "kernels", "apply"]
     return dict(zip(keys, ms.tolist()))
+
+
+def cem_batch_create(handles, step_end=None, stream_ptr=0) -> int:
+    n = len(handles)
+    arr = (C.c_void_p * n)(*handles)
+    lim = None if step_end is None else (C.c_long * n)(*[int(x) for x in step_end])
+    out = C.c_void_p()
+    rc = lib().cem_batch_create(arr, n, lim, stream_ptr or None, C.byref(out))
+    if rc != CEM_OK:
+        raise CemError(rc, lib().cem_last_error(None).decode())
+    return out.value
+
+
+def cem_batch_set_config(b, tile_rows, grid_main):
+    _chk(b, lib().cem_batch_set_config(b, int(tile_rows), int(grid_main)))
+
+
+def cem_batch_autotune(b, steps_per_candidate):
+    r, g = C.c_int(), C.c_int()
+    _chk(b, lib().cem_batch_autotune(b, int(steps_per_candidate), C.byref(r), C.byref(g)))
+    return r.value, g.value
 
 
 def cem_state_energy_noalloc(nx, ny, hx, hy, elem_active_ptr, E, nu, rho, plane_strain,
@@ -412,3 +437,40 @@ class Solver:
 
     def debug_apply_proposals(self, edge, elem, k, G):
         cem_debug_apply_proposals(self.h, edge, elem, k, G)
+
+
+# ---------------------------------------------------------------- batch
+class Batch:
+    """Many ``Solver`` members stepped in lock-step by one launch per kernel
+    kind (cem_batch_create).  Each member stops at its own step limit."""
+
+    def __init__(self, members, step_end=None, stream=None):
+        import torch
+        self.members = list(members)  # kept alive: their allocators serve the batch
+        dev = self.members[0]._stream.device if self.members[0]._stream is not None else None
+        self._stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.h = cem_batch_create([m.h for m in self.members], step_end,
+                                  self._stream.cuda_stream)
+
+    def close(self):
+        if self.h:
+            cem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        cem_step(self.h, n)
+
+    def counts(self):
+        return cem_get_counts(self.h)
+
+    def set_config(self, tile_rows, grid_main):
+        cem_batch_set_config(self.h, tile_rows, grid_main)
+
+    def autotune(self, steps_per_candidate=5):
+        return cem_batch_autotune(self.h, steps_per_candidate)

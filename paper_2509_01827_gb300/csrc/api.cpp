@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,8 @@
 #include "cem_internal.h"
 
 using namespace cem;
+
+struct BatchPlan;
 
 struct cem_handle {
   DevState d{};
@@ -54,6 +57,8 @@ struct cem_handle {
   void *scratch = nullptr;     // reusable device scratch for getters
   size_t scratch_bytes = 0;
   std::string err;
+  BatchPlan *batch = nullptr;   // set on a batch handle (cem_batch_create)
+  cem_handle *in_batch = nullptr;  // set on a member of a batch
 };
 
 namespace {
@@ -204,7 +209,7 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
   else e = launch_step_fp64(d, cur, first, energy, h->ss, marks ? marks + 1 : nullptr);
   if (e != cudaSuccess) return e;
   if (marks) cudaEventRecord(marks[4], h->st);
-  if (energy && (e = launch_energy_post(d, energy_parts_needed(d), h->st)) != cudaSuccess) return e;
+  if (energy && (e = launch_energy_post(d, energy_parts_step(d), h->st)) != cudaSuccess) return e;
   if (marks) {
     cudaEventRecord(marks[5], h->st);
     e = launch_select(d, TRACK_STEP, h->st);
@@ -250,6 +255,11 @@ cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
   *out = h->graphs[cur][energy];
   return CEM_OK;
 }
+
+cem_status batch_step(cem_handle *b, int n);
+cem_status batch_counts(cem_handle *b, cem_counts *out);
+void batch_release(cem_handle *b);
+void batch_detach(cem_handle *member);
 
 }  // namespace
 
@@ -315,6 +325,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
     return fail(nullptr, CEM_ERR_CUDA, "device set-up: %s", cudaGetErrorString(ce));
   }
   DevState &d = h->d;
+  d.step_end = INT_MAX;
+  d.cur_xor = 0;
   d.g.nx = desc->nx; d.g.ny = desc->ny; d.g.nn = (int)nn; d.g.ne = (int)ne;
   d.g.nh = desc->nx * (desc->ny + 1);
   d.g.ned = d.g.nh + (desc->nx + 1) * desc->ny;
@@ -420,6 +432,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
 void cem_mesh_destroy(cem_handle *h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  if (h->batch) batch_release(h);
+  if (h->in_batch) batch_detach(h);
   drop_graphs(h);
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
   for (void *p : h->blocks) {
@@ -442,6 +456,7 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
                             const float *gc_per_elem, double gc_uniform, int plane_strain,
                             double gamma, int gamma_mode, int mct_scope) {
   if (!h) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "not valid on a batch handle");
   if (h->material) return fail(h, CEM_ERR_STATE, "material already set");
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(rho > 0)) return fail(h, CEM_ERR_ARG, "bad material");
   if (mct_scope < 0 || mct_scope > 2 || gamma_mode < 0 || gamma_mode > 1)
@@ -511,6 +526,7 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
 cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items, int comp_mask,
                       int law, double a0, double t0, double tau) {
   if (!h) return CEM_ERR_ARG;
+  if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (h->step != 0) return fail(h, CEM_ERR_STATE, "loads must be set before the first step");
   if (n_items < 0 || (n_items > 0 && !items)) return fail(h, CEM_ERR_ARG, "bad items");
   if (law < 0 || law > 2) return fail(h, CEM_ERR_ARG, "bad law");
@@ -575,6 +591,7 @@ cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items, in
 
 cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_bytes, int on_device) {
   if (!h || !data) return CEM_ERR_ARG;
+  if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (h->step != 0) return fail(h, CEM_ERR_STATE, "fields can only be set before the first step");
   if (which != CEM_FIELD_U && which != CEM_FIELD_V) return fail(h, CEM_ERR_ARG, "field not settable");
   CUDA_TRY(h, cudaSetDevice(h->device));
@@ -604,6 +621,8 @@ cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_byt
 
 cem_status cem_step(cem_handle *h, int n) {
   if (!h) return CEM_ERR_ARG;
+  if (h->batch) return batch_step(h, n);
+  if (h->in_batch) return fail(h, CEM_ERR_STATE, "a member of a batch is stepped by the batch");
   if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
   if (n < 0) return fail(h, CEM_ERR_ARG, "negative step count");
   if (n == 0) return CEM_OK;
@@ -638,6 +657,7 @@ cem_status cem_step(cem_handle *h, int n) {
 
 cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
   if (!h || !ms) return CEM_ERR_ARG;
+  if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
   if (n < 1 || n > h->d.lam_cap) return fail(h, CEM_ERR_ARG, "1 <= n <= %d", h->d.lam_cap);
   CUDA_TRY(h, cudaSetDevice(h->device));
@@ -686,6 +706,7 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
 
 cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
   if (!h || !out) return CEM_ERR_ARG;
+  if (h->batch) return batch_counts(h, out);
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -721,6 +742,7 @@ cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
 
 cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int on_device) {
   if (!h || !out) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -769,6 +791,7 @@ cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int
 
 cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -807,6 +830,7 @@ cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out) {
 
 cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -862,6 +886,7 @@ static cem_status surface_rows(cem_handle *h, std::vector<int> &rows) {
 
 cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   std::vector<int> rows;
   cem_status rc = surface_rows(h, rows);
   if (rc != CEM_OK) return rc;
@@ -878,6 +903,7 @@ cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip, in
 
 cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   std::vector<int> rows;
   cem_status rc = surface_rows(h, rows);
   if (rc != CEM_OK) return rc;
@@ -922,6 +948,7 @@ cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out) 
 cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge, const int *elem,
                                      const int *k, const double *G) {
   if (!h) return CEM_ERR_ARG;
+  if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (!h->material) return fail(h, CEM_ERR_STATE, "material first");
   if (n < 0 || n > h->d.prop_cap) return fail(h, CEM_ERR_ARG, "bad proposal count");
   if (n == 0) return CEM_OK;
@@ -952,3 +979,380 @@ cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge, cons
 }
 
 }  // extern "C"
+
+// ===================================================================== batch
+// A batch steps many independent meshes in lock-step: one launch per kernel
+// kind covers every member (work lists of (member, block) items walked by
+// persistent grids), one CUDA graph per step.  Members keep their own device
+// state and stay queryable; each stops at its own step limit.
+struct BatchPlan {
+  std::vector<cem_handle *> members;
+  std::vector<long> step_end;
+  int precision = 0;
+  int energy_every = 0;
+  long step = 0;           // batch step (equals every active member's step)
+  int tile_rows = 16;      // FP32 tile height (8 or 16)
+  int grid_main = 0;       // persistent grid of the tile update
+  int sms = 0;
+  BatchDev bd{};
+  char *dev = nullptr;     // device block: states, work lists, counters
+  size_t dev_bytes = 0;
+  cudaGraphExec_t graphs[2] = {nullptr, nullptr};  // [energy]
+  std::vector<double> tune_ms;  // autotuner timings, candidate order
+};
+
+namespace {
+
+void batch_drop_graphs(BatchPlan *p) {
+  for (auto &g : p->graphs)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// Host copies of the members' states and the work lists for the current
+// tile height, uploaded into the batch's device block.
+cem_status batch_upload(cem_handle *b) {
+  BatchPlan *p = b->batch;
+  const int n = (int)p->members.size();
+  std::vector<DevState> ds((size_t)n);
+  std::vector<int4> wm, wp, wph, we, wf;
+  std::vector<int> nparts((size_t)n);
+  for (int s = 0; s < n; ++s) {
+    cem_handle *m = p->members[s];
+    DevState d = m->d;
+    d.step_end = (int)std::min<long>(p->step_end[s], (long)INT_MAX);
+    d.cur_xor = m->cur ^ (int)(m->step & 1);
+    ds[s] = d;
+    int gx, gy;
+    if (p->precision == CEM_FP32_MIXED) {
+      gx = (d.g.nx + 1 + 31) / 32;
+      gy = (d.g.ny + 1 + p->tile_rows - 1) / p->tile_rows;
+    } else {
+      gx = (d.g.nx + 1 + 31) / 32;
+      gy = tiles_fp64(d) / gx;
+    }
+    for (int y = 0; y < gy; ++y)
+      for (int x = 0; x < gx; ++x) wm.push_back(make_int4(s, x, y, gx | (gy << 16)));
+    const int tiles = gx * gy, gp = grid_pieces(d), gph = grid_phantoms(d);
+    for (int q = 0; q < gp; ++q) wp.push_back(make_int4(s, q, tiles, gp));
+    for (int q = 0; q < gph; ++q) wph.push_back(make_int4(s, q, tiles + gp, gph));
+    const int ge = grid_eval(d), gf = grid_finite(d);
+    for (int q = 0; q < ge; ++q) we.push_back(make_int4(s, q, 0, ge));
+    for (int q = 0; q < gf; ++q) wf.push_back(make_int4(s, q, 0, gf));
+    nparts[s] = tiles + gp + gph;
+  }
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_ds = 0, o_m = al(o_ds + ds.size() * sizeof(DevState));
+  const size_t o_p = al(o_m + wm.size() * 16), o_ph = al(o_p + wp.size() * 16);
+  const size_t o_e = al(o_ph + wph.size() * 16), o_f = al(o_e + we.size() * 16);
+  const size_t o_np = al(o_f + wf.size() * 16), o_ctr = al(o_np + nparts.size() * 4);
+  const size_t bytes = o_ctr + 256;
+  if (bytes > p->dev_bytes) {
+    // grows only when a smaller tile height needs longer lists
+    p->dev = (char *)dalloc(b, bytes);
+    if (!p->dev) return fail(b, CEM_ERR_CUDA, "batch device allocation failed");
+    p->dev_bytes = bytes;
+  }
+  std::vector<char> host(bytes, 0);
+  memcpy(host.data() + o_ds, ds.data(), ds.size() * sizeof(DevState));
+  memcpy(host.data() + o_m, wm.data(), wm.size() * 16);
+  memcpy(host.data() + o_p, wp.data(), wp.size() * 16);
+  memcpy(host.data() + o_ph, wph.data(), wph.size() * 16);
+  memcpy(host.data() + o_e, we.data(), we.size() * 16);
+  memcpy(host.data() + o_f, wf.data(), wf.size() * 16);
+  memcpy(host.data() + o_np, nparts.data(), nparts.size() * 4);
+  int *ctr = (int *)(host.data() + o_ctr);
+  ctr[0] = (int)p->step;  // batch step
+  ctr[1] = 0;             // arrivals
+  CUDA_TRY(b, cudaMemcpyAsync(p->dev, host.data(), bytes, cudaMemcpyHostToDevice, b->st));
+  CUDA_TRY(b, cudaStreamSynchronize(b->st));
+  BatchDev &bd = p->bd;
+  bd.ds = (const DevState *)(p->dev + o_ds);
+  bd.n = n;
+  bd.bstep = (int *)(p->dev + o_ctr);
+  bd.arrive = bd.bstep + 1;
+  bd.w_main = (const int4 *)(p->dev + o_m); bd.n_main = (int)wm.size();
+  bd.w_pieces = (const int4 *)(p->dev + o_p); bd.n_pieces = (int)wp.size();
+  bd.w_ph = (const int4 *)(p->dev + o_ph); bd.n_ph = (int)wph.size();
+  bd.w_eval = (const int4 *)(p->dev + o_e); bd.n_eval = (int)we.size();
+  bd.w_fin = (const int4 *)(p->dev + o_f); bd.n_fin = (int)wf.size();
+  bd.nparts = (const int *)(p->dev + o_np);
+  batch_drop_graphs(p);
+  return CEM_OK;
+}
+
+int batch_kernels_in_step(bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
+
+cudaError_t batch_enqueue_step(cem_handle *b, bool first, bool energy) {
+  BatchPlan *p = b->batch;
+  cudaError_t e;
+  if (energy && (e = launch_energy_pre_batch(p->bd, b->st)) != cudaSuccess) return e;
+  if (p->precision == CEM_FP32_MIXED)
+    e = launch_step_fp32_batch(p->bd, first, energy, p->tile_rows, p->grid_main, b->ss);
+  else
+    e = launch_step_fp64_batch(p->bd, first, energy, p->grid_main, b->ss);
+  if (e != cudaSuccess) return e;
+  if (energy && (e = launch_energy_post_batch(p->bd, b->st)) != cudaSuccess) return e;
+  return launch_apply_batch(p->bd, b->st);
+}
+
+cem_status batch_graph(cem_handle *b, int energy, cudaGraphExec_t *out) {
+  BatchPlan *p = b->batch;
+  if (!p->graphs[energy]) {
+    cudaGraph_t g;
+    CUDA_TRY(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = batch_enqueue_step(b, false, energy != 0);
+    cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+    if (e != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch end capture: %s", cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(&p->graphs[energy], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e3));
+  }
+  *out = p->graphs[energy];
+  return CEM_OK;
+}
+
+// Advances every member that has not reached its limit by n steps (fewer at
+// its limit).  ev_t0 / ev_t1, when given, bracket the steps on the stream.
+cem_status batch_run(cem_handle *b, int n, cudaEvent_t ev_t0, cudaEvent_t ev_t1) {
+  BatchPlan *p = b->batch;
+  int lam_cap = INT_MAX;
+  for (size_t s = 0; s < p->members.size(); ++s) {
+    cem_handle *m = p->members[s];
+    if (!m) return fail(b, CEM_ERR_STATE, "member %d was destroyed", (int)s);
+    if (m->step != std::min(p->step, p->step_end[s]))
+      return fail(b, CEM_ERR_STATE, "member %d is out of step with the batch", (int)s);
+    lam_cap = std::min(lam_cap, m->d.lam_cap);
+  }
+  if (ev_t0) CUDA_TRY(b, cudaEventRecord(ev_t0, b->st));
+  int done = 0;
+  while (done < n) {
+    const int chunk = std::min(n - done, lam_cap);
+    for (cem_handle *m : p->members) {
+      cem_status rc = upload_load_factors(m, chunk);
+      if (rc != CEM_OK) return fail(b, rc, "load factors: %s", m->err.c_str());
+    }
+    for (cem_handle *m : p->members) CUDA_TRY(b, cudaStreamSynchronize(m->st));
+    for (int q = 0; q < chunk; ++q) {
+      const bool energy = p->energy_every > 0 && (p->step % p->energy_every) == 0;
+      if (p->step == 0) {
+        CUDA_TRY(b, batch_enqueue_step(b, true, energy));
+      } else {
+        cudaGraphExec_t gx;
+        cem_status rc = batch_graph(b, energy ? 1 : 0, &gx);
+        if (rc != CEM_OK) return rc;
+        CUDA_TRY(b, cudaGraphLaunch(gx, b->st));
+      }
+      b->launches += batch_kernels_in_step(energy);
+      p->step += 1;
+    }
+    if (done + chunk == n && ev_t1) CUDA_TRY(b, cudaEventRecord(ev_t1, b->st));
+    CUDA_TRY(b, cudaStreamSynchronize(b->st));
+    for (size_t s = 0; s < p->members.size(); ++s) {
+      cem_handle *m = p->members[s];
+      const long adv = std::max(0L, std::min((long)chunk, p->step_end[s] - m->step));
+      m->step += adv;
+      m->cur ^= (int)(adv & 1);
+    }
+    done += chunk;
+  }
+  return CEM_OK;
+}
+
+cem_status batch_finish(cem_handle *b) {
+  BatchPlan *p = b->batch;
+  CUDA_TRY(b, launch_check_finite_batch(p->bd, b->st));
+  b->launches += 1;
+  CUDA_TRY(b, cudaStreamSynchronize(b->st));
+  for (size_t s = 0; s < p->members.size(); ++s) {
+    cem_handle *m = p->members[s];
+    cem_status rc = sync_status(m);
+    if (rc != CEM_OK) return fail(b, rc, "member %d: %s", (int)s, m->err.c_str());
+  }
+  return CEM_OK;
+}
+
+cem_status batch_step(cem_handle *b, int n) {
+  if (n < 0) return fail(b, CEM_ERR_ARG, "negative step count");
+  if (n == 0) return CEM_OK;
+  CUDA_TRY(b, cudaSetDevice(b->device));
+  cem_status rc = batch_run(b, n, nullptr, nullptr);
+  if (rc != CEM_OK) return rc;
+  return batch_finish(b);
+}
+
+cem_status batch_counts(cem_handle *b, cem_counts *out) {
+  BatchPlan *p = b->batch;
+  cem_counts sum{};
+  for (size_t s = 0; s < p->members.size(); ++s) {
+    cem_handle *m = p->members[s];
+    if (!m) return fail(b, CEM_ERR_STATE, "member %d was destroyed", (int)s);
+    cem_counts c;
+    cem_status rc = cem_get_counts(m, &c);
+    if (rc != CEM_OK) return fail(b, rc, "member %d: %s", (int)s, m->err.c_str());
+    sum.n_nodes += c.n_nodes;
+    sum.n_phantoms += c.n_phantoms;
+    sum.n_elems += c.n_elems;
+    sum.n_active += c.n_active;
+    sum.n_cracked += c.n_cracked;
+    sum.n_surface += c.n_surface;
+    sum.n_tips += c.n_tips;
+    sum.n_energy += c.n_energy;
+    sum.last_proposals += c.last_proposals;
+    sum.last_winners += c.last_winners;
+  }
+  sum.step = p->step;
+  sum.dt = 0.0;
+  sum.t = 0.0;
+  sum.kernel_launches = b->launches;
+  *out = sum;
+  return CEM_OK;
+}
+
+void batch_release(cem_handle *b) {
+  BatchPlan *p = b->batch;
+  batch_drop_graphs(p);
+  for (cem_handle *m : p->members)
+    if (m) m->in_batch = nullptr;
+  delete p;
+  b->batch = nullptr;
+}
+
+void batch_detach(cem_handle *member) {
+  BatchPlan *p = member->in_batch->batch;
+  if (p)
+    for (auto &m : p->members)
+      if (m == member) m = nullptr;
+  member->in_batch = nullptr;
+}
+
+}  // namespace
+
+cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_end,
+                            void *cuda_stream, cem_handle **out) {
+  if (!out) return fail(nullptr, CEM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (!members || n < 1 || n > (1 << 16)) return fail(nullptr, CEM_ERR_ARG, "1 <= n <= 65536 members");
+  for (int s = 0; s < n; ++s) {
+    cem_handle *m = members[s];
+    if (!m || m->batch) return fail(nullptr, CEM_ERR_ARG, "member %d is not a mesh handle", s);
+    if (m->in_batch) return fail(nullptr, CEM_ERR_STATE, "member %d is already in a batch", s);
+    if (!m->material) return fail(nullptr, CEM_ERR_STATE, "member %d has no material", s);
+    for (int r = 0; r < s; ++r)
+      if (members[r] == m) return fail(nullptr, CEM_ERR_ARG, "member %d repeated", s);
+    const cem_handle *m0 = members[0];
+    if (m->device != m0->device || m->d.precision != m0->d.precision ||
+        m->energy_every != m0->energy_every || m->step != m0->step)
+      return fail(nullptr, CEM_ERR_ARG,
+                  "member %d differs from member 0 in device, precision, energy_every or step", s);
+    if (step_end && step_end[s] < m->step)
+      return fail(nullptr, CEM_ERR_ARG, "member %d: step limit before its current step", s);
+    if (m->d.g.nx + 1 >= (1 << 15) || m->d.g.ny + 1 >= (1 << 15))
+      return fail(nullptr, CEM_ERR_ARG, "member %d: batched meshes are limited to 32766 x 32766", s);
+  }
+  cem_handle *m0 = members[0];
+  cem_handle *b = new (std::nothrow) cem_handle();
+  if (!b) return fail(nullptr, CEM_ERR_ARG, "out of host memory");
+  b->device = m0->device;
+  b->alloc = m0->alloc;
+  b->free_fn = m0->free_fn;
+  b->ctx = m0->ctx;
+  b->material = true;
+  b->st = (cudaStream_t)cuda_stream;
+  cudaError_t ce = cudaSetDevice(b->device);
+  if (ce == cudaSuccess && !b->st) {
+    ce = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    b->own_stream = ce == cudaSuccess;
+  }
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->ss.aux1, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->ss.aux2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.join1, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.join2, cudaEventDisableTiming);
+  b->ss.main = b->st;
+  int sms = 0;
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  for (int s = 0; s < n && ce == cudaSuccess; ++s) ce = cudaStreamSynchronize(members[s]->st);
+  if (ce != cudaSuccess) {
+    cem_mesh_destroy(b);
+    return fail(nullptr, CEM_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(ce));
+  }
+  BatchPlan *p = new (std::nothrow) BatchPlan();
+  if (!p) {
+    cem_mesh_destroy(b);
+    return fail(nullptr, CEM_ERR_ARG, "out of host memory");
+  }
+  b->batch = p;
+  p->members.assign(members, members + n);
+  p->step_end.resize((size_t)n);
+  for (int s = 0; s < n; ++s) p->step_end[s] = step_end ? step_end[s] : (long)INT_MAX;
+  p->precision = m0->d.precision;
+  p->energy_every = m0->energy_every;
+  p->step = m0->step;
+  p->sms = sms;
+  p->tile_rows = 16;
+  p->grid_main = 3 * sms;
+  cem_status rc = batch_upload(b);
+  if (rc != CEM_OK) {
+    g_create_error = b->err;
+    cem_mesh_destroy(b);
+    return rc;
+  }
+  for (int s = 0; s < n; ++s) members[s]->in_batch = b;
+  *out = b;
+  return CEM_OK;
+}
+
+cem_status cem_batch_set_config(cem_handle *b, int tile_rows, int grid_main) {
+  if (!b) return CEM_ERR_ARG;
+  if (!b->batch) return fail(b, CEM_ERR_STATE, "not a batch handle");
+  BatchPlan *p = b->batch;
+  if (tile_rows != 8 && tile_rows != 16) return fail(b, CEM_ERR_ARG, "tile_rows must be 8 or 16");
+  if (grid_main < 1 || grid_main > 64 * p->sms) return fail(b, CEM_ERR_ARG, "1 <= grid_main <= 64 * SMs");
+  CUDA_TRY(b, cudaSetDevice(b->device));
+  const bool relist = p->precision == CEM_FP32_MIXED && tile_rows != p->tile_rows;
+  p->tile_rows = p->precision == CEM_FP32_MIXED ? tile_rows : 16;
+  if (grid_main != p->grid_main) batch_drop_graphs(p);
+  p->grid_main = grid_main;
+  if (relist) return batch_upload(b);
+  return CEM_OK;
+}
+
+cem_status cem_batch_autotune(cem_handle *b, int steps_per_candidate, int *tile_rows,
+                              int *grid_main) {
+  if (!b) return CEM_ERR_ARG;
+  if (!b->batch) return fail(b, CEM_ERR_STATE, "not a batch handle");
+  BatchPlan *p = b->batch;
+  if (steps_per_candidate < 1) return fail(b, CEM_ERR_ARG, "steps_per_candidate >= 1");
+  CUDA_TRY(b, cudaSetDevice(b->device));
+  std::vector<std::pair<int, int>> cand;
+  const int rows[2] = {16, 8};
+  for (int r = 0; r < (p->precision == CEM_FP32_MIXED ? 2 : 1); ++r)
+    for (int k = 1; k <= 4; ++k) cand.push_back({rows[r], k * p->sms});
+  cudaEvent_t e0, e1;
+  CUDA_TRY(b, cudaEventCreate(&e0));
+  CUDA_TRY(b, cudaEventCreate(&e1));
+  p->tune_ms.assign(cand.size(), 0.0);
+  double best = 1e300;
+  std::pair<int, int> pick = {p->tile_rows, p->grid_main};
+  cem_status rc = CEM_OK;
+  for (size_t c = 0; c < cand.size() && rc == CEM_OK; ++c) {
+    rc = cem_batch_set_config(b, cand[c].first, cand[c].second);
+    if (rc == CEM_OK) rc = batch_run(b, 1, nullptr, nullptr);  // capture, untimed
+    if (rc == CEM_OK) rc = batch_run(b, steps_per_candidate, e0, e1);
+    if (rc == CEM_OK) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      p->tune_ms[c] = ms;
+      if (ms < best) { best = ms; pick = cand[c]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CEM_OK) return rc;
+  rc = cem_batch_set_config(b, pick.first, pick.second);
+  if (rc != CEM_OK) return rc;
+  if (tile_rows) *tile_rows = p->tile_rows;
+  if (grid_main) *grid_main = p->grid_main;
+  return batch_finish(b);
+}

@@ -30,7 +30,8 @@ struct Counters {
   int n_prop_last; // proposals of the last step (diagnostic)
   // planned by the selection kernel, committed by the apply kernel
   int pend_nwin, pend_nph, pend_nck, pend_nS, pend_dead;
-  int pad[3];
+  int pend_step;  // step of the planned splits (read by the apply kernel)
+  int pad[2];
 };
 
 struct Geo {
@@ -56,6 +57,10 @@ struct DevState {
   int precision;
   int ph_cap, ck_cap, list_cap, prop_cap, ncap;
   int lam_cap;
+  // batched stepping (cem_batch_create): the member takes no step at or
+  // after step_end (INT_MAX when stepped alone), and its current
+  // displacement buffer at batch step n is (n & 1) ^ cur_xor
+  int step_end, cur_xor;
 
   // node arrays over ncap = nn + ph_cap; FP64 mode
   double *ux[2], *uy[2];
@@ -126,6 +131,43 @@ struct DevState {
   int rec_cap;
 };
 
+// A virtual thread block.  Kernels stepped alone use the hardware block;
+// batched kernels take (member, block) items from a work list, so that every
+// member sees the same block decomposition (and the same fixed-order energy
+// partial sums) as when it is stepped alone.
+struct VBlk {
+  int x, y, gx, gy;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ VBlk hw_vblk() {
+  return VBlk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+}
+#endif
+
+// Device view of a batch of independent meshes stepped in lock-step by one
+// launch per kernel kind.  Work items are int4 (member, x, y, gx | gy << 16).
+struct BatchDev {
+  const DevState *ds;   // [n] device copies of the members' states
+  int n;
+  int *bstep;           // batch step; advanced by the last block of the apply kernel
+  int *arrive;          // arrival counter of that kernel (returns to 0)
+  const int4 *w_main; int n_main;      // tile update
+  const int4 *w_pieces; int n_pieces;  // piece forces
+  const int4 *w_ph; int n_ph;          // phantom update
+  const int4 *w_eval; int n_eval;      // surface evaluation
+  const int4 *w_fin; int n_fin;        // finiteness check
+  const int *nparts;    // [n] energy partial sums of each member
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ VBlk item_vblk(int4 it) {
+  return VBlk{it.y, it.z, it.w & 0xffff, it.w >> 16};
+}
+// member is stepped at batch step n
+__device__ __forceinline__ bool member_active(const DevState &d, int n) { return n < d.step_end; }
+__device__ __forceinline__ int member_cur(const DevState &d, int n) { return (n & 1) ^ d.cur_xor; }
+#endif
+
 // ------------------------------------------------------------------ launch
 // All launchers enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
@@ -160,7 +202,26 @@ cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *
 cudaError_t launch_fp64_to_fp32(const DevState &d, int cur, const double *ux,
                                 const double *uy, const double *vx, const double *vy,
                                 int n, cudaStream_t st);
-int energy_parts_needed(const DevState &d);
+int energy_parts_needed(const DevState &d);  // capacity of e_part
+int energy_parts_step(const DevState &d);    // partials one step writes (alone)
+
+// batched counterparts (see BatchDev); tile_rows selects the FP32 tile
+// update's tile height (8 or 16 node rows), grid_main its persistent grid
+int tiles_fp32(const DevState &d, int tile_rows);
+int tiles_fp64(const DevState &d);
+int grid_pieces(const DevState &d);
+int grid_phantoms(const DevState &d);
+int grid_eval(const DevState &d);
+int grid_finite(const DevState &d);
+cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, int tile_rows,
+                                   int grid_main, const StepStreams &ss);
+cudaError_t launch_step_fp64_batch(const BatchDev &b, bool first, bool energy, int grid_main,
+                                   const StepStreams &ss);
+cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st);
+cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st);
+cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st);
+cudaError_t launch_energy_post_batch(const BatchDev &b, cudaStream_t st);
+cudaError_t launch_check_finite_batch(const BatchDev &b, cudaStream_t st);
 
 // track modes
 enum : int { TRACK_STEP = 0, TRACK_PRECRACK = 1, TRACK_DEBUG = 2 };

@@ -33,7 +33,7 @@ __device__ double block_sum(double v) {
   return r;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(TB) k_energy_pre(DevState d) {
+__device__ __forceinline__ void energy_pre(const DevState &d) {
   Counters *c = d.cnt;
   int rec = c->n_rec;
   if (rec >= d.rec_cap) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(TB) k_energy_pre(DevState d) {
   }
 }
 
-__global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
+__device__ __forceinline__ void energy_post(const DevState &d, int nparts) {
   Counters *c = d.cnt;
   int rec = c->n_rec;
   if (rec >= d.rec_cap) return;
@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
   }
 }
 
-__global__ void k_check_finite(DevState d, int cur) {
+__device__ __forceinline__ void check_finite(const DevState &d, VBlk vb, int cur) {
   int n = d.g.nn + d.cnt->n_ph;
   bool bad = false;
-  for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
+  for (int N = vb.x * blockDim.x + threadIdx.x; N < n; N += vb.gx * blockDim.x) {
     double a, b, v, w;
     if (d.precision == 1) {
       const float4 U = d.u4[cur][N];
@@ -98,6 +98,45 @@ __global__ void k_check_finite(DevState d, int cur) {
     if (!isfinite(a) || !isfinite(b) || !isfinite(v) || !isfinite(w)) bad = true;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&d.cnt->status, STAT_NONFINITE);
+}
+
+__global__ void __launch_bounds__(TB) k_energy_pre(DevState d) { energy_pre(d); }
+
+__global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
+  energy_post(d, nparts);
+}
+
+__global__ void k_check_finite(DevState d, int cur) { check_finite(d, hw_vblk(), cur); }
+
+// batched counterparts: one CTA per member (energies), work list (check)
+__global__ void __launch_bounds__(TB) k_energy_pre_batch(BatchDev b) {
+  const int n = *b.bstep;
+  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
+    const DevState &d = b.ds[s];
+    if (!member_active(d, n)) continue;
+    energy_pre(d);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(TB) k_energy_post_batch(BatchDev b) {
+  const int n = *b.bstep;
+  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
+    const DevState &d = b.ds[s];
+    if (!member_active(d, n)) continue;
+    energy_post(d, b.nparts[s]);
+    __syncthreads();
+  }
+}
+
+// the members' last states: runs after the steps, whatever the batch step
+__global__ void k_check_finite_batch(BatchDev b) {
+  for (int w = blockIdx.x; w < b.n_fin; w += gridDim.x) {
+    const int4 it = b.w_fin[w];
+    const DevState &d = b.ds[it.x];
+    check_finite(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, d.cnt->step));
+    __syncthreads();
+  }
 }
 
 __global__ void k_f32_to_f64(DevState d, int cur, double *ux, double *uy, double *vx, double *vy,
@@ -149,8 +188,25 @@ cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int grid_finite(const DevState &d) { return grid_for(d.ncap, 256, 1216); }
+
 cudaError_t launch_check_finite(const DevState &d, int cur, cudaStream_t st) {
-  k_check_finite<<<grid_for(d.ncap, 256, 1216), 256, 0, st>>>(d, cur);
+  k_check_finite<<<grid_finite(d), 256, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st) {
+  k_energy_pre_batch<<<b.n < 1216 ? b.n : 1216, TB, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_post_batch(const BatchDev &b, cudaStream_t st) {
+  k_energy_post_batch<<<b.n < 1216 ? b.n : 1216, TB, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite_batch(const BatchDev &b, cudaStream_t st) {
+  k_check_finite_batch<<<grid_for(b.n_fin, 1, 1216), 256, 0, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -89,10 +89,10 @@ __device__ __noinline__ void recheck64(const DevState &d, const float4 *u, int e
   eval_G64(d, U, e, k0, G);
 }
 
-__global__ void k_eval32(DevState d, int cur) {
+__device__ __forceinline__ void eval32(const DevState &d, VBlk vb, int cur) {
   const int n = d.cnt->n_S;
   const U32x2 U{d.u4[cur]};
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  for (int base = vb.x * blockDim.x; base < n; base += vb.gx * blockDim.x) {
     int i = base + threadIdx.x;
     bool has = false;
     int key = 0, edge = 0, kk = -1;
@@ -127,6 +127,18 @@ __global__ void k_eval32(DevState d, int cur) {
   }
 }
 
+__global__ void k_eval32(DevState d, int cur) { eval32(d, hw_vblk(), cur); }
+
+__global__ void k_eval32_batch(BatchDev b) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_eval; w += gridDim.x) {
+    const int4 it = b.w_eval[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    eval32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n));
+  }
+}
+
 int grid_for(int n, int block, int maxb) {
   int b = (n + block - 1) / block;
   return b < 1 ? 1 : (b > maxb ? maxb : b);
@@ -134,8 +146,15 @@ int grid_for(int n, int block, int maxb) {
 
 }  // namespace
 
+int grid_eval(const DevState &d) { return grid_for(d.list_cap, 256, 1216); }
+
 cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st) {
-  k_eval32<<<grid_for(d.list_cap, 256, 1216), 256, 0, st>>>(d, cur);
+  k_eval32<<<grid_eval(d), 256, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval32_batch(const BatchDev &b, cudaStream_t st) {
+  k_eval32_batch<<<grid_for(b.n_eval, 1, 1216), 256, 0, st>>>(b);
   return cudaGetLastError();
 }
 

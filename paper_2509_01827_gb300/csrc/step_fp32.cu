@@ -129,13 +129,14 @@ __device__ __forceinline__ void update_plain(const DevState &d, int N, int cur, 
 
 // ------------------------------------------------------------------ pieces
 // Piece forces of split elements: own strain at each edge point, FP32.
-__global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
+__device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
+                                         int part_off) {
   const int n = 2 * d.cnt->n_ck;
   const Geo &g = d.g;
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
   double se = 0.0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+  for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int c = t >> 1, p = t & 1;
     float xh[4], xl[4], yh[4], yl[4];
 #pragma unroll
@@ -183,12 +184,17 @@ __global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
       se += acc;
     }
   }
-  if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + blockIdx.x));
+  if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + vb.x));
+}
+
+__global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
+  pieces32(d, hw_vblk(), cur, energy, part_off);
 }
 
 // -------------------------------------------------------------- main tile
-// One CTA of 32 x 8 threads owns a tile of TX x TY = 32 x 16 real nodes
-// (two rows per thread).  Shared memory holds, with a two-node halo:
+// One CTA of 32 x 8 threads owns a tile of TX x TY real nodes, TX = 32 and
+// TY = 8 or 16 (TY / 8 rows per thread).  Shared memory holds, with a
+// two-node halo:
 //   sU  displacement pairs (x.hi, x.lo, y.hi, y.lo) of nodes [i0-2, i0+TX+1] x [j0-2, j0+TY+1]
 //   sD  node differences D(i,j) = (ux(i+1,j)-ux(i,j), uy(i+1,j)-uy(i,j),
 //       ux(i,j+1)-ux(i,j), uy(i,j+1)-uy(i,j)) of nodes [i0-2, i0+TX] x [j0-2, j0+TY],
@@ -198,49 +204,56 @@ __global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
 //   sV  the same for the element right (.a) and left (.b) of vertical edges
 //       v(i,j), i in [i0-1, i0+TX], j in [j0-1, j0+TY)
 // sU is dead once sD is formed and shares its storage with sH.
-constexpr int TX = 32, TY = 16, BX = 32, BY = 8;
-constexpr int UXn = TX + 4, UYn = TY + 4;
-constexpr int DXn = TX + 3, DYn = TY + 3;
-constexpr int EXn = TX + 3, EYn = TY + 3;
-constexpr int HXn = TX + 1, HYn = TY + 2;
-constexpr int VXn = TX + 2, VYn = TY + 1;
+constexpr int TX = 32, BX = 32, BY = 8;
 
-struct SmemA {
-  float4 U[UYn][UXn];
-};
-struct SmemB {
-  float4 Ha[HYn][HXn], Hb[HYn][HXn];
-};
-union SmemMain {
-  SmemA a;
-  SmemB b;
-};
-struct SmemFastH {  // intact tiles: one stress per edge, as (xx, xy) and (yy, xy)
-  float2 P[HYn][HXn], Q[HYn][HXn];
-};
-struct SmemFastV {
-  float2 P[VYn][VXn], Q[VYn][VXn];
-};
-union SmemV {
-  struct {
-    float4 a[VYn][VXn], b[VYn][VXn];
-  } gen;
-  SmemFastV fast;
-};
-struct SmemTile {  // > 48 KB: dynamic shared memory
-  union {
-    SmemMain ab;
-    SmemFastH fh;
-  } u1;
-  float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
-  SmemV v;
-  uint8_t st[EYn][EXn];
+template <int TY>
+struct Tile {
+  static constexpr int RY = TY / BY;  // node rows per thread
+  static constexpr int UXn = TX + 4, UYn = TY + 4;
+  static constexpr int DXn = TX + 3, DYn = TY + 3;
+  static constexpr int EXn = TX + 3, EYn = TY + 3;
+  static constexpr int HXn = TX + 1, HYn = TY + 2;
+  static constexpr int VXn = TX + 2, VYn = TY + 1;
+  struct SmemA {
+    float4 U[UYn][UXn];
+  };
+  struct SmemB {
+    float4 Ha[HYn][HXn], Hb[HYn][HXn];
+  };
+  union SmemMain {
+    SmemA a;
+    SmemB b;
+  };
+  struct SmemFastH {  // intact tiles: one stress per edge, as (xx, xy) and (yy, xy)
+    float2 P[HYn][HXn], Q[HYn][HXn];
+  };
+  struct SmemFastV {
+    float2 P[VYn][VXn], Q[VYn][VXn];
+  };
+  union SmemV {
+    struct {
+      float4 a[VYn][VXn], b[VYn][VXn];
+    } gen;
+    SmemFastV fast;
+  };
+  struct Smem {  // > 48 KB for TY = 16: dynamic shared memory
+    union {
+      SmemMain ab;
+      SmemFastH fh;
+    } u1;
+    float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
+    SmemV v;
+    uint8_t st[EYn][EXn];
+  };
 };
 
-template <bool ENERGY>
-__global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int first) {
-  extern __shared__ float4 smem_dyn[];
-  SmemTile &T = *reinterpret_cast<SmemTile *>(smem_dyn);
+template <bool ENERGY, int TY>
+__device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur, int first,
+                                            typename Tile<TY>::Smem &T) {
+  using C = Tile<TY>;
+  constexpr int RY = C::RY, UXn = C::UXn, UYn = C::UYn, DXn = C::DXn, DYn = C::DYn;
+  constexpr int EXn = C::EXn, EYn = C::EYn, HXn = C::HXn, HYn = C::HYn, VXn = C::VXn,
+                VYn = C::VYn;
   float4 (*sU)[UXn] = T.u1.ab.a.U;
   float4 (*sHa)[HXn] = T.u1.ab.b.Ha, (*sHb)[HXn] = T.u1.ab.b.Hb;
   float2 (*fHP)[HXn] = T.u1.fh.P, (*fHQ)[HXn] = T.u1.fh.Q;
@@ -251,17 +264,17 @@ __global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int 
 
   const Geo &g = d.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = vb.x * TX, j0 = vb.y * TY;
   const int stride = g.nx + 1;
   const float4 *__restrict__ u4 = d.u4[cur];
 
-  // own nodes (i, j0+ty) and (i, j0+ty+8): issue their loads first
+  // own nodes (i, j0+ty+8r): issue their loads first
   const int i = i0 + tx;
-  float2 own_v[2];
-  float own_mi[2];
-  int own_nf[2];
+  float2 own_v[RY];
+  float own_mi[RY];
+  int own_nf[RY];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < RY; ++r) {
     const int j = j0 + ty + r * BY;
     if (i <= g.nx && j <= g.ny) {
       const int N = j * stride + i;
@@ -313,9 +326,9 @@ __global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int 
   }
   const bool general = __syncthreads_or(any_open) != 0;
   // own displacement pairs, needed by the update after sU is overwritten
-  float4 own_u[2];
-  own_u[0] = sU[ty + 2][tx + 2];
-  own_u[1] = sU[ty + BY + 2][tx + 2];
+  float4 own_u[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) own_u[r] = sU[ty + r * BY + 2][tx + 2];
   const int tid = tx + ty * BX;
   constexpr int NTH = BX * BY;
   for (int q = tid; q < DXn * DYn; q += NTH) {
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int 
   const float dt = m.dtf;
   const float dtv = first ? 0.5f * dt : dt;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < RY; ++r) {
     const int j = j0 + ty + r * BY;
     if (i > g.nx || j > g.ny) continue;
     // edge arrays: edge (i', j') at [j' - (j0-1)][i' - (i0-1)]
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int 
       fy = (2.f * rx) * (H1.y - H2.y) + hy2 * ((Hd0.x + Hd1.x) - (Hu0.x + Hu1.x)) +
            (2.f * ry) * (V1.x - V2.x) + hx2 * ((Vl0.y + Vl1.y) - (Vr0.y + Vr1.y));
     } else {
-          const float4 A1 = sHa[cj][ci - 1], B1 = sHb[cj][ci - 1];  // h(i-1, j): N right node
+      const float4 A1 = sHa[cj][ci - 1], B1 = sHb[cj][ci - 1];  // h(i-1, j): N right node
       const float4 A2 = sHa[cj][ci], B2 = sHb[cj][ci];          // h(i, j):   N left node
       fx = rx * ((A1.x + B1.x) - (A2.x + B2.x)) + hy2 * ((B1.z - A1.z) + (B2.z - A2.z));
       fy = rx * ((A1.z + B1.z) - (A2.z + B2.z)) + hy2 * ((B1.y - A1.y) + (B2.y - A2.y));
@@ -522,19 +535,25 @@ __global__ void __launch_bounds__(BX * BY, 3) k_main32(DevState d, int cur, int 
     else
       update_plain(d, N, cur, dtv, dt, fx, fy, own_u[r], own_v[r], own_mi[r]);
   }
-  if (ENERGY) {
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum2(ke, se, d.e_part + 2 * b);
-  }
+  if (ENERGY) block_sum2(ke, se, d.e_part + 2 * (vb.y * vb.gx + vb.x));
+}
+
+template <bool ENERGY, int TY>
+__global__ void __launch_bounds__(BX * BY, TY == 8 ? 4 : 3) k_main32(DevState d, int cur,
+                                                                      int first) {
+  extern __shared__ float4 smem_dyn[];
+  main32_tile<ENERGY, TY>(d, hw_vblk(), cur, first,
+                          *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn));
 }
 
 // ---------------------------------------------------------------- phantoms
-__global__ void k_phantom32(DevState d, int cur, int first, int energy, int part_off) {
+__device__ __forceinline__ void phantom32(const DevState &d, VBlk vb, int cur, int first,
+                                          int energy, int part_off) {
   const int n = d.cnt->n_ph;
   double ke = 0.0;
   const float dt = d.mat.dtf;
   const float dtv = first ? 0.5f * dt : dt;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+  for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
     int nu = d.ph_nuser[t];
     float fx = 0.f, fy = 0.f;
@@ -550,7 +569,52 @@ __global__ void k_phantom32(DevState d, int cur, int first, int energy, int part
     else
       update_plain(d, N, cur, dtv, dt, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N]);
   }
-  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + blockIdx.x));
+  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + vb.x));
+}
+
+__global__ void k_phantom32(DevState d, int cur, int first, int energy, int part_off) {
+  phantom32(d, hw_vblk(), cur, first, energy, part_off);
+}
+
+// ---------------------------------------------------------------- batched
+// One launch per kernel kind for every member of a batch.  The grids are
+// persistent: blocks walk the work list with a stride of the grid size.
+// 1-D items are (member, block, energy-partial offset, member's grid size).
+template <bool ENERGY, int TY>
+__global__ void __launch_bounds__(BX * BY, TY == 8 ? 4 : 3) k_main32_batch(BatchDev b,
+                                                                            int first) {
+  extern __shared__ float4 smem_dyn[];
+  auto &T = *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn);
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_main; w += gridDim.x) {
+    const int4 it = b.w_main[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    main32_tile<ENERGY, TY>(d, item_vblk(it), member_cur(d, n), first, T);
+    __syncthreads();
+  }
+}
+
+__global__ void k_pieces32_batch(BatchDev b, int energy) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_pieces; w += gridDim.x) {
+    const int4 it = b.w_pieces[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    pieces32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), energy, it.z);
+    __syncthreads();
+  }
+}
+
+__global__ void k_phantom32_batch(BatchDev b, int first, int energy) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_ph; w += gridDim.x) {
+    const int4 it = b.w_ph[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    phantom32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), first, energy, it.z);
+    __syncthreads();
+  }
 }
 
 int grid_for(int n, int block, int maxb) {
@@ -558,35 +622,67 @@ int grid_for(int n, int block, int maxb) {
   return b < 1 ? 1 : (b > maxb ? maxb : b);
 }
 
+template <bool ENERGY, int TY>
+cudaError_t set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(k_main32<ENERGY, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(typename Tile<TY>::Smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_main32_batch<ENERGY, TY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(typename Tile<TY>::Smem));
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t set_all_smem_attrs() {
+  cudaError_t e;
+  if ((e = set_smem_attr<true, 16>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<false, 16>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<true, 8>()) != cudaSuccess) return e;
+  return set_smem_attr<false, 8>();
+}
+
 }  // namespace
 
 cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_eval32_batch(const BatchDev &b, cudaStream_t st);
 
-int tiles_fp32(const DevState &d) {
-  return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + TY - 1) / TY);
+int tiles_fp32(const DevState &d, int tile_rows) {
+  return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + tile_rows - 1) / tile_rows);
 }
 
-int energy_parts_fp32(const DevState &d) { return tiles_fp32(d) + 2 * 304 + 8; }
+// energy partials: tiles of the smallest tile height first, then pieces and
+// phantom blocks (at most 304 each)
+int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + 2 * 304 + 8; }
+
+int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 304); }
+int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 304); }
+
+// energy partials one FP32 step writes with the given tile height
+int energy_parts_step_fp32(const DevState &d, int tile_rows) {
+  return tiles_fp32(d, tile_rows) + grid_pieces(d) + grid_phantoms(d);
+}
 
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
                              const StepStreams &ss, cudaEvent_t *marks) {
-  const dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
+  constexpr int TYs = 16;  // tile height of a mesh stepped alone
+  const dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TYs - 1) / TYs);
   const dim3 block(BX, BY);
   const int tiles = grid.x * grid.y;  // energy partials of the tiles come first
-  int gp = grid_for(2 * d.ck_cap, 256, 304);
-  int gph = grid_for(d.ph_cap, 256, 304);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_main32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SmemTile));
-    cudaFuncSetAttribute(k_main32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SmemTile));
-    attr = true;
-  }
+  const int gp = grid_pieces(d);
+  const int gph = grid_phantoms(d);
+  cudaError_t e = set_all_smem_attrs();
+  if (e != cudaSuccess) return e;
+  constexpr size_t smem = sizeof(Tile<TYs>::Smem);
   cudaStream_t st = ss.main;
   auto main_kernel = [&](cudaStream_t s) {
-    if (energy) k_main32<true><<<grid, block, sizeof(SmemTile), s>>>(d, cur, first ? 1 : 0);
-    else k_main32<false><<<grid, block, sizeof(SmemTile), s>>>(d, cur, first ? 1 : 0);
+    if (energy) k_main32<true, TYs><<<grid, block, smem, s>>>(d, cur, first ? 1 : 0);
+    else k_main32<false, TYs><<<grid, block, smem, s>>>(d, cur, first ? 1 : 0);
   };
   if (marks) {
     k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
@@ -595,13 +691,13 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
     cudaEventRecord(marks[1], st);
     k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
     cudaEventRecord(marks[2], st);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_eval32(d, cur, st);
   }
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
-  cudaError_t e = launch_eval32(d, cur, ss.aux2);
+  e = launch_eval32(d, cur, ss.aux2);
   if (e != cudaSuccess) return e;
   e = launch_select(d, TRACK_STEP, ss.aux2);
   if (e != cudaSuccess) return e;
@@ -610,6 +706,43 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
   cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
   main_kernel(st);
+  cudaEventRecord(ss.join1, ss.aux1);
+  cudaEventRecord(ss.join2, ss.aux2);
+  cudaStreamWaitEvent(st, ss.join1, 0);
+  cudaStreamWaitEvent(st, ss.join2, 0);
+  return cudaGetLastError();
+}
+
+// The same fork/join as launch_step_fp32, one launch per kernel kind for all
+// members of the batch.
+cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, int tile_rows,
+                                   int grid_main, const StepStreams &ss) {
+  cudaError_t e = set_all_smem_attrs();
+  if (e != cudaSuccess) return e;
+  const dim3 block(BX, BY);
+  const int gm = grid_main < 1 ? 1 : grid_main;
+  const int gp = grid_for(b.n_pieces, 1, 1216), gph = grid_for(b.n_ph, 1, 1216);
+  cudaStream_t st = ss.main;
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  e = launch_eval32_batch(b, ss.aux2);
+  if (e != cudaSuccess) return e;
+  e = launch_select_batch(b, ss.aux2);
+  if (e != cudaSuccess) return e;
+  k_pieces32_batch<<<gp, 256, 0, st>>>(b, energy ? 1 : 0);
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_phantom32_batch<<<gph, 256, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
+  const int f = first ? 1 : 0;
+  if (tile_rows == 8) {
+    constexpr size_t sm = sizeof(Tile<8>::Smem);
+    if (energy) k_main32_batch<true, 8><<<gm, block, sm, st>>>(b, f);
+    else k_main32_batch<false, 8><<<gm, block, sm, st>>>(b, f);
+  } else {
+    constexpr size_t sm = sizeof(Tile<16>::Smem);
+    if (energy) k_main32_batch<true, 16><<<gm, block, sm, st>>>(b, f);
+    else k_main32_batch<false, 16><<<gm, block, sm, st>>>(b, f);
+  }
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
   cudaStreamWaitEvent(st, ss.join1, 0);

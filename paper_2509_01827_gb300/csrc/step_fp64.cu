@@ -101,10 +101,11 @@ __device__ __forceinline__ void load_factors(const DevState &d, double &lamN, do
 }
 
 // ------------------------------------------------------------------ pieces
-__global__ void k_pieces64(DevState d, int cur, int energy, int part_off) {
+__device__ __forceinline__ void pieces64(const DevState &d, VBlk vb, int cur, int energy,
+                                         int part_off) {
   const int n = 2 * d.cnt->n_ck;
   double se = 0.0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+  for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int c = t >> 1, p = t & 1;
     double u[4], v[4];
 #pragma unroll
@@ -133,11 +134,16 @@ __global__ void k_pieces64(DevState d, int cur, int energy, int part_off) {
       se += acc;
     }
   }
-  if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + blockIdx.x));
+  if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + vb.x));
+}
+
+__global__ void k_pieces64(DevState d, int cur, int energy, int part_off) {
+  pieces64(d, hw_vblk(), cur, energy, part_off);
 }
 
 // -------------------------------------------------------------- main tile
-__global__ void __launch_bounds__(NT) k_main64(DevState d, int cur, int first, int energy) {
+__device__ __forceinline__ void main64_tile(const DevState &d, VBlk vb, int cur, int first,
+                                            int energy) {
   __shared__ double sux[UYn][UXn], suy[UYn][UXn];
   __shared__ uint8_t sst[EYn][EXn];
   // stress (3) and eps.sigma (1) used by the element below/left (lo) and
@@ -146,7 +152,7 @@ __global__ void __launch_bounds__(NT) k_main64(DevState d, int cur, int first, i
   __shared__ double vlo[VYn][VXn][4], vhi[VYn][VXn][4];
 
   const Geo &g = d.g;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = vb.x * TX, j0 = vb.y * TY;
   const int tid = threadIdx.x;
   const double *uxc = d.ux[cur], *uyc = d.uy[cur];
 
@@ -291,18 +297,23 @@ __global__ void __launch_bounds__(NT) k_main64(DevState d, int cur, int first, i
     }
   }
   if (energy) {
-    int b = blockIdx.y * gridDim.x + blockIdx.x;
+    int b = vb.y * vb.gx + vb.x;
     block_sum2(ke, se, d.e_part + 2 * b);
   }
 }
 
+__global__ void __launch_bounds__(NT) k_main64(DevState d, int cur, int first, int energy) {
+  main64_tile(d, hw_vblk(), cur, first, energy);
+}
+
 // ---------------------------------------------------------------- phantoms
-__global__ void k_phantom64(DevState d, int cur, int first, int energy, int part_off) {
+__device__ __forceinline__ void phantom64(const DevState &d, VBlk vb, int cur, int first,
+                                          int energy, int part_off) {
   const int n = d.cnt->n_ph;
   double ke = 0.0;
   double lamN, lamD;
   load_factors(d, lamN, lamD);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+  for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
     int nu = d.ph_nuser[t];
     double fx = 0.0, fy = 0.0;
@@ -315,14 +326,18 @@ __global__ void k_phantom64(DevState d, int cur, int first, int energy, int part
     }
     ke += update_node(d, N, cur, first != 0, fx, fy, 0, lamN, lamD);
   }
-  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + blockIdx.x));
+  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + vb.x));
 }
 
-__global__ void k_eval64(DevState d, int cur) {
+__global__ void k_phantom64(DevState d, int cur, int first, int energy, int part_off) {
+  phantom64(d, hw_vblk(), cur, first, energy, part_off);
+}
+
+__device__ __forceinline__ void eval64(const DevState &d, VBlk vb, int cur) {
   const int n = d.cnt->n_S;
   const U64 U{d.ux[cur], d.uy[cur]};
   // whole warps iterate together so that the ballot sees every lane
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  for (int base = vb.x * blockDim.x; base < n; base += vb.gx * blockDim.x) {
     int i = base + threadIdx.x;
     bool has = false;
     int key = 0, edge = 0, kk = -1;
@@ -344,6 +359,55 @@ __global__ void k_eval64(DevState d, int cur) {
       }
     }
     append_proposal(d, has, key, edge, kk, Gk);
+  }
+}
+
+__global__ void k_eval64(DevState d, int cur) { eval64(d, hw_vblk(), cur); }
+
+// ---------------------------------------------------------------- batched
+// One launch per kernel kind for every member of a batch (persistent grids
+// walking the work lists; 1-D items are (member, block, energy-partial
+// offset, member's grid size)).
+__global__ void __launch_bounds__(NT) k_main64_batch(BatchDev b, int first, int energy) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_main; w += gridDim.x) {
+    const int4 it = b.w_main[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    main64_tile(d, item_vblk(it), member_cur(d, n), first, energy);
+    __syncthreads();
+  }
+}
+
+__global__ void k_pieces64_batch(BatchDev b, int energy) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_pieces; w += gridDim.x) {
+    const int4 it = b.w_pieces[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    pieces64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), energy, it.z);
+    __syncthreads();
+  }
+}
+
+__global__ void k_phantom64_batch(BatchDev b, int first, int energy) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_ph; w += gridDim.x) {
+    const int4 it = b.w_ph[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    phantom64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), first, energy, it.z);
+    __syncthreads();
+  }
+}
+
+__global__ void k_eval64_batch(BatchDev b) {
+  const int n = *b.bstep;
+  for (int w = blockIdx.x; w < b.n_eval; w += gridDim.x) {
+    const int4 it = b.w_eval[w];
+    const DevState &d = b.ds[it.x];
+    if (!member_active(d, n)) continue;
+    eval64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n));
   }
 }
 
@@ -373,10 +437,20 @@ int grid_for(int n, int block, int maxb) {
 
 int energy_parts_fp32(const DevState &d);
 
+int tiles_fp64(const DevState &d) {
+  return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + TY - 1) / TY);
+}
+
 int energy_parts_needed(const DevState &d) {
   if (d.precision == 1) return energy_parts_fp32(d);
-  int tiles = ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + TY - 1) / TY);
-  return tiles + 2 * 304 + 8;
+  return tiles_fp64(d) + 2 * 304 + 8;
+}
+
+int energy_parts_step_fp32(const DevState &d, int tile_rows);
+
+int energy_parts_step(const DevState &d) {
+  if (d.precision == 1) return energy_parts_step_fp32(d, 16);
+  return tiles_fp64(d) + grid_pieces(d) + grid_phantoms(d);
 }
 
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st) {
@@ -388,9 +462,9 @@ cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy
                              const StepStreams &ss, cudaEvent_t *marks) {
   dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TY - 1) / TY);
   int tiles = grid.x * grid.y;
-  int gp = grid_for(2 * d.ck_cap, 256, 304);
-  int gph = grid_for(d.ph_cap, 256, 304);
-  const int ge = grid_for(d.list_cap, 256, 1216);
+  int gp = grid_pieces(d);
+  int gph = grid_phantoms(d);
+  const int ge = grid_eval(d);
   cudaStream_t st = ss.main;
   if (marks) {
     k_pieces64<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
@@ -411,6 +485,31 @@ cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy
   cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   k_phantom64<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
   k_main64<<<grid, NT, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0);
+  cudaEventRecord(ss.join1, ss.aux1);
+  cudaEventRecord(ss.join2, ss.aux2);
+  cudaStreamWaitEvent(st, ss.join1, 0);
+  cudaStreamWaitEvent(st, ss.join2, 0);
+  return cudaGetLastError();
+}
+
+// The same fork/join as launch_step_fp64, one launch per kernel kind for all
+// members of the batch.
+cudaError_t launch_step_fp64_batch(const BatchDev &b, bool first, bool energy, int grid_main,
+                                   const StepStreams &ss) {
+  const int gm = grid_main < 1 ? 1 : grid_main;
+  const int gp = grid_for(b.n_pieces, 1, 1216), gph = grid_for(b.n_ph, 1, 1216);
+  const int ge = grid_for(b.n_eval, 1, 1216);
+  cudaStream_t st = ss.main;
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  k_eval64_batch<<<ge, 256, 0, ss.aux2>>>(b);
+  cudaError_t e = launch_select_batch(b, ss.aux2);
+  if (e != cudaSuccess) return e;
+  k_pieces64_batch<<<gp, 256, 0, st>>>(b, energy ? 1 : 0);
+  cudaEventRecord(ss.fork, st);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_phantom64_batch<<<gph, 256, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
+  k_main64_batch<<<gm, NT, 0, st>>>(b, first ? 1 : 0, energy ? 1 : 0);
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
   cudaStreamWaitEvent(st, ss.join1, 0);

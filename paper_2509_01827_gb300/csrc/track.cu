@@ -235,8 +235,8 @@ __device__ void compact_surface(const DevState &d) {
 // split plan (sides, phantoms to reuse, area fractions, split-table slot,
 // first new phantom id, surface-list appends and tombstones) and the
 // counters the apply kernel commits.
-__global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
-  extern __shared__ unsigned long long smem[];
+__device__ __forceinline__ void select_plan(const DevState &d, int mode,
+                                            unsigned long long *smem) {
   unsigned long long *sk = smem;                    // [SORT_CAP]
   int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP]
   __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done;
@@ -450,22 +450,40 @@ __global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
     cnt->pend_nck = s_nck;
     cnt->pend_nS = s_nS;
     cnt->pend_dead = s_dead;
+    cnt->pend_step = cnt->step;
     cnt->n_prop_last = cnt->n_prop;
     cnt->n_prop = 0;
+  }
+}
+
+__global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
+  extern __shared__ unsigned long long smem[];
+  select_plan(d, mode, smem);
+}
+
+// one CTA per member of a batch
+__global__ void __launch_bounds__(TB) k_select_batch(BatchDev b) {
+  extern __shared__ unsigned long long smem[];
+  const int n = *b.bstep;
+  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
+    const DevState &d = b.ds[s];
+    if (!member_active(d, n)) continue;
+    select_plan(d, TRACK_STEP, smem);
+    __syncthreads();
   }
 }
 
 // Split writes: eight threads per planned winner (lanes 0-3: local nodes,
 // 4-7: their phantoms / the split record), winners in parallel.  Runs after
 // the node updates of the step, so new phantoms copy u^{n+1} and v^{n+1/2}.
-__global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+__device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_next, int mode) {
   Counters *cnt = d.cnt;
   const Geo &g = d.g;
   const int nw = cnt->pend_nwin;
-  const int step = cnt->step;
+  const int step = cnt->pend_step;
   const int lane32 = threadIdx.x & 31, lane = lane32 & 7, grp = lane32 >> 3;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int warp = (vb.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (vb.gx * blockDim.x) >> 5;
   for (int wb = warp * 4; wb < nw; wb += nwarps * 4) {
     const int w = wb + grp;
     const bool act = w < nw;
@@ -596,13 +614,37 @@ __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mod
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  // the commit changes no value that another block of this kernel reads
+  if (vb.x == 0 && threadIdx.x == 0) {
     cnt->n_ph = cnt->pend_nph;
     cnt->n_ck = cnt->pend_nck;
     cnt->n_S = cnt->pend_nS;
     cnt->n_dead += cnt->pend_dead;
     cnt->n_win_last = nw;
-    if (mode == TRACK_STEP) cnt->step = cnt->step + 1;
+    if (mode == TRACK_STEP) cnt->step = step + 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+  apply_plan(d, hw_vblk(), cur_next, mode);
+}
+
+// One CTA per member of a batch; the last CTA to finish advances the batch
+// step (every CTA has read it before it arrives).
+__global__ void __launch_bounds__(256) k_apply_batch(BatchDev b) {
+  const int n = *b.bstep;
+  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
+    const DevState &d = b.ds[s];
+    if (!member_active(d, n)) continue;
+    apply_plan(d, VBlk{0, 0, 1, 1}, member_cur(d, n) ^ 1, TRACK_STEP);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(b.arrive, 1) == (int)gridDim.x - 1) {
+      *b.arrive = 0;
+      *b.bstep = n + 1;
+    }
   }
 }
 
@@ -685,6 +727,24 @@ cudaError_t launch_build_surface(const DevState &d, cudaStream_t st) {
 
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st) {
   k_surface_info<<<256, 256, 0, st>>>(d, out3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st) {
+  size_t sm = SORT_CAP * sizeof(unsigned long long) + SORT_CAP * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_select_batch,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_select_batch<<<b.n < 304 ? b.n : 304, TB, sm, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st) {
+  k_apply_batch<<<b.n < 1216 ? b.n : 1216, 256, 0, st>>>(b);
   return cudaGetLastError();
 }
 

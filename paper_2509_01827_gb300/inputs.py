@@ -244,8 +244,8 @@ def fragmentation(n=2048, L=0.1, r=0.005, mode="neumann", p0=50e6, v0=2.0, seed=
     ne = n * n
     prob = Problem(name=name or f"fragmentation_{n}x{n}_{mode}", nx=n, ny=n, hx=h, hy=h,
                    material=mat, active=active, gc=gc, bcs=bcs, energy_every=energy_every,
-                   phantom_cap=phantom_cap or max(8192, ne // 16),
-                   crack_cap=crack_cap or max(8192, ne // 16))
+                   phantom_cap=phantom_cap or max(8192, ne // 4),
+                   crack_cap=crack_cap or max(8192, ne // 8))
     if steps is None:
         steps = int(math.ceil(t_end / estimate_dt(prob)))
     prob.steps = steps

@@ -1,0 +1,135 @@
+"""Batched stepping of independent meshes (needs a GPU).
+
+A batch runs one launch per kernel kind for all its members.  Each member
+must end exactly where it ends when stepped alone: bit-identical in FP64
+(fields, masses, cracks, energy records) and, with the same tile height, in
+the FP32-mixed mode too; members stop at their own step limits."""
+import numpy as np
+import pytest
+
+from paper_2509_01827_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_01827_gb300 import build
+    build.build()
+
+
+def _specimens():
+    """Three notched plates of different sizes, notches and tractions."""
+    out = []
+    for (nx, ny, notch, trac) in [(60, 24, 0.025, 2.5e6), (100, 40, 0.05, 1e6), (37, 19, 0.02, 3e6)]:
+        p = inputs.notched_plate(nx, ny, notch_len=notch, traction=trac, steps=0,
+                                 phantom_cap=4000, crack_cap=2000)
+        p.energy_every = 10
+        out.append(p)
+    return out
+
+
+def _state(s):
+    n = s.nodes()
+    c = s.cracks()
+    e = s.energy()
+    return n, c, e
+
+
+def _assert_same(a, b):
+    (na, ca, ea), (nb, cb, eb) = a, b
+    for k in ("ux", "uy", "vx", "vy", "m"):
+        np.testing.assert_array_equal(na[k], nb[k], err_msg=k)
+    for k in ("elem", "ka", "kb", "step", "ud", "nodes"):
+        np.testing.assert_array_equal(ca[k], cb[k], err_msg=k)
+    for k in ("step", "KE", "SE", "W_ext", "W_dir", "U_d"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_solo_runs(precision):
+    from paper_2509_01827_gb300.cem import Batch, Solver
+    probs = _specimens()
+    limits = [250, 400, 180]
+    solo = []
+    for p, lim in zip(probs, limits):
+        s = Solver(p, precision=precision)
+        s.step(lim)
+        solo.append(_state(s))
+        s.close()
+    members = [Solver(p, precision=precision) for p in probs]
+    b = Batch(members, step_end=limits)
+    b.step(150)
+    b.step(300)  # beyond every limit: members stop at theirs
+    assert b.counts()["step"] == 450
+    for m, lim, ref in zip(members, limits, solo):
+        assert m.counts()["step"] == lim
+        _assert_same(_state(m), ref)
+    assert sum(len(r[1]["elem"]) for r in solo) > 3 * 50  # the notches grew
+    b.close()
+
+
+def test_fp32_tile_rows_8_within_tolerance():
+    """Tile height 8 groups some FP32 sums differently: the fields agree with
+    the tile-16 run to the FP32-mixed tolerance before initiation."""
+    from paper_2509_01827_gb300.cem import CEM_FP32_MIXED, Batch, Solver
+    probs = _specimens()
+    runs = []
+    for rows in (16, 8):
+        members = [Solver(p, precision=CEM_FP32_MIXED) for p in probs]
+        b = Batch(members)
+        b.set_config(rows, 152)
+        b.step(120)
+        runs.append([m.nodes() for m in members])
+        b.close()
+    for a, c in zip(*runs):
+        for k in ("ux", "uy"):
+            assert np.max(np.abs(a[k] - c[k])) <= 1e-5 * np.max(np.abs(a[k]))
+
+
+def test_autotune_keeps_results_fp64():
+    from paper_2509_01827_gb300.cem import Batch, Solver
+    probs = _specimens()
+    members = [Solver(p) for p in probs]
+    b = Batch(members)
+    rows, grid = b.autotune(3)
+    assert rows in (8, 16) and grid >= 1
+    done = b.counts()["step"]
+    assert done == 4 * (1 + 3)  # FP64: four grid candidates, 1 untimed + 3 timed steps each
+    b.step(100)
+    total = b.counts()["step"]
+    for p, m in zip(probs, members):
+        s = Solver(p)
+        s.step(total)
+        _assert_same(_state(m), _state(s))
+        s.close()
+    b.close()
+
+
+def test_batch_rules():
+    from paper_2509_01827_gb300.cem import Batch, CemError, Solver, CEM_ERR_STATE, CEM_ERR_ARG
+    probs = _specimens()
+    members = [Solver(p) for p in probs]
+    b = Batch(members)
+    with pytest.raises(CemError) as ei:
+        members[0].step(1)  # a member is stepped by its batch
+    assert ei.value.code == CEM_ERR_STATE
+    from paper_2509_01827_gb300 import cem
+    with pytest.raises(CemError) as ei:
+        cem.cem_get_cracks(b.h, 4)  # getters read members
+    assert ei.value.code == CEM_ERR_STATE
+    with pytest.raises(CemError) as ei:
+        Batch(members[:1])  # already in a batch
+    assert ei.value.code == CEM_ERR_STATE
+    b.step(5)
+    members[1].close()  # detaches it; the batch refuses to step
+    with pytest.raises(CemError) as ei:
+        b.step(1)
+    assert ei.value.code == CEM_ERR_STATE
+    b.close()
+    members[0].step(1)  # free again once the batch is gone
+    other = Solver(probs[0])
+    other.step(1)
+    with pytest.raises(CemError) as ei:
+        Batch([members[0], other])  # different steps
+    assert ei.value.code == CEM_ERR_ARG
