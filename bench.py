@@ -15,6 +15,12 @@ update, surface evaluation, multi-tip tracking, and an energy record every
   method has), timed on a bounded sample on this host.
 Multi-GPU (torchrun): one independent replica per GPU (the path does not
 shard across GPUs); value = all ranks' element-updates / max rank time.
+
+--workload specimens_64: 64 notched plates from 100 x 40 to 400 x 160 (seed
+  1827), each run to 80 us with its own time step, stepped together as one
+  batch (one launch per kernel kind for all specimens); the launch
+  configuration comes from the autotuner on a separate copy of the batch.
+  value = sum over specimens of active elements * steps / batch time.
 """
 import argparse
 import json
@@ -173,9 +179,11 @@ def run_ours(args, rank, world):
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets ncu select the timed launches
     e0.record(stream)
     sol.step(args.steps)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     time.sleep(0.2)
     clk = clocks.stop()
@@ -276,13 +284,150 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_batch(args, rank, world):
+    """The 64-specimen sweep as one batch (see the module docstring)."""
+    import torch
+    from paper_2509_01827_gb300 import build as _build, inputs
+    from paper_2509_01827_gb300.cem import CEM_FP32_MIXED, CEM_FP64, Batch, Solver
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    prec = CEM_FP32_MIXED if args.precision == "fp32" else CEM_FP64
+    probs = inputs.batch_specimens(64)
+    for p in probs:
+        p.energy_every = 50
+    steps = [p.steps for p in probs]
+    total_updates = sum(p.n_active * n for p, n in zip(probs, steps))
+
+    def make():
+        ms = [Solver(p, precision=prec, device=dev) for p in probs]
+        return ms, Batch(ms, step_end=steps)
+
+    # autotune on a throwaway copy (its timed steps advance that copy)
+    ms_t, bt = make()
+    tile_rows, grid = bt.autotune(max(1, args.autotune_steps))
+    bt.close()
+    for m in ms_t:
+        m.close()
+
+    members, b = make()
+    b.set_config(tile_rows, grid)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    c0 = b.counts()
+    clocks.start()
+    time.sleep(0.3)
+    nrun = max(steps) - args.warmup
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(b._stream)
+    b.step(nrun)
+    e1.record(b._stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    time.sleep(0.2)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    c1 = b.counts()
+    launches = c1["kernel_launches"] - c0["kernel_launches"]
+    timed_updates = sum(p.n_active * max(0, n - args.warmup) for p, n in zip(probs, steps))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * timed_updates / (ms * 1e-3)
+    cracked = c1["n_cracked"]
+    b.close()
+    for m in members:
+        m.close()
+
+    # end to end: a fresh batch, one cem_step(batch, 1) per step from the host
+    members, b = make()
+    b.set_config(tile_rows, grid)
+    ne2e = max(1, min(args.e2e_steps, max(steps)))
+    upd = sum(p.n_active * min(n, ne2e) for p, n in zip(probs, steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        b.step(1)
+    e2e_s = time.perf_counter() - t0
+    b.close()
+    for m in members:
+        m.close()
+    e2e_val = world * upd / e2e_s
+
+    # the same specimens stepped one after another, each alone (a sample)
+    nsolo = min(len(probs), max(1, args.solo_sample))
+    solo_upd, solo_ms = 0, 0.0
+    for p, n in list(zip(probs, steps))[:nsolo]:
+        s = Solver(p, precision=prec, device=dev)
+        s.step(1)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s._stream)
+        s.step(n - 1)
+        f1.record(s._stream)
+        torch.cuda.synchronize()
+        solo_ms += f0.elapsed_time(f1)
+        solo_upd += p.n_active * (n - 1)
+        s.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": nrun, "warmup": args.warmup, "ms_per_step": ms / nrun,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "specimens_64", "specimens": len(probs),
+                   "meshes": "notched plates 100x40 .. 400x160 (s ~ U(1, 4), seed 1827)",
+                   "active_elements_total": sum(p.n_active for p in probs),
+                   "steps_per_specimen": [min(steps), max(steps)],
+                   "element_updates": total_updates, "energy_every": 50,
+                   "precision": args.precision, "tile_rows": tile_rows, "grid_main": grid,
+                   "l2": "state of all specimens about 0.1 GB: close to L2 (129 MB), "
+                         "no flush between steps",
+                   "parallelism": f"batch of 64, replicas x{world}",
+                   "cracked_elements_end": cracked},
+        "roofline": None,
+        "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 20 * len(probs),
+                "d2h_bytes_per_step": 64 * len(probs), "steps": ne2e,
+                "how": "one cem_step(batch, 1) call per step from the host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "solo_sequential": {"value": solo_upd / (solo_ms * 1e-3), "unit": METRIC,
+                            "specimens": nsolo,
+                            "how": "the first specimens stepped alone, one after another"},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(probs[0], args.cpu_budget)
+        line["cpu_baseline"]["sample"] = "specimen 0 only: " + line["cpu_baseline"]["sample"]
+    return line
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
-    prob = make_problem(args.workload)
+    if args.workload == "specimens_64":
+        from paper_2509_01827_gb300 import inputs
+        prob = inputs.batch_specimens(64)[0]
+    else:
+        prob = make_problem(args.workload)
     per = []
-    for _ in range(args.warmup):
-        pass
     t_all = time.perf_counter()
     for _ in range(max(1, args.steps_reference)):
         per.append(time_oracle(prob, args.cpu_budget / max(1, args.steps_reference)))
@@ -317,6 +462,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--steps-reference", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune-steps", type=int, default=5)
+    ap.add_argument("--solo-sample", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the tile kernel, when known")
     args = ap.parse_args()
@@ -328,7 +475,10 @@ def main():
         if world > 1:
             import torch
             torch.distributed.init_process_group("nccl")
-        line = run_ours(args, rank, world)
+        if args.workload == "specimens_64":
+            line = run_batch(args, rank, world)
+        else:
+            line = run_ours(args, rank, world)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()

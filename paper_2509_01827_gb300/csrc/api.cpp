@@ -156,9 +156,8 @@ int local_edge_host(const cem_handle *h, int e, int g) {
   return -1;
 }
 
-cem_status sync_status(cem_handle *h) {
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
-  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+// Status word of the counters mirrored in h->h_cnt.
+cem_status check_status(cem_handle *h) {
   int s = h->h_cnt->status;
   if (s & STAT_CAPACITY)
     return fail(h, CEM_ERR_CAPACITY,
@@ -168,6 +167,12 @@ cem_status sync_status(cem_handle *h) {
   if (s & STAT_NONFINITE) return fail(h, CEM_ERR_NONFINITE, "non-finite displacement or velocity");
   if (s & STAT_TIMEOUT) return fail(h, CEM_ERR_TIMEOUT, "device wait timed out");
   return CEM_OK;
+}
+
+cem_status sync_status(cem_handle *h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return check_status(h);
 }
 
 cem_status upload_loads(cem_handle *h) {
@@ -221,8 +226,10 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
   return e;
 }
 
-// Load factors of steps [h->step, h->step + chunk) into the device table.
-cem_status upload_load_factors(cem_handle *h, int chunk) {
+// Load factors of steps [h->step, h->step + chunk) into the device table,
+// enqueued on stream st (the handle's own stream by default).
+cem_status upload_load_factors(cem_handle *h, int chunk, cudaStream_t st = nullptr) {
+  if (!st) st = h->st;
   const DevState &d = h->d;
   const double dt = d.mat.dt;
   double *lamN = h->h_lam, *lamD = h->h_lam + d.lam_cap;
@@ -233,9 +240,9 @@ cem_status upload_load_factors(cem_handle *h, int chunk) {
   }
   int base = (int)h->step;
   h->h_cnt->lam_base = base;
-  CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN, chunk * 8, cudaMemcpyHostToDevice, h->st));
-  CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD, chunk * 8, cudaMemcpyHostToDevice, h->st));
-  CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &h->h_cnt->lam_base, 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN, chunk * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD, chunk * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &h->h_cnt->lam_base, 4, cudaMemcpyHostToDevice, st));
   // the pinned staging is reused only after the stream has been synchronised
   return CEM_OK;
 }
@@ -999,6 +1006,8 @@ struct BatchPlan {
   size_t dev_bytes = 0;
   cudaGraphExec_t graphs[2] = {nullptr, nullptr};  // [energy]
   std::vector<double> tune_ms;  // autotuner timings, candidate order
+  Counters *d_cnts = nullptr;   // [n] gathered counters (device)
+  Counters *h_cnts = nullptr;   // [n] pinned read-back
 };
 
 namespace {
@@ -1035,7 +1044,9 @@ cem_status batch_upload(cem_handle *b) {
     const int tiles = gx * gy, gp = grid_pieces(d), gph = grid_phantoms(d);
     for (int q = 0; q < gp; ++q) wp.push_back(make_int4(s, q, tiles, gp));
     for (int q = 0; q < gph; ++q) wph.push_back(make_int4(s, q, tiles + gp, gph));
-    const int ge = grid_eval(d), gf = grid_finite(d);
+    // the evaluation has no energy partials: a few virtual blocks per member
+    // walk its list (its length, not its capacity, sets the work)
+    const int ge = std::min(grid_eval(d), 8), gf = grid_finite(d);
     for (int q = 0; q < ge; ++q) we.push_back(make_int4(s, q, 0, ge));
     for (int q = 0; q < gf; ++q) wf.push_back(make_int4(s, q, 0, gf));
     nparts[s] = tiles + gp + gph;
@@ -1128,11 +1139,12 @@ cem_status batch_run(cem_handle *b, int n, cudaEvent_t ev_t0, cudaEvent_t ev_t1)
   int done = 0;
   while (done < n) {
     const int chunk = std::min(n - done, lam_cap);
+    // on the batch stream, ahead of the steps that read them; each member's
+    // pinned staging is reused only after the synchronisation below
     for (cem_handle *m : p->members) {
-      cem_status rc = upload_load_factors(m, chunk);
+      cem_status rc = upload_load_factors(m, chunk, b->st);
       if (rc != CEM_OK) return fail(b, rc, "load factors: %s", m->err.c_str());
     }
-    for (cem_handle *m : p->members) CUDA_TRY(b, cudaStreamSynchronize(m->st));
     for (int q = 0; q < chunk; ++q) {
       const bool energy = p->energy_every > 0 && (p->step % p->energy_every) == 0;
       if (p->step == 0) {
@@ -1159,14 +1171,20 @@ cem_status batch_run(cem_handle *b, int n, cudaEvent_t ev_t0, cudaEvent_t ev_t1)
   return CEM_OK;
 }
 
+// Finiteness check of every member, then one read-back of all counters.
 cem_status batch_finish(cem_handle *b) {
   BatchPlan *p = b->batch;
   CUDA_TRY(b, launch_check_finite_batch(p->bd, b->st));
-  b->launches += 1;
+  CUDA_TRY(b, launch_gather_counters(p->bd, p->d_cnts, b->st));
+  b->launches += 2;
+  const size_t n = p->members.size();
+  CUDA_TRY(b, cudaMemcpyAsync(p->h_cnts, p->d_cnts, n * sizeof(Counters), cudaMemcpyDeviceToHost,
+                              b->st));
   CUDA_TRY(b, cudaStreamSynchronize(b->st));
-  for (size_t s = 0; s < p->members.size(); ++s) {
+  for (size_t s = 0; s < n; ++s) {
     cem_handle *m = p->members[s];
-    cem_status rc = sync_status(m);
+    *m->h_cnt = p->h_cnts[s];
+    cem_status rc = check_status(m);
     if (rc != CEM_OK) return fail(b, rc, "member %d: %s", (int)s, m->err.c_str());
   }
   return CEM_OK;
@@ -1211,7 +1229,9 @@ cem_status batch_counts(cem_handle *b, cem_counts *out) {
 
 void batch_release(cem_handle *b) {
   BatchPlan *p = b->batch;
+  if (b->st) cudaStreamSynchronize(b->st);
   batch_drop_graphs(p);
+  if (p->h_cnts) cudaFreeHost(p->h_cnts);
   for (cem_handle *m : p->members)
     if (m) m->in_batch = nullptr;
   delete p;
@@ -1293,6 +1313,13 @@ cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_
   p->tile_rows = 16;
   p->grid_main = 3 * sms;
   cem_status rc = batch_upload(b);
+  if (rc == CEM_OK) {
+    p->d_cnts = (Counters *)dalloc(b, (size_t)n * sizeof(Counters));
+    if (!p->d_cnts ||
+        cudaHostAlloc((void **)&p->h_cnts, (size_t)n * sizeof(Counters), cudaHostAllocDefault) !=
+            cudaSuccess)
+      rc = fail(b, CEM_ERR_CUDA, "batch counter buffers");
+  }
   if (rc != CEM_OK) {
     g_create_error = b->err;
     cem_mesh_destroy(b);

@@ -222,6 +222,7 @@ cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_energy_post_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_check_finite_batch(const BatchDev &b, cudaStream_t st);
+cudaError_t launch_gather_counters(const BatchDev &b, Counters *out, cudaStream_t st);
 
 // track modes
 enum : int { TRACK_STEP = 0, TRACK_PRECRACK = 1, TRACK_DEBUG = 2 };

@@ -139,6 +139,12 @@ __global__ void k_check_finite_batch(BatchDev b) {
   }
 }
 
+// copies every member's counters into out[n] (one read-back for the batch)
+__global__ void k_gather_counters(BatchDev b, Counters *out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < b.n; s += gridDim.x * blockDim.x)
+    out[s] = *b.ds[s].cnt;
+}
+
 __global__ void k_f32_to_f64(DevState d, int cur, double *ux, double *uy, double *vx, double *vy,
                              int n) {
   for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < n; N += gridDim.x * blockDim.x) {
@@ -202,6 +208,11 @@ cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st) {
 
 cudaError_t launch_energy_post_batch(const BatchDev &b, cudaStream_t st) {
   k_energy_post_batch<<<b.n < 1216 ? b.n : 1216, TB, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_counters(const BatchDev &b, Counters *out, cudaStream_t st) {
+  k_gather_counters<<<grid_for(b.n, 128, 64), 128, 0, st>>>(b, out);
   return cudaGetLastError();
 }
 

@@ -629,14 +629,16 @@ __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mod
   apply_plan(d, hw_vblk(), cur_next, mode);
 }
 
-// One CTA per member of a batch; the last CTA to finish advances the batch
-// step (every CTA has read it before it arrives).
+// APPLY_VB virtual CTAs per member of a batch; the last CTA to finish
+// advances the batch step (every CTA has read it before it arrives).
+constexpr int APPLY_VB = 8;
+
 __global__ void __launch_bounds__(256) k_apply_batch(BatchDev b) {
   const int n = *b.bstep;
-  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
-    const DevState &d = b.ds[s];
+  for (int w = blockIdx.x; w < b.n * APPLY_VB; w += gridDim.x) {
+    const DevState &d = b.ds[w / APPLY_VB];
     if (!member_active(d, n)) continue;
-    apply_plan(d, VBlk{0, 0, 1, 1}, member_cur(d, n) ^ 1, TRACK_STEP);
+    apply_plan(d, VBlk{w % APPLY_VB, 0, APPLY_VB, 1}, member_cur(d, n) ^ 1, TRACK_STEP);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -744,7 +746,8 @@ cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st) {
 }
 
 cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st) {
-  k_apply_batch<<<b.n < 1216 ? b.n : 1216, 256, 0, st>>>(b);
+  const int nb = b.n * APPLY_VB;
+  k_apply_batch<<<nb < 2432 ? nb : 2432, 256, 0, st>>>(b);
   return cudaGetLastError();
 }
 

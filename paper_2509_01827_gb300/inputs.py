@@ -271,7 +271,8 @@ def batch_specimens(count=64, seed=1827, t_end=80e-6, smin=1.0, smax=4.0):
         notch = 0.030 + 0.030 * u[b, 1]
         trac = 0.5e6 + 2.5e6 * u[b, 2]
         p = notched_plate(nx=nx, ny=ny, notch_len=notch, traction=trac, steps=0,
-                          name=f"specimen_{b}")
+                          name=f"specimen_{b}", phantom_cap=max(8192, 4 * nx * ny),
+                          crack_cap=max(4096, nx * ny))
         p.steps = int(math.ceil(t_end / estimate_dt(p)))
         out.append(p)
     return out
