@@ -25,6 +25,7 @@ UNITS = [
     ("step_fp32.cu", []),
     ("eval_fp32.cu", ["-fmad=false"]),
     ("state_energy_noalloc.cu", ["-fmad=false"]),
+    ("surrogate.cu", []),
     ("api.cpp", []),
 ]
 HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh"]
@@ -37,7 +38,7 @@ def _stale(obj, deps):
 def _compile(src, extra):
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + \
-        [os.path.join(ROOT, "include", "cem.h")]
+        [os.path.join(ROOT, "include", "cem.h"), os.path.join(ROOT, "include", "cem_surrogate.h")]
     if not _stale(obj, deps):
         return obj
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -1,0 +1,669 @@
+// surrogate.cu -- kernels of the crack-map surrogate (a U-Net that maps a
+// notched-plate run's inputs to its cracked-element map; see
+// include/cem_surrogate.h).
+//
+// Activations are BF16 in NHWC layout, accumulation is FP32, weights are
+// kept in FP32 (master copy, Adam state) and mirrored in BF16 for the
+// tensor-core GEMMs.  The 3x3 convolution is an implicit GEMM
+//   y[p, n] = sum_k A[p, k] W[n, k],  p = pixel, k = (ky, kx, c)
+// whose A rows are gathered from the input on the fly (zero outside the
+// image) with 16-byte cp.async copies into a 3-stage shared-memory ring,
+// fed to mma.sync m16n8k16 BF16 through ldmatrix.  The data gradient is the
+// same kernel applied to the output gradient with the weights transposed and
+// flipped (written by the Adam kernel); the weight gradient is a second
+// implicit GEMM over pixels, split along the pixels into fixed chunks whose
+// FP32 partial sums are added in chunk order (deterministic).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cem_surrogate.h"
+
+namespace {
+
+typedef uint16_t bf16_t;  // BF16 storage
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float bf2f(bf16_t v) { return __uint_as_float((uint32_t)v << 16); }
+__device__ __forceinline__ bf16_t f2bf(float f) {
+  __nv_bfloat16 h = __float2bfloat16_rn(f);
+  return *reinterpret_cast<bf16_t *>(&h);
+}
+
+// ------------------------------------------------------------ conv 3x3
+constexpr int FBM = 128, FBN = 64, FBK = 32, FST = 3, FPAD = FBK + 8;
+
+struct ConvArgs {
+  const bf16_t *x;   // [P, ldx] input pixels (channels 0..Cin-1 used)
+  const bf16_t *w;   // [N, K] weights, K = 9 * Cin, k = (ky * 3 + kx) * Cin + c
+  const float *bias; // [N] or null
+  bf16_t *y;         // [P, ldy] output, channels yoff .. yoff + N - 1
+  int B, H, W, Cin, ldx, N, K, relu, ldy, yoff, P;
+};
+
+__global__ void __launch_bounds__(256) k_conv3x3(ConvArgs a) {
+  __shared__ __align__(128) bf16_t As[FST][FBM][FPAD];
+  __shared__ __align__(128) bf16_t Bs[FST][FBN][FPAD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int p0 = blockIdx.x * FBM, n0 = blockIdx.y * FBN;
+  const int HW = a.H * a.W, cpt = a.Cin >> 3;
+  const int KT = (a.K + FBK - 1) / FBK;
+  // this thread's two A rows and its 8-wide k chunk
+  const int kc = tid & 3;
+  int rb[2], rh[2], rw[2];
+  bool rok[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int p = p0 + (tid >> 2) + r * 64;
+    rok[r] = p < a.P;
+    const int pp = rok[r] ? p : 0;
+    rb[r] = pp / HW;
+    const int rem = pp - rb[r] * HW;
+    rh[r] = rem / a.W;
+    rw[r] = rem - rh[r] * a.W;
+  }
+  auto load_tile = [&](int kt, int s) {
+    const int q = kt * (FBK / 8) + kc;  // 8-wide chunk of k
+    const int tap = q / cpt, c0 = (q - tap * cpt) * 8;
+    const int ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int hh = rh[r] + ky - 1, ww = rw[r] + kx - 1;
+      const bool ok = rok[r] && tap < 9 && hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const bf16_t *src = ok ? a.x + ((size_t)(rb[r] * a.H + hh) * a.W + ww) * a.ldx + c0 : a.x;
+      cp_async16(&As[s][(tid >> 2) + r * 64][kc * 8], src, ok ? 16 : 0);
+    }
+    const int n = n0 + (tid >> 2), k = kt * FBK + kc * 8;
+    const bool okb = n < a.N && k < a.K;
+    const bf16_t *srcb = okb ? a.w + (size_t)n * a.K + k : a.w;
+    cp_async16(&Bs[s][tid >> 2][kc * 8], srcb, okb ? 16 : 0);
+  };
+
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+#pragma unroll
+  for (int s = 0; s < FST - 1; ++s) {
+    if (s < KT) load_tile(s, s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < KT; ++kt) {
+    cp_async_wait<FST - 2>();
+    __syncthreads();
+    const int nk = kt + FST - 1;
+    if (nk < KT) load_tile(nk, nk % FST);
+    cp_async_commit();
+    const int s = kt % FST;
+#pragma unroll
+    for (int kk = 0; kk < FBK; kk += 16) {
+      uint32_t af[2][4], bfr[2][4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+        ldsm_x4(af[mi], &As[s][wm * 32 + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+      for (int nj = 0; nj < 2; ++nj) {
+        const int mat = lane >> 3, r = lane & 7;
+        ldsm_x4(bfr[nj], &Bs[s][wn * 32 + nj * 16 + (mat >> 1) * 8 + r][kk + (mat & 1) * 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+          mma_bf16(acc[mi][ni], af[mi], bfr[ni >> 1][(ni & 1) * 2], bfr[ni >> 1][(ni & 1) * 2 + 1]);
+    }
+  }
+  cp_async_wait<0>();
+  // epilogue: bias, ReLU, BF16 pairs
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+      const int n = n0 + wn * 32 + ni * 8 + (lane & 3) * 2;
+      if (n >= a.N) continue;
+      const float b0 = a.bias ? a.bias[n] : 0.f, b1 = a.bias ? a.bias[n + 1] : 0.f;
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr) {
+        const int p = p0 + wm * 32 + mi * 16 + (lane >> 2) + hr * 8;
+        if (p >= a.P) continue;
+        float v0 = acc[mi][ni][hr * 2] + b0, v1 = acc[mi][ni][hr * 2 + 1] + b1;
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        const uint32_t pk = (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
+        *reinterpret_cast<uint32_t *>(a.y + (size_t)p * a.ldy + a.yoff + n) = pk;
+      }
+    }
+}
+
+// ---------------------------------------------------- conv 3x3 weight grad
+// dW[n, k] = sum_p dY[p, n] * A[p, k] over the pixels of split z, written
+// to ws[z][n][k]; k = (ky * 3 + kx) * Cin + c as in the forward weights.
+constexpr int GBM = 64, GBN = 64, GBK = 32, GST = 3, GPAD = 64 + 8;
+
+struct WgradArgs {
+  const bf16_t *x;   // [P, ldx] forward input
+  const bf16_t *dy;  // [P, lddy] output gradient (channels 0..N-1)
+  float *ws;         // [splits][N][K]
+  int B, H, W, Cin, ldx, lddy, N, K, P, chunk;  // chunk: pixels per split
+};
+
+__global__ void __launch_bounds__(256) k_conv3x3_wgrad(WgradArgs a) {
+  __shared__ __align__(128) bf16_t As[GST][GBK][GPAD];  // [pixel][n]
+  __shared__ __align__(128) bf16_t Bs[GST][GBK][GPAD];  // [pixel][k]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, each 32 (n) x 16 (k)
+  const int m0 = blockIdx.x * GBM, k0 = blockIdx.y * GBN, z = blockIdx.z;
+  const int pbeg = z * a.chunk, pend = min(a.P, pbeg + a.chunk);
+  const int HW = a.H * a.W, cpt = a.Cin >> 3;
+  const int KT = (pend - pbeg + GBK - 1) / GBK;
+  const int prow = tid >> 3, ch = tid & 7;
+  // this thread's k chunk is fixed: tap and channel
+  const int kq = (k0 >> 3) + ch;
+  const int tap = kq / cpt, c0 = (kq - tap * cpt) * 8;
+  const int ky = tap / 3, kx = tap - ky * 3;
+  const bool kok = k0 + ch * 8 < a.K;
+  const bool nok = m0 + ch * 8 < a.N;
+  auto load_tile = [&](int kt, int s) {
+    const int p = pbeg + kt * GBK + prow;
+    const bool pok = p < pend;
+    const bf16_t *srca = (pok && nok) ? a.dy + (size_t)p * a.lddy + m0 + ch * 8 : a.dy;
+    cp_async16(&As[s][prow][ch * 8], srca, (pok && nok) ? 16 : 0);
+    bool ok = pok && kok;
+    const bf16_t *srcb = a.x;
+    if (ok) {
+      const int b = p / HW, rem = p - b * HW, h = rem / a.W, w = rem - h * a.W;
+      const int hh = h + ky - 1, ww = w + kx - 1;
+      ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      if (ok) srcb = a.x + ((size_t)(b * a.H + hh) * a.W + ww) * a.ldx + c0;
+    }
+    cp_async16(&Bs[s][prow][ch * 8], srcb, ok ? 16 : 0);
+  };
+  float acc[2][2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll
+  for (int s = 0; s < GST - 1; ++s) {
+    if (s < KT) load_tile(s, s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < KT; ++kt) {
+    cp_async_wait<GST - 2>();
+    __syncthreads();
+    const int nk = kt + GST - 1;
+    if (nk < KT) load_tile(nk, nk % GST);
+    cp_async_commit();
+    const int s = kt % GST;
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      const int mat = lane >> 3, r = lane & 7;
+      uint32_t af[2][4], bq[4];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+        ldsm_x4_t(af[mi], &As[s][kk + (mat >> 1) * 8 + r][wm * 32 + mi * 16 + (mat & 1) * 8]);
+      ldsm_x4_t(bq, &Bs[s][kk + (mat & 1) * 8 + r][wn * 16 + (mat >> 1) * 8]);
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        mma_bf16(acc[mi][0], af[mi], bq[0], bq[1]);
+        mma_bf16(acc[mi][1], af[mi], bq[2], bq[3]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  float *out = a.ws + (size_t)z * a.N * a.K;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni) {
+      const int k = k0 + wn * 16 + ni * 8 + (lane & 3) * 2;
+      if (k >= a.K) continue;
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr) {
+        const int n = m0 + wm * 32 + mi * 16 + (lane >> 2) + hr * 8;
+        if (n >= a.N) continue;
+        *reinterpret_cast<float2 *>(out + (size_t)n * a.K + k) =
+            make_float2(acc[mi][ni][hr * 2], acc[mi][ni][hr * 2 + 1]);
+      }
+    }
+}
+
+// out[i] = sum_z ws[z][i] in z order
+__global__ void k_reduce_splits(const float *ws, int splits, long n, float *out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += ws[(size_t)z * n + i];
+    out[i] = s;
+  }
+}
+
+// per-channel sums of a BF16 [P, ld] tensor over fixed pixel chunks:
+// ws[chunk][c]; the chunks are then added in order by k_reduce_splits
+__global__ void k_colsum_chunks(const bf16_t *t, int P, int C, int ld, int chunk, float *ws) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int z = blockIdx.y;
+  if (c >= C) return;
+  const int pend = min(P, (z + 1) * chunk);
+  float s = 0.f;
+  for (int p = z * chunk; p < pend; ++p) s += bf2f(t[(size_t)p * ld + c]);
+  ws[(size_t)z * C + c] = s;
+}
+
+// ------------------------------------------------------------- elementwise
+// dy[p, c] = 0 where y[p, c] <= 0 (gradient through ReLU, given its output)
+__global__ void k_relu_bwd(bf16_t *dy, int lddy, const bf16_t *y, int ldy, long P, int C) {
+  const long n = P * C;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long p = i / C;
+    const int c = (int)(i - p * C);
+    if (!(bf2f(y[p * ldy + c]) > 0.f)) dy[p * lddy + c] = 0;
+  }
+}
+
+// 2x2 max pooling: x [B, 2H, 2W, C] (pixel stride ldx) -> y [B, H, W, C]
+__global__ void k_maxpool2(const bf16_t *x, int ldx, int B, int H, int W, int C, bf16_t *y) {
+  const long n = (long)B * H * W * C;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long pix = i / C;
+    const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
+    const size_t base = ((size_t)(b * 2 * H + 2 * h) * (2 * W) + 2 * w) * ldx + c;
+    const float v0 = bf2f(x[base]), v1 = bf2f(x[base + ldx]);
+    const float v2 = bf2f(x[base + (size_t)2 * W * ldx]), v3 = bf2f(x[base + (size_t)2 * W * ldx + ldx]);
+    y[i] = f2bf(fmaxf(fmaxf(v0, v1), fmaxf(v2, v3)));
+  }
+}
+
+// gradient of 2x2 max pooling to the first maximum of each window, plus an
+// optional skip gradient (dskip [.., ldskip] at channel offset skoff):
+// dx [B, 2H, 2W, C] dense
+__global__ void k_maxpool2_bwd(const bf16_t *x, int ldx, const bf16_t *dy, const bf16_t *dskip,
+                               int ldskip, int skoff, int B, int H, int W, int C, bf16_t *dx) {
+  const long n = (long)B * H * W * C;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long pix = i / C;
+    const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
+    size_t src[4], dst[4];
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int hh = 2 * h + (q >> 1), ww = 2 * w + (q & 1);
+      const size_t pp = (size_t)(b * 2 * H + hh) * (2 * W) + ww;
+      src[q] = pp * ldx + c;
+      dst[q] = pp;
+      v[q] = bf2f(x[src[q]]);
+    }
+    const float m = fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
+    const float g = bf2f(dy[i]);
+    bool taken = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float o = 0.f;
+      if (!taken && v[q] == m) {
+        o = g;
+        taken = true;
+      }
+      if (dskip) o += bf2f(dskip[dst[q] * ldskip + skoff + c]);
+      dx[dst[q] * C + c] = f2bf(o);
+    }
+  }
+}
+
+// nearest 2x upsampling: x [B, H, W, C] dense -> y [B, 2H, 2W, ldy] at channel offset yoff
+__global__ void k_upsample2(const bf16_t *x, int B, int H, int W, int C, bf16_t *y, int ldy,
+                            int yoff) {
+  const long n = (long)B * 4 * H * W * C;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long pix = i / C;  // output pixel
+    const int ww = (int)(pix % (2 * W)), hh = (int)((pix / (2 * W)) % (2 * H));
+    const int b = (int)(pix / ((long)4 * W * H));
+    y[(size_t)pix * ldy + yoff + c] = x[((size_t)(b * H + hh / 2) * W + ww / 2) * C + c];
+  }
+}
+
+// gradient of nearest 2x upsampling: dy [B, 2H, 2W, lddy] channels 0..C-1 -> dx [B, H, W, C]
+__global__ void k_upsample2_bwd(const bf16_t *dy, int lddy, int B, int H, int W, int C,
+                                bf16_t *dx) {
+  const long n = (long)B * H * W * C;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long pix = i / C;
+    const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t pp = (size_t)(b * 2 * H + 2 * h + (q >> 1)) * (2 * W) + 2 * w + (q & 1);
+      s += bf2f(dy[pp * lddy + c]);
+    }
+    dx[i] = f2bf(s);
+  }
+}
+
+// ------------------------------------------------------------------- head
+// z[p] = b + sum_c x[p, c] w[c]   (1x1 convolution to one logit, FP32)
+__global__ void k_head_fwd(const bf16_t *x, int P, int C, const float *w, const float *b, float *z) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float s = b[0];
+    for (int c = 0; c < C; ++c) s += bf2f(x[(size_t)p * C + c]) * w[c];
+    z[p] = s;
+  }
+}
+
+// dx[p, c] = dz[p] w[c]; per-chunk partials of dw[c] = sum_p dz[p] x[p, c]
+// and db = sum_p dz[p] into ws[chunk][C + 1]
+__global__ void k_head_bwd(const bf16_t *x, int P, int C, const float *w, const float *dz,
+                           bf16_t *dx, int chunk, float *ws) {
+  const int z = blockIdx.x;
+  const int pend = min(P, (z + 1) * chunk);
+  __shared__ float red[33][33];
+  const int c = threadIdx.x & 31, lane_p = threadIdx.x >> 5;  // 32 channels x 8 pixel lanes
+  float s = 0.f, sb = 0.f;
+  for (int p = z * chunk + lane_p; p < pend; p += 8) {
+    const float g = dz[p];
+    for (int cc = c; cc < C; cc += 32) {
+      const float xv = bf2f(x[(size_t)p * C + cc]);
+      dx[(size_t)p * C + cc] = f2bf(g * w[cc]);
+      if (cc == c) s += g * xv;
+    }
+    sb += g;
+  }
+  red[lane_p][c] = s;
+  if (c == 0) red[lane_p][32] = sb;
+  __syncthreads();
+  if (lane_p == 0) {
+    float t = 0.f, tb = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      t += red[q][c];
+      tb += red[q][32];
+    }
+    if (c < C) ws[(size_t)z * (C + 1) + c] = t;
+    if (c == 0) ws[(size_t)z * (C + 1) + C] = tb;
+  }
+}
+
+// ------------------------------------------------------------------- loss
+// class-weighted binary cross-entropy with logits, mean over n elements:
+// dz = (pw t (sigma - 1) + (1 - t) sigma) / n; per-block loss partials
+__global__ void k_bce(const float *z, const uint8_t *t, long n, float pw, float *dz, float *ws) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float zi = z[i];
+    const float tt = t[i] ? 1.f : 0.f;
+    // log(1 + e^-z) and log(1 + e^z) without overflow
+    const float sp_neg = fmaxf(-zi, 0.f) + log1pf(expf(-fabsf(zi)));
+    const float sp_pos = sp_neg + zi;
+    s += pw * tt * sp_neg + (1.f - tt) * sp_pos;
+    const float sig = 1.f / (1.f + expf(-zi));
+    dz[i] = (pw * tt * (sig - 1.f) + (1.f - tt) * sig) / (float)n;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ws[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_scaled(const float *ws, int m, float scale, float *out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < m; ++i) s += ws[i];
+    out[0] = s * scale;
+  }
+}
+
+// ------------------------------------------------------------------- adam
+// w -= lr * mhat / (sqrt(vhat) + eps); BF16 copy of w, and for 3x3 weights
+// [Cout][3][3][Cin] the transposed, flipped copy wt[Cin][3][3][Cout] with
+// wt[c][ky][kx][o] = w[o][2-ky][2-kx][c] used by the data gradient
+__global__ void k_adam(float *w, const float *g, float *m, float *v, long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2, bf16_t *wb, bf16_t *wt, int Cout,
+                       int Cin) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    const bf16_t h = f2bf(wi);
+    if (wb) wb[i] = h;
+    if (wt) {
+      const int c = (int)(i % Cin);
+      const long r = i / Cin;
+      const int kx = (int)(r % 3), ky = (int)((r / 3) % 3), o = (int)(r / 9);
+      wt[(((size_t)c * 3 + (2 - ky)) * 3 + (2 - kx)) * Cout + o] = h;
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float *x, long n, bf16_t *y) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = f2bf(x[i]);
+}
+
+// dw[c] = sum_z ws[z][c], db = sum_z ws[z][C], in chunk order
+__global__ void k_reduce_head(const float *ws, int nz, int C, float *dw, float *db) {
+  for (int c = threadIdx.x; c <= C; c += blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += ws[(size_t)z * (C + 1) + c];
+    if (c < C) dw[c] = s;
+    else db[0] = s;
+  }
+}
+
+int grid_1d(long n, int block) {
+  long b = (n + block - 1) / block;
+  return (int)(b < 1 ? 1 : (b > 4 * 1216 ? 4 * 1216 : b));
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const void *w,
+                   const float *bias, int Cout, int relu, void *y, int ldy, int yoff,
+                   void *stream) {
+  if (!x || !w || !y || B < 1 || H < 1 || W < 1 || Cin < 8 || (Cin & 7) || ldx < Cin ||
+      (ldx & 7) || Cout < 2 || (Cout & 1) || ldy < yoff + Cout || (yoff & 1))
+    return CEM_SG_ERR_ARG;
+  ConvArgs a;
+  a.x = (const bf16_t *)x;
+  a.w = (const bf16_t *)w;
+  a.bias = bias;
+  a.y = (bf16_t *)y;
+  a.B = B; a.H = H; a.W = W; a.Cin = Cin; a.ldx = ldx; a.N = Cout; a.K = 9 * Cin;
+  a.relu = relu; a.ldy = ldy; a.yoff = yoff; a.P = B * H * W;
+  dim3 grid((a.P + FBM - 1) / FBM, (Cout + FBN - 1) / FBN);
+  k_conv3x3<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+long cem_sg_wgrad_workspace(int B, int H, int W, int Cin, int Cout) {
+  const long P = (long)B * H * W;
+  long splits = (P + 4095) / 4096;
+  if (splits > 256) splits = 256;
+  return splits * (long)Cout * 9 * Cin * 4 + (long)Cout * 4 * 1024;
+}
+
+int cem_sg_conv3x3_wgrad(const void *x, int ldx, const void *dy, int lddy, int B, int H, int W,
+                         int Cin, int Cout, float *dw, float *db, void *ws, long ws_bytes,
+                         void *stream) {
+  if (!x || !dy || !dw || !ws || B < 1 || H < 1 || W < 1 || Cin < 8 || (Cin & 7) ||
+      (ldx & 7) || ldx < Cin || Cout < 8 || (Cout & 7) || lddy < Cout || (lddy & 7))
+    return CEM_SG_ERR_ARG;
+  if (ws_bytes < cem_sg_wgrad_workspace(B, H, W, Cin, Cout)) return CEM_SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  WgradArgs a;
+  a.x = (const bf16_t *)x;
+  a.dy = (const bf16_t *)dy;
+  a.ws = (float *)ws;
+  a.B = B; a.H = H; a.W = W; a.Cin = Cin; a.ldx = ldx; a.lddy = lddy; a.N = Cout;
+  a.K = 9 * Cin; a.P = B * H * W;
+  int splits = (a.P + 4095) / 4096;
+  if (splits > 256) splits = 256;
+  a.chunk = ((a.P + splits - 1) / splits + GBK - 1) / GBK * GBK;
+  splits = (a.P + a.chunk - 1) / a.chunk;
+  dim3 grid((Cout + GBM - 1) / GBM, (a.K + GBN - 1) / GBN, splits);
+  k_conv3x3_wgrad<<<grid, 256, 0, st>>>(a);
+  const long nw = (long)Cout * a.K;
+  k_reduce_splits<<<grid_1d(nw, 256), 256, 0, st>>>(a.ws, splits, nw, dw);
+  if (db) {
+    // bias: per-channel sums over fixed pixel chunks, then in chunk order
+    const int chunk = a.P / 1024 + 1 > 4096 ? a.P / 1024 + 1 : 4096;  // at most 1024 chunks
+    const int nz = (a.P + chunk - 1) / chunk;
+    float *wsb = a.ws;  // reused after the weight reduction (same stream)
+    k_colsum_chunks<<<dim3((Cout + 127) / 128, nz), 128, 0, st>>>(a.dy, a.P, Cout, lddy, chunk, wsb);
+    k_reduce_splits<<<grid_1d(Cout, 128), 128, 0, st>>>(wsb, nz, Cout, db);
+  }
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_relu_bwd(void *dy, int lddy, const void *y, int ldy, long P, int C, void *stream) {
+  if (!dy || !y || P < 0 || C < 1 || lddy < C || ldy < C) return CEM_SG_ERR_ARG;
+  k_relu_bwd<<<grid_1d(P * C, 256), 256, 0, (cudaStream_t)stream>>>((bf16_t *)dy, lddy,
+                                                                    (const bf16_t *)y, ldy, P, C);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_maxpool2(const void *x, int ldx, int B, int H, int W, int C, void *y, void *stream) {
+  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 1 || ldx < C) return CEM_SG_ERR_ARG;
+  const long n = (long)B * H * W * C;
+  k_maxpool2<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)x, ldx, B, H, W, C,
+                                                               (bf16_t *)y);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_maxpool2_bwd(const void *x, int ldx, const void *dy, const void *dskip, int ldskip,
+                        int skoff, int B, int H, int W, int C, void *dx, void *stream) {
+  if (!x || !dy || !dx || B < 1 || H < 1 || W < 1 || C < 1 || ldx < C ||
+      (dskip && ldskip < skoff + C))
+    return CEM_SG_ERR_ARG;
+  const long n = (long)B * H * W * C;
+  k_maxpool2_bwd<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      (const bf16_t *)x, ldx, (const bf16_t *)dy, (const bf16_t *)dskip, ldskip, skoff, B, H, W, C,
+      (bf16_t *)dx);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_upsample2(const void *x, int B, int H, int W, int C, void *y, int ldy, int yoff,
+                     void *stream) {
+  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 1 || ldy < yoff + C) return CEM_SG_ERR_ARG;
+  const long n = (long)B * 4 * H * W * C;
+  k_upsample2<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)x, B, H, W, C,
+                                                                (bf16_t *)y, ldy, yoff);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_upsample2_bwd(const void *dy, int lddy, int B, int H, int W, int C, void *dx,
+                         void *stream) {
+  if (!dy || !dx || B < 1 || H < 1 || W < 1 || C < 1 || lddy < C) return CEM_SG_ERR_ARG;
+  const long n = (long)B * H * W * C;
+  k_upsample2_bwd<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)dy, lddy, B, H,
+                                                                    W, C, (bf16_t *)dx);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_head_fwd(const void *x, int P, int C, const float *w, const float *b, float *z,
+                    void *stream) {
+  if (!x || !w || !b || !z || P < 1 || C < 1) return CEM_SG_ERR_ARG;
+  k_head_fwd<<<grid_1d(P, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)x, P, C, w, b, z);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+long cem_sg_head_workspace(int P, int C) {
+  const long nz = (P + 4095) / 4096;
+  return nz * (C + 1) * 4;
+}
+
+int cem_sg_head_bwd(const void *x, int P, int C, const float *w, const float *dz, void *dx,
+                    float *dw, float *db, void *ws, long ws_bytes, void *stream) {
+  if (!x || !w || !dz || !dx || !dw || !db || !ws || P < 1 || C < 1 || C > 32)
+    return CEM_SG_ERR_ARG;
+  if (ws_bytes < cem_sg_head_workspace(P, C)) return CEM_SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = 4096, nz = (P + chunk - 1) / chunk;
+  float *wsf = (float *)ws;
+  k_head_bwd<<<nz, 256, 0, st>>>((const bf16_t *)x, P, C, w, dz, (bf16_t *)dx, chunk, wsf);
+  k_reduce_head<<<1, 64, 0, st>>>(wsf, nz, C, dw, db);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+long cem_sg_bce_workspace(long n) { return 4 * 1216 * 4 + 16; }
+
+int cem_sg_bce(const float *z, const unsigned char *t, long n, float pos_weight, float *dz,
+               float *loss, void *ws, long ws_bytes, void *stream) {
+  if (!z || !t || !dz || !loss || !ws || n < 1) return CEM_SG_ERR_ARG;
+  if (ws_bytes < cem_sg_bce_workspace(n)) return CEM_SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int g = grid_1d(n, 256);
+  k_bce<<<g, 256, 0, st>>>(z, t, n, pos_weight, dz, (float *)ws);
+  k_sum_scaled<<<1, 32, 0, st>>>((const float *)ws, g, 1.f / (float)n, loss);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_adam(float *w, const float *g, float *m, float *v, long n, float lr, float beta1,
+                float beta2, float eps, int step, void *w_bf16, void *wt_bf16, int Cout, int Cin,
+                void *stream) {
+  if (!w || !g || !m || !v || n < 1 || step < 1 || !(lr >= 0.f)) return CEM_SG_ERR_ARG;
+  if (wt_bf16 && (Cout < 1 || Cin < 1 || (long)Cout * 9 * Cin != n)) return CEM_SG_ERR_ARG;
+  const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+  k_adam<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      w, g, m, v, n, lr, beta1, beta2, eps, c1, c2, (bf16_t *)w_bf16, (bf16_t *)wt_bf16, Cout, Cin);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_to_bf16(const float *x, long n, void *y, void *stream) {
+  if (!x || !y || n < 0) return CEM_SG_ERR_ARG;
+  k_to_bf16<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(x, n, (bf16_t *)y);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -9,10 +9,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "cem.h")).read()
+def declared_functions(header="cem.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(cem_[a-z_]+)\s*\(", src))
+    names = set(re.findall(r"\b(cem_[a-z0-9_]+)\s*\(", src))
     return sorted(n for n in names if not n.endswith("_fn"))
 
 
@@ -32,6 +32,25 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     # the binding wraps exactly the declared entry points
     assert sorted(cem.SIGNATURES) == declared_functions()
+
+
+def test_surrogate_abi_exported_and_bound():
+    from paper_2509_01827_gb300 import build
+    from paper_2509_01827_gb300 import surrogate
+    lib = ctypes.CDLL(build.build())
+    names = declared_functions("cem_surrogate.h")
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(surrogate.SG_SIGNATURES) == names
+
+
+def test_surrogate_argument_checks_without_gpu():
+    """Shape checks come before any launch: bad channel counts are errors."""
+    from paper_2509_01827_gb300 import surrogate
+    L = surrogate.sg()
+    assert L.cem_sg_conv3x3(1, 1, 4, 4, 3, 3, 1, None, 8, 0, 1, 8, 0, None) == -1  # Cin % 8
+    assert L.cem_sg_wgrad_workspace(1, 4, 4, 8, 8) > 0
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
