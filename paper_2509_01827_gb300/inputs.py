@@ -278,6 +278,22 @@ def batch_specimens(count=64, seed=1827, t_end=80e-6, smin=1.0, smax=4.0):
     return out
 
 
+def surrogate_run(seed, nx=400, ny=160, t_end=80e-6, gc_mean=3.0, gc_shape=10.0):
+    """One run of the surrogate's data set: the 400 x 160 notched plate with
+    traction ~ U(0.5, 3) MPa (Philox stream 1), notch length ~ U(30, 60) mm
+    (stream 2) and a Weibull G_c field (mean 3 J/m^2, shape 10, stream 0),
+    all drawn from `seed`, run to t_end.  Returns the problem and the drawn
+    scalars."""
+    trac = 0.5e6 + 2.5e6 * float(uniform01(1, seed, stream=1)[0])
+    notch = 0.030 + 0.030 * float(uniform01(1, seed, stream=2)[0])
+    ne = nx * ny
+    p = notched_plate(nx=nx, ny=ny, notch_len=notch, traction=trac, steps=0,
+                      name=f"surrogate_run_{seed}", phantom_cap=4 * ne, crack_cap=ne)
+    p.gc = weibull_gc(ne, gc_mean, gc_shape, seed)
+    p.steps = int(math.ceil(t_end / estimate_dt(p)))
+    return p, {"traction": trac, "notch_len": notch, "seed": int(seed)}
+
+
 CONFIGS = {
     "notched_plate_100x40": lambda: notched_plate(100, 40, steps=2000),
     "notched_plate_400x160": lambda: notched_plate(400, 160, steps=int(math.ceil(80e-6 / estimate_dt(notched_plate(400, 160, steps=0))))),

@@ -1,0 +1,224 @@
+"""Data set, training and evaluation of the crack-map surrogate.
+
+    python -m paper_2509_01827_gb300.train_surrogate --train 4096 --test 256
+
+1. Data: each seed gives a 400 x 160 notched-plate run (traction, notch
+   length and Weibull G_c drawn from the seed; inputs.surrogate_run), stepped
+   to 80 us by the explicit solver in batches (cem_batch_create); the target
+   is the run's cracked-element map.  Training seeds 0 .. N-1, test seeds
+   10^6 .. 10^6 + M - 1.
+2. Input image per run (H = 160 element rows, W = 400 element columns, 8
+   channels, the last five zero): traction / 3 MPa, the notch (1 on the
+   pre-cracked elements), (G_c - 3 J/m^2) / 0.36 J/m^2 (the Weibull field's
+   standard deviation).
+3. Training: the U-Net of surrogate.py, weighted binary cross-entropy
+   (cracked elements weighted by the training set's intact/cracked ratio,
+   capped at 20), Adam with a cosine learning-rate decay, batch 64.
+4. Evaluation: mean Jaccard index of the predicted cracked set (logit >
+   threshold, threshold chosen on held-out training runs) on the test runs,
+   beside the no-learning floor of a straight crack along the notch row.
+Prints one JSON line.
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import inputs
+
+H_EL, W_EL = 160, 400
+GC_SD = 0.36  # standard deviation of the Weibull(k = 10, mean 3) field, J/m^2
+
+
+def encode(prob, meta):
+    """Input image [H * W, 8] float32 of one run (row-major element order)."""
+    nx, ny = prob.nx, prob.ny
+    img = np.zeros((ny, nx, 8), np.float32)
+    img[..., 0] = meta["traction"] / 3e6
+    notch = np.zeros(nx * ny, np.float32)
+    notch[np.asarray(prob.precracks)[:, 0]] = 1.0
+    img[..., 1] = notch.reshape(ny, nx)
+    img[..., 2] = ((np.asarray(prob.gc, np.float64) - 3.0) / GC_SD).reshape(ny, nx)
+    return img.reshape(-1, 8)
+
+
+def straight_crack(prob):
+    """No-learning floor: the notch row cracked across the whole plate."""
+    nx, ny = prob.nx, prob.ny
+    m = np.zeros((ny, nx), bool)
+    m[ny // 2 - 1, :] = True
+    return m.reshape(-1)
+
+
+def jaccard(a, b):
+    a = np.asarray(a, bool)
+    b = np.asarray(b, bool)
+    u = np.logical_or(a, b).sum()
+    return 1.0 if u == 0 else float(np.logical_and(a, b).sum()) / float(u)
+
+
+def generate(seeds, chunk=256, device=0, log=print):
+    """Runs the solver for every seed; returns device tensors X [N, P, 8] BF16,
+    Y [N, P] uint8, the host floors and the solver's seconds per run."""
+    import torch
+    from .cem import CEM_FP32_MIXED, Batch, Solver
+    from .surrogate import _p, sg
+    n = len(seeds)
+    P = H_EL * W_EL
+    X = torch.empty((n, P, 8), dtype=torch.bfloat16, device=f"cuda:{device}")
+    Y = torch.empty((n, P), dtype=torch.uint8, device=f"cuda:{device}")
+    floors = np.zeros(n)
+    solve_s = 0.0
+    config = None
+    for c0 in range(0, n, chunk):
+        part = seeds[c0:c0 + chunk]
+        runs = [inputs.surrogate_run(s) for s in part]
+        members = [Solver(p, precision=CEM_FP32_MIXED, device=device) for p, _ in runs]
+        b = Batch(members)
+        if config is None:
+            config = b.autotune(2)
+        else:
+            b.set_config(*config)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(runs[0][0].steps - b.counts()["step"])
+        torch.cuda.synchronize()
+        solve_s += time.perf_counter() - t0
+        for k, ((p, meta), m) in enumerate(zip(runs, members)):
+            st = m.state()
+            y = (st == 1).astype(np.uint8)
+            Y[c0 + k].copy_(torch.from_numpy(y))
+            img = torch.from_numpy(encode(p, meta)).to(X.device)
+            _ = sg().cem_sg_to_bf16(_p(img), img.numel(), _p(X[c0 + k]),
+                                    torch.cuda.current_stream().cuda_stream)
+            floors[c0 + k] = jaccard(straight_crack(p), y)
+        b.close()
+        for m in members:
+            m.close()
+        log(f"generated {min(n, c0 + chunk)}/{n} runs")
+    torch.cuda.synchronize()
+    return X, Y, floors, solve_s / n
+
+
+def predict(net, X, B):
+    """Logits of every run of X (padded to whole batches)."""
+    import torch
+    n = X.shape[0]
+    out = torch.empty((n, X.shape[1]), dtype=torch.float32, device=X.device)
+    for c0 in range(0, n, B):
+        k = min(B, n - c0)
+        net.x8[: k * X.shape[1]].copy_(X[c0:c0 + k].reshape(-1, 8))
+        if k < B:
+            net.x8[k * X.shape[1]:].zero_()
+        net.forward()
+        out[c0:c0 + k].copy_(net.z[: k * X.shape[1]].reshape(k, -1))
+    return out
+
+
+def mean_jaccard(Z, Y, thr):
+    import torch
+    pred = Z > thr
+    tgt = Y.bool()
+    inter = (pred & tgt).sum(1).double()
+    union = (pred | tgt).sum(1).double()
+    j = torch.where(union > 0, inter / union.clamp(min=1), torch.ones_like(union))
+    return float(j.mean().item()), j.cpu().numpy()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--train", type=int, default=4096)
+    ap.add_argument("--test", type=int, default=256)
+    ap.add_argument("--val", type=int, default=256, help="training runs held out for the threshold")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--chunk", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--save", default=None,
+                    help="write the FP32 parameters and 8 test maps (.npz)")
+    args = ap.parse_args()
+    import torch
+    from . import build as _build
+    from .surrogate import UNet
+    _build.build()
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, flush=True)
+
+    t0 = time.perf_counter()
+    Xtr, Ytr, floor_tr, s_run = generate(list(range(args.train)), args.chunk, log=log)
+    Xte, Yte, floor_te, _ = generate(list(range(10**6, 10**6 + args.test)), args.chunk, log=log)
+    gen_s = time.perf_counter() - t0
+    nval = min(args.val, args.train // 4)
+    ntr = args.train - nval
+    frac = float(Ytr[:ntr].float().mean().item())
+    pos_weight = float(min(20.0, (1.0 - frac) / max(frac, 1e-6)))
+    net = UNet(args.batch, H_EL, W_EL, pos_weight=pos_weight, lr=args.lr, seed=args.seed)
+    rng = np.random.default_rng(args.seed)
+    steps_per_epoch = ntr // args.batch
+    total = steps_per_epoch * args.epochs
+    P = H_EL * W_EL
+    hist = []
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    it = 0
+    for ep in range(args.epochs):
+        perm = torch.from_numpy(rng.permutation(ntr)).to(Xtr.device)
+        ep_loss = torch.zeros((), dtype=torch.float32, device=Xtr.device)
+        for s in range(steps_per_epoch):
+            idx = perm[s * args.batch:(s + 1) * args.batch]
+            net.x8.copy_(Xtr.index_select(0, idx).reshape(-1, 8))
+            tgt = Ytr.index_select(0, idx).reshape(-1)
+            lr = args.lr * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * it / max(1, total))))
+            net.forward()
+            loss = net.loss_and_grad(tgt)
+            net.backward()
+            net.adam_step(lr=lr)
+            ep_loss += loss[0]
+            it += 1
+        hist.append(float(ep_loss.item()) / steps_per_epoch)
+        log(f"epoch {ep}: loss {hist[-1]:.4f}")
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    # threshold on held-out training runs
+    Zv = predict(net, Xtr[ntr:], args.batch)
+    best_thr, best_j = 0.0, -1.0
+    for thr in np.linspace(-3, 3, 25):
+        j, _ = mean_jaccard(Zv, Ytr[ntr:], float(thr))
+        if j > best_j:
+            best_thr, best_j = float(thr), j
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    Zte = predict(net, Xte, args.batch)
+    torch.cuda.synchronize()
+    infer_s = (time.perf_counter() - t2) / args.test
+    j_te, j_all = mean_jaccard(Zte, Yte, best_thr)
+    j_te0, _ = mean_jaccard(Zte, Yte, 0.0)
+    out = {
+        "workload": "surrogate_400x160", "train_runs": ntr, "val_runs": nval,
+        "test_runs": args.test, "epochs": args.epochs, "batch": args.batch,
+        "params": int(sum(p["w"].numel() + p["b"].numel() for p in net.convs.values())
+                      + net.head["w"].numel() + 1),
+        "cracked_fraction_train": frac, "pos_weight": pos_weight,
+        "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+        "threshold": best_thr, "val_jaccard": best_j,
+        "test_mean_jaccard": j_te, "test_mean_jaccard_thr0": j_te0,
+        "test_jaccard_p10_p50_p90": [float(np.percentile(j_all, q)) for q in (10, 50, 90)],
+        "straight_crack_floor_test": float(np.mean(floor_te)),
+        "solver_seconds_per_run_batched": s_run,
+        "network_seconds_per_run": infer_s,
+        "generation_s": gen_s, "training_s": train_s,
+        "train_steps": total,
+    }
+    if args.save:
+        k = min(8, args.test)
+        np.savez_compressed(args.save, **net.params_numpy(),
+                            test_target=Yte[:k].cpu().numpy().reshape(k, H_EL, W_EL),
+                            test_pred=(Zte[:k] > best_thr).cpu().numpy().reshape(k, H_EL, W_EL))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
