@@ -136,6 +136,25 @@ def time_oracle(prob, budget_s=15.0, max_steps=60):
                       f"set-up {setup:.1f}s not timed", "seconds": round(el, 3)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over all ranks (x itself on one rank); NCCL on the GPU,
+    any process group (gloo on the CPU in the tests)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, ms_per_rank, world, device="cuda"):
+    """Whole-job throughput of independent replicas: the units of all ranks
+    divided by the slowest rank's time.  Returns (units/s, max ms)."""
+    ms = max_over_ranks(ms_per_rank, world, device)
+    return world * units_per_rank / (ms * 1e-3), ms
+
+
 # ------------------------------------------------------------------ ours
 def bytes_per_update(precision):
     """Algorithmic bytes of the tile kernel per (real node, element) pair."""
@@ -187,15 +206,11 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     time.sleep(0.2)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    value, ms = replica_throughput(nact * args.steps, e0.elapsed_time(e1), world)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     c1 = sol.counts()
     launches = c1["kernel_launches"] - c0["kernel_launches"]
-    value = world * nact * args.steps / (ms * 1e-3)
 
     # per-kernel device time over a profiled window of the same run
     nprof = max(1, min(args.profile_steps, 4000))
@@ -219,12 +234,7 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     for _ in range(ne2e):
         sol.step(1)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * nact * ne2e / e2e_s
+    e2e_val, _ = replica_throughput(nact * ne2e, (time.perf_counter() - t0) * 1e3, world)
 
     companion = None
     if args.companion and rank == 0 and world == 1:
@@ -345,11 +355,7 @@ def run_batch(args, rank, world):
     c1 = b.counts()
     launches = c1["kernel_launches"] - c0["kernel_launches"]
     timed_updates = sum(p.n_active * max(0, n - args.warmup) for p, n in zip(probs, steps))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * timed_updates / (ms * 1e-3)
+    value, ms = replica_throughput(timed_updates, ms, world)
     cracked = c1["n_cracked"]
     b.close()
     for m in members:
@@ -364,11 +370,10 @@ def run_batch(args, rank, world):
     t0 = time.perf_counter()
     for _ in range(ne2e):
         b.step(1)
-    e2e_s = time.perf_counter() - t0
+    e2e_val, _ = replica_throughput(upd, (time.perf_counter() - t0) * 1e3, world)
     b.close()
     for m in members:
         m.close()
-    e2e_val = world * upd / e2e_s
 
     # the same specimens stepped one after another, each alone (a sample)
     nsolo = min(len(probs), max(1, args.solo_sample))
