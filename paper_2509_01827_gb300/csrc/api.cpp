@@ -399,6 +399,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.ck_ud, (size_t)d.ck_cap) && dalloc_n(h, d.ck_step, (size_t)d.ck_cap) &&
        dalloc_n(h, d.ph_owner, (size_t)d.ph_cap) && dalloc_n(h, d.ph_creator, (size_t)d.ph_cap) &&
        dalloc_n(h, d.ph_nuser, (size_t)d.ph_cap) && dalloc_n(h, d.ph_users, (size_t)d.ph_cap * 4) &&
+       dalloc_n(h, d.ph_upf, (size_t)d.ph_cap * 4) &&
        dalloc_n(h, d.S, (size_t)d.list_cap) && dalloc_n(h, d.S_info, (size_t)d.list_cap) &&
        dalloc_n(h, d.S_G, (size_t)d.list_cap) && dalloc_n(h, d.spos, (size_t)d.g.ned) &&
        dalloc_n(h, d.pr_key, (size_t)d.prop_cap) && dalloc_n(h, d.pr_edge, (size_t)d.prop_cap) &&

@@ -98,6 +98,7 @@ struct DevState {
   int *ph_creator;       // e * 4 + a
   int *ph_nuser;
   int *ph_users;         // [ph_cap * 4], (e << 3) | (p << 2) | a, sorted by e
+  int *ph_upf;           // [ph_cap * 4], piece-force index c*16 + p*8 + 2a of each user, -1 unused
 
   // surface list [list_cap]
   int *S;                // edge id or -1 (tombstone)
@@ -166,6 +167,29 @@ __device__ __forceinline__ VBlk item_vblk(int4 it) {
 // member is stepped at batch step n
 __device__ __forceinline__ bool member_active(const DevState &d, int n) { return n < d.step_end; }
 __device__ __forceinline__ int member_cur(const DevState &d, int n) { return (n & 1) ^ d.cur_xor; }
+
+// A block's share of a work list: a contiguous range, so that consecutive
+// items mostly belong to one member.
+__device__ __forceinline__ void block_range(int n, int &begin, int &end) {
+  begin = (int)(((long long)n * blockIdx.x) / gridDim.x);
+  end = (int)(((long long)n * (blockIdx.x + 1)) / gridDim.x);
+}
+
+// Copies member s's state into the block's shared copy `sh` when it is not
+// already there (block-uniform; `held` is the member held, -1 at first).
+// Kernels then read the state from shared memory instead of re-loading its
+// fields from global memory after every store.
+__device__ __forceinline__ void stage_member(const DevState *ds, int s, DevState &sh, int &held) {
+  if (s == held) return;
+  __syncthreads();  // every thread is done with the previous member
+  const int nt = blockDim.x * blockDim.y;
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  const int *src = reinterpret_cast<const int *>(ds + s);
+  int *dst = reinterpret_cast<int *>(&sh);
+  for (int i = t; i < (int)(sizeof(DevState) / 4); i += nt) dst[i] = src[i];
+  __syncthreads();
+  held = s;
+}
 #endif
 
 // ------------------------------------------------------------------ launch

@@ -110,31 +110,38 @@ __global__ void k_check_finite(DevState d, int cur) { check_finite(d, hw_vblk(),
 
 // batched counterparts: one CTA per member (energies), work list (check)
 __global__ void __launch_bounds__(TB) k_energy_pre_batch(BatchDev b) {
+  __shared__ DevState sd;
+  int held = -1;
   const int n = *b.bstep;
   for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
-    const DevState &d = b.ds[s];
-    if (!member_active(d, n)) continue;
-    energy_pre(d);
+    stage_member(b.ds, s, sd, held);
+    if (!member_active(sd, n)) continue;
+    energy_pre(sd);
     __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(TB) k_energy_post_batch(BatchDev b) {
+  __shared__ DevState sd;
+  int held = -1;
   const int n = *b.bstep;
   for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
-    const DevState &d = b.ds[s];
-    if (!member_active(d, n)) continue;
-    energy_post(d, b.nparts[s]);
+    stage_member(b.ds, s, sd, held);
+    if (!member_active(sd, n)) continue;
+    energy_post(sd, b.nparts[s]);
     __syncthreads();
   }
 }
 
 // the members' last states: runs after the steps, whatever the batch step
 __global__ void k_check_finite_batch(BatchDev b) {
-  for (int w = blockIdx.x; w < b.n_fin; w += gridDim.x) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
+  block_range(b.n_fin, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_fin[w];
-    const DevState &d = b.ds[it.x];
-    check_finite(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, d.cnt->step));
+    stage_member(b.ds, it.x, sd, held);
+    check_finite(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, sd.cnt->step));
     __syncthreads();
   }
 }

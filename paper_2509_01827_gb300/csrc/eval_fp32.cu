@@ -130,12 +130,15 @@ __device__ __forceinline__ void eval32(const DevState &d, VBlk vb, int cur) {
 __global__ void k_eval32(DevState d, int cur) { eval32(d, hw_vblk(), cur); }
 
 __global__ void k_eval32_batch(BatchDev b) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_eval; w += gridDim.x) {
+  block_range(b.n_eval, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_eval[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    eval32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n));
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    eval32(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n));
   }
 }
 

@@ -138,10 +138,12 @@ __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, in
   double se = 0.0;
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int c = t >> 1, p = t & 1;
+    const int4 nd = reinterpret_cast<const int4 *>(d.ck_node)[c * 2 + p];
+    const int nds[4] = {nd.x, nd.y, nd.z, nd.w};
     float xh[4], xl[4], yh[4], yl[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const float4 U = d.u4[cur][d.ck_node[c * 8 + p * 4 + a]];
+      const float4 U = d.u4[cur][nds[a]];
       xh[a] = U.x; xl[a] = U.y; yh[a] = U.z; yl[a] = U.w;
     }
     // edge differences: a = u1-u0 (bottom), b = u2-u3 (top), c = u3-u0 (left), e = u2-u1 (right)
@@ -553,17 +555,20 @@ __device__ __forceinline__ void phantom32(const DevState &d, VBlk vb, int cur, i
   double ke = 0.0;
   const float dt = d.mat.dtf;
   const float dtv = first ? 0.5f * dt : dt;
+  const float2 *__restrict__ pf2 = reinterpret_cast<const float2 *>(d.pff);
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
-    int nu = d.ph_nuser[t];
+    // users' piece-force indices in increasing element id, -1 unused
+    const int4 uf = reinterpret_cast<const int4 *>(d.ph_upf)[t];
+    const float2 f0 = uf.x >= 0 ? pf2[uf.x >> 1] : make_float2(0.f, 0.f);
+    const float2 f1 = uf.y >= 0 ? pf2[uf.y >> 1] : make_float2(0.f, 0.f);
+    const float2 f2 = uf.z >= 0 ? pf2[uf.z >> 1] : make_float2(0.f, 0.f);
+    const float2 f3 = uf.w >= 0 ? pf2[uf.w >> 1] : make_float2(0.f, 0.f);
     float fx = 0.f, fy = 0.f;
-    for (int q = 0; q < nu; ++q) {
-      int u = d.ph_users[t * 4 + q];
-      int e = u >> 3, p = (u >> 2) & 1, a = u & 3;
-      int c = d.crack_of[e];
-      fx += d.pff[c * 16 + p * 8 + 2 * a];
-      fy += d.pff[c * 16 + p * 8 + 2 * a + 1];
-    }
+    fx += f0.x; fy += f0.y;
+    fx += f1.x; fy += f1.y;
+    fx += f2.x; fy += f2.y;
+    fx += f3.x; fy += f3.y;
     if (energy)
       ke += update_special(d, N, cur, first, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N], 0, 1);
     else
@@ -585,34 +590,43 @@ __global__ void __launch_bounds__(BX * BY, TY == 8 ? 4 : 3) k_main32_batch(Batch
                                                                             int first) {
   extern __shared__ float4 smem_dyn[];
   auto &T = *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn);
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_main; w += gridDim.x) {
+  block_range(b.n_main, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_main[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    main32_tile<ENERGY, TY>(d, item_vblk(it), member_cur(d, n), first, T);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    main32_tile<ENERGY, TY>(sd, item_vblk(it), member_cur(sd, n), first, T);
     __syncthreads();
   }
 }
 
 __global__ void k_pieces32_batch(BatchDev b, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_pieces; w += gridDim.x) {
+  block_range(b.n_pieces, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_pieces[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    pieces32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), energy, it.z);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    pieces32(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), energy, it.z);
     __syncthreads();
   }
 }
 
 __global__ void k_phantom32_batch(BatchDev b, int first, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_ph; w += gridDim.x) {
+  block_range(b.n_ph, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_ph[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    phantom32(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), first, energy, it.z);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    phantom32(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), first, energy, it.z);
     __syncthreads();
   }
 }
@@ -657,11 +671,11 @@ int tiles_fp32(const DevState &d, int tile_rows) {
 }
 
 // energy partials: tiles of the smallest tile height first, then pieces and
-// phantom blocks (at most 304 each)
-int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + 2 * 304 + 8; }
+// phantom blocks (at most 1216 each)
+int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + 2 * 1216 + 8; }
 
-int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 304); }
-int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 304); }
+int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 1216); }
+int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 1216); }
 
 // energy partials one FP32 step writes with the given tile height
 int energy_parts_step_fp32(const DevState &d, int tile_rows) {

@@ -315,14 +315,15 @@ __device__ __forceinline__ void phantom64(const DevState &d, VBlk vb, int cur, i
   load_factors(d, lamN, lamD);
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
-    int nu = d.ph_nuser[t];
+    // users' piece-force indices in increasing element id, -1 unused
+    const int4 uf = reinterpret_cast<const int4 *>(d.ph_upf)[t];
+    const int us[4] = {uf.x, uf.y, uf.z, uf.w};
     double fx = 0.0, fy = 0.0;
-    for (int q = 0; q < nu; ++q) {
-      int u = d.ph_users[t * 4 + q];
-      int e = u >> 3, p = (u >> 2) & 1, a = u & 3;
-      int c = d.crack_of[e];
-      fx = fx + d.pf[c * 16 + p * 8 + 2 * a];
-      fy = fy + d.pf[c * 16 + p * 8 + 2 * a + 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (us[q] < 0) break;
+      fx = fx + d.pf[us[q]];
+      fy = fy + d.pf[us[q] + 1];
     }
     ke += update_node(d, N, cur, first != 0, fx, fy, 0, lamN, lamD);
   }
@@ -369,45 +370,58 @@ __global__ void k_eval64(DevState d, int cur) { eval64(d, hw_vblk(), cur); }
 // walking the work lists; 1-D items are (member, block, energy-partial
 // offset, member's grid size)).
 __global__ void __launch_bounds__(NT) k_main64_batch(BatchDev b, int first, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_main; w += gridDim.x) {
+  block_range(b.n_main, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_main[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    main64_tile(d, item_vblk(it), member_cur(d, n), first, energy);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    main64_tile(sd, item_vblk(it), member_cur(sd, n), first, energy);
     __syncthreads();
   }
 }
 
 __global__ void k_pieces64_batch(BatchDev b, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_pieces; w += gridDim.x) {
+  block_range(b.n_pieces, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_pieces[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    pieces64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), energy, it.z);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    pieces64(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), energy, it.z);
     __syncthreads();
   }
 }
 
 __global__ void k_phantom64_batch(BatchDev b, int first, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_ph; w += gridDim.x) {
+  block_range(b.n_ph, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_ph[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    phantom64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n), first, energy, it.z);
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    phantom64(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), first, energy, it.z);
     __syncthreads();
   }
 }
 
 __global__ void k_eval64_batch(BatchDev b) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n_eval; w += gridDim.x) {
+  block_range(b.n_eval, w0, w1);
+  for (int w = w0; w < w1; ++w) {
     const int4 it = b.w_eval[w];
-    const DevState &d = b.ds[it.x];
-    if (!member_active(d, n)) continue;
-    eval64(d, VBlk{it.y, 0, it.w, 1}, member_cur(d, n));
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    eval64(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n));
+    __syncthreads();
   }
 }
 
@@ -443,7 +457,7 @@ int tiles_fp64(const DevState &d) {
 
 int energy_parts_needed(const DevState &d) {
   if (d.precision == 1) return energy_parts_fp32(d);
-  return tiles_fp64(d) + 2 * 304 + 8;
+  return tiles_fp64(d) + 2 * 1216 + 8;
 }
 
 int energy_parts_step_fp32(const DevState &d, int tile_rows);

@@ -464,11 +464,13 @@ __global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
 // one CTA per member of a batch
 __global__ void __launch_bounds__(TB) k_select_batch(BatchDev b) {
   extern __shared__ unsigned long long smem[];
+  __shared__ DevState sd;
+  int held = -1;
   const int n = *b.bstep;
   for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
-    const DevState &d = b.ds[s];
-    if (!member_active(d, n)) continue;
-    select_plan(d, TRACK_STEP, smem);
+    stage_member(b.ds, s, sd, held);
+    if (!member_active(sd, n)) continue;
+    select_plan(sd, TRACK_STEP, smem);
     __syncthreads();
   }
 }
@@ -507,6 +509,7 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
         d.ph_owner[t] = N;
         d.ph_creator[t] = e * 4 + a;
         d.ph_nuser[t] = 0;
+        reinterpret_cast<int4 *>(d.ph_upf)[t] = make_int4(-1, -1, -1, -1);
         d.Wn[P] = 0.0;
         d.Wd[P] = 0.0;
         if (d.precision == 1) {
@@ -549,23 +552,30 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
       if (nu >= 4) {
         atomicOr(&cnt->status, STAT_CAPACITY);
       } else {
-        int us[4];
+        int us[4], uf[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) us[q] = q < nu ? d.ph_users[t * 4 + q] : 0x7fffffff;
+        for (int q = 0; q < 4; ++q) {
+          us[q] = q < nu ? d.ph_users[t * 4 + q] : 0x7fffffff;
+          uf[q] = q < nu ? d.ph_upf[t * 4 + q] : -1;
+        }
         const int code = (e << 3) | (p << 2) | a;
-        int out[4], o = 0;
+        const int cf = c * 16 + p * 8 + 2 * a;  // where this piece's force on a lands
+        int out[4], outf[4], o = 0;
         bool placed = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (!placed && (q >= nu || (us[q] >> 3) > e)) {
-            if (o < 4) out[o] = code;
+            if (o < 4) { out[o] = code; outf[o] = cf; }
             ++o;
             placed = true;
           }
-          if (q < nu && o < 4) { out[o] = us[q]; ++o; }
+          if (q < nu && o < 4) { out[o] = us[q]; outf[o] = uf[q]; ++o; }
         }
-        if (!placed && o < 4) out[o] = code;
-        for (int q = 0; q <= nu; ++q) d.ph_users[t * 4 + q] = out[q];
+        if (!placed && o < 4) { out[o] = code; outf[o] = cf; }
+        for (int q = 0; q <= nu; ++q) {
+          d.ph_users[t * 4 + q] = out[q];
+          d.ph_upf[t * 4 + q] = outf[q];
+        }
         d.ph_nuser[t] = nu + 1;
       }
     }
@@ -634,11 +644,14 @@ __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mod
 constexpr int APPLY_VB = 8;
 
 __global__ void __launch_bounds__(256) k_apply_batch(BatchDev b) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int w = blockIdx.x; w < b.n * APPLY_VB; w += gridDim.x) {
-    const DevState &d = b.ds[w / APPLY_VB];
-    if (!member_active(d, n)) continue;
-    apply_plan(d, VBlk{w % APPLY_VB, 0, APPLY_VB, 1}, member_cur(d, n) ^ 1, TRACK_STEP);
+  block_range(b.n * APPLY_VB, w0, w1);
+  for (int w = w0; w < w1; ++w) {
+    stage_member(b.ds, w / APPLY_VB, sd, held);
+    if (!member_active(sd, n)) continue;
+    apply_plan(sd, VBlk{w % APPLY_VB, 0, APPLY_VB, 1}, member_cur(sd, n) ^ 1, TRACK_STEP);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
