@@ -541,7 +541,7 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
 }
 
 template <bool ENERGY, int TY>
-__global__ void __launch_bounds__(BX * BY, TY == 8 ? 4 : 3) k_main32(DevState d, int cur,
+__global__ void __launch_bounds__(BX * BY, 4) k_main32(DevState d, int cur,
                                                                       int first) {
   extern __shared__ float4 smem_dyn[];
   main32_tile<ENERGY, TY>(d, hw_vblk(), cur, first,
@@ -586,7 +586,7 @@ __global__ void k_phantom32(DevState d, int cur, int first, int energy, int part
 // persistent: blocks walk the work list with a stride of the grid size.
 // 1-D items are (member, block, energy-partial offset, member's grid size).
 template <bool ENERGY, int TY>
-__global__ void __launch_bounds__(BX * BY, TY == 8 ? 4 : 3) k_main32_batch(BatchDev b,
+__global__ void __launch_bounds__(BX * BY, 4) k_main32_batch(BatchDev b,
                                                                             int first) {
   extern __shared__ float4 smem_dyn[];
   auto &T = *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn);
