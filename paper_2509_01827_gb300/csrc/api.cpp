@@ -408,6 +408,10 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.pl_reuse, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_tomb, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.pl_c, (size_t)d.prop_cap) && dalloc_n(h, d.pl_ph0, (size_t)d.prop_cap) &&
        dalloc_n(h, d.pl_app0, (size_t)d.prop_cap) && dalloc_n(h, d.pl_alpha, (size_t)d.prop_cap * 2) &&
+       dalloc_n(h, d.pl_mreal, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_mph, (size_t)d.prop_cap * 4) &&
+       dalloc_n(h, d.pl_mold, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_dm, (size_t)d.prop_cap * 4) &&
+       dalloc_n(h, d.pl_users, (size_t)d.prop_cap * 16) && dalloc_n(h, d.pl_upf, (size_t)d.prop_cap * 16) &&
+       dalloc_n(h, d.pl_nu, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.cnt, 1) && dalloc_n(h, d.lamN, (size_t)d.lam_cap) &&
        dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
   d.e_part_cap = energy_parts_needed(d);

@@ -121,6 +121,13 @@ struct DevState {
   int *pl_ph0;           // first new phantom id
   int *pl_app0;          // first surface-list position of its appended edges
   double *pl_alpha;      // [2] piece area fractions
+  // per local node a of each plan, computed by the selection kernel so that
+  // the split writes need no dependent loads: the real node's mass after the
+  // split, its phantom's mass after it, the phantom's mass before (-1: new),
+  // the mass the phantom gains, and the phantom's complete user list
+  double *pl_mreal, *pl_mph, *pl_mold, *pl_dm;  // [4]
+  int *pl_users, *pl_upf;  // [16]: 4 users of the phantom of each local node
+  int *pl_nu;              // [4]
 
   Counters *cnt;
   double *lamN, *lamD;   // [lam_cap] load factors of steps lam_base + i

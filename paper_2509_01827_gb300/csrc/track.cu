@@ -17,12 +17,15 @@
 //      segment between the entry and exit edge midpoints (crack patterns I
 //      and II, Fig. 2-3), phantoms shared with a cracked neighbour across a
 //      cut edge, area fractions, split-table slot, phantom ids and
-//      surface-list positions by prefix sums in increasing element id.
-// k_apply (many CTAs, eight threads per winner) runs after the node updates:
-// it writes the split records, creates phantoms (copies of u^{n+1},
-// v^{n+1/2}), recomputes the lumped masses it touches, merges momentum into
-// shared phantoms, records U_d = G_c * segment length, tombstones and
-// appends surface-list entries, and commits the counters.
+//      surface-list positions by prefix sums in increasing element id, and
+//      the lumped masses and phantom user lists the split will produce (no
+//      other winner touches the same nodes), so that the writes below need
+//      no dependent reads.
+// k_apply (many CTAs, eight threads per winner) runs after the node updates
+// and only writes the plan: split records, phantoms (copies of u^{n+1},
+// v^{n+1/2}), masses, the momentum-conserving merge into shared phantoms,
+// U_d = G_c * segment length, surface-list tombstones and appends, and the
+// counters.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,52 +74,45 @@ __device__ int block_exscan(int v, int *total) {
 // gives rho A_p / 4 of the piece that holds N (the whole area if intact).
 // Loads are issued level by level for the four elements, the sum keeps the
 // canonical order.
-__device__ double mass_real(const DevState &d, int N) {
+
+// Lumped mass of phantom P: its users (sorted by element) give rho A_p / 4.
+
+// Lumped mass of real node N once element e (N its local node a) is split
+// with piece sides side[] and area fractions alpha[]: rho A_p / 4 of every
+// piece around N that uses N, in increasing element id (the planned piece in
+// place of the intact element e).
+__device__ double mass_real_planned(const DevState &d, int N, int e, const int side[4],
+                                    const double alpha[2]) {
   const Geo &g = d.g;
   const int r = g.nx + 1, i = N % r, j = N / r;
   const int di[4] = {-1, 0, -1, 0}, dj[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
-  int e[4], st[4], c[4];
+  int eq[4], st[4], c[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int ei = i + di[q], ej = j + dj[q];
-    e[q] = (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) ? -1 : ej * g.nx + ei;
+    eq[q] = (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) ? -1 : ej * g.nx + ei;
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) st[q] = e[q] < 0 ? ST_OUT : (int)d.estate[e[q]];
+  for (int q = 0; q < 4; ++q)
+    st[q] = eq[q] < 0 ? ST_OUT : (eq[q] == e ? ST_CRACKED : (int)d.estate[eq[q]]);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) c[q] = st[q] == ST_CRACKED ? d.crack_of[e[q]] : -1;
+  for (int q = 0; q < 4; ++q)
+    c[q] = (st[q] == ST_CRACKED && eq[q] != e) ? d.crack_of[eq[q]] : -1;
   double Ap[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     Ap[q] = g.A;
-    if (c[q] >= 0) {
-      const int side = (d.ck_info[c[q]] >> (4 + la[q])) & 1;
-      Ap[q] = d.ck_Ap[c[q] * 2 + side];
+    if (eq[q] == e) {
+      Ap[q] = alpha[side[la[q]]] * g.A;
+    } else if (c[q] >= 0) {
+      const int sd = (d.ck_info[c[q]] >> (4 + la[q])) & 1;
+      Ap[q] = d.ck_Ap[c[q] * 2 + sd];
     }
   }
   double acc = 0.0;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (st[q] != ST_OUT) acc = acc + d.mat.rho * Ap[q] * 0.25;
-  return acc;
-}
-
-// Lumped mass of phantom P: its users (sorted by element) give rho A_p / 4.
-__device__ double mass_phantom(const DevState &d, int P) {
-  const int t = P - d.g.nn;
-  const int nu = d.ph_nuser[t];
-  int u[4], c[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) u[q] = q < nu ? d.ph_users[t * 4 + q] : -1;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) c[q] = u[q] >= 0 ? d.crack_of[u[q] >> 3] : -1;
-  double Ap[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) Ap[q] = c[q] >= 0 ? d.ck_Ap[c[q] * 2 + ((u[q] >> 2) & 1)] : 0.0;
-  double acc = 0.0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (q < nu) acc = acc + d.mat.rho * Ap[q] * 0.25;
   return acc;
 }
 
@@ -241,7 +237,8 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
   int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP]
   __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done;
   __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_reuse[WB][4], b_app[WB],
-      b_tomb[WB][4];
+      b_tomb[WB][4], b_c[WB];
+  __shared__ double b_alpha[WB][2];
   Counters *cnt = d.cnt;
   const Geo &g = d.g;
   const int tid = threadIdx.x;
@@ -431,8 +428,70 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
         d.pl_c[w] = s_nck + wl;
         d.pl_ph0[w] = g.nn + s_nph + pre_new;
         d.pl_app0[w] = s_nS + pre_app;
+        b_alpha[wl][0] = alpha[0];
+        b_alpha[wl][1] = alpha[1];
+        b_c[wl] = s_nck + wl;
       }
       if (act && lane == 0 && !s_stop) atomicAdd(&s_dead, ndead);
+      __syncthreads();
+      if (act && lane < 4 && !s_stop) {
+        // local node a: masses after the split and the phantom's user list
+        const int w = base + wl, e = b_e[wl], a = lane;
+        int side[4];
+        for (int q = 0; q < 4; ++q) side[q] = b_side[wl][q];
+        const double alpha[2] = {b_alpha[wl][0], b_alpha[wl][1]};
+        const int N = elem_node(g, e, a);
+        d.pl_mreal[w * 4 + a] = mass_real_planned(d, N, e, side, alpha);
+        const int p = 1 - side[a];  // the piece that uses the phantom of a
+        const int code = (e << 3) | (p << 2) | a, cf = b_c[wl] * 16 + p * 8 + 2 * a;
+        const double Anew = alpha[p] * g.A;
+        const int P = b_reuse[wl][a];
+        int us[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff}, uf[4] = {-1, -1, -1, -1};
+        int nu = 0;
+        double mold = -1.0;
+        if (P >= 0) {
+          const int t = P - g.nn;
+          nu = d.ph_nuser[t];
+          for (int q = 0; q < nu && q < 4; ++q) {
+            us[q] = d.ph_users[t * 4 + q];
+            uf[q] = d.ph_upf[t * 4 + q];
+          }
+          mold = d.m[P];
+        }
+        // insert the new user in increasing element id (as the split writes did)
+        int out[4] = {-1, -1, -1, -1}, outf[4] = {-1, -1, -1, -1}, o = 0;
+        bool placed = false;
+        for (int q = 0; q < 4; ++q) {
+          if (!placed && (q >= nu || (us[q] >> 3) > e)) {
+            if (o < 4) { out[o] = code; outf[o] = cf; }
+            ++o;
+            placed = true;
+          }
+          if (q < nu && o < 4) { out[o] = us[q]; outf[o] = uf[q]; ++o; }
+        }
+        if (!placed && o < 4) { out[o] = code; outf[o] = cf; }
+        // the phantom's mass: rho A_p / 4 of each user piece, in list order
+        double acc = 0.0;
+        const int nun = nu < 4 ? nu + 1 : 4;
+        for (int q = 0; q < nun; ++q) {
+          double Ap;
+          if (out[q] == code) {
+            Ap = Anew;
+          } else {
+            const int cu = d.crack_of[out[q] >> 3];
+            Ap = d.ck_Ap[cu * 2 + ((out[q] >> 2) & 1)];
+          }
+          acc = acc + d.mat.rho * Ap * 0.25;
+        }
+        d.pl_mph[w * 4 + a] = acc;
+        d.pl_mold[w * 4 + a] = mold;
+        d.pl_dm[w * 4 + a] = d.mat.rho * Anew * 0.25;
+        d.pl_nu[w * 4 + a] = nu;  // users before the insertion (4: list full)
+        for (int q = 0; q < 4; ++q) {
+          d.pl_users[w * 16 + a * 4 + q] = out[q];
+          d.pl_upf[w * 16 + a * 4 + q] = outf[q];
+        }
+      }
       __syncthreads();
       if (tid == 0 && !s_stop) {
         s_nph += tot_new;
@@ -489,18 +548,19 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
   for (int wb = warp * 4; wb < nw; wb += nwarps * 4) {
     const int w = wb + grp;
     const bool act = w < nw;
-    int e = 0, info = 0, c = 0, sd = 0, a = lane & 3, P = -1, N = 0;
-    double mold = -1.0;
-    if (act) {
-      e = d.pl_e[w];
-      info = d.pl_info[w];
-      c = d.pl_c[w];
-      sd = (info >> (4 + a)) & 1;
-      N = elem_node(g, e, a);
-    }
-    // phase A: phantoms and node lists (lanes 0-3); the split record (lane 4)
+    const int a = lane & 3;
     if (act && lane < 4) {
-      P = d.pl_reuse[w * 4 + a];
+      // local node a: its phantom (new or shared), node lists, user list,
+      // masses; the momentum-conserving merge into a shared phantom
+      const int e = d.pl_e[w], info = d.pl_info[w], c = d.pl_c[w];
+      const int sd = (info >> (4 + a)) & 1;
+      const int N = elem_node(g, e, a);
+      int P = d.pl_reuse[w * 4 + a];
+      const double mold = d.pl_mold[w * 4 + a], mnew = d.pl_mph[w * 4 + a];
+      const int nu = d.pl_nu[w * 4 + a];
+      const int4 us = reinterpret_cast<const int4 *>(d.pl_users)[w * 4 + a];
+      const int4 uf = reinterpret_cast<const int4 *>(d.pl_upf)[w * 4 + a];
+      const double mreal = d.pl_mreal[w * 4 + a], dm = d.pl_dm[w * 4 + a];
       if (P < 0) {
         int rank = 0;
         for (int q = 0; q < a; ++q) rank += d.pl_reuse[w * 4 + q] < 0;
@@ -508,8 +568,6 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
         const int t = P - g.nn;
         d.ph_owner[t] = N;
         d.ph_creator[t] = e * 4 + a;
-        d.ph_nuser[t] = 0;
-        reinterpret_cast<int4 *>(d.ph_upf)[t] = make_int4(-1, -1, -1, -1);
         d.Wn[P] = 0.0;
         d.Wd[P] = 0.0;
         if (d.precision == 1) {
@@ -519,93 +577,35 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
           d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
           d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
         }
-      } else {
-        mold = d.m[P];
+      } else if (mold >= 0.0) {
+        // merge: the phantom gains mass dm moving with its real node
+        if (d.precision == 1) {
+          const float2 vp = d.v2[P], vn = d.v2[N];
+          const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
+          const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
+          d.v2[P] = make_float2((float)vx, (float)vy);
+        } else {
+          d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
+          d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
+        }
       }
       d.ck_node[c * 8 + sd * 4 + a] = N;
       d.ck_node[c * 8 + (1 - sd) * 4 + a] = P;
-    } else if (act && lane == 4) {
-      const int ka = info & 3, kb = (info >> 2) & 3;
-      d.ck_elem[c] = e;
-      d.ck_info[c] = info & 0xff;
-      d.ck_Ap[c * 2] = d.pl_alpha[w * 2] * g.A;
-      d.ck_Ap[c * 2 + 1] = d.pl_alpha[w * 2 + 1] * g.A;
-      d.ck_step[c] = mode == TRACK_PRECRACK ? -1 : step;
-      if (mode == TRACK_PRECRACK) {
-        d.ck_ud[c] = 0.0;
-      } else {
-        const double xa = (xi_g(ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(ka) + 1.0) * (0.5 * g.hy);
-        const double xb = (xi_g(kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(kb) + 1.0) * (0.5 * g.hy);
-        const double sx = xb - xa, sy = yb - ya;
-        const double L = sqrt(sx * sx + sy * sy);
-        d.ck_ud[c] = (double)d.gc[e] * L;
-      }
-      d.crack_of[e] = c;
-      d.estate[e] = ST_CRACKED;
-    }
-    __syncwarp();
-    // phase B: users of the phantoms, kept sorted by element id
-    if (act && lane < 4) {
-      const int p = 1 - sd;
       const int t = P - g.nn;
-      const int nu = d.ph_nuser[t];
       if (nu >= 4) {
         atomicOr(&cnt->status, STAT_CAPACITY);
       } else {
-        int us[4], uf[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          us[q] = q < nu ? d.ph_users[t * 4 + q] : 0x7fffffff;
-          uf[q] = q < nu ? d.ph_upf[t * 4 + q] : -1;
-        }
-        const int code = (e << 3) | (p << 2) | a;
-        const int cf = c * 16 + p * 8 + 2 * a;  // where this piece's force on a lands
-        int out[4], outf[4], o = 0;
-        bool placed = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (!placed && (q >= nu || (us[q] >> 3) > e)) {
-            if (o < 4) { out[o] = code; outf[o] = cf; }
-            ++o;
-            placed = true;
-          }
-          if (q < nu && o < 4) { out[o] = us[q]; outf[o] = uf[q]; ++o; }
-        }
-        if (!placed && o < 4) { out[o] = code; outf[o] = cf; }
-        for (int q = 0; q <= nu; ++q) {
-          d.ph_users[t * 4 + q] = out[q];
-          d.ph_upf[t * 4 + q] = outf[q];
-        }
+        reinterpret_cast<int4 *>(d.ph_users)[t] = us;
+        reinterpret_cast<int4 *>(d.ph_upf)[t] = uf;
         d.ph_nuser[t] = nu + 1;
       }
-    }
-    __syncwarp();
-    // phase C: masses of the real nodes (lanes 0-3) and their phantoms
-    // (lanes 4-7, momentum-conserving merge into a reused phantom)
-    const int Pn = __shfl_sync(0xffffffffu, P, (lane32 & ~7) | a);
-    const double mo = __shfl_sync(0xffffffffu, mold, (lane32 & ~7) | a);
-    if (act && lane < 4) {
-      set_mass(d, N, mass_real(d, N));
+      set_mass(d, N, mreal);
+      set_mass(d, P, mnew);
     } else if (act) {
-      const int p = 1 - sd;
-      const double mnew = mass_phantom(d, Pn);
-      if (mo >= 0.0) {
-        const double dm = d.mat.rho * (d.pl_alpha[w * 2 + p] * g.A) * 0.25;
-        if (d.precision == 1) {
-          const float2 vp = d.v2[Pn], vn = d.v2[N];
-          const double vx = ((mo * (double)vp.x) + dm * (double)vn.x) / mnew;
-          const double vy = ((mo * (double)vp.y) + dm * (double)vn.y) / mnew;
-          d.v2[Pn] = make_float2((float)vx, (float)vy);
-        } else {
-          d.vx[Pn] = (mo * d.vx[Pn] + dm * d.vx[N]) / mnew;
-          d.vy[Pn] = (mo * d.vy[Pn] + dm * d.vy[N]) / mnew;
-        }
-      }
-      set_mass(d, Pn, mnew);
-    }
-    // phase D: surface list -- lanes 0-3 handle local edge k = lane
-    if (act && lane < 4) {
-      const int k = lane;
+      // lanes 4-7: surface list at local edge k = lane - 4; lane 4 also
+      // writes the split record
+      const int e = d.pl_e[w], info = d.pl_info[w];
+      const int k = lane - 4;
       const int ed = elem_edge(g, e, k);
       const int app = (info >> 8) & 15;
       if ((app >> k) & 1) {
@@ -621,6 +621,26 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
           d.S[pos] = -1;
           d.spos[ed] = -1;
         }
+      }
+      if (lane == 4) {
+        const int c = d.pl_c[w];
+        const int ka = info & 3, kb = (info >> 2) & 3;
+        d.ck_elem[c] = e;
+        d.ck_info[c] = info & 0xff;
+        d.ck_Ap[c * 2] = d.pl_alpha[w * 2] * g.A;
+        d.ck_Ap[c * 2 + 1] = d.pl_alpha[w * 2 + 1] * g.A;
+        d.ck_step[c] = mode == TRACK_PRECRACK ? -1 : step;
+        if (mode == TRACK_PRECRACK) {
+          d.ck_ud[c] = 0.0;
+        } else {
+          const double xa = (xi_g(ka) + 1.0) * (0.5 * g.hx), ya = (eta_g(ka) + 1.0) * (0.5 * g.hy);
+          const double xb = (xi_g(kb) + 1.0) * (0.5 * g.hx), yb = (eta_g(kb) + 1.0) * (0.5 * g.hy);
+          const double sx = xb - xa, sy = yb - ya;
+          const double L = sqrt(sx * sx + sy * sy);
+          d.ck_ud[c] = (double)d.gc[e] * L;
+        }
+        d.crack_of[e] = c;
+        d.estate[e] = ST_CRACKED;
       }
     }
   }
