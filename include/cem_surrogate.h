@@ -36,11 +36,14 @@ extern "C" {
 #define CEM_SG_ERR_CUDA -2
 
 /* y[p, yoff + o] = act(bias[o] + sum_{ky,kx,c} x[p + (ky-1, kx-1), c] w[o][ky][kx][c]),
- * zero outside the image, act = ReLU when relu != 0.  Cin, ldx multiples of
- * 8; Cout, yoff even; bias may be NULL.  Implicit GEMM on the tensor cores. */
+ * zero outside the image, act = ReLU when relu != 0, and set to zero where
+ * mask[p, o] <= 0 when mask (pixel stride ldmask) is given -- the data
+ * gradient of a layer whose input is a ReLU output.  Cin, ldx multiples of 8;
+ * Cout, yoff, ldmask even; bias, mask may be NULL.  Implicit GEMM on the
+ * tensor cores. */
 int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const void *w,
-                   const float *bias, int Cout, int relu, void *y, int ldy, int yoff,
-                   void *stream);
+                   const float *bias, int Cout, int relu, const void *mask, int ldmask, void *y,
+                   int ldy, int yoff, void *stream);
 
 /* Workspace bytes cem_sg_conv3x3_wgrad needs for this shape. */
 long cem_sg_wgrad_workspace(int B, int H, int W, int Cin, int Cout);
@@ -59,15 +62,18 @@ int cem_sg_conv3x3_wgrad(const void *x, int ldx, const void *dy, int lddy, int B
 int cem_sg_relu_bwd(void *dy, int lddy, const void *y, int ldy, long P, int C, void *stream);
 
 /* 2x2 max pooling of x [B, 2H, 2W] (pixel stride ldx, channels 0..C-1) into
- * dense y [B, H, W, C]. */
+ * dense y [B, H, W, C].  Pooling and upsampling need C, strides and channel
+ * offsets that are multiples of 8 (16-byte vectors). */
 int cem_sg_maxpool2(const void *x, int ldx, int B, int H, int W, int C, void *y, void *stream);
 
 /* Its gradient: dy [B, H, W, C] goes to the first maximum (window order
  * (0,0), (0,1), (1,0), (1,1)) of each window of x; dskip (channels skoff ..
- * skoff+C-1 of a [B, 2H, 2W, ldskip] tensor, may be NULL) is added; dx is
- * dense [B, 2H, 2W, C]. */
+ * skoff+C-1 of a [B, 2H, 2W, ldskip] tensor, may be NULL) is added; with
+ * relu_mask the result is zero where x <= 0 (x a ReLU output); dx is dense
+ * [B, 2H, 2W, C]. */
 int cem_sg_maxpool2_bwd(const void *x, int ldx, const void *dy, const void *dskip, int ldskip,
-                        int skoff, int B, int H, int W, int C, void *dx, void *stream);
+                        int skoff, int B, int H, int W, int C, int relu_mask, void *dx,
+                        void *stream);
 
 /* Nearest 2x upsampling of dense x [B, H, W, C] into channels yoff ..
  * yoff+C-1 of y [B, 2H, 2W, ldy]. */
@@ -75,9 +81,10 @@ int cem_sg_upsample2(const void *x, int B, int H, int W, int C, void *y, int ldy
                      void *stream);
 
 /* Its gradient: dx [B, H, W, C] = sum of each 2x2 block of dy's channels
- * 0..C-1 (dy [B, 2H, 2W, lddy]). */
-int cem_sg_upsample2_bwd(const void *dy, int lddy, int B, int H, int W, int C, void *dx,
-                         void *stream);
+ * 0..C-1 (dy [B, 2H, 2W, lddy]), zero where mask [B, H, W, ldmask] <= 0
+ * when mask is given (the upsampled tensor a ReLU output). */
+int cem_sg_upsample2_bwd(const void *dy, int lddy, int B, int H, int W, int C, const void *mask,
+                         int ldmask, void *dx, void *stream);
 
 /* 1x1 head: z[p] = b[0] + sum_c x[p, c] w[c] (FP32 logits, x dense [P, C]). */
 int cem_sg_head_fwd(const void *x, int P, int C, const float *w, const float *b, float *z,
@@ -85,8 +92,9 @@ int cem_sg_head_fwd(const void *x, int P, int C, const float *w, const float *b,
 
 long cem_sg_head_workspace(int P, int C);
 
-/* Its gradients: dx[p, c] = dz[p] w[c] (BF16), dw[c] = sum_p dz[p] x[p, c],
- * db[0] = sum_p dz[p].  C <= 32. */
+/* Its gradients: dx[p, c] = dz[p] w[c] where x[p, c] > 0, else 0 (x is a
+ * ReLU output; BF16), dw[c] = sum_p dz[p] x[p, c], db[0] = sum_p dz[p].
+ * C <= 32. */
 int cem_sg_head_bwd(const void *x, int P, int C, const float *w, const float *dz, void *dx,
                     float *dw, float *db, void *ws, long ws_bytes, void *stream);
 

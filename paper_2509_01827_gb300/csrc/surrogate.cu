@@ -70,7 +70,8 @@ struct ConvArgs {
   const bf16_t *w;   // [N, K] weights, K = 9 * Cin, k = (ky * 3 + kx) * Cin + c
   const float *bias; // [N] or null
   bf16_t *y;         // [P, ldy] output, channels yoff .. yoff + N - 1
-  int B, H, W, Cin, ldx, N, K, relu, ldy, yoff, P;
+  const bf16_t *mask;  // [P, ldm] or null: outputs where mask <= 0 are set to 0
+  int B, H, W, Cin, ldx, N, K, relu, ldy, yoff, P, ldm;
 };
 
 __global__ void __launch_bounds__(256) k_conv3x3(ConvArgs a) {
@@ -168,6 +169,11 @@ __global__ void __launch_bounds__(256) k_conv3x3(ConvArgs a) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
         }
+        if (a.mask) {
+          const uint32_t mk = *reinterpret_cast<const uint32_t *>(a.mask + (size_t)p * a.ldm + n);
+          if (!(bf2f((bf16_t)(mk & 0xffff)) > 0.f)) v0 = 0.f;
+          if (!(bf2f((bf16_t)(mk >> 16)) > 0.f)) v1 = 0.f;
+        }
         const uint32_t pk = (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
         *reinterpret_cast<uint32_t *>(a.y + (size_t)p * a.ldy + a.yoff + n) = pk;
       }
@@ -183,6 +189,7 @@ struct WgradArgs {
   const bf16_t *x;   // [P, ldx] forward input
   const bf16_t *dy;  // [P, lddy] output gradient (channels 0..N-1)
   float *ws;         // [splits][N][K]
+  float *wsb;        // [splits][N] bias partials (null: no bias gradient)
   int B, H, W, Cin, ldx, lddy, N, K, P, chunk;  // chunk: pixels per split
 };
 
@@ -224,6 +231,10 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(WgradArgs a) {
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  // bias: the k-tile-0 blocks also sum dY over their pixels, channel
+  // n = tid & 63 over pixel rows (tid >> 6) + 4 r of each staged tile
+  const bool do_bias = a.wsb && blockIdx.y == 0;
+  float bsum = 0.f;
 #pragma unroll
   for (int s = 0; s < GST - 1; ++s) {
     if (s < KT) load_tile(s, s);
@@ -236,6 +247,10 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(WgradArgs a) {
     if (nk < KT) load_tile(nk, nk % GST);
     cp_async_commit();
     const int s = kt % GST;
+    if (do_bias) {
+#pragma unroll
+      for (int r = 0; r < GBK / 4; ++r) bsum += bf2f(As[s][(tid >> 6) + 4 * r][tid & 63]);
+    }
 #pragma unroll
     for (int kk = 0; kk < GBK; kk += 16) {
       const int mat = lane >> 3, r = lane & 7;
@@ -252,6 +267,13 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(WgradArgs a) {
     }
   }
   cp_async_wait<0>();
+  if (do_bias) {
+    __shared__ float red[4][64];
+    red[tid >> 6][tid & 63] = bsum;
+    __syncthreads();
+    if (tid < 64 && m0 + tid < a.N)
+      a.wsb[(size_t)z * a.N + m0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+  }
   float *out = a.ws + (size_t)z * a.N * a.K;
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
@@ -278,17 +300,6 @@ __global__ void k_reduce_splits(const float *ws, int splits, long n, float *out)
   }
 }
 
-// per-channel sums of a BF16 [P, ld] tensor over fixed pixel chunks:
-// ws[chunk][c]; the chunks are then added in order by k_reduce_splits
-__global__ void k_colsum_chunks(const bf16_t *t, int P, int C, int ld, int chunk, float *ws) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int z = blockIdx.y;
-  if (c >= C) return;
-  const int pend = min(P, (z + 1) * chunk);
-  float s = 0.f;
-  for (int p = z * chunk; p < pend; ++p) s += bf2f(t[(size_t)p * ld + c]);
-  ws[(size_t)z * C + c] = s;
-}
 
 // ------------------------------------------------------------- elementwise
 // dy[p, c] = 0 where y[p, c] <= 0 (gradient through ReLU, given its output)
@@ -301,52 +312,88 @@ __global__ void k_relu_bwd(bf16_t *dy, int lddy, const bf16_t *y, int ldy, long 
   }
 }
 
-// 2x2 max pooling: x [B, 2H, 2W, C] (pixel stride ldx) -> y [B, H, W, C]
+// Pooling and upsampling move 8 channels (16 bytes) per thread; channel
+// counts, strides and offsets are multiples of 8.
+__device__ __forceinline__ void unpack8(uint4 v, float f[8]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    f[2 * q] = bf2f((bf16_t)(w[q] & 0xffff));
+    f[2 * q + 1] = bf2f((bf16_t)(w[q] >> 16));
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float f[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = (uint32_t)f2bf(f[2 * q]) | ((uint32_t)f2bf(f[2 * q + 1]) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ uint4 ld8(const bf16_t *p) { return *reinterpret_cast<const uint4 *>(p); }
+__device__ __forceinline__ void st8(bf16_t *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+// 2x2 max pooling: x [B, 2H, 2W] (pixel stride ldx) -> y [B, H, W, C] dense
 __global__ void k_maxpool2(const bf16_t *x, int ldx, int B, int H, int W, int C, bf16_t *y) {
-  const long n = (long)B * H * W * C;
+  const int C8 = C >> 3;
+  const long n = (long)B * H * W * C8;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long pix = i / C;
+    const int c = (int)(i % C8) * 8;
+    const long pix = i / C8;
     const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
     const size_t base = ((size_t)(b * 2 * H + 2 * h) * (2 * W) + 2 * w) * ldx + c;
-    const float v0 = bf2f(x[base]), v1 = bf2f(x[base + ldx]);
-    const float v2 = bf2f(x[base + (size_t)2 * W * ldx]), v3 = bf2f(x[base + (size_t)2 * W * ldx + ldx]);
-    y[i] = f2bf(fmaxf(fmaxf(v0, v1), fmaxf(v2, v3)));
+    const size_t row = (size_t)2 * W * ldx;
+    float v[4][8], o[8];
+    unpack8(ld8(x + base), v[0]);
+    unpack8(ld8(x + base + ldx), v[1]);
+    unpack8(ld8(x + base + row), v[2]);
+    unpack8(ld8(x + base + row + ldx), v[3]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o[q] = fmaxf(fmaxf(v[0][q], v[1][q]), fmaxf(v[2][q], v[3][q]));
+    st8(y + (size_t)pix * C + c, pack8(o));
   }
 }
 
 // gradient of 2x2 max pooling to the first maximum of each window, plus an
-// optional skip gradient (dskip [.., ldskip] at channel offset skoff):
-// dx [B, 2H, 2W, C] dense
+// optional skip gradient (dskip [.., ldskip] at channel offset skoff), zero
+// where x <= 0 when relu_mask (x is a ReLU output): dx [B, 2H, 2W, C] dense
 __global__ void k_maxpool2_bwd(const bf16_t *x, int ldx, const bf16_t *dy, const bf16_t *dskip,
-                               int ldskip, int skoff, int B, int H, int W, int C, bf16_t *dx) {
-  const long n = (long)B * H * W * C;
+                               int ldskip, int skoff, int B, int H, int W, int C, int relu_mask,
+                               bf16_t *dx) {
+  const int C8 = C >> 3;
+  const long n = (long)B * H * W * C8;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long pix = i / C;
+    const int c = (int)(i % C8) * 8;
+    const long pix = i / C8;
     const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
-    size_t src[4], dst[4];
-    float v[4];
+    float v[4][8], g[8];
+    size_t pp[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int hh = 2 * h + (q >> 1), ww = 2 * w + (q & 1);
-      const size_t pp = (size_t)(b * 2 * H + hh) * (2 * W) + ww;
-      src[q] = pp * ldx + c;
-      dst[q] = pp;
-      v[q] = bf2f(x[src[q]]);
+      pp[q] = (size_t)(b * 2 * H + 2 * h + (q >> 1)) * (2 * W) + 2 * w + (q & 1);
+      unpack8(ld8(x + pp[q] * ldx + c), v[q]);
     }
-    const float m = fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
-    const float g = bf2f(dy[i]);
-    bool taken = false;
+    unpack8(ld8(dy + (size_t)pix * C + c), g);
+    float m[8];
+    bool taken[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      m[k] = fmaxf(fmaxf(v[0][k], v[1][k]), fmaxf(v[2][k], v[3][k]));
+      taken[k] = false;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float o = 0.f;
-      if (!taken && v[q] == m) {
-        o = g;
-        taken = true;
+      float sk[8], o[8];
+      if (dskip) unpack8(ld8(dskip + pp[q] * ldskip + skoff + c), sk);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        o[k] = 0.f;
+        if (!taken[k] && v[q][k] == m[k]) {
+          o[k] = g[k];
+          taken[k] = true;
+        }
+        if (dskip) o[k] += sk[k];
+        if (relu_mask && !(v[q][k] > 0.f)) o[k] = 0.f;
       }
-      if (dskip) o += bf2f(dskip[dst[q] * ldskip + skoff + c]);
-      dx[dst[q] * C + c] = f2bf(o);
+      st8(dx + pp[q] * C + c, pack8(o));
     }
   }
 }
@@ -354,31 +401,43 @@ __global__ void k_maxpool2_bwd(const bf16_t *x, int ldx, const bf16_t *dy, const
 // nearest 2x upsampling: x [B, H, W, C] dense -> y [B, 2H, 2W, ldy] at channel offset yoff
 __global__ void k_upsample2(const bf16_t *x, int B, int H, int W, int C, bf16_t *y, int ldy,
                             int yoff) {
-  const long n = (long)B * 4 * H * W * C;
+  const int C8 = C >> 3;
+  const long n = (long)B * 4 * H * W * C8;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long pix = i / C;  // output pixel
+    const int c = (int)(i % C8) * 8;
+    const long pix = i / C8;  // output pixel
     const int ww = (int)(pix % (2 * W)), hh = (int)((pix / (2 * W)) % (2 * H));
     const int b = (int)(pix / ((long)4 * W * H));
-    y[(size_t)pix * ldy + yoff + c] = x[((size_t)(b * H + hh / 2) * W + ww / 2) * C + c];
+    st8(y + (size_t)pix * ldy + yoff + c, ld8(x + ((size_t)(b * H + hh / 2) * W + ww / 2) * C + c));
   }
 }
 
-// gradient of nearest 2x upsampling: dy [B, 2H, 2W, lddy] channels 0..C-1 -> dx [B, H, W, C]
+// gradient of nearest 2x upsampling: dy [B, 2H, 2W, lddy] channels 0..C-1 ->
+// dx [B, H, W, C], zero where mask <= 0 (mask [B, H, W, ldm], may be null)
 __global__ void k_upsample2_bwd(const bf16_t *dy, int lddy, int B, int H, int W, int C,
-                                bf16_t *dx) {
-  const long n = (long)B * H * W * C;
+                                const bf16_t *mask, int ldm, bf16_t *dx) {
+  const int C8 = C >> 3;
+  const long n = (long)B * H * W * C8;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long pix = i / C;
+    const int c = (int)(i % C8) * 8;
+    const long pix = i / C8;
     const int w = (int)(pix % W), h = (int)((pix / W) % H), b = (int)(pix / ((long)W * H));
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, t[8];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const size_t pp = (size_t)(b * 2 * H + 2 * h + (q >> 1)) * (2 * W) + 2 * w + (q & 1);
-      s += bf2f(dy[pp * lddy + c]);
+      unpack8(ld8(dy + pp * lddy + c), t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += t[k];
     }
-    dx[i] = f2bf(s);
+    if (mask) {
+      float mk[8];
+      unpack8(ld8(mask + (size_t)pix * ldm + c), mk);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (!(mk[k] > 0.f)) s[k] = 0.f;
+    }
+    st8(dx + (size_t)pix * C + c, pack8(s));
   }
 }
 
@@ -405,7 +464,8 @@ __global__ void k_head_bwd(const bf16_t *x, int P, int C, const float *w, const 
     const float g = dz[p];
     for (int cc = c; cc < C; cc += 32) {
       const float xv = bf2f(x[(size_t)p * C + cc]);
-      dx[(size_t)p * C + cc] = f2bf(g * w[cc]);
+      // x is a ReLU output: its gradient is zero where x <= 0
+      dx[(size_t)p * C + cc] = xv > 0.f ? f2bf(g * w[cc]) : (bf16_t)0;
       if (cc == c) s += g * xv;
     }
     sb += g;
@@ -509,10 +569,11 @@ int grid_1d(long n, int block) {
 extern "C" {
 
 int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const void *w,
-                   const float *bias, int Cout, int relu, void *y, int ldy, int yoff,
-                   void *stream) {
+                   const float *bias, int Cout, int relu, const void *mask, int ldmask, void *y,
+                   int ldy, int yoff, void *stream) {
   if (!x || !w || !y || B < 1 || H < 1 || W < 1 || Cin < 8 || (Cin & 7) || ldx < Cin ||
-      (ldx & 7) || Cout < 2 || (Cout & 1) || ldy < yoff + Cout || (yoff & 1))
+      (ldx & 7) || Cout < 2 || (Cout & 1) || ldy < yoff + Cout || (yoff & 1) ||
+      (mask && (ldmask < Cout || (ldmask & 1))))
     return CEM_SG_ERR_ARG;
   ConvArgs a;
   a.x = (const bf16_t *)x;
@@ -521,6 +582,8 @@ int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const v
   a.y = (bf16_t *)y;
   a.B = B; a.H = H; a.W = W; a.Cin = Cin; a.ldx = ldx; a.N = Cout; a.K = 9 * Cin;
   a.relu = relu; a.ldy = ldy; a.yoff = yoff; a.P = B * H * W;
+  a.mask = (const bf16_t *)mask;
+  a.ldm = ldmask;
   dim3 grid((a.P + FBM - 1) / FBM, (Cout + FBN - 1) / FBN);
   k_conv3x3<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
@@ -551,18 +614,12 @@ int cem_sg_conv3x3_wgrad(const void *x, int ldx, const void *dy, int lddy, int B
   if (splits > 256) splits = 256;
   a.chunk = ((a.P + splits - 1) / splits + GBK - 1) / GBK * GBK;
   splits = (a.P + a.chunk - 1) / a.chunk;
+  a.wsb = db ? a.ws + (size_t)splits * Cout * a.K : nullptr;
   dim3 grid((Cout + GBM - 1) / GBM, (a.K + GBN - 1) / GBN, splits);
   k_conv3x3_wgrad<<<grid, 256, 0, st>>>(a);
   const long nw = (long)Cout * a.K;
   k_reduce_splits<<<grid_1d(nw, 256), 256, 0, st>>>(a.ws, splits, nw, dw);
-  if (db) {
-    // bias: per-channel sums over fixed pixel chunks, then in chunk order
-    const int chunk = a.P / 1024 + 1 > 4096 ? a.P / 1024 + 1 : 4096;  // at most 1024 chunks
-    const int nz = (a.P + chunk - 1) / chunk;
-    float *wsb = a.ws;  // reused after the weight reduction (same stream)
-    k_colsum_chunks<<<dim3((Cout + 127) / 128, nz), 128, 0, st>>>(a.dy, a.P, Cout, lddy, chunk, wsb);
-    k_reduce_splits<<<grid_1d(Cout, 128), 128, 0, st>>>(wsb, nz, Cout, db);
-  }
+  if (db) k_reduce_splits<<<grid_1d(Cout, 128), 128, 0, st>>>(a.wsb, splits, Cout, db);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 
@@ -574,40 +631,46 @@ int cem_sg_relu_bwd(void *dy, int lddy, const void *y, int ldy, long P, int C, v
 }
 
 int cem_sg_maxpool2(const void *x, int ldx, int B, int H, int W, int C, void *y, void *stream) {
-  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 1 || ldx < C) return CEM_SG_ERR_ARG;
-  const long n = (long)B * H * W * C;
+  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 8 || (C & 7) || ldx < C || (ldx & 7))
+    return CEM_SG_ERR_ARG;
+  const long n = (long)B * H * W * (C >> 3);
   k_maxpool2<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)x, ldx, B, H, W, C,
                                                                (bf16_t *)y);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 
 int cem_sg_maxpool2_bwd(const void *x, int ldx, const void *dy, const void *dskip, int ldskip,
-                        int skoff, int B, int H, int W, int C, void *dx, void *stream) {
-  if (!x || !dy || !dx || B < 1 || H < 1 || W < 1 || C < 1 || ldx < C ||
-      (dskip && ldskip < skoff + C))
+                        int skoff, int B, int H, int W, int C, int relu_mask, void *dx,
+                        void *stream) {
+  if (!x || !dy || !dx || B < 1 || H < 1 || W < 1 || C < 8 || (C & 7) || ldx < C || (ldx & 7) ||
+      (dskip && (ldskip < skoff + C || (ldskip & 7) || (skoff & 7))))
     return CEM_SG_ERR_ARG;
-  const long n = (long)B * H * W * C;
+  const long n = (long)B * H * W * (C >> 3);
   k_maxpool2_bwd<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(
       (const bf16_t *)x, ldx, (const bf16_t *)dy, (const bf16_t *)dskip, ldskip, skoff, B, H, W, C,
-      (bf16_t *)dx);
+      relu_mask, (bf16_t *)dx);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 
 int cem_sg_upsample2(const void *x, int B, int H, int W, int C, void *y, int ldy, int yoff,
                      void *stream) {
-  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 1 || ldy < yoff + C) return CEM_SG_ERR_ARG;
-  const long n = (long)B * 4 * H * W * C;
+  if (!x || !y || B < 1 || H < 1 || W < 1 || C < 8 || (C & 7) || ldy < yoff + C || (ldy & 7) ||
+      (yoff & 7))
+    return CEM_SG_ERR_ARG;
+  const long n = (long)B * 4 * H * W * (C >> 3);
   k_upsample2<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)x, B, H, W, C,
                                                                 (bf16_t *)y, ldy, yoff);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 
-int cem_sg_upsample2_bwd(const void *dy, int lddy, int B, int H, int W, int C, void *dx,
-                         void *stream) {
-  if (!dy || !dx || B < 1 || H < 1 || W < 1 || C < 1 || lddy < C) return CEM_SG_ERR_ARG;
-  const long n = (long)B * H * W * C;
-  k_upsample2_bwd<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16_t *)dy, lddy, B, H,
-                                                                    W, C, (bf16_t *)dx);
+int cem_sg_upsample2_bwd(const void *dy, int lddy, int B, int H, int W, int C, const void *mask,
+                         int ldmask, void *dx, void *stream) {
+  if (!dy || !dx || B < 1 || H < 1 || W < 1 || C < 8 || (C & 7) || lddy < C || (lddy & 7) ||
+      (mask && (ldmask < C || (ldmask & 7))))
+    return CEM_SG_ERR_ARG;
+  const long n = (long)B * H * W * (C >> 3);
+  k_upsample2_bwd<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      (const bf16_t *)dy, lddy, B, H, W, C, (const bf16_t *)mask, ldmask, (bf16_t *)dx);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 

@@ -25,14 +25,14 @@ _f = C.c_float
 
 # name -> (restype, argtypes); every entry point of include/cem_surrogate.h
 SG_SIGNATURES = {
-    "cem_sg_conv3x3": (_i, [_v, _i, _i, _i, _i, _i, _v, _v, _i, _i, _v, _i, _i, _v]),
+    "cem_sg_conv3x3": (_i, [_v, _i, _i, _i, _i, _i, _v, _v, _i, _i, _v, _i, _v, _i, _i, _v]),
     "cem_sg_wgrad_workspace": (_l, [_i, _i, _i, _i, _i]),
     "cem_sg_conv3x3_wgrad": (_i, [_v, _i, _v, _i, _i, _i, _i, _i, _i, _v, _v, _v, _l, _v]),
     "cem_sg_relu_bwd": (_i, [_v, _i, _v, _i, _l, _i, _v]),
     "cem_sg_maxpool2": (_i, [_v, _i, _i, _i, _i, _i, _v, _v]),
-    "cem_sg_maxpool2_bwd": (_i, [_v, _i, _v, _v, _i, _i, _i, _i, _i, _i, _v, _v]),
+    "cem_sg_maxpool2_bwd": (_i, [_v, _i, _v, _v, _i, _i, _i, _i, _i, _i, _i, _v, _v]),
     "cem_sg_upsample2": (_i, [_v, _i, _i, _i, _i, _v, _i, _i, _v]),
-    "cem_sg_upsample2_bwd": (_i, [_v, _i, _i, _i, _i, _i, _v, _v]),
+    "cem_sg_upsample2_bwd": (_i, [_v, _i, _i, _i, _i, _i, _v, _i, _v, _v]),
     "cem_sg_head_fwd": (_i, [_v, _i, _i, _v, _v, _v, _v]),
     "cem_sg_head_workspace": (_l, [_i, _i]),
     "cem_sg_head_bwd": (_i, [_v, _i, _i, _v, _v, _v, _v, _v, _v, _l, _v]),
@@ -184,8 +184,8 @@ class UNet:
     def _conv(self, name, x, ldx, y, ldy, yoff, relu=1, H=None, W=None, Cin=None):
         p = self.convs[name]
         _ok(sg().cem_sg_conv3x3(_p(x), self.B, H, W, Cin if Cin else p["cin"], ldx, _p(p["wb"]),
-                                _p(p["b"]), p["cout"], relu, _p(y), ldy, yoff, self._stream()),
-            "conv " + name)
+                                _p(p["b"]), p["cout"], relu, None, 0, _p(y), ldy, yoff,
+                                self._stream()), "conv " + name)
 
     def forward(self):
         """Logits self.z [B*H*W] (FP32) of the current input."""
@@ -223,19 +223,20 @@ class UNet:
                                       _p(p["gw"]), _p(p["gb"]), _p(self.ws), self.ws_bytes,
                                       self._stream()), "wgrad " + name)
 
-    def _dgrad(self, name, dy, out, H, W):
-        """out = data gradient of conv `name` (dense [P, cin])."""
+    def _dgrad(self, name, dy, out, H, W, mask=None):
+        """out = data gradient of conv `name` (dense [P, cin]); zero where
+        mask (the conv's input, a ReLU output) is <= 0 when given."""
         p = self.convs[name]
         _ok(sg().cem_sg_conv3x3(_p(dy), self.B, H, W, p["cout"], p["cout"], _p(p["wt"]), None,
-                                p["cin"], 0, _p(out), p["cin"], 0, self._stream()),
+                                p["cin"], 0, None if mask is None else _p(mask),
+                                p["cin"], _p(out), p["cin"], 0, self._stream()),
             "dgrad " + name)
-
-    def _relu_bwd(self, g, y, ldy, off, P, Cc):
-        _ok(sg().cem_sg_relu_bwd(_p(g), Cc, _p(y, off), ldy, P, Cc, self._stream()), "relu_bwd")
 
     def backward(self, dz=None):
         """Gradients of sum(dz * z) into every parameter's gw / gb; dz
-        defaults to the loss gradient left by loss()."""
+        defaults to the loss gradient left by loss().  Every ReLU's gradient
+        mask is applied by the kernel that produces the gradient (head, data
+        gradients, upsampling and pooling gradients)."""
         L_, st, ch, L = sg(), self._stream(), self.chans, self.L
         dz = self.dz if dz is None else dz
         hd = self.head
@@ -244,31 +245,25 @@ class UNet:
                                _p(self.ws), self.ws_bytes, st), "head_bwd")
         for l in range(L - 1):
             H, W = self.dims[l]
-            P = self.P[l]
-            self._relu_bwd(self.gA[l], self.db[l], ch[l], 0, P, ch[l])
             self._wgrad(f"d{l}b", self.da[l], ch[l], self.gA[l], ch[l], H, W)
-            self._dgrad(f"d{l}b", self.gA[l], self.gB[l], H, W)
-            self._relu_bwd(self.gB[l], self.da[l], ch[l], 0, P, ch[l])
+            self._dgrad(f"d{l}b", self.gA[l], self.gB[l], H, W, mask=self.da[l])
             self._wgrad(f"d{l}a", self.cat[l], self.ldcat[l], self.gB[l], ch[l], H, W)
             self._dgrad(f"d{l}a", self.gB[l], self.gcat[l], H, W)
             h2, w2 = self.dims[l + 1]
+            up_in = self.db[l + 1] if l + 1 < L - 1 else self.eb_bot
             _ok(L_.cem_sg_upsample2_bwd(_p(self.gcat[l]), self.ldcat[l], self.B, h2, w2, ch[l + 1],
-                                        _p(self.gA[l + 1]), st), "upsample_bwd")
+                                        _p(up_in), ch[l + 1], _p(self.gA[l + 1]), st),
+                "upsample_bwd")
         for l in range(L - 1, -1, -1):
             H, W = self.dims[l]
-            P = self.P[l]
             if l < L - 1:
                 h2, w2 = self.dims[l + 1]
                 _ok(L_.cem_sg_maxpool2_bwd(_p(self.cat[l], ch[l + 1]), self.ldcat[l],
                                            _p(self.gpool[l]), _p(self.gcat[l], ch[l + 1]),
-                                           self.ldcat[l], 0, self.B, h2, w2, ch[l],
+                                           self.ldcat[l], 0, self.B, h2, w2, ch[l], 1,
                                            _p(self.gA[l]), st), "maxpool_bwd")
-                self._relu_bwd(self.gA[l], self.cat[l], self.ldcat[l], ch[l + 1], P, ch[l])
-            else:
-                self._relu_bwd(self.gA[l], self.eb_bot, ch[l], 0, P, ch[l])
             self._wgrad(f"e{l}b", self.ea[l], ch[l], self.gA[l], ch[l], H, W)
-            self._dgrad(f"e{l}b", self.gA[l], self.gB[l], H, W)
-            self._relu_bwd(self.gB[l], self.ea[l], ch[l], 0, P, ch[l])
+            self._dgrad(f"e{l}b", self.gA[l], self.gB[l], H, W, mask=self.ea[l])
             if l == 0:
                 self._wgrad("e0a", self.x8, 8, self.gB[0], ch[0], H, W)
             else:

@@ -49,7 +49,7 @@ def test_surrogate_argument_checks_without_gpu():
     """Shape checks come before any launch: bad channel counts are errors."""
     from paper_2509_01827_gb300 import surrogate
     L = surrogate.sg()
-    assert L.cem_sg_conv3x3(1, 1, 4, 4, 3, 3, 1, None, 8, 0, 1, 8, 0, None) == -1  # Cin % 8
+    assert L.cem_sg_conv3x3(1, 1, 4, 4, 3, 3, 1, None, 8, 0, None, 0, 1, 8, 0, None) == -1  # Cin % 8
     assert L.cem_sg_wgrad_workspace(1, 4, 4, 8, 8) > 0
 
 

@@ -60,8 +60,8 @@ def test_conv3x3_forward(relu):
     ldy, yoff = Cout + 8, 8  # write into a channel slice
     y = torch.zeros((B * H * W, ldy), dtype=torch.bfloat16, device="cuda")
     xd, wd, bd = _t(x, torch.bfloat16), _t(w, torch.bfloat16), _t(b, torch.float32)
-    rc = sg().cem_sg_conv3x3(_p(xd), B, H, W, Cin, Cin, _p(wd), _p(bd), Cout, relu, _p(y), ldy,
-                             yoff, 0)
+    rc = sg().cem_sg_conv3x3(_p(xd), B, H, W, Cin, Cin, _p(wd), _p(bd), Cout, relu, None, 0, _p(y),
+                             ldy, yoff, 0)
     assert rc == 0
     torch.cuda.synchronize()
     yg = y.float().cpu().numpy().reshape(B, H, W, ldy)
@@ -93,13 +93,21 @@ def test_conv3x3_weight_gradient_and_data_gradient():
     # data gradient: the forward kernel with the transposed, flipped weights
     wt = np.transpose(w[:, ::-1, ::-1, :], (3, 1, 2, 0)).copy()  # [Cin][3][3][Cout]
     dx = torch.empty((B * H * W, Cin), dtype=torch.bfloat16, device="cuda")
-    assert L.cem_sg_conv3x3(_p(dyd), B, H, W, Cout, Cout, _p(_t(wt, torch.bfloat16)), None, Cin, 0,
+    wtd = _t(wt, torch.bfloat16)
+    assert L.cem_sg_conv3x3(_p(dyd), B, H, W, Cout, Cout, _p(wtd), None, Cin, 0, None, 0,
                             _p(dx), Cin, 0, 0) == 0
+    # the same with the ReLU mask of the layer's input applied in the epilogue
+    dxm = torch.empty_like(dx)
+    assert L.cem_sg_conv3x3(_p(dyd), B, H, W, Cout, Cout, _p(wtd), None, Cin, 0, _p(xd), Cin,
+                            _p(dxm), Cin, 0, 0) == 0
     torch.cuda.synchronize()
     # BF16 x BF16 products are exact in FP32; only the FP32 sums round
     assert _rel(dw.cpu().numpy(), dw_ref) < 1e-5
     assert _rel(db.cpu().numpy(), db_ref) < 1e-5
-    assert _rel(dx.float().cpu().numpy().reshape(B, H, W, Cin), dx_ref) < 1e-2
+    dxg = dx.float().cpu().numpy().reshape(B, H, W, Cin)
+    assert _rel(dxg, dx_ref) < 1e-2
+    np.testing.assert_array_equal(dxm.float().cpu().numpy().reshape(B, H, W, Cin),
+                                  np.where(x > 0, dxg, 0.0))
 
 
 def test_adam_writes_flipped_copy():
@@ -145,19 +153,29 @@ def test_pool_upsample_exact():
     y = torch.empty((B * H * W, C), dtype=torch.bfloat16, device="cuda")
     dx = torch.empty((B * 4 * H * W, C), dtype=torch.bfloat16, device="cuda")
     assert L.cem_sg_maxpool2(_p(xd), C, B, H, W, C, _p(y), 0) == 0
-    assert L.cem_sg_maxpool2_bwd(_p(xd), C, _p(dyd), _p(skd), C, 0, B, H, W, C, _p(dx), 0) == 0
+    assert L.cem_sg_maxpool2_bwd(_p(xd), C, _p(dyd), _p(skd), C, 0, B, H, W, C, 0, _p(dx), 0) == 0
+    dxr = torch.empty_like(dx)  # with the ReLU mask of x
+    assert L.cem_sg_maxpool2_bwd(_p(xd), C, _p(dyd), _p(skd), C, 0, B, H, W, C, 1, _p(dxr), 0) == 0
     up = torch.zeros((B * 4 * H * W, C + 8), dtype=torch.bfloat16, device="cuda")
     assert L.cem_sg_upsample2(_p(dyd), B, H, W, C, _p(up), C + 8, 8, 0) == 0
     dup = torch.empty((B * H * W, C), dtype=torch.bfloat16, device="cuda")
-    assert L.cem_sg_upsample2_bwd(_p(up, 8), C + 8, B, H, W, C, _p(dup), 0) == 0
+    assert L.cem_sg_upsample2_bwd(_p(up, 8), C + 8, B, H, W, C, None, 0, _p(dup), 0) == 0
+    mk = bf16_round(r.standard_normal((B, H, W, C)))
+    dupm = torch.empty_like(dup)
+    assert L.cem_sg_upsample2_bwd(_p(up, 8), C + 8, B, H, W, C, _p(_t(mk, torch.bfloat16)), C,
+                                  _p(dupm), 0) == 0
     torch.cuda.synchronize()
     np.testing.assert_array_equal(y.float().cpu().numpy().reshape(B, H, W, C), so.maxpool2(x))
     ref_dx = bf16_round(so.maxpool2_bwd(x, dy) + skip)
     np.testing.assert_array_equal(dx.float().cpu().numpy().reshape(x.shape), ref_dx)
+    np.testing.assert_array_equal(dxr.float().cpu().numpy().reshape(x.shape),
+                                  np.where(x > 0, ref_dx, 0.0))
     np.testing.assert_array_equal(up.float().cpu().numpy().reshape(B, 2 * H, 2 * W, C + 8)[..., 8:],
                                   so.upsample2(dy))
-    np.testing.assert_array_equal(dup.float().cpu().numpy().reshape(B, H, W, C),
-                                  bf16_round(so.upsample2_bwd(so.upsample2(dy))))
+    ref_up = bf16_round(so.upsample2_bwd(so.upsample2(dy)))
+    np.testing.assert_array_equal(dup.float().cpu().numpy().reshape(B, H, W, C), ref_up)
+    np.testing.assert_array_equal(dupm.float().cpu().numpy().reshape(B, H, W, C),
+                                  np.where(mk > 0, ref_up, 0.0))
 
 
 def test_bce_and_head():
@@ -194,7 +212,8 @@ def test_bce_and_head():
     dxr, dwr, dbr = so.conv2d_bwd(x.reshape(1, 1, P, C), w.reshape(1, 1, 1, C), dzr.reshape(1, 1, P, 1), 0)
     assert _rel(dw.cpu().numpy(), dwr.reshape(C)) < 1e-4
     assert _rel(db.cpu().numpy(), dbr) < 1e-4
-    assert _rel(dx.float().cpu().numpy(), dxr.reshape(P, C)) < 1e-2
+    # the head's input is a ReLU output: no gradient where it is <= 0
+    assert _rel(dx.float().cpu().numpy(), np.where(x > 0, dxr.reshape(P, C), 0.0)) < 1e-2
 
 
 def _unet_bf16_reference(p, x, t, chans, pw):
