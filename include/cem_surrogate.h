@@ -116,6 +116,19 @@ int cem_sg_adam(float *w, const float *g, float *m, float *v, long n, float lr, 
                 float beta2, float eps, int step, void *w_bf16, void *wt_bf16, int Cout, int Cin,
                 void *stream);
 
+/* Selects the tensor-core path of cem_sg_conv3x3 for later calls: 1 (the
+ * default) = tcgen05 MMAs with a TMEM accumulator and a 4-stage
+ * shared-memory ring (one CTA per SM, 128 threads), 0 = warp-level mma.sync
+ * m16n8k16 with register accumulators.  Both compute the same sums (FP32
+ * accumulation in a different order).  Process-wide; not synchronised with
+ * work in flight. */
+int cem_sg_set_gemm_path(int use_tcgen05);
+
+/* Number of tcgen05 CTAs whose bounded wait for their MMAs gave up since the
+ * library was loaded (their output tile is left unwritten; 0 in a healthy
+ * run).  Synchronises with the device. */
+int cem_sg_timeouts(int *count);
+
 /* y = BF16(x), n elements. */
 int cem_sg_to_bf16(const float *x, long n, void *y, void *stream);
 

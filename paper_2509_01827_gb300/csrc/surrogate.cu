@@ -180,6 +180,291 @@ __global__ void __launch_bounds__(256) k_conv3x3(ConvArgs a) {
     }
 }
 
+// ------------------------------------------------ conv 3x3 on tcgen05
+// The same implicit GEMM on the 5th-generation tensor cores: a CTA of four
+// warps owns 128 pixels x BN channels; K advances 64 at a time (one 128-byte
+// swizzle atom of BF16).  Operands are gathered with 16-byte cp.async copies
+// straight into the K-major 128-byte-swizzled layout the MMA descriptors
+// describe (row r of a tile at r * 128 bytes, its 16-byte chunk c at
+// chunk position c ^ (r & 7)), in a 4-stage ring.  One thread issues
+// tcgen05.mma (M = 128, N = BN, K = 16 each) into a TMEM accumulator of BN
+// FP32 columns; tcgen05.commit arrives on the stage's mbarrier when the MMAs
+// reading it are done, which frees the stage for the next copies.  The
+// epilogue reads TMEM with tcgen05.ld (warp w: rows 32w .. 32w+31).  Every
+// mbarrier wait is bounded; a wait that gives up records a timeout
+// (cem_sg_timeouts) and the CTA stops issuing work and frees its TMEM.
+constexpr int TCM = 128, TCK = 64, TCS = 4;
+constexpr long TC_SPIN = 1L << 24;  // mbarrier polls (with a short sleep) before a wait gives up
+
+__device__ int g_tc_timeouts;  // waits that gave up (device-wide, cumulative)
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+// true when the barrier's phase with the given parity has completed
+// (non-blocking test)
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, int parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity));
+  return ok != 0;
+}
+// bounded wait: about a second at most, then false
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, int parity) {
+  for (long i = 0; i < TC_SPIN; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int BN>
+struct TcSmem {
+  uint8_t A[TCS][TCM * 128];
+  uint8_t B[TCS][BN * 128];
+  uint64_t mma_bar[TCS];
+  uint32_t tmem;
+  int fail;
+};
+// the epilogue stages a 128 x (BN + 8) BF16 tile over the operand ring
+static_assert(TCM * (32 + 8) * 2 <= TCS * TCM * 128 + TCS * 32 * 128, "staging");
+static_assert(TCM * (256 + 8) * 2 <= TCS * TCM * 128 + TCS * 256 * 128, "staging");
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_conv3x3_tc(ConvArgs a) {
+  extern __shared__ uint8_t tc_raw[];
+  TcSmem<BN> &T = *reinterpret_cast<TcSmem<BN> *>(
+      (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p0 = blockIdx.x * TCM, n0 = blockIdx.y * BN;
+  const int HW = a.H * a.W, cpt = a.Cin >> 3;
+  const int KB = (a.K + TCK - 1) / TCK;
+  const int c = tid & 7;  // this thread's 16-byte chunk column in every tile row
+
+  if (tid == 0) {
+    for (int s = 0; s < TCS; ++s) mbar_init(&T.mma_bar[s], 1);
+    T.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&T.tmem)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tmem = T.tmem;
+
+  // rows of A this thread copies: (tid >> 3) + 16 i, i < 8
+  int rh[8], rw[8], rb[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int p = p0 + (tid >> 3) + 16 * i;
+    if (p < a.P) {
+      rb[i] = p / HW;
+      const int rem = p - rb[i] * HW;
+      rh[i] = rem / a.W;
+      rw[i] = rem - rh[i] * a.W;
+    } else {
+      rb[i] = -1; rh[i] = 0; rw[i] = 0;
+    }
+  }
+  auto load_stage = [&](int kb, int s) {
+    const int q = kb * (TCK / 8) + c;  // 8-wide k chunk
+    const int tap = q / cpt, c0 = (q - tap * cpt) * 8;
+    const int ky = tap / 3, kx = tap - ky * 3;
+    const uint32_t abase = smem_u32(T.A[s]), bbase = smem_u32(T.B[s]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = (tid >> 3) + 16 * i;
+      const int hh = rh[i] + ky - 1, ww = rw[i] + kx - 1;
+      const bool ok = rb[i] >= 0 && tap < 9 && hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const bf16_t *src = ok ? a.x + ((size_t)(rb[i] * a.H + hh) * a.W + ww) * a.ldx + c0 : a.x;
+      const uint32_t dst = abase + row * 128 + ((c ^ (row & 7)) << 4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(ok ? 16 : 0));
+    }
+    const int k = kb * TCK + c * 8;
+#pragma unroll
+    for (int i = 0; i < BN / 16; ++i) {
+      const int row = (tid >> 3) + 16 * i;
+      const int n = n0 + row;
+      const bool ok = n < a.N && k < a.K;
+      const bf16_t *src = ok ? a.w + (size_t)n * a.K + k : a.w;
+      const uint32_t dst = bbase + row * 128 + ((c ^ (row & 7)) << 4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(ok ? 16 : 0));
+    }
+  };
+
+  constexpr uint32_t idesc = tc_idesc(TCM, BN);
+  bool failed = false;
+#pragma unroll
+  for (int s = 0; s < TCS - 1; ++s) {
+    if (s < KB) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int kb = 0; kb < KB && !failed; ++kb) {
+    const int s = kb % TCS;
+    cp_async_wait<TCS - 2>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint64_t ad = sw128_desc(smem_u32(T.A[s])), bd = sw128_desc(smem_u32(T.B[s]));
+#pragma unroll
+      for (int k = 0; k < TCK / 16; ++k) {
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        // +32 bytes (encoded +2) per K = 16 slice inside the swizzle atom
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad + 2 * k), "l"(bd + 2 * k), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&T.mma_bar[s])));
+    }
+    const int nk = kb + TCS - 1;
+    if (nk < KB) {
+      if (kb >= 1 && !mbar_wait(&T.mma_bar[(kb - 1) % TCS], ((kb - 1) / TCS) & 1)) {
+        failed = true;
+        T.fail = 1;
+      }
+      if (!failed) load_stage(nk, nk % TCS);
+    }
+    cp_async_commit();
+    failed = __syncthreads_or(failed) != 0;
+  }
+  cp_async_wait<0>();
+  // all MMAs done: the last commit tracks every earlier one
+  if (!failed && !mbar_wait(&T.mma_bar[(KB - 1) % TCS], ((KB - 1) / TCS) & 1)) failed = true;
+  failed = __syncthreads_or(failed) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+  if (!failed) {
+    // TMEM -> (bias, ReLU) -> BF16 tile in shared memory (the operand ring is
+    // free now), then coalesced 16-byte stores with the mask applied
+    constexpr int LDS = BN + 8;  // padded row of the staged tile (bf16)
+    bf16_t *stile = reinterpret_cast<bf16_t *>(T.A[0]);
+    const int m = warp * 32 + lane;  // TMEM lane = tile row
+#pragma unroll 1
+    for (int cb = 0; cb < BN; cb += 32) {
+      uint32_t r[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+            "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+            "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+            "=r"(r[31])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const int n = n0 + cb + j;
+        float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+        if (a.bias && n < a.N) {
+          v0 += a.bias[n];
+          v1 += a.bias[n + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        *reinterpret_cast<uint32_t *>(stile + m * LDS + cb + j) =
+            (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
+      }
+    }
+    __syncthreads();
+    const bool vec = (a.N & 7) == 0 && (a.ldy & 7) == 0 && (a.yoff & 7) == 0 &&
+                     (!a.mask || (a.ldm & 7) == 0);
+    for (int idx = tid; idx < TCM * (BN / 8); idx += 128) {
+      const int row = idx / (BN / 8), ch = (idx - row * (BN / 8)) * 8;
+      const int p = p0 + row, n = n0 + ch;
+      if (p >= a.P || n >= a.N) continue;
+      uint4 v = *reinterpret_cast<const uint4 *>(stile + row * LDS + ch);
+      if (vec) {
+        if (a.mask) {
+          const uint4 mk = *reinterpret_cast<const uint4 *>(a.mask + (size_t)p * a.ldm + n);
+          uint32_t *vw = reinterpret_cast<uint32_t *>(&v);
+          const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!(bf2f((bf16_t)(mw[q] & 0xffff)) > 0.f)) vw[q] &= 0xffff0000u;
+            if (!(bf2f((bf16_t)(mw[q] >> 16)) > 0.f)) vw[q] &= 0x0000ffffu;
+          }
+        }
+        *reinterpret_cast<uint4 *>(a.y + (size_t)p * a.ldy + a.yoff + n) = v;
+      } else {
+        const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < 4 && n + 2 * q < a.N; ++q) {
+          uint32_t w2 = vw[q];
+          if (a.mask) {
+            const uint32_t mk =
+                *reinterpret_cast<const uint32_t *>(a.mask + (size_t)p * a.ldm + n + 2 * q);
+            if (!(bf2f((bf16_t)(mk & 0xffff)) > 0.f)) w2 &= 0xffff0000u;
+            if (!(bf2f((bf16_t)(mk >> 16)) > 0.f)) w2 &= 0x0000ffffu;
+          }
+          *reinterpret_cast<uint32_t *>(a.y + (size_t)p * a.ldy + a.yoff + n + 2 * q) = w2;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicAdd(&g_tc_timeouts, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+}
+
+template <int BN>
+size_t tc_smem_bytes() {
+  return sizeof(TcSmem<BN>) + 1024;
+}
+
+template <int BN>
+cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes<BN>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((a.P + TCM - 1) / TCM, (a.N + BN - 1) / BN);
+  k_conv3x3_tc<BN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a);
+  return cudaGetLastError();
+}
+
+int g_use_tc = 1;  // cem_sg_set_gemm_path
+
 // ---------------------------------------------------- conv 3x3 weight grad
 // dW[n, k] = sum_p dY[p, n] * A[p, k] over the pixels of split z, written
 // to ws[z][n][k]; k = (ky * 3 + kx) * Cin + c as in the forward weights.
@@ -584,8 +869,15 @@ int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const v
   a.relu = relu; a.ldy = ldy; a.yoff = yoff; a.P = B * H * W;
   a.mask = (const bf16_t *)mask;
   a.ldm = ldmask;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (g_use_tc) {
+    cudaError_t e = Cout > 128 ? launch_conv_tc<256>(a, st)
+                  : Cout > 64 ? launch_conv_tc<128>(a, st)
+                  : Cout > 32 ? launch_conv_tc<64>(a, st) : launch_conv_tc<32>(a, st);
+    return e == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+  }
   dim3 grid((a.P + FBM - 1) / FBM, (Cout + FBN - 1) / FBN);
-  k_conv3x3<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  k_conv3x3<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 
@@ -721,6 +1013,17 @@ int cem_sg_adam(float *w, const float *g, float *m, float *v, long n, float lr, 
   k_adam<<<grid_1d(n, 256), 256, 0, (cudaStream_t)stream>>>(
       w, g, m, v, n, lr, beta1, beta2, eps, c1, c2, (bf16_t *)w_bf16, (bf16_t *)wt_bf16, Cout, Cin);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+int cem_sg_set_gemm_path(int use_tcgen05) {
+  g_use_tc = use_tcgen05 ? 1 : 0;
+  return CEM_SG_OK;
+}
+
+int cem_sg_timeouts(int *count) {
+  if (!count) return CEM_SG_ERR_ARG;
+  return cudaMemcpyFromSymbol(count, g_tc_timeouts, sizeof(int)) == cudaSuccess ? CEM_SG_OK
+                                                                             : CEM_SG_ERR_CUDA;
 }
 
 int cem_sg_to_bf16(const float *x, long n, void *y, void *stream) {

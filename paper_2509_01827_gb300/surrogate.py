@@ -40,6 +40,8 @@ SG_SIGNATURES = {
     "cem_sg_bce": (_i, [_v, _v, _l, _f, _v, _v, _v, _l, _v]),
     "cem_sg_adam": (_i, [_v, _v, _v, _v, _l, _f, _f, _f, _f, _i, _v, _v, _i, _i, _v]),
     "cem_sg_to_bf16": (_i, [_v, _l, _v, _v]),
+    "cem_sg_set_gemm_path": (_i, [_i]),
+    "cem_sg_timeouts": (_i, [C.POINTER(_i)]),
 }
 
 _SG = None

@@ -324,3 +324,34 @@ def test_training_reduces_loss():
     td = torch.tensor(t.reshape(-1), device="cuda")
     losses = [float(net.train_step(td).item()) for _ in range(60)]
     assert losses[-1] < 0.5 * losses[0], losses[::10]
+
+
+@pytest.mark.parametrize("cin,cout", [(8, 32), (24, 40), (32, 64), (64, 128), (96, 32), (128, 256), (40, 96), (16, 18)])
+def test_tcgen05_and_mma_paths_agree(cin, cout):
+    """The tcgen05 (TMEM) and mma.sync paths of the 3x3 convolution against the
+    oracle, ragged pixel counts, every N tile width; no bounded wait gives up."""
+    import ctypes
+    import torch
+    from paper_2509_01827_gb300.surrogate import _p, sg
+    x, w, b = _conv_case(B=2, H=9, W=23, Cin=cin, Cout=cout, seed=cin + cout)
+    B, H, W, _ = x.shape
+    L = sg()
+    xd, wd, bd = _t(x, torch.bfloat16), _t(w, torch.bfloat16), _t(b, torch.float32)
+    mk = _t(bf16_round(np.random.default_rng(9).standard_normal((B, H, W, cout))), torch.bfloat16)
+    ref = so.relu(so.conv2d(x, w, b, 1))
+    mref = np.where(mk.float().cpu().numpy().reshape(B, H, W, cout) > 0, ref, 0.0)
+    out = {}
+    try:
+        for path in (1, 0):
+            assert L.cem_sg_set_gemm_path(path) == 0
+            y = torch.zeros((B * H * W, cout), dtype=torch.bfloat16, device="cuda")
+            assert L.cem_sg_conv3x3(_p(xd), B, H, W, cin, cin, _p(wd), _p(bd), cout, 1, _p(mk),
+                                    cout, _p(y), cout, 0, 0) == 0
+            torch.cuda.synchronize()
+            out[path] = y.float().cpu().numpy().reshape(B, H, W, cout)
+    finally:
+        L.cem_sg_set_gemm_path(1)
+    n = ctypes.c_int(-1)
+    assert L.cem_sg_timeouts(ctypes.byref(n)) == 0 and n.value == 0
+    for path in (1, 0):
+        assert _rel(out[path], mref) < 1e-2, path
