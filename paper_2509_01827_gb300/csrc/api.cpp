@@ -54,6 +54,7 @@ struct cem_handle {
   bool own_stream = false;
   StepStreams ss{};           // fork/join streams and events of one step
   long launches = 0;           // kernels enqueued (graph replays count their nodes)
+  long lam_lo = 0, lam_n = 0;  // steps [lam_lo, lam_lo + lam_n) have device load factors
   void *scratch = nullptr;     // reusable device scratch for getters
   size_t scratch_bytes = 0;
   std::string err;
@@ -240,6 +241,8 @@ cem_status upload_load_factors(cem_handle *h, int chunk, cudaStream_t st = nullp
   }
   int base = (int)h->step;
   h->h_cnt->lam_base = base;
+  h->lam_lo = h->step;
+  h->lam_n = chunk;
   CUDA_TRY(h, cudaMemcpyAsync(d.lamN, lamN, chunk * 8, cudaMemcpyHostToDevice, st));
   CUDA_TRY(h, cudaMemcpyAsync(d.lamD, lamD, chunk * 8, cudaMemcpyHostToDevice, st));
   CUDA_TRY(h, cudaMemcpyAsync(&d.cnt->lam_base, &h->h_cnt->lam_base, 4, cudaMemcpyHostToDevice, st));
@@ -642,9 +645,15 @@ cem_status cem_step(cem_handle *h, int n) {
   const DevState &d = h->d;
   int done = 0;
   while (done < n) {
-    int chunk = std::min(n - done, d.lam_cap);
-    cem_status rc = upload_load_factors(h, chunk);
-    if (rc != CEM_OK) return rc;
+    cem_status rc;
+    if (h->step < h->lam_lo || h->step >= h->lam_lo + h->lam_n) {
+      // a fresh table of load factors (the pinned staging is rewritten only
+      // after the copies that read it have finished)
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      rc = upload_load_factors(h, d.lam_cap);
+      if (rc != CEM_OK) return rc;
+    }
+    const int chunk = (int)std::min((long)(n - done), h->lam_lo + h->lam_n - h->step);
     for (int q = 0; q < chunk; ++q) {
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
@@ -659,11 +668,10 @@ cem_status cem_step(cem_handle *h, int n) {
       h->cur ^= 1;
       h->step += 1;
     }
-    CUDA_TRY(h, cudaStreamSynchronize(h->st));
     done += chunk;
   }
-  CUDA_TRY(h, launch_check_finite(d, h->cur, h->st));
-  h->launches += 1;
+  // one read-back of the status word (non-finite velocities and capacity
+  // overflows are flagged by the kernels themselves)
   return sync_status(h);
 }
 
@@ -1028,7 +1036,7 @@ cem_status batch_upload(cem_handle *b) {
   BatchPlan *p = b->batch;
   const int n = (int)p->members.size();
   std::vector<DevState> ds((size_t)n);
-  std::vector<int4> wm, wp, wph, we, wf;
+  std::vector<int4> wm, wp, wph, we;
   std::vector<int> nparts((size_t)n);
   for (int s = 0; s < n; ++s) {
     cem_handle *m = p->members[s];
@@ -1051,16 +1059,15 @@ cem_status batch_upload(cem_handle *b) {
     for (int q = 0; q < gph; ++q) wph.push_back(make_int4(s, q, tiles + gp, gph));
     // the evaluation has no energy partials: a few virtual blocks per member
     // walk its list (its length, not its capacity, sets the work)
-    const int ge = std::min(grid_eval(d), 8), gf = grid_finite(d);
+    const int ge = std::min(grid_eval(d), 8);
     for (int q = 0; q < ge; ++q) we.push_back(make_int4(s, q, 0, ge));
-    for (int q = 0; q < gf; ++q) wf.push_back(make_int4(s, q, 0, gf));
     nparts[s] = tiles + gp + gph;
   }
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_ds = 0, o_m = al(o_ds + ds.size() * sizeof(DevState));
   const size_t o_p = al(o_m + wm.size() * 16), o_ph = al(o_p + wp.size() * 16);
-  const size_t o_e = al(o_ph + wph.size() * 16), o_f = al(o_e + we.size() * 16);
-  const size_t o_np = al(o_f + wf.size() * 16), o_ctr = al(o_np + nparts.size() * 4);
+  const size_t o_e = al(o_ph + wph.size() * 16);
+  const size_t o_np = al(o_e + we.size() * 16), o_ctr = al(o_np + nparts.size() * 4);
   const size_t bytes = o_ctr + 256;
   if (bytes > p->dev_bytes) {
     // grows only when a smaller tile height needs longer lists
@@ -1074,7 +1081,6 @@ cem_status batch_upload(cem_handle *b) {
   memcpy(host.data() + o_p, wp.data(), wp.size() * 16);
   memcpy(host.data() + o_ph, wph.data(), wph.size() * 16);
   memcpy(host.data() + o_e, we.data(), we.size() * 16);
-  memcpy(host.data() + o_f, wf.data(), wf.size() * 16);
   memcpy(host.data() + o_np, nparts.data(), nparts.size() * 4);
   int *ctr = (int *)(host.data() + o_ctr);
   ctr[0] = (int)p->step;  // batch step
@@ -1090,7 +1096,6 @@ cem_status batch_upload(cem_handle *b) {
   bd.w_pieces = (const int4 *)(p->dev + o_p); bd.n_pieces = (int)wp.size();
   bd.w_ph = (const int4 *)(p->dev + o_ph); bd.n_ph = (int)wph.size();
   bd.w_eval = (const int4 *)(p->dev + o_e); bd.n_eval = (int)we.size();
-  bd.w_fin = (const int4 *)(p->dev + o_f); bd.n_fin = (int)wf.size();
   bd.nparts = (const int *)(p->dev + o_np);
   batch_drop_graphs(p);
   return CEM_OK;
@@ -1144,10 +1149,12 @@ cem_status batch_run(cem_handle *b, int n, cudaEvent_t ev_t0, cudaEvent_t ev_t1)
   int done = 0;
   while (done < n) {
     const int chunk = std::min(n - done, lam_cap);
-    // on the batch stream, ahead of the steps that read them; each member's
-    // pinned staging is reused only after the synchronisation below
+    // on the batch stream, ahead of the steps that read them, when a
+    // member's resident table does not cover the chunk; each member's pinned
+    // staging is reused only after the synchronisation below
     for (cem_handle *m : p->members) {
-      cem_status rc = upload_load_factors(m, chunk, b->st);
+      if (m->step >= m->lam_lo && m->step + chunk <= m->lam_lo + m->lam_n) continue;
+      cem_status rc = upload_load_factors(m, lam_cap, b->st);
       if (rc != CEM_OK) return fail(b, rc, "load factors: %s", m->err.c_str());
     }
     for (int q = 0; q < chunk; ++q) {
@@ -1176,12 +1183,12 @@ cem_status batch_run(cem_handle *b, int n, cudaEvent_t ev_t0, cudaEvent_t ev_t1)
   return CEM_OK;
 }
 
-// Finiteness check of every member, then one read-back of all counters.
+// One read-back of all members' counters (the kernels flag non-finite
+// velocities and capacity overflows in them).
 cem_status batch_finish(cem_handle *b) {
   BatchPlan *p = b->batch;
-  CUDA_TRY(b, launch_check_finite_batch(p->bd, b->st));
   CUDA_TRY(b, launch_gather_counters(p->bd, p->d_cnts, b->st));
-  b->launches += 2;
+  b->launches += 1;
   const size_t n = p->members.size();
   CUDA_TRY(b, cudaMemcpyAsync(p->h_cnts, p->d_cnts, n * sizeof(Counters), cudaMemcpyDeviceToHost,
                               b->st));

@@ -163,7 +163,6 @@ struct BatchDev {
   const int4 *w_pieces; int n_pieces;  // piece forces
   const int4 *w_ph; int n_ph;          // phantom update
   const int4 *w_eval; int n_eval;      // surface evaluation
-  const int4 *w_fin; int n_fin;        // finiteness check
   const int *nparts;    // [n] energy partial sums of each member
 };
 
@@ -227,7 +226,6 @@ cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);
 cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st);
 cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st);
-cudaError_t launch_check_finite(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *uy,
                                 double *vx, double *vy, int n, cudaStream_t st);
 cudaError_t launch_fp64_to_fp32(const DevState &d, int cur, const double *ux,
@@ -243,7 +241,6 @@ int tiles_fp64(const DevState &d);
 int grid_pieces(const DevState &d);
 int grid_phantoms(const DevState &d);
 int grid_eval(const DevState &d);
-int grid_finite(const DevState &d);
 cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, int tile_rows,
                                    int grid_main, const StepStreams &ss);
 cudaError_t launch_step_fp64_batch(const BatchDev &b, bool first, bool energy, int grid_main,
@@ -252,7 +249,6 @@ cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_energy_post_batch(const BatchDev &b, cudaStream_t st);
-cudaError_t launch_check_finite_batch(const BatchDev &b, cudaStream_t st);
 cudaError_t launch_gather_counters(const BatchDev &b, Counters *out, cudaStream_t st);
 
 // track modes

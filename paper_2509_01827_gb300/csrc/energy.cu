@@ -1,4 +1,4 @@
-// energy.cu -- FP64 energy records, finiteness check and precision
+// energy.cu -- FP64 energy records, batched counter read-back and precision
 // conversions (compiled with -fmad=false).
 //
 // An energy record at step n holds KE of the mid-step velocity
@@ -80,25 +80,6 @@ __device__ __forceinline__ void energy_post(const DevState &d, int nparts) {
   }
 }
 
-__device__ __forceinline__ void check_finite(const DevState &d, VBlk vb, int cur) {
-  int n = d.g.nn + d.cnt->n_ph;
-  bool bad = false;
-  for (int N = vb.x * blockDim.x + threadIdx.x; N < n; N += vb.gx * blockDim.x) {
-    double a, b, v, w;
-    if (d.precision == 1) {
-      const float4 U = d.u4[cur][N];
-      const float2 V = d.v2[N];
-      a = (double)U.x + (double)U.y;
-      b = (double)U.z + (double)U.w;
-      v = V.x;
-      w = V.y;
-    } else {
-      a = d.ux[cur][N]; b = d.uy[cur][N]; v = d.vx[N]; w = d.vy[N];
-    }
-    if (!isfinite(a) || !isfinite(b) || !isfinite(v) || !isfinite(w)) bad = true;
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&d.cnt->status, STAT_NONFINITE);
-}
 
 __global__ void __launch_bounds__(TB) k_energy_pre(DevState d) { energy_pre(d); }
 
@@ -106,9 +87,7 @@ __global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
   energy_post(d, nparts);
 }
 
-__global__ void k_check_finite(DevState d, int cur) { check_finite(d, hw_vblk(), cur); }
-
-// batched counterparts: one CTA per member (energies), work list (check)
+// batched counterparts: one CTA per member
 __global__ void __launch_bounds__(TB) k_energy_pre_batch(BatchDev b) {
   __shared__ DevState sd;
   int held = -1;
@@ -133,18 +112,6 @@ __global__ void __launch_bounds__(TB) k_energy_post_batch(BatchDev b) {
   }
 }
 
-// the members' last states: runs after the steps, whatever the batch step
-__global__ void k_check_finite_batch(BatchDev b) {
-  __shared__ DevState sd;
-  int held = -1, w0, w1;
-  block_range(b.n_fin, w0, w1);
-  for (int w = w0; w < w1; ++w) {
-    const int4 it = b.w_fin[w];
-    stage_member(b.ds, it.x, sd, held);
-    check_finite(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, sd.cnt->step));
-    __syncthreads();
-  }
-}
 
 // copies every member's counters into out[n] (one read-back for the batch)
 __global__ void k_gather_counters(BatchDev b, Counters *out) {
@@ -201,12 +168,6 @@ cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int grid_finite(const DevState &d) { return grid_for(d.ncap, 256, 1216); }
-
-cudaError_t launch_check_finite(const DevState &d, int cur, cudaStream_t st) {
-  k_check_finite<<<grid_finite(d), 256, 0, st>>>(d, cur);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st) {
   k_energy_pre_batch<<<b.n < 1216 ? b.n : 1216, TB, 0, st>>>(b);
@@ -223,10 +184,6 @@ cudaError_t launch_gather_counters(const BatchDev &b, Counters *out, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_check_finite_batch(const BatchDev &b, cudaStream_t st) {
-  k_check_finite_batch<<<grid_for(b.n_fin, 1, 1216), 256, 0, st>>>(b);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *uy, double *vx,
                                 double *vy, int n, cudaStream_t st) {

@@ -15,6 +15,8 @@
 // central-difference update.
 #include <cuda_runtime.h>
 
+#include <cfloat>
+
 #include "cem_internal.h"
 #include "q4_fp64.cuh"
 
@@ -109,6 +111,7 @@ __device__ __noinline__ double update_special(const DevState &d, int N, int cur,
     d.Wd[N] += dtd * w;
   }
   d.v2[N] = make_float2(vxn, vyn);
+  if (!(fabsf(vxn) <= FLT_MAX) || !(fabsf(vyn) <= FLT_MAX)) atomicOr(&d.cnt->status, STAT_NONFINITE);
   df_add(U.x, U.y, dt * vxn);
   df_add(U.z, U.w, dt * vyn);
   d.u4[cur ^ 1][N] = U;
@@ -122,6 +125,8 @@ __device__ __forceinline__ void update_plain(const DevState &d, int N, int cur, 
   const float vxn = fmaf(dtv, -fx * minv, vo.x);
   const float vyn = fmaf(dtv, -fy * minv, vo.y);
   d.v2[N] = make_float2(vxn, vyn);
+  // a non-finite velocity (NaN or Inf) is reported through the status word
+  if (!(fabsf(vxn) <= FLT_MAX) || !(fabsf(vyn) <= FLT_MAX)) atomicOr(&d.cnt->status, STAT_NONFINITE);
   df_add(U.x, U.y, dt * vxn);
   df_add(U.z, U.w, dt * vyn);
   d.u4[cur ^ 1][N] = U;

@@ -14,6 +14,8 @@
 //                proposals are appended with a warp ballot.
 #include <cuda_runtime.h>
 
+#include <cfloat>
+
 #include "cem_internal.h"
 #include "q4_fp64.cuh"
 #include "eval_common.cuh"
@@ -89,6 +91,8 @@ __device__ __forceinline__ double update_node(const DevState &d, int N, int cur,
   }
   d.vx[N] = vxn;
   d.vy[N] = vyn;
+  // a non-finite velocity (NaN or Inf) is reported through the status word
+  if (!(fabs(vxn) <= DBL_MAX) || !(fabs(vyn) <= DBL_MAX)) atomicOr(&d.cnt->status, STAT_NONFINITE);
   d.ux[cur ^ 1][N] = d.ux[cur][N] + dt * vxn;
   d.uy[cur ^ 1][N] = d.uy[cur][N] + dt * vyn;
   return 0.5 * (d.m[N] * (vbx * vbx + vby * vby));
