@@ -13,7 +13,8 @@
    standard deviation).
 3. Training: the U-Net of surrogate.py, weighted binary cross-entropy
    (cracked elements weighted by the training set's intact/cracked ratio,
-   capped at 20), Adam with a cosine learning-rate decay, batch 64.
+   capped at 20), Adam with a linear warm-up over 5% of the steps and a
+   cosine learning-rate decay, batch 64.
 4. Evaluation: mean Jaccard index of the predicted cracked set (logit >
    threshold, threshold chosen on held-out training runs) on the test runs,
    beside the no-learning floor of a straight crack along the notch row.
@@ -127,6 +128,49 @@ def mean_jaccard(Z, Y, thr):
     return float(j.mean().item()), j.cpu().numpy()
 
 
+def bench_steps(B, n):
+    """Times forward, backward (loss included) and Adam of the surrogate on
+    synthetic inputs (3 random channels, 7% cracked targets) after 3 warm-up
+    steps; returns milliseconds per step and the FLOP rate of the convolutions."""
+    import torch
+    from .surrogate import UNet
+    net = UNet(B, H_EL, W_EL, pos_weight=12.0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(B * H_EL * W_EL, 8, device="cuda", generator=g)
+    x[:, 3:] = 0
+    net.set_input(x)
+    t = (torch.rand(B * H_EL * W_EL, device="cuda", generator=g) < 0.07).to(torch.uint8)
+    for _ in range(3):
+        net.train_step(t)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    for _ in range(n):
+        net.forward()
+    ev[1].record()
+    for _ in range(n):
+        net.loss_and_grad(t)
+        net.backward()
+    ev[2].record()
+    for _ in range(n):
+        net.adam_step()
+    ev[3].record()
+    torch.cuda.synchronize()
+    fwd, bwd, adam = (ev[k].elapsed_time(ev[k + 1]) / n for k in range(3))
+    # 3x3 convolution FLOPs: 2 * pixels * 9 * Cin * Cout per conv forward; the
+    # backward does a data gradient (none for the first conv) and a weight gradient
+    flops_f = flops_b = 0.0
+    for name, p in net.convs.items():
+        l = int(name[1])
+        h, w = net.dims[l]
+        f = 2.0 * B * h * w * 9 * p["cin"] * p["cout"]
+        flops_f += f
+        flops_b += f * (1 if name == "e0a" else 2)
+    return {"batch": B, "steps": n, "fwd_ms": fwd, "bwd_ms": bwd, "adam_ms": adam,
+            "step_ms": fwd + bwd + adam, "conv_tflop_per_step": (flops_f + flops_b) / 1e12,
+            "conv_tflops": (flops_f + flops_b) / ((fwd + bwd + adam) * 1e-3) / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--train", type=int, default=4096)
@@ -137,6 +181,8 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--bench-steps", type=int, default=0,
+                    help="only time this many training steps of batch --batch on synthetic inputs")
     ap.add_argument("--save", default=None,
                     help="write the FP32 parameters and 8 test maps (.npz)")
     args = ap.parse_args()
@@ -146,6 +192,9 @@ def main():
     _build.build()
     torch.cuda.set_device(0)
     log = lambda m: print(m, flush=True)
+    if args.bench_steps:
+        print(json.dumps(bench_steps(args.batch, args.bench_steps)))
+        return
 
     t0 = time.perf_counter()
     Xtr, Ytr, floor_tr, s_run = generate(list(range(args.train)), args.chunk, log=log)
@@ -171,7 +220,10 @@ def main():
             idx = perm[s * args.batch:(s + 1) * args.batch]
             net.x8.copy_(Xtr.index_select(0, idx).reshape(-1, 8))
             tgt = Ytr.index_select(0, idx).reshape(-1)
-            lr = args.lr * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * it / max(1, total))))
+            # linear warm-up over the first 5% of the steps, then cosine decay
+            warm = max(1, total // 20)
+            lr = args.lr * min(1.0, (it + 1) / warm) * \
+                (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * it / max(1, total))))
             net.forward()
             loss = net.loss_and_grad(tgt)
             net.backward()
