@@ -586,6 +586,267 @@ __global__ void k_reduce_splits(const float *ws, int splits, long n, float *out)
 }
 
 
+// ------------------------------------------- weight gradient on tcgen05
+// dW^T[k'][o] = sum_p A[p][k'] dY[p][o] with k' = (ky * 3 + kx) * Cin + c and
+// A the shifted input (zero outside the image): M = k' (128 per CTA), N = o
+// (BN), K = pixels, split into fixed pixel chunks (grid z) whose FP32 tiles
+// go to a workspace and are added in chunk order.  Both operands are read in
+// their natural NHWC layout, i.e. MN-major for the MMA: in shared memory
+// each pixel is a 128-byte row of 64 k' (or o) values, 8 pixels form a
+// 1024-byte swizzle atom (16-byte chunk c of row r at c ^ (r & 7)), atoms
+// along K are 1024 bytes apart (SBO) and 64-wide atoms along M or N are
+// 8192 bytes apart (LBO).  One thread issues the MMAs (K = 16 = two atoms
+// each), tcgen05.commit frees the stage, the epilogue writes the transposed
+// tile (coalesced along k') with tcgen05.ld.
+constexpr int WTM = 128, WTK = 64;
+
+// MN-major, 128-byte swizzle
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__host__ __device__ constexpr uint32_t tc_idesc_mn(int M, int N) {
+  return tc_idesc(M, N) | (1u << 15) | (1u << 16);
+}
+
+template <int BN>
+struct TwSmem {
+  uint8_t A[TCS][WTM * WTK * 2];  // 16 KB: 2 atoms along k' of 64 pixels x 128 B
+  uint8_t B[TCS][BN * WTK * 2];   // BN / 64 atoms along o
+  uint64_t mma_bar[TCS];
+  uint32_t tmem;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_conv3x3_wgrad_tc(WgradArgs a) {
+  extern __shared__ uint8_t tw_raw[];
+  TwSmem<BN> &T = *reinterpret_cast<TwSmem<BN> *>(
+      (reinterpret_cast<uintptr_t>(tw_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * WTM, n0 = blockIdx.y * BN, z = blockIdx.z;
+  const int pbeg = z * a.chunk, pend = min(a.P, pbeg + a.chunk);
+  const int KB = (pend - pbeg + WTK - 1) / WTK;
+  const int HW = a.H * a.W;
+
+  if (tid == 0) {
+    for (int s = 0; s < TCS; ++s) mbar_init(&T.mma_bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&T.tmem)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tmem = T.tmem;
+
+  // A: this thread's k' chunk (8 values) is fixed; its pixel rows are
+  // (tid >> 4) + 8 i of each stage
+  const int ck = tid & 15;
+  const int kq = m0 + ck * 8;
+  const bool kok = kq < a.K;
+  const int tap = kok ? kq / a.Cin : 0, c0 = kok ? kq - tap * a.Cin : 0;
+  const int ky = tap / 3, kx = tap - ky * 3;
+  const uint32_t aoff_c = (uint32_t)((ck >> 3) * 8192);
+  // (b, h, w) of this thread's first pixel row, advanced by 8 pixels per
+  // row and 64 per stage without divisions (W >= 8 keeps each carry single)
+  int pb0, ph0, pw0;
+  {
+    const int p = pbeg + (tid >> 4);
+    pb0 = p / HW;
+    const int rem = p - pb0 * HW;
+    ph0 = rem / a.W;
+    pw0 = rem - ph0 * a.W;
+  }
+  auto advance = [&](int &b, int &h, int &w, int n) {
+    w += n;
+    while (w >= a.W) {
+      w -= a.W;
+      if (++h == a.H) { h = 0; ++b; }
+    }
+  };
+  auto load_stage = [&](int kb, int s) {
+    const int pst = pbeg + kb * WTK;
+    const uint32_t abase = smem_u32(T.A[s]), bbase = smem_u32(T.B[s]);
+    int b = pb0, h = ph0, w = pw0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int pr = (tid >> 4) + 8 * i;
+      const int p = pst + pr;
+      bool ok = kok && p < pend;
+      const bf16_t *src = a.x;
+      if (ok) {
+        const int hh = h + ky - 1, ww = w + kx - 1;
+        ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+        if (ok) src = a.x + ((size_t)(b * a.H + hh) * a.W + ww) * a.ldx + c0;
+      }
+      if (i < 7) advance(b, h, w, 8);
+      const int g = pr >> 3, r = pr & 7;
+      const uint32_t dst = abase + aoff_c + g * 1024 + r * 128 + (((ck & 7) ^ r) << 4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(ok ? 16 : 0));
+    }
+    advance(pb0, ph0, pw0, WTK);  // stages are loaded in increasing order
+    constexpr int CPR = BN / 8;            // 16-byte chunks per pixel row
+    constexpr int RPP = 128 / CPR;         // pixel rows per pass
+#pragma unroll
+    for (int i = 0; i < WTK / RPP; ++i) {
+      const int pr = tid / CPR + RPP * i, cc = tid % CPR;
+      const int p = pst + pr, n = n0 + cc * 8;
+      const bool ok = p < pend && n < a.N;
+      const bf16_t *src = ok ? a.dy + (size_t)p * a.lddy + n : a.dy;
+      const int g = pr >> 3, r = pr & 7;
+      const uint32_t dst = bbase + (cc >> 3) * 8192 + g * 1024 + r * 128 + (((cc & 7) ^ r) << 4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(ok ? 16 : 0));
+    }
+  };
+
+  constexpr uint32_t idesc = tc_idesc_mn(WTM, BN);
+  bool failed = false;
+#pragma unroll
+  for (int s = 0; s < TCS - 1; ++s) {
+    if (s < KB) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int kb = 0; kb < KB && !failed; ++kb) {
+    const int s = kb % TCS;
+    cp_async_wait<TCS - 2>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t as = smem_u32(T.A[s]), bs = smem_u32(T.B[s]);
+#pragma unroll
+      for (int k = 0; k < WTK / 16; ++k) {
+        // B: with a single 64-wide atom along o the atom stride is unused
+        const uint64_t ad = mn_desc(as + k * 2048, 8192),
+                       bd = mn_desc(bs + k * 2048, BN > 64 ? 8192 : 1024);
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&T.mma_bar[s])));
+    }
+    const int nk = kb + TCS - 1;
+    if (nk < KB) {
+      if (kb >= 1 && !mbar_wait(&T.mma_bar[(kb - 1) % TCS], ((kb - 1) / TCS) & 1)) failed = true;
+      if (!failed) load_stage(nk, nk % TCS);
+    }
+    cp_async_commit();
+    failed = __syncthreads_or(failed) != 0;
+  }
+  cp_async_wait<0>();
+  if (!failed && KB > 0 && !mbar_wait(&T.mma_bar[(KB - 1) % TCS], ((KB - 1) / TCS) & 1))
+    failed = true;
+  failed = __syncthreads_or(failed) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+  float *out = a.ws + (size_t)z * a.N * a.K;
+  const int kr = m0 + warp * 32 + lane;  // this lane's k' row of the tile
+  if (!failed) {
+#pragma unroll 1
+    for (int cb = 0; cb < BN; cb += 32) {
+      uint32_t r[32];
+      if (KB > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = 0u;
+      }
+      if (kr < a.K) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + cb + j;
+          if (n < a.N) out[(size_t)n * a.K + kr] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicAdd(&g_tc_timeouts, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+}
+
+// per-channel sums of dY [P, ld] (channels 0..C-1, C a multiple of 8) over
+// fixed pixel chunks: ws[chunk][C]; 16-byte loads, a fixed reduction order
+__global__ void __launch_bounds__(256) k_colsum8(const bf16_t *t, int P, int C, int ld,
+                                                 int chunk, float *ws) {
+  __shared__ float red[256][9];
+  const int C8 = C >> 3;
+  const int lanes = 256 / C8;  // pixel lanes per block (C <= 2048)
+  const int cg = threadIdx.x % C8, pl = threadIdx.x / C8;
+  const int z = blockIdx.x;
+  const int pend = min(P, (z + 1) * chunk);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (pl < lanes) {
+    for (int p = z * chunk + pl; p < pend; p += lanes) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(t + (size_t)p * ld + cg * 8);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s[2 * q] += bf2f((bf16_t)(w[q] & 0xffff));
+        s[2 * q + 1] += bf2f((bf16_t)(w[q] >> 16));
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = s[q];
+  __syncthreads();
+  if (threadIdx.x < C8) {
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int l = 0; l < lanes; ++l)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += red[l * C8 + threadIdx.x][q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ws[(size_t)z * C + threadIdx.x * 8 + q] = acc[q];
+  }
+}
+
+template <int BN>
+size_t tw_smem_bytes() {
+  return sizeof(TwSmem<BN>) + 1024;
+}
+
+template <int BN>
+cudaError_t launch_wgrad_tc(const WgradArgs &a, int splits, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_wgrad_tc<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tw_smem_bytes<BN>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((a.K + WTM - 1) / WTM, (a.N + BN - 1) / BN, splits);
+  k_conv3x3_wgrad_tc<BN><<<grid, 128, tw_smem_bytes<BN>(), st>>>(a);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- elementwise
 // dy[p, c] = 0 where y[p, c] <= 0 (gradient through ReLU, given its output)
 __global__ void k_relu_bwd(bf16_t *dy, int lddy, const bf16_t *y, int ldy, long P, int C) {
@@ -906,10 +1167,27 @@ int cem_sg_conv3x3_wgrad(const void *x, int ldx, const void *dy, int lddy, int B
   if (splits > 256) splits = 256;
   a.chunk = ((a.P + splits - 1) / splits + GBK - 1) / GBK * GBK;
   splits = (a.P + a.chunk - 1) / a.chunk;
+  const long nw = (long)Cout * a.K;
+  if (g_use_tc) {
+    // tcgen05: dW^T tiles of 128 k' x BN outputs; bias sums by a separate
+    // coalesced reduction into the workspace after the weight partials
+    a.wsb = nullptr;
+    cudaError_t e = Cout > 128 ? launch_wgrad_tc<256>(a, splits, st)
+                  : Cout > 64 ? launch_wgrad_tc<128>(a, splits, st)
+                              : launch_wgrad_tc<64>(a, splits, st);
+    if (e != cudaSuccess) return CEM_SG_ERR_CUDA;
+    k_reduce_splits<<<grid_1d(nw, 256), 256, 0, st>>>(a.ws, splits, nw, dw);
+    if (db) {
+      float *wsb = a.ws + (size_t)splits * Cout * a.K;
+      const int bch = (a.P + splits - 1) / splits;
+      k_colsum8<<<splits, 256, 0, st>>>(a.dy, a.P, Cout, lddy, bch, wsb);
+      k_reduce_splits<<<grid_1d(Cout, 128), 128, 0, st>>>(wsb, splits, Cout, db);
+    }
+    return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+  }
   a.wsb = db ? a.ws + (size_t)splits * Cout * a.K : nullptr;
   dim3 grid((Cout + GBM - 1) / GBM, (a.K + GBN - 1) / GBN, splits);
   k_conv3x3_wgrad<<<grid, 256, 0, st>>>(a);
-  const long nw = (long)Cout * a.K;
   k_reduce_splits<<<grid_1d(nw, 256), 256, 0, st>>>(a.ws, splits, nw, dw);
   if (db) k_reduce_splits<<<grid_1d(Cout, 128), 128, 0, st>>>(a.wsb, splits, Cout, db);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;

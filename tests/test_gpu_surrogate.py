@@ -355,3 +355,34 @@ def test_tcgen05_and_mma_paths_agree(cin, cout):
     assert L.cem_sg_timeouts(ctypes.byref(n)) == 0 and n.value == 0
     for path in (1, 0):
         assert _rel(out[path], mref) < 1e-2, path
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 24), (8, 32), (32, 64), (64, 128), (40, 96), (128, 256)])
+def test_weight_gradient_paths_agree(cin, cout):
+    """Weight and bias gradients on the tcgen05 path and on the mma.sync path
+    against the oracle (BF16 products are exact in FP32)."""
+    import ctypes
+    import torch
+    from paper_2509_01827_gb300.surrogate import _p, sg
+    x, w, b = _conv_case(B=2, H=9, W=23, Cin=cin, Cout=cout, seed=3 * cin + cout)
+    B, H, W, _ = x.shape
+    dy = bf16_round(np.random.default_rng(cout).standard_normal((B, H, W, cout)))
+    _, dw_ref, db_ref = so.conv2d_bwd(x, w, dy, 1)
+    L = sg()
+    ws_bytes = L.cem_sg_wgrad_workspace(B, H, W, cin, cout)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    xd, dyd = _t(x, torch.bfloat16), _t(dy, torch.bfloat16)
+    try:
+        for path in (1, 0):
+            assert L.cem_sg_set_gemm_path(path) == 0
+            dw = torch.full((cout, 3, 3, cin), float("nan"), dtype=torch.float32, device="cuda")
+            db = torch.full((cout,), float("nan"), dtype=torch.float32, device="cuda")
+            assert L.cem_sg_conv3x3_wgrad(_p(xd), cin, _p(dyd), cout, B, H, W, cin, cout, _p(dw),
+                                          _p(db), _p(ws), ws_bytes, 0) == 0
+            torch.cuda.synchronize()
+            assert _rel(dw.cpu().numpy(), dw_ref) < 1e-5, path
+            assert _rel(db.cpu().numpy(), db_ref) < 1e-5, path
+    finally:
+        L.cem_sg_set_gemm_path(1)
+    n = ctypes.c_int(-1)
+    assert L.cem_sg_timeouts(ctypes.byref(n)) == 0 and n.value == 0
