@@ -402,7 +402,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.ck_ud, (size_t)d.ck_cap) && dalloc_n(h, d.ck_step, (size_t)d.ck_cap) &&
        dalloc_n(h, d.ph_owner, (size_t)d.ph_cap) && dalloc_n(h, d.ph_creator, (size_t)d.ph_cap) &&
        dalloc_n(h, d.ph_nuser, (size_t)d.ph_cap) && dalloc_n(h, d.ph_users, (size_t)d.ph_cap * 4) &&
-       dalloc_n(h, d.ph_upf, (size_t)d.ph_cap * 4) &&
+       dalloc_n(h, d.ph_upf, (size_t)d.ph_cap * 4) && dalloc_n(h, d.ph_uap, (size_t)d.ph_cap * 4) &&
        dalloc_n(h, d.S, (size_t)d.list_cap) && dalloc_n(h, d.S_info, (size_t)d.list_cap) &&
        dalloc_n(h, d.S_G, (size_t)d.list_cap) && dalloc_n(h, d.spos, (size_t)d.g.ned) &&
        dalloc_n(h, d.pr_key, (size_t)d.prop_cap) && dalloc_n(h, d.pr_edge, (size_t)d.prop_cap) &&
@@ -414,11 +414,12 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.pl_mreal, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_mph, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.pl_mold, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_dm, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.pl_users, (size_t)d.prop_cap * 16) && dalloc_n(h, d.pl_upf, (size_t)d.prop_cap * 16) &&
+       dalloc_n(h, d.pl_uap, (size_t)d.prop_cap * 16) &&
        dalloc_n(h, d.pl_nu, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.cnt, 1) && dalloc_n(h, d.lamN, (size_t)d.lam_cap) &&
        dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
   d.e_part_cap = energy_parts_needed(d);
-  ok = ok && dalloc_n(h, d.e_part, (size_t)d.e_part_cap * 2);
+  ok = ok && dalloc_n(h, d.e_part, (size_t)d.e_part_cap * 2) && dalloc_n(h, d.e_pre, (size_t)EPRE * 3);
   if (!ok || cudaHostAlloc((void **)&h->h_cnt, sizeof(Counters), cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void **)&h->h_lam, 2 * sizeof(double) * d.lam_cap, cudaHostAllocDefault) != cudaSuccess) {
     g_create_error = "device allocation failed";

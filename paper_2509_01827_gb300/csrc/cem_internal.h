@@ -99,6 +99,7 @@ struct DevState {
   int *ph_nuser;
   int *ph_users;         // [ph_cap * 4], (e << 3) | (p << 2) | a, sorted by e
   int *ph_upf;           // [ph_cap * 4], piece-force index c*16 + p*8 + 2a of each user, -1 unused
+  double *ph_uap;        // [ph_cap * 4], area of each user's piece
 
   // surface list [list_cap]
   int *S;                // edge id or -1 (tombstone)
@@ -127,6 +128,7 @@ struct DevState {
   // the mass the phantom gains, and the phantom's complete user list
   double *pl_mreal, *pl_mph, *pl_mold, *pl_dm;  // [4]
   int *pl_users, *pl_upf;  // [16]: 4 users of the phantom of each local node
+  double *pl_uap;          // [16]: their piece areas
   int *pl_nu;              // [4]
 
   Counters *cnt;
@@ -135,6 +137,7 @@ struct DevState {
   // energy
   double *e_part;        // per-block partial sums
   int e_part_cap;
+  double *e_pre;         // [EPRE * 3] partial sums of the energy prologue
   double *erec;          // [rec_cap * 7]
   int rec_cap;
 };
@@ -143,6 +146,11 @@ struct DevState {
 // batched kernels take (member, block) items from a work list, so that every
 // member sees the same block decomposition (and the same fixed-order energy
 // partial sums) as when it is stepped alone.
+// The energy prologue sums the boundary work and the dissipated energy in
+// EPRE fixed chunks (one block of EPRE_TB threads each), added in order by
+// the epilogue.
+constexpr int EPRE = 128, EPRE_TB = 256;
+
 struct VBlk {
   int x, y, gx, gy;
 };

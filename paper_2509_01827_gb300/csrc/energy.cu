@@ -33,21 +33,54 @@ __device__ double block_sum(double v) {
   return r;  // valid in thread 0
 }
 
-__device__ __forceinline__ void energy_pre(const DevState &d) {
+// Part b of the prologue: chunk b of the loaded/prescribed boundary nodes'
+// work and of the splits' dissipated energy, summed by one block of EPRE_TB
+// threads into e_pre[3b..3b+2].  The chunking depends only on the counts, so
+// a mesh stepped alone and the same mesh in a batch add in the same order.
+__device__ __forceinline__ void energy_pre_part(const DevState &d, int b) {
   Counters *c = d.cnt;
-  int rec = c->n_rec;
-  if (rec >= d.rec_cap) {
-    if (threadIdx.x == 0) atomicOr(&c->status, STAT_CAPACITY);
+  if (c->n_rec >= d.rec_cap) {
+    if (b == 0 && threadIdx.x == 0) atomicOr(&c->status, STAT_CAPACITY);
     return;
   }
+  const int nbc = d.n_bc, nck = c->n_ck;
+  const int kb = (nbc + EPRE - 1) / EPRE, kc = (nck + EPRE - 1) / EPRE;
+  const int b0 = b * kb, b1 = min(nbc, b0 + kb), c0 = b * kc, c1 = min(nck, c0 + kc);
   double wn = 0.0, wd = 0.0, ud = 0.0;
-  for (int q = threadIdx.x; q < d.n_bc; q += TB) {
-    int N = d.bc_nodes[q];
+  for (int q = b0 + threadIdx.x; q < b1; q += EPRE_TB) {
+    const int N = d.bc_nodes[q];
     wn += d.Wn[N];
     wd += d.Wd[N];
   }
-  int nck = c->n_ck;
-  for (int q = threadIdx.x; q < nck; q += TB) ud += d.ck_ud[q];
+  for (int q = c0 + threadIdx.x; q < c1; q += EPRE_TB) ud += d.ck_ud[q];
+  wn = block_sum(wn);
+  wd = block_sum(wd);
+  ud = block_sum(ud);
+  if (threadIdx.x == 0) {
+    d.e_pre[3 * b] = wn;
+    d.e_pre[3 * b + 1] = wd;
+    d.e_pre[3 * b + 2] = ud;
+  }
+}
+
+// The record: step, time, the prologue's sums (work and dissipation before
+// the step) and the step's kinetic and strain energy partials.
+__device__ __forceinline__ void energy_post(const DevState &d, int nparts) {
+  Counters *c = d.cnt;
+  int rec = c->n_rec;
+  if (rec >= d.rec_cap) return;
+  double ke = 0.0, se = 0.0, wn = 0.0, wd = 0.0, ud = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += TB) {
+    ke += d.e_part[2 * q];
+    se += d.e_part[2 * q + 1];
+  }
+  if (threadIdx.x < EPRE) {
+    wn = d.e_pre[3 * threadIdx.x];
+    wd = d.e_pre[3 * threadIdx.x + 1];
+    ud = d.e_pre[3 * threadIdx.x + 2];
+  }
+  ke = block_sum(ke);
+  se = block_sum(se);
   wn = block_sum(wn);
   wd = block_sum(wd);
   ud = block_sum(ud);
@@ -55,47 +88,35 @@ __device__ __forceinline__ void energy_pre(const DevState &d) {
     double *r = d.erec + (size_t)rec * 7;
     r[0] = (double)c->step;
     r[1] = (double)c->step * d.mat.dt;
+    r[2] = ke;
+    r[3] = se;
     r[4] = wn;
     r[5] = wd;
     r[6] = ud;
-  }
-}
-
-__device__ __forceinline__ void energy_post(const DevState &d, int nparts) {
-  Counters *c = d.cnt;
-  int rec = c->n_rec;
-  if (rec >= d.rec_cap) return;
-  double ke = 0.0, se = 0.0;
-  for (int q = threadIdx.x; q < nparts; q += TB) {
-    ke += d.e_part[2 * q];
-    se += d.e_part[2 * q + 1];
-  }
-  ke = block_sum(ke);
-  se = block_sum(se);
-  if (threadIdx.x == 0) {
-    double *r = d.erec + (size_t)rec * 7;
-    r[2] = ke;
-    r[3] = se;
     c->n_rec = rec + 1;
   }
 }
 
 
-__global__ void __launch_bounds__(TB) k_energy_pre(DevState d) { energy_pre(d); }
+__global__ void __launch_bounds__(EPRE_TB) k_energy_pre(DevState d) {
+  energy_pre_part(d, blockIdx.x);
+}
 
 __global__ void __launch_bounds__(TB) k_energy_post(DevState d, int nparts) {
   energy_post(d, nparts);
 }
 
-// batched counterparts: one CTA per member
-__global__ void __launch_bounds__(TB) k_energy_pre_batch(BatchDev b) {
+// batched counterparts: EPRE prologue parts per member; one CTA per member
+// for the epilogue
+__global__ void __launch_bounds__(EPRE_TB) k_energy_pre_batch(BatchDev b) {
   __shared__ DevState sd;
-  int held = -1;
+  int held = -1, w0, w1;
   const int n = *b.bstep;
-  for (int s = blockIdx.x; s < b.n; s += gridDim.x) {
-    stage_member(b.ds, s, sd, held);
+  block_range(b.n * EPRE, w0, w1);
+  for (int w = w0; w < w1; ++w) {
+    stage_member(b.ds, w / EPRE, sd, held);
     if (!member_active(sd, n)) continue;
-    energy_pre(sd);
+    energy_pre_part(sd, w % EPRE);
     __syncthreads();
   }
 }
@@ -159,7 +180,7 @@ int grid_for(int n, int block, int maxb) {
 }  // namespace
 
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st) {
-  k_energy_pre<<<1, TB, 0, st>>>(d);
+  k_energy_pre<<<EPRE, EPRE_TB, 0, st>>>(d);
   return cudaGetLastError();
 }
 
@@ -170,7 +191,8 @@ cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st) {
 
 
 cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st) {
-  k_energy_pre_batch<<<b.n < 1216 ? b.n : 1216, TB, 0, st>>>(b);
+  const int items = b.n * EPRE;
+  k_energy_pre_batch<<<items < 1216 ? items : 1216, EPRE_TB, 0, st>>>(b);
   return cudaGetLastError();
 }
 

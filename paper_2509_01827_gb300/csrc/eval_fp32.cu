@@ -22,14 +22,14 @@ __device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl)
   return (bh - ah) + (bl - al);
 }
 
-// Own FP32 strain of intact element e at its edge k (Eq. 4 at the edge point).
-__device__ void own_strain32(const DevState &d, const U32x2 &U, int e, int k, float eps[3]) {
-  const Geo &g = d.g;
+// Own FP32 strain of an intact element at its edge k (Eq. 4 at the edge
+// point), from its four nodes' displacement pairs in local order.
+__device__ __forceinline__ void own_strain32(const Geo &g, const float4 (&q)[4], int k,
+                                             float eps[3]) {
   float xh[4], xl[4], yh[4], yl[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const float4 q = U.u[elem_node(g, e, a)];
-    xh[a] = q.x; xl[a] = q.y; yh[a] = q.z; yl[a] = q.w;
+    xh[a] = q[a].x; xl[a] = q[a].y; yh[a] = q[a].z; yl[a] = q[a].w;
   }
   const float rx = g.rxf, ry = g.ryf, hx2 = 0.5f * rx, hy2 = 0.5f * ry;
   float au = df_diff(xh[0], xl[0], xh[1], xl[1]), bu = df_diff(xh[3], xl[3], xh[2], xl[2]);
@@ -44,13 +44,57 @@ __device__ void own_strain32(const DevState &d, const U32x2 &U, int e, int k, fl
   }
 }
 
-__device__ void used_stress32(const DevState &d, const U32x2 &U, int e, int k, float s[3]) {
+// Everything the FP32 evaluation of surface point (e, k0) reads, loaded in
+// one level: the displacement pairs of e's nodes, the states of its four
+// neighbours, the two far nodes of each neighbour inside the mesh (across
+// the edges other than k0) and G_c of e.
+struct EvalPatch {
+  float4 ue[4];     // e's nodes, local order
+  float4 far[4][2]; // neighbour across edge k: its two nodes not on edge k
+  int st[4];        // neighbour states (ST_OUT outside the mesh)
+  float gc;
+};
+
+__device__ __forceinline__ void load_patch(const DevState &d, const U32x2 &U, int e, int k0,
+                                           EvalPatch &P) {
+  const Geo &g = d.g;
+  const int i = e % g.nx, j = e / g.nx, r = g.nx + 1;
+  const int n0 = j * r + i, n1 = n0 + 1, n2 = n0 + r + 1, n3 = n0 + r;
+  const int nd[4] = {n0, n1, n2, n3};
+  // far nodes of the neighbour below, right, above, left
+  const int fa[4][2] = {{n0 - r, n1 - r}, {n1 + 1, n2 + 1}, {n2 + r, n3 + r}, {n0 - 1, n3 - 1}};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) P.ue[a] = U.u[nd[a]];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int f = elem_neighbor(g, e, k);
+    P.st[k] = estatus(d, f);
+    const bool use = f >= 0 && k != k0;
+    P.far[k][0] = use ? U.u[fa[k][0]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    P.far[k][1] = use ? U.u[fa[k][1]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  P.gc = d.gc[e];
+}
+
+// The neighbour across edge k in its own local node order.
+__device__ __forceinline__ void neighbour_nodes(const EvalPatch &P, int k, float4 (&q)[4]) {
+  switch (k) {
+    case 0: q[0] = P.far[0][0]; q[1] = P.far[0][1]; q[2] = P.ue[1]; q[3] = P.ue[0]; break;
+    case 1: q[0] = P.ue[1]; q[1] = P.far[1][0]; q[2] = P.far[1][1]; q[3] = P.ue[2]; break;
+    case 2: q[0] = P.ue[3]; q[1] = P.ue[2]; q[2] = P.far[2][0]; q[3] = P.far[2][1]; break;
+    default: q[0] = P.far[3][0]; q[1] = P.ue[0]; q[2] = P.ue[3]; q[3] = P.far[3][1]; break;
+  }
+}
+
+__device__ __forceinline__ void used_stress32(const DevState &d, const EvalPatch &P, int k,
+                                              float s[3]) {
   float e1[3];
-  own_strain32(d, U, e, k, e1);
-  int f = elem_neighbor(d.g, e, k);
-  if (estatus(d, f) == ST_INTACT) {
+  own_strain32(d.g, P.ue, k, e1);
+  if (P.st[k] == ST_INTACT) {
+    float4 q[4];
+    neighbour_nodes(P, k, q);
     float e2[3];
-    own_strain32(d, U, f, (k + 2) & 3, e2);
+    own_strain32(d.g, q, (k + 2) & 3, e2);
     for (int c = 0; c < 3; ++c) e1[c] = 0.5f * (e1[c] + e2[c]);
   }
   const Mat &m = d.mat;
@@ -59,22 +103,26 @@ __device__ void used_stress32(const DevState &d, const U32x2 &U, int e, int k, f
   s[2] = m.D33f * e1[2];
 }
 
-__device__ void eval_G32(const DevState &d, const U32x2 &U, int e, int k0, float G[4]) {
+__device__ __forceinline__ void eval_G32(const DevState &d, const EvalPatch &P, int k0,
+                                         float G[4]) {
   const Geo &g = d.g;
-  int N1 = elem_node(g, e, k0), N2 = elem_node(g, e, (k0 + 1) & 3);
   const float DX = g.DXf[k0], DY = g.DYf[k0];
-  const float4 P1 = U.u[N1], P2 = U.u[N2];
+  float4 P1 = P.ue[0], P2 = P.ue[1];
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+    if (a == k0) { P1 = P.ue[a]; P2 = P.ue[(a + 1) & 3]; }
   float dux = df_diff(P1.x, P1.y, P2.x, P2.y);
   float duy = df_diff(P1.z, P1.w, P2.z, P2.w);
   // |x_N2 - x_N1|^2 - |X_N2 - X_N1|^2 without cancellation
   float stretch = 2.f * (DX * dux + DY * duy) + (dux * dux + duy * duy);
   float H = stretch > 0.f ? 1.f : 0.f;
   float ddx = dux * H, ddy = duy * H;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (k == k0) { G[k] = -1.f; continue; }
     const float nx = g.nxf[k0][k], ny = g.nyf[k0][k];
     float s[3];
-    used_stress32(d, U, e, k, s);
+    used_stress32(d, P, k, s);
     float tx = s[0] * nx + s[2] * ny;
     float ty = s[2] * nx + s[1] * ny;
     G[k] = 0.5f * (ddx * tx + ddy * ty);
@@ -99,13 +147,16 @@ __device__ __forceinline__ void eval32(const DevState &d, VBlk vb, int cur) {
     double Gk = 0.0;
     if (i < n) {
       edge = d.S[i];
+      const int info = d.S_info[i];
       if (edge >= 0) {
-        key = d.S_info[i];
+        key = info;
         int e = key >> 2, k0 = key & 3;
         if (d.mat.scope != 2 || is_tip_edge(d, e, k0)) {
+          EvalPatch P;
+          load_patch(d, U, e, k0, P);
           float G32[4];
-          eval_G32(d, U, e, k0, G32);
-          float gc = d.gc[e];
+          eval_G32(d, P, k0, G32);
+          float gc = P.gc;
           bool near = false;
           for (int k = 0; k < 4; ++k)
             if (k != k0 && fabsf(G32[k] / gc - 1.f) < 1e-3f) near = true;

@@ -119,9 +119,9 @@ __device__ __noinline__ double update_special(const DevState &d, int N, int cur,
 }
 
 // Update of a node without loads: FP32 only.
-__device__ __forceinline__ void update_plain(const DevState &d, int N, int cur, float dtv,
-                                             float dt, float fx, float fy, float4 U, float2 vo,
-                                             float minv) {
+__device__ __forceinline__ float2 update_plain(const DevState &d, int N, int cur, float dtv,
+                                               float dt, float fx, float fy, float4 U, float2 vo,
+                                               float minv) {
   const float vxn = fmaf(dtv, -fx * minv, vo.x);
   const float vyn = fmaf(dtv, -fy * minv, vo.y);
   d.v2[N] = make_float2(vxn, vyn);
@@ -130,64 +130,79 @@ __device__ __forceinline__ void update_plain(const DevState &d, int N, int cur, 
   df_add(U.x, U.y, dt * vxn);
   df_add(U.z, U.w, dt * vyn);
   d.u4[cur ^ 1][N] = U;
+  return make_float2(vxn, vyn);
 }
 
 // ------------------------------------------------------------------ pieces
-// Piece forces of split elements: own strain at each edge point, FP32.
-__device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
-                                         int part_off) {
-  const int n = 2 * d.cnt->n_ck;
+// One piece of split element c (side p): strains and stresses at its four
+// edge points (Eq. 4 at the edge midpoints, from the displacements of the
+// piece's own nodes) and its nodal forces f[2a], f[2a+1] at local nodes
+// a = 0..3, FP32.  The piece kernel (every force, for the phantom update)
+// and the tile kernel (the forces at real nodes) both evaluate pieces here.
+struct Piece32 {
+  float ex[4], ey[4], gx[4];
+  Stress3 s[4];
+  float qA;
+  float f[8];
+};
+
+__device__ __forceinline__ void piece32(const DevState &d, int c, int p, int cur, Piece32 &P) {
   const Geo &g = d.g;
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
+  const int4 nd = reinterpret_cast<const int4 *>(d.ck_node)[c * 2 + p];
+  const int nds[4] = {nd.x, nd.y, nd.z, nd.w};
+  float xh[4], xl[4], yh[4], yl[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 U = d.u4[cur][nds[a]];
+    xh[a] = U.x; xl[a] = U.y; yh[a] = U.z; yl[a] = U.w;
+  }
+  // edge differences: a = u1-u0 (bottom), b = u2-u3 (top), c = u3-u0 (left), e = u2-u1 (right)
+  float au = df_diff(xh[0], xl[0], xh[1], xl[1]), bu = df_diff(xh[3], xl[3], xh[2], xl[2]);
+  float cu = df_diff(xh[0], xl[0], xh[3], xl[3]), eu = df_diff(xh[1], xl[1], xh[2], xl[2]);
+  float av = df_diff(yh[0], yl[0], yh[1], yl[1]), bv = df_diff(yh[3], yl[3], yh[2], yl[2]);
+  float cv = df_diff(yh[0], yl[0], yh[3], yl[3]), ev = df_diff(yh[1], yl[1], yh[2], yl[2]);
+  P.ex[0] = rx * au;          P.ey[0] = hy2 * (cv + ev); P.gx[0] = fmaf(hy2, cu + eu, rx * av);
+  P.ex[1] = hx2 * (au + bu);  P.ey[1] = ry * ev;         P.gx[1] = fmaf(ry, eu, hx2 * (av + bv));
+  P.ex[2] = rx * bu;          P.ey[2] = hy2 * (cv + ev); P.gx[2] = fmaf(hy2, cu + eu, rx * bv);
+  P.ex[3] = hx2 * (au + bu);  P.ey[3] = ry * cv;         P.gx[3] = fmaf(ry, cu, hx2 * (av + bv));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) P.s[k] = stress32(d.mat, P.ex[k], P.ey[k], P.gx[k]);
+  P.qA = (float)(d.ck_Ap[c * 2 + p] * 0.25);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float cx = dxn(k, a) * hx2, cy = dyn(k, a) * hy2;
+      sx = fmaf(cx, P.s[k].xx, fmaf(cy, P.s[k].xy, sx));
+      sy = fmaf(cy, P.s[k].yy, fmaf(cx, P.s[k].xy, sy));
+    }
+    P.f[2 * a] = sx * P.qA;
+    P.f[2 * a + 1] = sy * P.qA;
+  }
+}
+
+// Piece forces of split elements, written for the phantom update.
+__device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
+                                         int part_off) {
+  const int n = 2 * d.cnt->n_ck;
   double se = 0.0;
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
-    int c = t >> 1, p = t & 1;
-    const int4 nd = reinterpret_cast<const int4 *>(d.ck_node)[c * 2 + p];
-    const int nds[4] = {nd.x, nd.y, nd.z, nd.w};
-    float xh[4], xl[4], yh[4], yl[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float4 U = d.u4[cur][nds[a]];
-      xh[a] = U.x; xl[a] = U.y; yh[a] = U.z; yl[a] = U.w;
-    }
-    // edge differences: a = u1-u0 (bottom), b = u2-u3 (top), c = u3-u0 (left), e = u2-u1 (right)
-    float au = df_diff(xh[0], xl[0], xh[1], xl[1]), bu = df_diff(xh[3], xl[3], xh[2], xl[2]);
-    float cu = df_diff(xh[0], xl[0], xh[3], xl[3]), eu = df_diff(xh[1], xl[1], xh[2], xl[2]);
-    float av = df_diff(yh[0], yl[0], yh[1], yl[1]), bv = df_diff(yh[3], yl[3], yh[2], yl[2]);
-    float cv = df_diff(yh[0], yl[0], yh[3], yl[3]), ev = df_diff(yh[1], yl[1], yh[2], yl[2]);
-    // strains at edge points 0..3 (Eq. 4 at the edge midpoints)
-    float ex[4], ey[4], gx[4];
-    ex[0] = rx * au;          ey[0] = hy2 * (cv + ev); gx[0] = fmaf(hy2, cu + eu, rx * av);
-    ex[1] = hx2 * (au + bu);  ey[1] = ry * ev;         gx[1] = fmaf(ry, eu, hx2 * (av + bv));
-    ex[2] = rx * bu;          ey[2] = hy2 * (cv + ev); gx[2] = fmaf(hy2, cu + eu, rx * bv);
-    ex[3] = hx2 * (au + bu);  ey[3] = ry * cv;         gx[3] = fmaf(ry, cu, hx2 * (av + bv));
-    Stress3 s[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s[k] = stress32(d.mat, ex[k], ey[k], gx[k]);
-    const float qA = (float)(d.ck_Ap[c * 2 + p] * 0.25);
-    float f[8];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float sx = 0.f, sy = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float cx = dxn(k, a) * hx2, cy = dyn(k, a) * hy2;
-        sx = fmaf(cx, s[k].xx, fmaf(cy, s[k].xy, sx));
-        sy = fmaf(cy, s[k].yy, fmaf(cx, s[k].xy, sy));
-      }
-      f[2 * a] = sx * qA;
-      f[2 * a + 1] = sy * qA;
-    }
+    const int c = t >> 1, p = t & 1;
+    Piece32 P;
+    piece32(d, c, p, cur, P);
     float *o = d.pff + c * 16 + p * 8;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) o[q] = f[q];
+    for (int q = 0; q < 8; ++q) o[q] = P.f[q];
     if (energy) {
       double acc = 0.0;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        acc += 0.5 * (double)qA *
-               ((double)ex[k] * s[k].xx + (double)ey[k] * s[k].yy + (double)gx[k] * s[k].xy);
+        acc += 0.5 * (double)P.qA *
+               ((double)P.ex[k] * P.s[k].xx + (double)P.ey[k] * P.s[k].yy +
+                (double)P.gx[k] * P.s[k].xy);
       se += acc;
     }
   }
@@ -206,12 +221,50 @@ __global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
 //   sD  node differences D(i,j) = (ux(i+1,j)-ux(i,j), uy(i+1,j)-uy(i,j),
 //       ux(i,j+1)-ux(i,j), uy(i,j+1)-uy(i,j)) of nodes [i0-2, i0+TX] x [j0-2, j0+TY],
 //       formed from the pairs as (hi_b - hi_a) + (lo_b - lo_a)
-//   sH  stresses (xx, yy, xy) used by the element above (.a) and below (.b)
-//       horizontal edges h(i,j), i in [i0-1, i0+TX), j in [j0-1, j0+TY]
-//   sV  the same for the element right (.a) and left (.b) of vertical edges
-//       v(i,j), i in [i0-1, i0+TX], j in [j0-1, j0+TY)
-// sU is dead once sD is formed and shares its storage with sH.
+//   sH  horizontal edges h(i,j), i in [i0-1, i0+TX), j in [j0-1, j0+TY]:
+//       with A the stress (xx, yy, xy) used by the element above and B the
+//       one used by the element below (zero where that element is not
+//       intact), AB = (A.yy, A.xy, B.yy, B.xy) and P = (A.xx + B.xx,
+//       A.xy + B.xy)
+//   sV  vertical edges v(i,j), i in [i0-1, i0+TX], j in [j0-1, j0+TY): with
+//       R the stress used by the element right and L by the element left,
+//       AB = (R.xx, R.xy, L.xx, L.xy) and P = (R.xy + L.xy, R.yy + L.yy)
+// Tiles whose halo holds only intact elements keep one stress per edge
+// instead.  sU is dead once sD is formed and shares its storage with sH;
+// sD is dead once the edge stresses are formed and then holds the forces
+// at real nodes of the split elements that touch the tile's nodes (the
+// window of elements [i0-1, i0+TX-1] x [j0-1, j0+TY-1]), KSLOT elements at
+// a time, with the window's split elements listed in increasing id.
 constexpr int TX = 32, BX = 32, BY = 8;
+
+// Rank of this thread's flag among the set flags of the block, in thread
+// order, and their total.  Every thread of the block calls it.
+__device__ __forceinline__ int block_rank(bool flag, int &total) {
+  constexpr int NWARP = BX * BY / 32;
+  __shared__ int s_cnt[NWARP];
+  const int tid = threadIdx.x + threadIdx.y * BX, lane = tid & 31, w = tid >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) s_cnt[w] = __popc(b);
+  __syncthreads();
+  int off = 0, tot = 0;
+#pragma unroll
+  for (int q = 0; q < NWARP; ++q) {
+    const int n = s_cnt[q];
+    off += q < w ? n : 0;
+    tot += n;
+  }
+  __syncthreads();
+  total = tot;
+  return off + __popc(b & ((1u << lane) - 1u));
+}
+
+// the low / high half of a float4 in shared memory (one 8-byte load)
+__device__ __forceinline__ float2 lo2(const float4 &v) {
+  return reinterpret_cast<const float2 *>(&v)[0];
+}
+__device__ __forceinline__ float2 hi2(const float4 &v) {
+  return reinterpret_cast<const float2 *>(&v)[1];
+}
 
 template <int TY>
 struct Tile {
@@ -225,7 +278,8 @@ struct Tile {
     float4 U[UYn][UXn];
   };
   struct SmemB {
-    float4 Ha[HYn][HXn], Hb[HYn][HXn];
+    float4 AB[HYn][HXn];
+    float2 P[HYn][HXn];
   };
   union SmemMain {
     SmemA a;
@@ -239,16 +293,31 @@ struct Tile {
   };
   union SmemV {
     struct {
-      float4 a[VYn][VXn], b[VYn][VXn];
+      float4 AB[VYn][VXn];
+      float2 P[VYn][VXn];
     } gen;
     SmemFastV fast;
   };
+  static constexpr int WXn = TX + 1, WYn = TY + 1, NWIN = WXn * WYn;
+  static constexpr int KSLOT = (2 * DYn * DXn * (int)sizeof(float2) - 4 * NWIN) / 32;
+  struct SmemD {
+    float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
+  };
+  struct SmemPieces {
+    float2 slot[KSLOT][4];  // force at local node a of split element slot
+    uint16_t list[NWIN];    // window index of the n-th split element
+    uint16_t map[NWIN];     // rank of a split element in the list
+  };
+  static_assert(sizeof(SmemPieces) <= sizeof(SmemD), "piece slots fit in sD");
   struct Smem {  // > 48 KB for TY = 16: dynamic shared memory
     union {
       SmemMain ab;
       SmemFastH fh;
     } u1;
-    float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
+    union {
+      SmemD d;
+      SmemPieces pc;
+    } u2;
     SmemV v;
     uint8_t st[EYn][EXn];
   };
@@ -262,10 +331,12 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
   constexpr int EXn = C::EXn, EYn = C::EYn, HXn = C::HXn, HYn = C::HYn, VXn = C::VXn,
                 VYn = C::VYn;
   float4 (*sU)[UXn] = T.u1.ab.a.U;
-  float4 (*sHa)[HXn] = T.u1.ab.b.Ha, (*sHb)[HXn] = T.u1.ab.b.Hb;
+  float4 (*sHAB)[HXn] = T.u1.ab.b.AB;
+  float2 (*sHP)[HXn] = T.u1.ab.b.P;
   float2 (*fHP)[HXn] = T.u1.fh.P, (*fHQ)[HXn] = T.u1.fh.Q;
-  float2 (*sDx)[DXn] = T.Dx, (*sDy)[DXn] = T.Dy;
-  float4 (*sVa)[VXn] = T.v.gen.a, (*sVb)[VXn] = T.v.gen.b;
+  float2 (*sDx)[DXn] = T.u2.d.Dx, (*sDy)[DXn] = T.u2.d.Dy;
+  float4 (*sVAB)[VXn] = T.v.gen.AB;
+  float2 (*sVP)[VXn] = T.v.gen.P;
   float2 (*fVP)[VXn] = T.v.fast.P, (*fVQ)[VXn] = T.v.fast.Q;
   uint8_t (*sst)[EXn] = T.st;
 
@@ -350,7 +421,7 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry, hx4 = 0.25f * rx, hy4 = 0.25f * ry;
   const float qA = g.qAf;
-  double se = 0.0;
+  float se = 0.f;  // strain energy of this thread's edges / qA (energy steps)
 
   if (!general) {
     // every element around the tile is intact: smoothed strain on every
@@ -368,7 +439,7 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
         fHP[ly][lx] = make_float2(st.xx, st.xy);
         fHQ[ly][lx] = make_float2(st.yy, st.xy);
         if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
-          se += (double)qA * (double)(exx * st.xx + eyy * st.yy + gxy * st.xy);
+          se += exx * st.xx + eyy * st.yy + gxy * st.xy;
       }
     }
     for (int q = tid; q < VXn * VYn; q += NTH) {
@@ -384,7 +455,7 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
         fVP[ly][lx] = make_float2(st.xx, st.xy);
         fVQ[ly][lx] = make_float2(st.yy, st.xy);
         if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
-          se += (double)qA * (double)(exx * st.xx + eyy * st.yy + gxy * st.xy);
+          se += exx * st.xx + eyy * st.yy + gxy * st.xy;
       }
     }
   } else {
@@ -420,10 +491,10 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
           if (sa == ST_INTACT) Ta = S;
           if (sb == ST_INTACT) Tb = S;
           if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
-            se += (double)qA * (double)(w * (exx * s.xx + eyy * s.yy + gxy * s.xy));
+            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
         }
-        sHa[ly][lx] = Ta;
-        sHb[ly][lx] = Tb;
+        sHAB[ly][lx] = make_float4(Ta.y, Ta.z, Tb.y, Tb.z);
+        sHP[ly][lx] = make_float2(Ta.x + Tb.x, Ta.z + Tb.z);
       }
     }
     // vertical edges v(ii,jj), ii = i0-1+lx, jj = j0-1+ly:
@@ -458,23 +529,20 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
           if (sr == ST_INTACT) Ta = S;
           if (sl == ST_INTACT) Tb = S;
           if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
-            se += (double)qA * (double)(w * (exx * s.xx + eyy * s.yy + gxy * s.xy));
+            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
         }
-        sVa[ly][lx] = Ta;
-        sVb[ly][lx] = Tb;
+        sVAB[ly][lx] = make_float4(Ta.x, Ta.z, Tb.x, Tb.z);
+        sVP[ly][lx] = make_float2(Ta.z + Tb.z, Ta.y + Tb.y);
       }
     }
     __syncthreads();
   }
   __syncthreads();
 
-  double ke = 0.0;
-  const float dt = m.dtf;
-  const float dtv = first ? 0.5f * dt : dt;
+  // element forces of the own nodes
+  float fxr[RY], fyr[RY];
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
-    const int j = j0 + ty + r * BY;
-    if (i > g.nx || j > g.ny) continue;
     // edge arrays: edge (i', j') at [j' - (j0-1)][i' - (i0-1)]
     const int ci = tx + 1, cj = ty + r * BY + 1;
     float fx, fy;
@@ -493,56 +561,122 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
       fy = (2.f * rx) * (H1.y - H2.y) + hy2 * ((Hd0.x + Hd1.x) - (Hu0.x + Hu1.x)) +
            (2.f * ry) * (V1.x - V2.x) + hx2 * ((Vl0.y + Vl1.y) - (Vr0.y + Vr1.y));
     } else {
-      const float4 A1 = sHa[cj][ci - 1], B1 = sHb[cj][ci - 1];  // h(i-1, j): N right node
-      const float4 A2 = sHa[cj][ci], B2 = sHb[cj][ci];          // h(i, j):   N left node
-      fx = rx * ((A1.x + B1.x) - (A2.x + B2.x)) + hy2 * ((B1.z - A1.z) + (B2.z - A2.z));
-      fy = rx * ((A1.z + B1.z) - (A2.z + B2.z)) + hy2 * ((B1.y - A1.y) + (B2.y - A2.y));
-      // h(i-1, j+1), h(i, j+1): N is a lower node of their below element;
-      // h(i-1, j-1), h(i, j-1): N is an upper node of their above element
-      const float4 Bu0 = sHb[cj + 1][ci - 1], Bu1 = sHb[cj + 1][ci];
-      const float4 Ad0 = sHa[cj - 1][ci - 1], Ad1 = sHa[cj - 1][ci];
-      fx += hy2 * ((Ad0.z + Ad1.z) - (Bu0.z + Bu1.z));
-      fy += hy2 * ((Ad0.y + Ad1.y) - (Bu0.y + Bu1.y));
-      // v(i, j-1): N top node; v(i, j): N bottom node (a = right, b = left)
-      const float4 R1 = sVa[cj - 1][ci], L1 = sVb[cj - 1][ci];
-      const float4 R2 = sVa[cj][ci], L2 = sVb[cj][ci];
-      fx += ry * ((R1.z + L1.z) - (R2.z + L2.z)) + hx2 * ((L1.x - R1.x) + (L2.x - R2.x));
-      fy += ry * ((R1.y + L1.y) - (R2.y + L2.y)) + hx2 * ((L1.z - R1.z) + (L2.z - R2.z));
-      // v(i-1, j-1), v(i-1, j): N is a right node of their right element;
-      // v(i+1, j-1), v(i+1, j): N is a left node of their left element
-      const float4 Rl0 = sVa[cj - 1][ci - 1], Rl1 = sVa[cj][ci - 1];
-      const float4 Lr0 = sVb[cj - 1][ci + 1], Lr1 = sVb[cj][ci + 1];
+      // h(i-1, j), h(i, j): N is the right / left node of both elements
+      const float2 P1 = sHP[cj][ci - 1], P2 = sHP[cj][ci];
+      const float4 Q1 = sHAB[cj][ci - 1], Q2 = sHAB[cj][ci];
+      fx = rx * (P1.x - P2.x) + hy2 * ((Q1.w - Q1.y) + (Q2.w - Q2.y));
+      fy = rx * (P1.y - P2.y) + hy2 * ((Q1.z - Q1.x) + (Q2.z - Q2.x));
+      // h(i-1, j+1), h(i, j+1): N is a lower node of their below element (B);
+      // h(i-1, j-1), h(i, j-1): N is an upper node of their above element (A)
+      const float2 Bu0 = hi2(sHAB[cj + 1][ci - 1]), Bu1 = hi2(sHAB[cj + 1][ci]);
+      const float2 Ad0 = lo2(sHAB[cj - 1][ci - 1]), Ad1 = lo2(sHAB[cj - 1][ci]);
+      fx += hy2 * ((Ad0.y + Ad1.y) - (Bu0.y + Bu1.y));
+      fy += hy2 * ((Ad0.x + Ad1.x) - (Bu0.x + Bu1.x));
+      // v(i, j-1): N top node; v(i, j): N bottom node of both elements
+      const float2 S1 = sVP[cj - 1][ci], S2 = sVP[cj][ci];
+      const float4 W1 = sVAB[cj - 1][ci], W2 = sVAB[cj][ci];
+      fx += ry * (S1.x - S2.x) + hx2 * ((W1.z - W1.x) + (W2.z - W2.x));
+      fy += ry * (S1.y - S2.y) + hx2 * ((W1.w - W1.y) + (W2.w - W2.y));
+      // v(i-1, j-1), v(i-1, j): N is a right node of their right element (R);
+      // v(i+1, j-1), v(i+1, j): N is a left node of their left element (L)
+      const float2 Rl0 = lo2(sVAB[cj - 1][ci - 1]), Rl1 = lo2(sVAB[cj][ci - 1]);
+      const float2 Lr0 = hi2(sVAB[cj - 1][ci + 1]), Lr1 = hi2(sVAB[cj][ci + 1]);
       fx += hx2 * ((Rl0.x + Rl1.x) - (Lr0.x + Lr1.x));
-      fy += hx2 * ((Rl0.z + Rl1.z) - (Lr0.z + Lr1.z));
+      fy += hx2 * ((Rl0.y + Rl1.y) - (Lr0.y + Lr1.y));
     }
-    fx *= qA;
-    fy *= qA;
-    // pieces of split neighbours in increasing element id; element states at
-    // [ej - (j0-2)][ei - (i0-2)]
-    const int ey0 = j - 1 - (j0 - 2), ex0 = i - 1 - (i0 - 2);
-    const int s00 = sst[ey0][ex0], s01 = sst[ey0][ex0 + 1], s10 = sst[ey0 + 1][ex0],
-              s11 = sst[ey0 + 1][ex0 + 1];
-    if (general && ((s00 | s01 | s10 | s11) & ST_CRACKED)) {
-      const int sts[4] = {s00, s01, s10, s11};
-      const int dei[4] = {-1, 0, -1, 0}, dej[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
+    fxr[r] = fx * qA;
+    fyr[r] = fy * qA;
+  }
+
+  if (general) {
+    // forces of the pieces of split elements at the own nodes, added in
+    // increasing element id.  Window element (wx, wy) is (i0-1+wx, j0-1+wy),
+    // its state sst[wy+1][wx+1].  The pieces are evaluated here from their
+    // nodes' displacements, so the update does not wait for the piece kernel.
+    __syncthreads();  // sD is dead: its storage now holds the piece forces
+    constexpr int WXn = C::WXn, NWIN = C::NWIN, KSLOT = C::KSLOT;
+    uint16_t *wlist = T.u2.pc.list, *wmap = T.u2.pc.map;
+    float2 (*slot)[4] = T.u2.pc.slot;
+    int nl = 0;
+    for (int q0 = 0; q0 < NWIN; q0 += NTH) {
+      const int q = q0 + tid;
+      bool cr = false;
+      if (q < NWIN) {
+        const int wy = q / WXn, wx = q - wy * WXn;
+        cr = sst[wy + 1][wx + 1] == ST_CRACKED;
+      }
+      int tot;
+      const int rk = nl + block_rank(cr, tot);
+      if (q < NWIN) wmap[q] = cr ? (uint16_t)rk : (uint16_t)0xffff;
+      if (cr) wlist[rk] = (uint16_t)q;
+      nl += tot;
+    }
+    __syncthreads();
+    for (int base = 0; base < nl; base += KSLOT) {
+      const int nb = nl - base < KSLOT ? nl - base : KSLOT;
+      for (int t = tid; t < 2 * nb; t += NTH) {
+        const int li = base + (t >> 1), p = t & 1;
+        const int q = wlist[li];
+        const int wy = q / WXn, wx = q - wy * WXn;
+        const int c = d.crack_of[(j0 - 1 + wy) * g.nx + i0 - 1 + wx];
+        const int info = d.ck_info[c];
+        Piece32 P;
+        piece32(d, c, p, cur, P);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (sts[k] == ST_CRACKED) {
-          const int c = d.crack_of[(j + dej[k]) * g.nx + i + dei[k]];
-          const int side = (d.ck_info[c] >> (4 + la[k])) & 1;
-          fx += d.pff[c * 16 + side * 8 + 2 * la[k]];
-          fy += d.pff[c * 16 + side * 8 + 2 * la[k] + 1];
+        for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
+          if (((info >> (4 + a)) & 1) == p)
+            slot[li - base][a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        // elements (i-1, j-1), (i, j-1), (i-1, j), (i, j) of node (i, j) and
+        // the node's local index in each
+        const int wy0 = ty + r * BY, wx0 = tx;
+        const int dwx[4] = {0, 1, 0, 1}, dwy[4] = {0, 0, 1, 1}, la[4] = {2, 3, 1, 0};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int q = (wy0 + dwy[k]) * WXn + wx0 + dwx[k];
+          if (sst[wy0 + dwy[k] + 1][wx0 + dwx[k] + 1] == ST_CRACKED) {
+            const int li = wmap[q];
+            if (li >= base && li < base + nb) {
+              const float2 F = slot[li - base][la[k]];
+              fxr[r] += F.x;
+              fyr[r] += F.y;
+            }
+          }
         }
       }
+      __syncthreads();
     }
+  }
+
+  double ke = 0.0;  // nodes with loads or prescribed velocities (FP64 path)
+  float ke2 = 0.f;  // 2 KE of the other nodes
+  const float dt = m.dtf;
+  const float dtv = first ? 0.5f * dt : dt;
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const int j = j0 + ty + r * BY;
+    if (i > g.nx || j > g.ny) continue;
+    const float fx = fxr[r], fy = fyr[r];
     const int N = j * stride + i;
-    if (ENERGY || own_nf[r])
+    if (own_nf[r]) {
       ke += update_special(d, N, cur, first, fx, fy, own_u[r], own_v[r], own_mi[r], own_nf[r],
                            ENERGY ? 1 : 0);
-    else
-      update_plain(d, N, cur, dtv, dt, fx, fy, own_u[r], own_v[r], own_mi[r]);
+    } else {
+      const float2 vn = update_plain(d, N, cur, dtv, dt, fx, fy, own_u[r], own_v[r], own_mi[r]);
+      if (ENERGY && own_mi[r] > 0.f) {
+        // KE of the mid-step velocity, FP32 like the velocities themselves
+        const float bx = first ? own_v[r].x : 0.5f * (own_v[r].x + vn.x);
+        const float by = first ? own_v[r].y : 0.5f * (own_v[r].y + vn.y);
+        ke2 += __fdividef(fmaf(bx, bx, by * by), own_mi[r]);
+      }
+    }
   }
-  if (ENERGY) block_sum2(ke, se, d.e_part + 2 * (vb.y * vb.gx + vb.x));
+  if (ENERGY)
+    block_sum2(ke + 0.5 * (double)ke2, (double)qA * (double)se,
+               d.e_part + 2 * (vb.y * vb.gx + vb.x));
 }
 
 template <bool ENERGY, int TY>
@@ -714,15 +848,16 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
     if (e != cudaSuccess) return e;
     return launch_eval32(d, cur, st);
   }
+  // the tile update evaluates the pieces it needs itself, so it does not
+  // wait for the piece kernel; the phantom update does
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   e = launch_eval32(d, cur, ss.aux2);
   if (e != cudaSuccess) return e;
   e = launch_select(d, TRACK_STEP, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
-  cudaEventRecord(ss.fork, st);
-  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_pieces32<<<gp, 256, 0, ss.aux1>>>(d, cur, energy ? 1 : 0, tiles);
   k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
   main_kernel(st);
   cudaEventRecord(ss.join1, ss.aux1);
@@ -744,13 +879,12 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
   cudaStream_t st = ss.main;
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
+  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   e = launch_eval32_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
   e = launch_select_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_pieces32_batch<<<gp, 256, 0, st>>>(b, energy ? 1 : 0);
-  cudaEventRecord(ss.fork, st);
-  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
+  k_pieces32_batch<<<gp, 256, 0, ss.aux1>>>(b, energy ? 1 : 0);
   k_phantom32_batch<<<gph, 256, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
   const int f = first ? 1 : 0;
   if (tile_rows == 8) {

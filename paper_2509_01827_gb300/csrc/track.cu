@@ -36,9 +36,15 @@ namespace cem {
 
 namespace {
 
-constexpr int TB = 1024;           // threads of the tracking CTA
+constexpr int TB = 512;            // threads of the tracking CTA (128 registers each)
 constexpr int SORT_CAP = 8192;     // proposals per step (power of two)
 constexpr int WB = TB / 8;         // winners split per batch (eight threads each)
+
+// dynamic shared memory of the selection CTA: sorted keys, winners and the
+// proposals' G, edge and exit edge
+constexpr size_t select_smem_bytes() {
+  return SORT_CAP * (sizeof(unsigned long long) + sizeof(int) + sizeof(double) + sizeof(int) + 1);
+}
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of v over the block; returns the prefix, *total = sum.
@@ -70,52 +76,6 @@ __device__ int block_exscan(int v, int *total) {
   return pre;
 }
 
-// Lumped mass of real node N: every element around it (in increasing id)
-// gives rho A_p / 4 of the piece that holds N (the whole area if intact).
-// Loads are issued level by level for the four elements, the sum keeps the
-// canonical order.
-
-// Lumped mass of phantom P: its users (sorted by element) give rho A_p / 4.
-
-// Lumped mass of real node N once element e (N its local node a) is split
-// with piece sides side[] and area fractions alpha[]: rho A_p / 4 of every
-// piece around N that uses N, in increasing element id (the planned piece in
-// place of the intact element e).
-__device__ double mass_real_planned(const DevState &d, int N, int e, const int side[4],
-                                    const double alpha[2]) {
-  const Geo &g = d.g;
-  const int r = g.nx + 1, i = N % r, j = N / r;
-  const int di[4] = {-1, 0, -1, 0}, dj[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
-  int eq[4], st[4], c[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int ei = i + di[q], ej = j + dj[q];
-    eq[q] = (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) ? -1 : ej * g.nx + ei;
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    st[q] = eq[q] < 0 ? ST_OUT : (eq[q] == e ? ST_CRACKED : (int)d.estate[eq[q]]);
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    c[q] = (st[q] == ST_CRACKED && eq[q] != e) ? d.crack_of[eq[q]] : -1;
-  double Ap[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    Ap[q] = g.A;
-    if (eq[q] == e) {
-      Ap[q] = alpha[side[la[q]]] * g.A;
-    } else if (c[q] >= 0) {
-      const int sd = (d.ck_info[c[q]] >> (4 + la[q])) & 1;
-      Ap[q] = d.ck_Ap[c[q] * 2 + sd];
-    }
-  }
-  double acc = 0.0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (st[q] != ST_OUT) acc = acc + d.mat.rho * Ap[q] * 0.25;
-  return acc;
-}
-
 __device__ void set_mass(const DevState &d, int N, double m) {
   d.m[N] = m;
   double mi = m > 0.0 ? 1.0 / m : 0.0;
@@ -123,53 +83,34 @@ __device__ void set_mass(const DevState &d, int N, double m) {
   if (d.precision == 1) d.minvf[N] = (float)mi;
 }
 
-// Phantom of local node a of element e that the split (entry ka, exit kb)
-// reuses: the one held by the cracked neighbour across a cut edge of e that
-// contains the node, if that edge is cut in the neighbour too (first such
-// edge in increasing local edge index); -1 when a new phantom is needed.
-__device__ int reuse_lookup(const DevState &d, int e, int ka, int kb, int a) {
-  const Geo &g = d.g;
-  const int k1 = (a + 3) & 3, k2 = a;
-  const int kk[2] = {k1 < k2 ? k1 : k2, k1 < k2 ? k2 : k1};
-  const int N = elem_node(g, e, a);
-  for (int q = 0; q < 2; ++q) {
-    const int k = kk[q];
-    if (k != ka && k != kb) continue;
-    const int f = elem_neighbor(g, e, k);
-    if (estatus(d, f) != ST_CRACKED) continue;
-    const int cf = d.crack_of[f];
-    const int inf = d.ck_info[cf];
-    const int kf = (k + 2) & 3;
-    if ((inf & 3) != kf && ((inf >> 2) & 3) != kf) continue;
-    int af = -1;
-    for (int b = 0; b < 4; ++b)
-      if (elem_node(g, f, b) == N) af = b;
-    const int sf = (inf >> (4 + af)) & 1;
-    return d.ck_node[cf * 8 + (1 - sf) * 4 + af];
-  }
-  return -1;
-}
-
 // Area fractions of the two pieces by the shoelace formula in natural
-// coordinates (the reference square has area 4).
-__device__ void area_fractions(int ka, int kb, const int side[4], double alpha[2]) {
+// coordinates (the reference square has area 4).  A piece's polygon visits
+// the element's nodes and edge points in counter-clockwise order, keeping
+// the nodes on its side and the two edge points of the segment; the terms
+// are added in that order with the closing term last.
+__device__ __forceinline__ void area_fractions(int ka, int kb, const int side[4], double alpha[2]) {
+#pragma unroll
   for (int p = 0; p < 2; ++p) {
-    double px[6], py[6];
-    int nv = 0;
+    double x0 = 0.0, y0 = 0.0, xp = 0.0, yp = 0.0, twice = 0.0;
+    bool have = false;
+#pragma unroll
     for (int w = 0; w < 8; ++w) {
-      if ((w & 1) == 0) {
-        const int a = w >> 1;
-        if (side[a] == p) { px[nv] = xi_n(a); py[nv] = eta_n(a); ++nv; }
+      const int q = w >> 1;
+      const bool in = (w & 1) == 0 ? side[q] == p : (q == ka || q == kb);
+      if (!in) continue;
+      const double x = (w & 1) == 0 ? xi_n(q) : xi_g(q);
+      const double y = (w & 1) == 0 ? eta_n(q) : eta_g(q);
+      if (!have) {
+        x0 = x;
+        y0 = y;
+        have = true;
       } else {
-        const int k = w >> 1;
-        if (k == ka || k == kb) { px[nv] = xi_g(k); py[nv] = eta_g(k); ++nv; }
+        twice = twice + (xp * y - x * yp);
       }
+      xp = x;
+      yp = y;
     }
-    double twice = 0.0;
-    for (int v = 0; v < nv; ++v) {
-      const int w = (v + 1) % nv;
-      twice = twice + (px[v] * py[w] - px[w] * py[v]);
-    }
+    twice = twice + (xp * y0 - x0 * yp);
     alpha[p] = fabs(twice) * 0.5 / 4.0;
   }
 }
@@ -225,55 +166,165 @@ __device__ void compact_surface(const DevState &d) {
   }
 }
 
+// What the split of element e needs about its local node a (real node N),
+// read in two levels of independent loads: the phantom the split reuses and,
+// for N's lumped mass after the split, the states of the elements around N
+// and the areas of their pieces that hold N.
+struct NodePlan {
+  int P;          // phantom to reuse, or -1
+  int qe;         // position of e among the four elements around N
+  int st[4];      // their states (e counted as split, ST_OUT outside)
+  double Ap[4];   // area of the piece of each holding N (e's filled in later)
+};
+
+__device__ __forceinline__ void node_plan(const DevState &d, int e, int ka, int kb, int a,
+                                          NodePlan &np) {
+  const Geo &g = d.g;
+  const int N = elem_node(g, e, a);
+  const int r = g.nx + 1, i = N % r, j = N / r;
+  const int di[4] = {-1, 0, -1, 0}, dj[4] = {-1, -1, 0, 0}, la[4] = {2, 3, 1, 0};
+  int eq[4], st[4], cq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ei = i + di[q], ej = j + dj[q];
+    eq[q] = (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) ? -1 : ej * g.nx + ei;
+  }
+  // level 1: states and split-table slots of the four elements
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    st[q] = eq[q] < 0 ? ST_OUT : (int)d.estate[eq[q]];
+    cq[q] = eq[q] < 0 ? -1 : d.crack_of[eq[q]];
+  }
+  // level 2: split records of the split ones
+  int inf[4], nd[4][2];
+  double A2[4][2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    inf[q] = 0;
+    nd[q][0] = nd[q][1] = -1;
+    A2[q][0] = A2[q][1] = 0.0;
+    if (st[q] == ST_CRACKED && eq[q] != e && cq[q] >= 0) {
+      const int c = cq[q];
+      inf[q] = d.ck_info[c];
+      A2[q][0] = d.ck_Ap[c * 2];
+      A2[q][1] = d.ck_Ap[c * 2 + 1];
+      nd[q][0] = d.ck_node[c * 8 + la[q]];
+      nd[q][1] = d.ck_node[c * 8 + 4 + la[q]];
+    }
+  }
+  np.qe = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (eq[q] == e) np.qe = q;
+    np.st[q] = eq[q] < 0 ? ST_OUT : (eq[q] == e ? ST_CRACKED : st[q]);
+    np.Ap[q] = g.A;
+    if (st[q] == ST_CRACKED && eq[q] != e && cq[q] >= 0)
+      np.Ap[q] = ((inf[q] >> (4 + la[q])) & 1) ? A2[q][1] : A2[q][0];
+  }
+  // the phantom to reuse: across the cut edges of e that contain N (first
+  // in increasing local edge index), held by a split neighbour whose own
+  // segment also cuts that edge
+  np.P = -1;
+  const int k1 = (a + 3) & 3, k2 = a;
+  const int kk[2] = {k1 < k2 ? k1 : k2, k1 < k2 ? k2 : k1};
+#pragma unroll
+  for (int t = 1; t >= 0; --t) {
+    const int k = kk[t];
+    if (k != ka && k != kb) continue;
+    const int f = elem_neighbor(g, e, k), kf = (k + 2) & 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (f >= 0 && eq[q] == f && st[q] == ST_CRACKED && cq[q] >= 0 &&
+          ((inf[q] & 3) == kf || ((inf[q] >> 2) & 3) == kf))
+        np.P = ((inf[q] >> (4 + la[q])) & 1) ? nd[q][0] : nd[q][1];
+    }
+  }
+}
+
 // Selection and planning (one CTA).  Reads the step's proposals and the
 // current crack state, never writes it: the node-update kernels may run
 // concurrently.  Produces, for each winner in increasing element id, its
 // split plan (sides, phantoms to reuse, area fractions, split-table slot,
 // first new phantom id, surface-list appends and tombstones) and the
-// counters the apply kernel commits.
+// counters the apply kernel commits.  Global loads are issued in few
+// dependent levels (the proposals' fields are staged in shared memory with
+// the keys), since this single CTA runs beside the node updates.
 __device__ __forceinline__ void select_plan(const DevState &d, int mode,
                                             unsigned long long *smem) {
-  unsigned long long *sk = smem;                    // [SORT_CAP]
-  int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP]
-  __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done;
+  unsigned long long *sk = smem;                    // [SORT_CAP] sorted (key << 32 | index)
+  int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP] winners (sorted positions)
+  double *oG = (double *)(swin + SORT_CAP);         // [SORT_CAP] G of proposal i
+  int *oE = (int *)(oG + SORT_CAP);                 // [SORT_CAP] its edge
+  uint8_t *oK = (uint8_t *)(oE + SORT_CAP);         // [SORT_CAP] its exit edge
+  __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done, s_compact;
   __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_reuse[WB][4], b_app[WB],
       b_tomb[WB][4], b_c[WB];
   __shared__ double b_alpha[WB][2];
+  // sides of the four nodes (bit a) and area fractions of a split entering
+  // at edge point ka and leaving at kb, for the 12 pairs ka != kb
+  __shared__ int s_sides[16];
+  __shared__ double s_alpha[16][2];
   Counters *cnt = d.cnt;
   const Geo &g = d.g;
   const int tid = threadIdx.x;
-  // stable compaction of the surface list when half of it is dead (the
-  // evaluation of this step has finished; nothing else reads the list now)
-  if (mode == TRACK_STEP && cnt->n_dead > 1024 && 2 * cnt->n_dead > cnt->n_S) compact_surface(d);
-  __syncthreads();
+  if (tid >= 32 && tid < 48) {
+    const int ka = (tid - 32) >> 2, kb = (tid - 32) & 3;
+    int side[4] = {0, 0, 0, 0}, bits = 0;
+    double alpha[2] = {0.0, 0.0};
+    if (ka != kb) {
+      const double pax = xi_g(ka), pay = eta_g(ka), pbx = xi_g(kb), pby = eta_g(kb);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double cross = (pbx - pax) * (eta_n(a) - pay) - (pby - pay) * (xi_n(a) - pax);
+        side[a] = cross > 0.0 ? 0 : 1;
+        bits |= side[a] << a;
+      }
+      area_fractions(ka, kb, side, alpha);
+    }
+    s_sides[tid - 32] = bits;
+    s_alpha[tid - 32][0] = alpha[0];
+    s_alpha[tid - 32][1] = alpha[1];
+  }
   if (tid == 0) {
+    const int n_dead = cnt->n_dead, nS = cnt->n_S;
     int n = cnt->n_prop;
     if (n > d.prop_cap) n = d.prop_cap;
     s_n = n;
-    s_nwin = 0;
-    s_stop = 0;
     s_nph = cnt->n_ph;
     s_nck = cnt->n_ck;
-    s_nS = cnt->n_S;
+    s_nS = nS;
+    // stable compaction of the surface list when half of it is dead (the
+    // evaluation of this step has finished; nothing else reads the list now)
+    s_compact = mode == TRACK_STEP && n_dead > 1024 && 2 * n_dead > nS;
+    s_nwin = 0;
+    s_stop = 0;
     s_dead = 0;
     s_done = 0;
   }
   __syncthreads();
+  if (s_compact) {
+    compact_surface(d);
+    __syncthreads();
+    if (tid == 0) s_nS = cnt->n_S;
+    __syncthreads();
+  }
   const int n = s_n;
   if (n > 0) {
-    // ---- load keys; debug proposals that are not surface points (or not
-    //      tips under the tips-only scope) sort to the end
+    // ---- load keys and fields; debug proposals that are not surface points
+    //      (or not tips under the tips-only scope) sort to the end
     int P2 = 1;
     while (P2 < n) P2 <<= 1;
     for (int i = tid; i < P2; i += TB) {
       unsigned long long v = ~0ull;
       if (i < n) {
-        int key = d.pr_key[i];
+        const int key = d.pr_key[i], ed = d.pr_edge[i], kx = d.pr_k[i];
+        oG[i] = d.pr_G[i];
+        oE[i] = ed;
+        oK[i] = (uint8_t)kx;
         bool valid = true;
         if (mode == TRACK_DEBUG) {
-          int ed = d.pr_edge[i];
           int pos = d.spos[ed];
-          valid = pos >= 0 && d.S_info[pos] == key && d.pr_k[i] != (key & 3);
+          valid = pos >= 0 && d.S_info[pos] == key && kx != (key & 3);
           if (!valid) atomicOr(&cnt->pad[0], 1);
           if (valid && d.mat.scope == 2) valid = tip_of(d, key >> 2, key & 3);
         }
@@ -282,17 +333,35 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
       sk[i] = v;
     }
     __syncthreads();
-    for (int k = 2; k <= P2; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < P2; i += TB) {
-          int l = i ^ j;
-          if (l > i) {
-            unsigned long long a = sk[i], b = sk[l];
-            bool up = (i & k) == 0;
-            if ((a > b) == up) { sk[i] = b; sk[l] = a; }
+    if (P2 <= 32) {
+      // one warp sorts up to 32 keys (no block-wide barriers)
+      if (tid < 32) {
+        for (int k = 2; k <= P2; k <<= 1) {
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            const int i = tid, l = i ^ j;
+            if (i < P2 && l > i) {
+              unsigned long long a = sk[i], b = sk[l];
+              bool up = (i & k) == 0;
+              if ((a > b) == up) { sk[i] = b; sk[l] = a; }
+            }
+            __syncwarp();
           }
         }
-        __syncthreads();
+      }
+      __syncthreads();
+    } else {
+      for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = tid; i < P2; i += TB) {
+            int l = i ^ j;
+            if (l > i) {
+              unsigned long long a = sk[i], b = sk[l];
+              bool up = (i & k) == 0;
+              if ((a > b) == up) { sk[i] = b; sk[l] = a; }
+            }
+          }
+          __syncthreads();
+        }
       }
     }
     __shared__ int s_valid;
@@ -309,8 +378,7 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
         int best = -1;
         for (int i = 0; i < nv; ++i) {
           int idx = (int)(sk[i] & 0xffffffffu);
-          if (best < 0 || key_greater(d.pr_G[idx], d.pr_edge[idx], d.pr_G[best], d.pr_edge[best]))
-            best = idx;
+          if (best < 0 || key_greater(oG[idx], oE[idx], oG[best], oE[best])) best = idx;
         }
         int wi = -1;
         for (int i = 0; i < nv; ++i)
@@ -327,8 +395,8 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
           if (mode != TRACK_PRECRACK) {
             int idx = (int)(sk[i] & 0xffffffffu);
             int key = (int)(sk[i] >> 32), e = key >> 2;
-            double G = d.pr_G[idx];
-            int ed = d.pr_edge[idx];
+            double G = oG[idx];
+            int ed = oE[idx];
             int ei = e % g.nx, ej = e / g.nx;
             for (int dj = -1; dj <= 1 && win; ++dj) {
               int row = ej + dj;
@@ -339,7 +407,7 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
               for (; q < nv && (int)(sk[q] >> 32) <= hi_e * 4 + 3; ++q) {
                 if (q == i) continue;
                 int qi = (int)(sk[q] & 0xffffffffu);
-                if (!key_greater(G, ed, d.pr_G[qi], d.pr_edge[qi])) { win = 0; break; }
+                if (!key_greater(G, ed, oG[qi], oE[qi])) { win = 0; break; }
               }
             }
           }
@@ -365,27 +433,44 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
         const int key = (int)(sk[i] >> 32);
         b_e[wl] = key >> 2;
         b_ka[wl] = key & 3;
-        b_kb[wl] = d.pr_k[idx];
+        b_kb[wl] = oK[idx];
         b_app[wl] = 0;
       }
       __syncthreads();
+      NodePlan np;
+      int nu = 0;
+      int4 u4 = make_int4(0, 0, 0, 0), f4 = u4;
+      double2 A01 = make_double2(0.0, 0.0), A23 = A01;
+      double mold = -1.0;
       if (act && lane < 4) {
-        // local node a: side and the phantom to reuse
+        // local node a: side, the phantom to reuse and the mass inputs, then
+        // (consumed only after the scans below) the reused phantom's user
+        // list with its users' piece areas
         const int e = b_e[wl], ka = b_ka[wl], kb = b_kb[wl], a = lane;
-        const double pax = xi_g(ka), pay = eta_g(ka), pbx = xi_g(kb), pby = eta_g(kb);
-        const double cross = (pbx - pax) * (eta_n(a) - pay) - (pby - pay) * (xi_n(a) - pax);
-        b_side[wl][a] = cross > 0.0 ? 0 : 1;
-        b_reuse[wl][a] = reuse_lookup(d, e, ka, kb, a);
+        b_side[wl][a] = (s_sides[ka * 4 + kb] >> a) & 1;
+        node_plan(d, e, ka, kb, a, np);
+        b_reuse[wl][a] = np.P;
+        if (np.P >= 0) {
+          const int t = np.P - g.nn;
+          nu = d.ph_nuser[t];
+          u4 = reinterpret_cast<const int4 *>(d.ph_users)[t];
+          f4 = reinterpret_cast<const int4 *>(d.ph_upf)[t];
+          A01 = reinterpret_cast<const double2 *>(d.ph_uap)[2 * t];
+          A23 = reinterpret_cast<const double2 *>(d.ph_uap)[2 * t + 1];
+          mold = d.m[np.P];
+        }
       } else if (act) {
         // local edge k: appended to the surface list if the element across
         // it is intact, else its current entry (if any) becomes a tombstone
         const int e = b_e[wl], k = lane - 4;
         const int f = elem_neighbor(g, e, k);
+        const int ed = elem_edge(g, e, k);
+        const int sf = estatus(d, f), pos = d.spos[ed];
         b_tomb[wl][k] = -1;
-        if (estatus(d, f) == ST_INTACT) {
+        if (sf == ST_INTACT) {
           atomicOr(&b_app[wl], 1 << k);
         } else {
-          b_tomb[wl][k] = d.spos[elem_edge(g, e, k)];
+          b_tomb[wl][k] = pos;
         }
       }
       __syncthreads();
@@ -410,13 +495,9 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
       }
       __syncthreads();
       if (act && lane == 0 && !s_stop) {
-        const int w = base + wl;
-        int side[4];
-        for (int a = 0; a < 4; ++a) side[a] = b_side[wl][a];
-        double alpha[2];
-        area_fractions(b_ka[wl], b_kb[wl], side, alpha);
-        int info = b_ka[wl] | (b_kb[wl] << 2) | (b_app[wl] << 8);
-        for (int a = 0; a < 4; ++a) info |= side[a] << (4 + a);
+        const int w = base + wl, pk = b_ka[wl] * 4 + b_kb[wl];
+        const double alpha[2] = {s_alpha[pk][0], s_alpha[pk][1]};
+        const int info = b_ka[wl] | (b_kb[wl] << 2) | (b_app[wl] << 8) | (s_sides[pk] << 4);
         d.pl_e[w] = b_e[wl];
         d.pl_info[w] = info;
         for (int a = 0; a < 4; ++a) {
@@ -437,52 +518,53 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
       if (act && lane < 4 && !s_stop) {
         // local node a: masses after the split and the phantom's user list
         const int w = base + wl, e = b_e[wl], a = lane;
-        int side[4];
-        for (int q = 0; q < 4; ++q) side[q] = b_side[wl][q];
+        const int sa = b_side[wl][a];
         const double alpha[2] = {b_alpha[wl][0], b_alpha[wl][1]};
-        const int N = elem_node(g, e, a);
-        d.pl_mreal[w * 4 + a] = mass_real_planned(d, N, e, side, alpha);
-        const int p = 1 - side[a];  // the piece that uses the phantom of a
+        // the real node: rho A_p / 4 of every piece around it that uses it,
+        // in increasing element id (the planned piece in place of e)
+        double mreal = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double Ap = q == np.qe ? alpha[sa] * g.A : np.Ap[q];
+          if (np.st[q] != ST_OUT) mreal = mreal + d.mat.rho * Ap * 0.25;
+        }
+        d.pl_mreal[w * 4 + a] = mreal;
+        // the reused phantom's users (sorted by element) and their areas
+        int us[4] = {u4.x, u4.y, u4.z, u4.w}, uf[4] = {f4.x, f4.y, f4.z, f4.w};
+        double Au[4] = {A01.x, A01.y, A23.x, A23.y};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q >= nu) { us[q] = 0x7fffffff; uf[q] = -1; Au[q] = 0.0; }
+        const int p = 1 - sa;  // the piece that uses the phantom of a
         const int code = (e << 3) | (p << 2) | a, cf = b_c[wl] * 16 + p * 8 + 2 * a;
         const double Anew = alpha[p] * g.A;
-        const int P = b_reuse[wl][a];
-        int us[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff}, uf[4] = {-1, -1, -1, -1};
-        int nu = 0;
-        double mold = -1.0;
-        if (P >= 0) {
-          const int t = P - g.nn;
-          nu = d.ph_nuser[t];
-          for (int q = 0; q < nu && q < 4; ++q) {
-            us[q] = d.ph_users[t * 4 + q];
-            uf[q] = d.ph_upf[t * 4 + q];
+        // insert the new user in increasing element id (as the split writes
+        // did): before the first user of a larger element; a full list of
+        // four keeps its first four entries
+        int pos = 4;
+#pragma unroll
+        for (int q = 3; q >= 0; --q)
+          if (q >= nu || (us[q] >> 3) > e) pos = q;
+        int out[4], outf[4];
+        double outA[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (t < pos) {
+            out[t] = us[t]; outf[t] = uf[t]; outA[t] = Au[t];
+          } else if (t == pos) {
+            out[t] = code; outf[t] = cf; outA[t] = Anew;
+          } else if (t - 1 < nu) {
+            out[t] = us[t - 1]; outf[t] = uf[t - 1]; outA[t] = Au[t - 1];
+          } else {
+            out[t] = -1; outf[t] = -1; outA[t] = 0.0;
           }
-          mold = d.m[P];
         }
-        // insert the new user in increasing element id (as the split writes did)
-        int out[4] = {-1, -1, -1, -1}, outf[4] = {-1, -1, -1, -1}, o = 0;
-        bool placed = false;
-        for (int q = 0; q < 4; ++q) {
-          if (!placed && (q >= nu || (us[q] >> 3) > e)) {
-            if (o < 4) { out[o] = code; outf[o] = cf; }
-            ++o;
-            placed = true;
-          }
-          if (q < nu && o < 4) { out[o] = us[q]; outf[o] = uf[q]; ++o; }
-        }
-        if (!placed && o < 4) { out[o] = code; outf[o] = cf; }
         // the phantom's mass: rho A_p / 4 of each user piece, in list order
         double acc = 0.0;
         const int nun = nu < 4 ? nu + 1 : 4;
-        for (int q = 0; q < nun; ++q) {
-          double Ap;
-          if (out[q] == code) {
-            Ap = Anew;
-          } else {
-            const int cu = d.crack_of[out[q] >> 3];
-            Ap = d.ck_Ap[cu * 2 + ((out[q] >> 2) & 1)];
-          }
-          acc = acc + d.mat.rho * Ap * 0.25;
-        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nun) acc = acc + d.mat.rho * outA[q] * 0.25;
         d.pl_mph[w * 4 + a] = acc;
         d.pl_mold[w * 4 + a] = mold;
         d.pl_dm[w * 4 + a] = d.mat.rho * Anew * 0.25;
@@ -490,6 +572,7 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
         for (int q = 0; q < 4; ++q) {
           d.pl_users[w * 16 + a * 4 + q] = out[q];
           d.pl_upf[w * 16 + a * 4 + q] = outf[q];
+          d.pl_uap[w * 16 + a * 4 + q] = outA[q];
         }
       }
       __syncthreads();
@@ -597,6 +680,9 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
       } else {
         reinterpret_cast<int4 *>(d.ph_users)[t] = us;
         reinterpret_cast<int4 *>(d.ph_upf)[t] = uf;
+        const double2 *ua = reinterpret_cast<const double2 *>(d.pl_uap + w * 16 + a * 4);
+        reinterpret_cast<double2 *>(d.ph_uap)[2 * t] = ua[0];
+        reinterpret_cast<double2 *>(d.ph_uap)[2 * t + 1] = ua[1];
         d.ph_nuser[t] = nu + 1;
       }
       set_mass(d, N, mreal);
@@ -738,7 +824,7 @@ __global__ void k_surface_info(DevState d, int *out3) {
 }  // namespace
 
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
-  size_t sm = SORT_CAP * sizeof(unsigned long long) + SORT_CAP * sizeof(int);
+  size_t sm = select_smem_bytes();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -766,7 +852,7 @@ cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st) {
 }
 
 cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st) {
-  size_t sm = SORT_CAP * sizeof(unsigned long long) + SORT_CAP * sizeof(int);
+  size_t sm = select_smem_bytes();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_select_batch,
