@@ -250,6 +250,19 @@ cem_status upload_load_factors(cem_handle *h, int chunk, cudaStream_t st = nullp
   return CEM_OK;
 }
 
+// The streams of a step's side branches (evaluation + selection, piece
+// forces + phantom update) get the highest priority: their short kernels
+// then take SM slots as the tile update's CTAs retire instead of queueing
+// behind its remaining waves.  Step graphs are instantiated so that kernel
+// nodes keep the priority of the stream they were captured from.
+cudaError_t create_aux_streams(StepStreams &ss) {
+  int least = 0, greatest = 0;
+  cudaError_t ce = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux1, cudaStreamNonBlocking, greatest);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux2, cudaStreamNonBlocking, greatest);
+  return ce;
+}
+
 cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
   if (!h->graphs[cur][energy]) {
     cudaGraph_t g;
@@ -258,7 +271,8 @@ cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
-    cudaError_t e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g, 0);
+    cudaError_t e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g,
+                                          cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
   }
@@ -324,8 +338,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
     ce = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
     h->own_stream = ce == cudaSuccess;
   }
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->ss.aux1, cudaStreamNonBlocking);
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->ss.aux2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = create_aux_streams(h->ss);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.join1, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ss.join2, cudaEventDisableTiming);
@@ -416,6 +429,9 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.pl_users, (size_t)d.prop_cap * 16) && dalloc_n(h, d.pl_upf, (size_t)d.prop_cap * 16) &&
        dalloc_n(h, d.pl_uap, (size_t)d.prop_cap * 16) &&
        dalloc_n(h, d.pl_nu, (size_t)d.prop_cap * 4) &&
+       dalloc_n(h, d.sel_sk, (size_t)d.prop_cap) && dalloc_n(h, d.sel_win, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.sel_G, (size_t)d.prop_cap) && dalloc_n(h, d.sel_E, (size_t)d.prop_cap) &&
+       dalloc_n(h, d.sel_K, (size_t)d.prop_cap) &&
        dalloc_n(h, d.cnt, 1) && dalloc_n(h, d.lamN, (size_t)d.lam_cap) &&
        dalloc_n(h, d.lamD, (size_t)d.lam_cap) && dalloc_n(h, d.erec, (size_t)d.rec_cap * 7);
   d.e_part_cap = energy_parts_needed(d);
@@ -1126,7 +1142,8 @@ cem_status batch_graph(cem_handle *b, int energy, cudaGraphExec_t *out) {
     cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
     if (e != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch end capture: %s", cudaGetErrorString(e2));
-    cudaError_t e3 = cudaGraphInstantiate(&p->graphs[energy], g, 0);
+    cudaError_t e3 = cudaGraphInstantiate(&p->graphs[energy], g,
+                                          cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(b, CEM_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e3));
   }
@@ -1297,8 +1314,7 @@ cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_
     ce = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
     b->own_stream = ce == cudaSuccess;
   }
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->ss.aux1, cudaStreamNonBlocking);
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->ss.aux2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = create_aux_streams(b->ss);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.join1, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ss.join2, cudaEventDisableTiming);

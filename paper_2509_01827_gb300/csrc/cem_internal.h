@@ -131,6 +131,14 @@ struct DevState {
   double *pl_uap;          // [16]: their piece areas
   int *pl_nu;              // [4]
 
+  // selection scratch for steps with more proposals than its shared memory
+  // holds [prop_cap]: sorted keys, winners, G, edge and exit edge
+  unsigned long long *sel_sk;
+  int *sel_win;
+  double *sel_G;
+  int *sel_E;
+  uint8_t *sel_K;
+
   Counters *cnt;
   double *lamN, *lamD;   // [lam_cap] load factors of steps lam_base + i
 

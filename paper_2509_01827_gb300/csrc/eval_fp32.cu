@@ -178,9 +178,9 @@ __device__ __forceinline__ void eval32(const DevState &d, VBlk vb, int cur) {
   }
 }
 
-__global__ void k_eval32(DevState d, int cur) { eval32(d, hw_vblk(), cur); }
+__global__ void __launch_bounds__(256, 4) k_eval32(DevState d, int cur) { eval32(d, hw_vblk(), cur); }
 
-__global__ void k_eval32_batch(BatchDev b) {
+__global__ void __launch_bounds__(256, 4) k_eval32_batch(BatchDev b) {
   __shared__ DevState sd;
   int held = -1, w0, w1;
   const int n = *b.bstep;

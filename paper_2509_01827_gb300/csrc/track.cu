@@ -36,14 +36,20 @@ namespace cem {
 
 namespace {
 
-constexpr int TB = 512;            // threads of the tracking CTA (128 registers each)
+// The selection CTA is sized to fit in the SM resources one tile-update CTA
+// frees (256 threads x 64 registers, under 48 KB of shared memory), so that
+// it runs beside the tile update.
+constexpr int TB = 256;            // threads of the tracking CTA
 constexpr int SORT_CAP = 8192;     // proposals per step (power of two)
+constexpr int SEL_SMEM_CAP = 1024; // proposals staged in shared memory (power of two)
 constexpr int WB = TB / 8;         // winners split per batch (eight threads each)
 
 // dynamic shared memory of the selection CTA: sorted keys, winners and the
-// proposals' G, edge and exit edge
+// proposals' G, edge and exit edge, for up to SEL_SMEM_CAP proposals (steps
+// with more use the global scratch of the same layout)
 constexpr size_t select_smem_bytes() {
-  return SORT_CAP * (sizeof(unsigned long long) + sizeof(int) + sizeof(double) + sizeof(int) + 1);
+  return SEL_SMEM_CAP *
+         (sizeof(unsigned long long) + sizeof(int) + sizeof(double) + sizeof(int) + 1);
 }
 
 // ------------------------------------------------------------ block scan
@@ -251,11 +257,6 @@ __device__ __forceinline__ void node_plan(const DevState &d, int e, int ka, int 
 // the keys), since this single CTA runs beside the node updates.
 __device__ __forceinline__ void select_plan(const DevState &d, int mode,
                                             unsigned long long *smem) {
-  unsigned long long *sk = smem;                    // [SORT_CAP] sorted (key << 32 | index)
-  int *swin = (int *)(smem + SORT_CAP);             // [SORT_CAP] winners (sorted positions)
-  double *oG = (double *)(swin + SORT_CAP);         // [SORT_CAP] G of proposal i
-  int *oE = (int *)(oG + SORT_CAP);                 // [SORT_CAP] its edge
-  uint8_t *oK = (uint8_t *)(oE + SORT_CAP);         // [SORT_CAP] its exit edge
   __shared__ int s_n, s_nwin, s_stop, s_nph, s_nck, s_nS, s_dead, s_done, s_compact;
   __shared__ int b_e[WB], b_ka[WB], b_kb[WB], b_side[WB][4], b_reuse[WB][4], b_app[WB],
       b_tomb[WB][4], b_c[WB];
@@ -309,6 +310,14 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
     __syncthreads();
   }
   const int n = s_n;
+  // sorted (key << 32 | index), winners (sorted positions), and G, edge and
+  // exit edge of proposal i
+  const bool staged = n <= SEL_SMEM_CAP;
+  unsigned long long *sk = staged ? smem : d.sel_sk;
+  int *swin = staged ? (int *)(smem + SEL_SMEM_CAP) : d.sel_win;
+  double *oG = staged ? (double *)(smem + SEL_SMEM_CAP) + SEL_SMEM_CAP / 2 : d.sel_G;
+  int *oE = staged ? (int *)(oG + SEL_SMEM_CAP) : d.sel_E;
+  uint8_t *oK = staged ? (uint8_t *)(oE + SEL_SMEM_CAP) : d.sel_K;
   if (n > 0) {
     // ---- load keys and fields; debug proposals that are not surface points
     //      (or not tips under the tips-only scope) sort to the end
@@ -598,13 +607,13 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
   }
 }
 
-__global__ void __launch_bounds__(TB) k_select(DevState d, int mode) {
+__global__ void __launch_bounds__(TB, 4) k_select(DevState d, int mode) {
   extern __shared__ unsigned long long smem[];
   select_plan(d, mode, smem);
 }
 
 // one CTA per member of a batch
-__global__ void __launch_bounds__(TB) k_select_batch(BatchDev b) {
+__global__ void __launch_bounds__(TB, 4) k_select_batch(BatchDev b) {
   extern __shared__ unsigned long long smem[];
   __shared__ DevState sd;
   int held = -1;
