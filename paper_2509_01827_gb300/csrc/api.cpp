@@ -1071,7 +1071,10 @@ cem_status batch_upload(cem_handle *b) {
     }
     for (int y = 0; y < gy; ++y)
       for (int x = 0; x < gx; ++x) wm.push_back(make_int4(s, x, y, gx | (gy << 16)));
-    const int tiles = gx * gy, gp = grid_pieces(d), gph = grid_phantoms(d);
+    // the FP32 step has no piece kernel: its tile and phantom updates
+    // evaluate the pieces themselves
+    const int tiles = gx * gy, gph = grid_phantoms(d);
+    const int gp = p->precision == CEM_FP32_MIXED ? 0 : grid_pieces(d);
     for (int q = 0; q < gp; ++q) wp.push_back(make_int4(s, q, tiles, gp));
     for (int q = 0; q < gph; ++q) wph.push_back(make_int4(s, q, tiles + gp, gph));
     // the evaluation has no energy partials: a few virtual blocks per member

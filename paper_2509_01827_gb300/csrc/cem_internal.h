@@ -217,13 +217,16 @@ __device__ __forceinline__ void stage_member(const DevState *ds, int s, DevState
 // ------------------------------------------------------------------ launch
 // All launchers enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
-// Streams of one step.  The piece forces run first on `main`; then the tile
-// update of real nodes (main), the phantom update (aux1, needs only the piece
-// forces) and the surface evaluation followed by the tracking selection
-// (aux2, read only the previous state) run concurrently and join back into
-// `main`, where the split writes follow.  With marks (profiling) the four
-// step kernels run one after the other on `main`, marks[0..2] are recorded
-// after the first three, and the caller launches selection and writes.
+// Streams of one step.  The tile update of real nodes (main), the phantom
+// update (aux1) and the surface evaluation followed by the tracking
+// selection (aux2, read only the previous state) run concurrently and join
+// back into `main`, where the split writes follow; the side branches' streams
+// have the highest priority.  In FP32 the tile and phantom updates evaluate
+// the split pieces they need themselves; in FP64 the piece forces run on
+// `main` before the tile and phantom updates.  With marks (profiling) the four step kernels
+// (the FP32 piece evaluation timed on its own) run one after the other on
+// `main`, marks[0..2] are recorded after the first three, and the caller
+// launches selection and writes.
 struct StepStreams {
   cudaStream_t main, aux1, aux2;
   cudaEvent_t fork, join1, join2;

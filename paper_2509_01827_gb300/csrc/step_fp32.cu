@@ -137,8 +137,10 @@ __device__ __forceinline__ float2 update_plain(const DevState &d, int N, int cur
 // One piece of split element c (side p): strains and stresses at its four
 // edge points (Eq. 4 at the edge midpoints, from the displacements of the
 // piece's own nodes) and its nodal forces f[2a], f[2a+1] at local nodes
-// a = 0..3, FP32.  The piece kernel (every force, for the phantom update)
-// and the tile kernel (the forces at real nodes) both evaluate pieces here.
+// a = 0..3, FP32.  The tile kernel (forces at real nodes), the phantom
+// update (forces at phantom nodes) and the piece kernel (every force; the
+// profiling path) all evaluate pieces here, so a force is the same wherever
+// it is used.
 struct Piece32 {
   float ex[4], ey[4], gx[4];
   Stress3 s[4];
@@ -146,7 +148,8 @@ struct Piece32 {
   float f[8];
 };
 
-__device__ __forceinline__ void piece32(const DevState &d, int c, int p, int cur, Piece32 &P) {
+__device__ __forceinline__ void piece32_state(const DevState &d, int c, int p, int cur,
+                                              Piece32 &P) {
   const Geo &g = d.g;
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
@@ -170,21 +173,46 @@ __device__ __forceinline__ void piece32(const DevState &d, int c, int p, int cur
 #pragma unroll
   for (int k = 0; k < 4; ++k) P.s[k] = stress32(d.mat, P.ex[k], P.ey[k], P.gx[k]);
   P.qA = (float)(d.ck_Ap[c * 2 + p] * 0.25);
+}
+
+// the piece's force at its local node a
+__device__ __forceinline__ float2 piece32_force(const Geo &g, const Piece32 &P, int a) {
+  const float hx2 = 0.5f * g.rxf, hy2 = 0.5f * g.ryf;
+  float sx = 0.f, sy = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float cx = dxn(k, a) * hx2, cy = dyn(k, a) * hy2;
+    sx = fmaf(cx, P.s[k].xx, fmaf(cy, P.s[k].xy, sx));
+    sy = fmaf(cy, P.s[k].yy, fmaf(cx, P.s[k].xy, sy));
+  }
+  // rounded products (never fused into the caller's sums), so that a force
+  // is the same in every kernel that adds it
+  return make_float2(__fmul_rn(sx, P.qA), __fmul_rn(sy, P.qA));
+}
+
+__device__ __forceinline__ void piece32(const DevState &d, int c, int p, int cur, Piece32 &P) {
+  piece32_state(d, c, p, cur, P);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    float sx = 0.f, sy = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float cx = dxn(k, a) * hx2, cy = dyn(k, a) * hy2;
-      sx = fmaf(cx, P.s[k].xx, fmaf(cy, P.s[k].xy, sx));
-      sy = fmaf(cy, P.s[k].yy, fmaf(cx, P.s[k].xy, sy));
-    }
-    P.f[2 * a] = sx * P.qA;
-    P.f[2 * a + 1] = sy * P.qA;
+    const float2 F = piece32_force(d.g, P, a);
+    P.f[2 * a] = F.x;
+    P.f[2 * a + 1] = F.y;
   }
 }
 
-// Piece forces of split elements, written for the phantom update.
+// strain energy of a piece, FP64 sums of its four edge points' shares
+__device__ __forceinline__ double piece32_energy(const Piece32 &P) {
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    acc += 0.5 * (double)P.qA *
+           ((double)P.ex[k] * P.s[k].xx + (double)P.ey[k] * P.s[k].yy + (double)P.gx[k] * P.s[k].xy);
+  return acc;
+}
+
+// Piece forces of split elements (the profiling path times the pieces'
+// evaluation on its own; the step itself has the tile and phantom kernels
+// evaluate them).
 __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
                                          int part_off) {
   const int n = 2 * d.cnt->n_ck;
@@ -196,15 +224,7 @@ __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, in
     float *o = d.pff + c * 16 + p * 8;
 #pragma unroll
     for (int q = 0; q < 8; ++q) o[q] = P.f[q];
-    if (energy) {
-      double acc = 0.0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        acc += 0.5 * (double)P.qA *
-               ((double)P.ex[k] * P.s[k].xx + (double)P.ey[k] * P.s[k].yy +
-                (double)P.gx[k] * P.s[k].xy);
-      se += acc;
-    }
+    if (energy) se += piece32_energy(P);
   }
   if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + vb.x));
 }
@@ -421,7 +441,8 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry, hx4 = 0.25f * rx, hy4 = 0.25f * ry;
   const float qA = g.qAf;
-  float se = 0.f;  // strain energy of this thread's edges / qA (energy steps)
+  float se = 0.f;    // strain energy of this thread's edges / qA (energy steps)
+  double sep = 0.0;  // strain energy of the pieces of the split elements it owns
 
   if (!general) {
     // every element around the tile is intact: smoothed strain on every
@@ -626,6 +647,8 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
         for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
           if (((info >> (4 + a)) & 1) == p)
             slot[li - base][a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
+        // the tile owns elements [i0, i0+TX) x [j0, j0+TY)
+        if (ENERGY && wx >= 1 && wx <= TX && wy >= 1 && wy <= TY) sep += piece32_energy(P);
       }
       __syncthreads();
 #pragma unroll
@@ -675,7 +698,7 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
     }
   }
   if (ENERGY)
-    block_sum2(ke + 0.5 * (double)ke2, (double)qA * (double)se,
+    block_sum2(ke + 0.5 * (double)ke2, (double)qA * (double)se + sep,
                d.e_part + 2 * (vb.y * vb.gx + vb.x));
 }
 
@@ -694,20 +717,24 @@ __device__ __forceinline__ void phantom32(const DevState &d, VBlk vb, int cur, i
   double ke = 0.0;
   const float dt = d.mat.dtf;
   const float dtv = first ? 0.5f * dt : dt;
-  const float2 *__restrict__ pf2 = reinterpret_cast<const float2 *>(d.pff);
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
-    // users' piece-force indices in increasing element id, -1 unused
+    // users' piece-force indices c*16 + p*8 + 2a in increasing element id,
+    // -1 unused: the phantom is local node a of piece p of split c, whose
+    // force there is evaluated here
     const int4 uf = reinterpret_cast<const int4 *>(d.ph_upf)[t];
-    const float2 f0 = uf.x >= 0 ? pf2[uf.x >> 1] : make_float2(0.f, 0.f);
-    const float2 f1 = uf.y >= 0 ? pf2[uf.y >> 1] : make_float2(0.f, 0.f);
-    const float2 f2 = uf.z >= 0 ? pf2[uf.z >> 1] : make_float2(0.f, 0.f);
-    const float2 f3 = uf.w >= 0 ? pf2[uf.w >> 1] : make_float2(0.f, 0.f);
+    const int ufs[4] = {uf.x, uf.y, uf.z, uf.w};
     float fx = 0.f, fy = 0.f;
-    fx += f0.x; fy += f0.y;
-    fx += f1.x; fy += f1.y;
-    fx += f2.x; fy += f2.y;
-    fx += f3.x; fy += f3.y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (ufs[q] >= 0) {
+        Piece32 P;
+        piece32_state(d, ufs[q] >> 4, (ufs[q] >> 3) & 1, cur, P);
+        const float2 F = piece32_force(d.g, P, (ufs[q] >> 1) & 3);
+        fx += F.x;
+        fy += F.y;
+      }
+    }
     if (energy)
       ke += update_special(d, N, cur, first, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N], 0, 1);
     else
@@ -738,20 +765,6 @@ __global__ void __launch_bounds__(BX * BY, 4) k_main32_batch(BatchDev b,
     stage_member(b.ds, it.x, sd, held);
     if (!member_active(sd, n)) continue;
     main32_tile<ENERGY, TY>(sd, item_vblk(it), member_cur(sd, n), first, T);
-    __syncthreads();
-  }
-}
-
-__global__ void k_pieces32_batch(BatchDev b, int energy) {
-  __shared__ DevState sd;
-  int held = -1, w0, w1;
-  const int n = *b.bstep;
-  block_range(b.n_pieces, w0, w1);
-  for (int w = w0; w < w1; ++w) {
-    const int4 it = b.w_pieces[w];
-    stage_member(b.ds, it.x, sd, held);
-    if (!member_active(sd, n)) continue;
-    pieces32(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), energy, it.z);
     __syncthreads();
   }
 }
@@ -818,7 +831,7 @@ int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 1216); }
 
 // energy partials one FP32 step writes with the given tile height
 int energy_parts_step_fp32(const DevState &d, int tile_rows) {
-  return tiles_fp32(d, tile_rows) + grid_pieces(d) + grid_phantoms(d);
+  return tiles_fp32(d, tile_rows) + grid_phantoms(d);
 }
 
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
@@ -838,18 +851,20 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
     else k_main32<false, TYs><<<grid, block, smem, s>>>(d, cur, first ? 1 : 0);
   };
   if (marks) {
-    k_pieces32<<<gp, 256, 0, st>>>(d, cur, energy ? 1 : 0, tiles);
+    // the pieces' evaluation alone (its energy partials land past the
+    // phantom update's and are not summed), then the step's own kernels
+    k_pieces32<<<gp, 256, 0, st>>>(d, cur, 0, tiles + gph);
     cudaEventRecord(marks[0], st);
     main_kernel(st);
     cudaEventRecord(marks[1], st);
-    k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+    k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
     cudaEventRecord(marks[2], st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_eval32(d, cur, st);
   }
-  // the tile update evaluates the pieces it needs itself, so it does not
-  // wait for the piece kernel; the phantom update does
+  // the tile update and the phantom update evaluate the pieces they need
+  // themselves, so the three branches start together
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
   cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
@@ -857,8 +872,7 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
   if (e != cudaSuccess) return e;
   e = launch_select(d, TRACK_STEP, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_pieces32<<<gp, 256, 0, ss.aux1>>>(d, cur, energy ? 1 : 0, tiles);
-  k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles + gp);
+  k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
   main_kernel(st);
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
@@ -875,7 +889,7 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
   if (e != cudaSuccess) return e;
   const dim3 block(BX, BY);
   const int gm = grid_main < 1 ? 1 : grid_main;
-  const int gp = grid_for(b.n_pieces, 1, 1216), gph = grid_for(b.n_ph, 1, 1216);
+  const int gph = grid_for(b.n_ph, 1, 1216);
   cudaStream_t st = ss.main;
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
@@ -884,7 +898,6 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
   if (e != cudaSuccess) return e;
   e = launch_select_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_pieces32_batch<<<gp, 256, 0, ss.aux1>>>(b, energy ? 1 : 0);
   k_phantom32_batch<<<gph, 256, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
   const int f = first ? 1 : 0;
   if (tile_rows == 8) {
