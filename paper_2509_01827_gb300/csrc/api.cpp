@@ -1081,7 +1081,8 @@ cem_status batch_upload(cem_handle *b) {
     // walk its list (its length, not its capacity, sets the work)
     const int ge = std::min(grid_eval(d), 8);
     for (int q = 0; q < ge; ++q) we.push_back(make_int4(s, q, 0, ge));
-    nparts[s] = tiles + gp + gph;
+    // FP32 phantom blocks write one energy partial per warp
+    nparts[s] = tiles + gp + (p->precision == CEM_FP32_MIXED ? kPhWarps : 1) * gph;
   }
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_ds = 0, o_m = al(o_ds + ds.size() * sizeof(DevState));

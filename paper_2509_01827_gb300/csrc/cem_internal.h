@@ -158,6 +158,8 @@ struct DevState {
 // EPRE fixed chunks (one block of EPRE_TB threads each), added in order by
 // the epilogue.
 constexpr int EPRE = 128, EPRE_TB = 256;
+// warps of an FP32 phantom-update block; each writes its own energy partial
+constexpr int kPhWarps = 8;
 
 struct VBlk {
   int x, y, gx, gy;
@@ -215,6 +217,19 @@ __device__ __forceinline__ void stage_member(const DevState *ds, int s, DevState
 #endif
 
 // ------------------------------------------------------------------ launch
+// The kernels that run beside the FP32 tile update ask for the shared-memory
+// split the tile update itself runs in (164 KB of shared memory for its
+// four 40 KB CTAs, the rest L1).  An SM changes its L1 / shared split only
+// when it is empty, so a side kernel left at its own small split would keep
+// the tile update off every SM it occupies until it drains.  71% of the 228
+// KB maximum is the smallest request that maps to the 164 KB split.
+constexpr int kSideCarveoutPct = 71;
+template <class K>
+inline cudaError_t match_tile_carveout(K *kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              kSideCarveoutPct);
+}
+
 // All launchers enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_init_masses(const DevState &d, cudaStream_t st);
 // Streams of one step.  The tile update of real nodes (main), the phantom

@@ -179,7 +179,20 @@ int grid_for(int n, int block, int maxb) {
 
 }  // namespace
 
+cudaError_t energy_carveouts() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = match_tile_carveout(k_energy_pre);
+  if (e == cudaSuccess) e = match_tile_carveout(k_energy_post);
+  if (e == cudaSuccess) e = match_tile_carveout(k_energy_pre_batch);
+  if (e == cudaSuccess) e = match_tile_carveout(k_energy_post_batch);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st) {
+  cudaError_t e = energy_carveouts();
+  if (e != cudaSuccess) return e;
   k_energy_pre<<<EPRE, EPRE_TB, 0, st>>>(d);
   return cudaGetLastError();
 }
@@ -191,6 +204,8 @@ cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st) {
 
 
 cudaError_t launch_energy_pre_batch(const BatchDev &b, cudaStream_t st) {
+  cudaError_t e = energy_carveouts();
+  if (e != cudaSuccess) return e;
   const int items = b.n * EPRE;
   k_energy_pre_batch<<<items < 1216 ? items : 1216, EPRE_TB, 0, st>>>(b);
   return cudaGetLastError();

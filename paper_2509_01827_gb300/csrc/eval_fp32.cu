@@ -200,14 +200,27 @@ int grid_for(int n, int block, int maxb) {
 
 }  // namespace
 
-int grid_eval(const DevState &d) { return grid_for(d.list_cap, 256, 1216); }
+int grid_eval(const DevState &d) { return grid_for(d.list_cap, 256, 152); }
+
+cudaError_t eval32_carveouts() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = match_tile_carveout(k_eval32);
+  if (e == cudaSuccess) e = match_tile_carveout(k_eval32_batch);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
 
 cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st) {
+  cudaError_t e = eval32_carveouts();
+  if (e != cudaSuccess) return e;
   k_eval32<<<grid_eval(d), 256, 0, st>>>(d, cur);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eval32_batch(const BatchDev &b, cudaStream_t st) {
+  cudaError_t e = eval32_carveouts();
+  if (e != cudaSuccess) return e;
   k_eval32_batch<<<grid_for(b.n_eval, 1, 1216), 256, 0, st>>>(b);
   return cudaGetLastError();
 }

@@ -25,6 +25,18 @@ namespace cem {
 namespace {
 
 
+// Per-warp sums of the phantom update's kinetic energy, written to
+// out[2w], out[2w + 1] for warp w of the block (fixed order, no shared
+// memory: a kernel with static shared memory gets its own L1 / shared split
+// and could not share SMs with the tile update).
+__device__ __forceinline__ void warp_sum_parts(double a, double *out) {
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) {
+    out[2 * (threadIdx.x >> 5)] = a;
+    out[2 * (threadIdx.x >> 5) + 1] = 0.0;
+  }
+}
+
 __device__ __forceinline__ void block_sum2(double a, double b, double *out) {
   __shared__ double wa[32], wb[32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -740,7 +752,7 @@ __device__ __forceinline__ void phantom32(const DevState &d, VBlk vb, int cur, i
     else
       update_plain(d, N, cur, dtv, dt, fx, fy, d.u4[cur][N], d.v2[N], d.minvf[N]);
   }
-  if (energy) block_sum2(ke, 0.0, d.e_part + 2 * (part_off + vb.x));
+  if (energy) warp_sum_parts(ke, d.e_part + 2 * (part_off + vb.x * kPhWarps));
 }
 
 __global__ void k_phantom32(DevState d, int cur, int first, int energy, int part_off) {
@@ -806,6 +818,13 @@ cudaError_t set_smem_attr() {
 }
 
 cudaError_t set_all_smem_attrs() {
+  static bool side = false;
+  if (!side) {
+    cudaError_t e = match_tile_carveout(k_phantom32);
+    if (e == cudaSuccess) e = match_tile_carveout(k_phantom32_batch);
+    if (e != cudaSuccess) return e;
+    side = true;
+  }
   cudaError_t e;
   if ((e = set_smem_attr<true, 16>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<false, 16>()) != cudaSuccess) return e;
@@ -822,16 +841,18 @@ int tiles_fp32(const DevState &d, int tile_rows) {
   return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + tile_rows - 1) / tile_rows);
 }
 
-// energy partials: tiles of the smallest tile height first, then pieces and
-// phantom blocks (at most 1216 each)
-int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + 2 * 1216 + 8; }
+// energy partials: tiles of the smallest tile height first, then the
+// phantom update's warps (at most 1216 blocks of kPhWarps)
+int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + kPhWarps * 1216 + 8; }
 
 int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 1216); }
-int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 1216); }
+// side-branch grids: two phantom blocks and one evaluation block per SM, so that
+// they start together with the tile update and share the SMs with it
+int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 304); }
 
 // energy partials one FP32 step writes with the given tile height
 int energy_parts_step_fp32(const DevState &d, int tile_rows) {
-  return tiles_fp32(d, tile_rows) + grid_phantoms(d);
+  return tiles_fp32(d, tile_rows) + kPhWarps * grid_phantoms(d);
 }
 
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
@@ -857,7 +878,7 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
     cudaEventRecord(marks[0], st);
     main_kernel(st);
     cudaEventRecord(marks[1], st);
-    k_phantom32<<<gph, 256, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
+    k_phantom32<<<gph, 32 * kPhWarps, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
     cudaEventRecord(marks[2], st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -872,7 +893,7 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
   if (e != cudaSuccess) return e;
   e = launch_select(d, TRACK_STEP, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_phantom32<<<gph, 256, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
+  k_phantom32<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
   main_kernel(st);
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
@@ -898,7 +919,7 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
   if (e != cudaSuccess) return e;
   e = launch_select_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_phantom32_batch<<<gph, 256, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
+  k_phantom32_batch<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
   const int f = first ? 1 : 0;
   if (tile_rows == 8) {
     constexpr size_t sm = sizeof(Tile<8>::Smem);

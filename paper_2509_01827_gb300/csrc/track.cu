@@ -838,6 +838,8 @@ cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
+    if (e == cudaSuccess) e = match_tile_carveout(k_select);
+    if (e == cudaSuccess) e = match_tile_carveout(k_apply);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -866,6 +868,8 @@ cudaError_t launch_select_batch(const BatchDev &b, cudaStream_t st) {
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_select_batch,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = match_tile_carveout(k_select_batch);
+    if (e == cudaSuccess) e = match_tile_carveout(k_apply_batch);
     if (e != cudaSuccess) return e;
     attr = true;
   }
