@@ -778,27 +778,52 @@ __global__ void __launch_bounds__(256) k_apply_batch(BatchDev b) {
   }
 }
 
-// Builds the surface list from scratch in edge-id order (one CTA).
-__global__ void __launch_bounds__(TB) k_build_surface(DevState d) {
-  const Geo &g = d.g;
-  int out = 0;
-  for (int base = 0; base < g.ned; base += TB) {
-    int gid = base + threadIdx.x;
-    int live = 0, info = 0;
-    if (gid < g.ned) {
-      int lo, klo, hi, khi;
-      edge_sides(g, gid, lo, klo, hi, khi);
-      bool ilo = estatus(d, lo) == ST_INTACT, ihi = estatus(d, hi) == ST_INTACT;
-      if (ilo != ihi) {
-        live = 1;
-        info = ilo ? lo * 4 + klo : hi * 4 + khi;
-      }
-      d.spos[gid] = -1;
-    }
+// Builds the surface list from scratch in edge-id order, in two passes over
+// fixed contiguous edge ranges (one per block): the live surface points of
+// each range are counted, then each block writes its range's points in
+// order after the points of the ranges before it.  The selection's winner
+// scratch holds the per-range counts (it is idle at set-up).
+constexpr int kSurfBlocks = 1216;
+
+__device__ __forceinline__ bool surface_point(const DevState &d, int gid, int &info) {
+  int lo, klo, hi, khi;
+  edge_sides(d.g, gid, lo, klo, hi, khi);
+  const bool ilo = estatus(d, lo) == ST_INTACT, ihi = estatus(d, hi) == ST_INTACT;
+  info = ilo ? lo * 4 + klo : hi * 4 + khi;
+  return ilo != ihi;
+}
+
+__global__ void __launch_bounds__(TB) k_surface_count(DevState d, int chunk) {
+  const int e0 = blockIdx.x * chunk, e1 = min(d.g.ned, e0 + chunk);
+  int live = 0;
+  for (int gid = e0 + threadIdx.x; gid < e1; gid += TB) {
+    int info;
+    live += surface_point(d, gid, info) ? 1 : 0;
+    d.spos[gid] = -1;
+  }
+  int tot;
+  block_exscan(live, &tot);
+  if (threadIdx.x == 0) d.sel_win[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(TB) k_surface_write(DevState d, int chunk) {
+  __shared__ int s_out;
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int q = 0; q < (int)blockIdx.x; ++q) o += d.sel_win[q];
+    s_out = o;
+  }
+  __syncthreads();
+  int out = s_out;
+  const int e0 = blockIdx.x * chunk, e1 = min(d.g.ned, e0 + chunk);
+  for (int base = e0; base < e1; base += TB) {
+    const int gid = base + threadIdx.x;
+    int info = 0;
+    const int live = gid < e1 && surface_point(d, gid, info) ? 1 : 0;
     int tot;
-    int pos = block_exscan(live, &tot);
+    const int pos = block_exscan(live, &tot);
     if (live) {
-      int dst = out + pos;
+      const int dst = out + pos;
       if (dst < d.list_cap) {
         d.S[dst] = gid;
         d.S_info[dst] = info;
@@ -807,9 +832,8 @@ __global__ void __launch_bounds__(TB) k_build_surface(DevState d) {
       }
     }
     out += tot;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
     if (out > d.list_cap) {
       atomicOr(&d.cnt->status, STAT_CAPACITY);
       out = d.list_cap;
@@ -853,7 +877,10 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
 }
 
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st) {
-  k_build_surface<<<1, TB, 0, st>>>(d);
+  const int chunk = (d.g.ned + kSurfBlocks - 1) / kSurfBlocks;
+  const int blocks = (d.g.ned + chunk - 1) / chunk;
+  k_surface_count<<<blocks, TB, 0, st>>>(d, chunk);
+  k_surface_write<<<blocks, TB, 0, st>>>(d, chunk);
   return cudaGetLastError();
 }
 
