@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -49,6 +50,8 @@ struct cem_handle {
   long step = 0;
   int energy_every = 0;
   cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][energy]
+  // graphs of kGraphSteps consecutive steps, keyed by cur | energy mask << 1
+  std::map<unsigned, cudaGraphExec_t> multi;
   Counters *h_cnt = nullptr;  // pinned
   double *h_lam = nullptr;    // pinned staging of the load-factor table
   bool own_stream = false;
@@ -197,6 +200,8 @@ void drop_graphs(cem_handle *h) {
   for (auto &row : h->graphs)
     for (auto &g : row)
       if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (auto &kv : h->multi) cudaGraphExecDestroy(kv.second);
+  h->multi.clear();
 }
 
 int kernels_in_step(bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
@@ -277,6 +282,34 @@ cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
   }
   *out = h->graphs[cur][energy];
+  return CEM_OK;
+}
+
+// Consecutive steps replayed as one graph: the launch of a graph costs a few
+// microseconds of idle GPU between graphs, which a dependency inside one
+// graph does not.  kGraphSteps is even, so the displacement buffer index is
+// the same after the group as before it.
+constexpr int kGraphSteps = 8;
+
+cem_status multi_graph_for(cem_handle *h, int cur, unsigned mask, cudaGraphExec_t *out) {
+  const unsigned key = (unsigned)cur | (mask << 1);
+  auto it = h->multi.find(key);
+  if (it == h->multi.end()) {
+    cudaGraph_t g;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < kGraphSteps && e == cudaSuccess; ++q)
+      e = enqueue_step(h, cur ^ (q & 1), false, ((mask >> q) & 1) != 0);
+    cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
+    if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
+    cudaGraphExec_t x = nullptr;
+    cudaError_t e3 = cudaGraphInstantiate(&x, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
+    it = h->multi.emplace(key, x).first;
+  }
+  *out = it->second;
   return CEM_OK;
 }
 
@@ -671,7 +704,24 @@ cem_status cem_step(cem_handle *h, int n) {
       if (rc != CEM_OK) return rc;
     }
     const int chunk = (int)std::min((long)(n - done), h->lam_lo + h->lam_n - h->step);
-    for (int q = 0; q < chunk; ++q) {
+    for (int q = 0; q < chunk;) {
+      if (h->step > 0 && chunk - q >= kGraphSteps) {
+        unsigned mask = 0;
+        long kernels = 0;
+        for (int r = 0; r < kGraphSteps; ++r) {
+          const bool en = h->energy_every > 0 && ((h->step + r) % h->energy_every) == 0;
+          mask |= (en ? 1u : 0u) << r;
+          kernels += kernels_in_step(en);
+        }
+        cudaGraphExec_t gx;
+        rc = multi_graph_for(h, h->cur, mask, &gx);
+        if (rc != CEM_OK) return rc;
+        CUDA_TRY(h, cudaGraphLaunch(gx, h->st));
+        h->launches += kernels;
+        h->step += kGraphSteps;
+        q += kGraphSteps;
+        continue;
+      }
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
         CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
@@ -684,6 +734,7 @@ cem_status cem_step(cem_handle *h, int n) {
       h->launches += kernels_in_step(energy);
       h->cur ^= 1;
       h->step += 1;
+      ++q;
     }
     done += chunk;
   }
