@@ -717,6 +717,9 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
 template <bool ENERGY, int TY>
 __global__ void __launch_bounds__(BX * BY, 4) k_main32(DevState d, int cur,
                                                                       int first) {
+  // the split writes that follow may be placed once every tile CTA has
+  // started (they wait for this kernel's completion themselves)
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ float4 smem_dyn[];
   main32_tile<ENERGY, TY>(d, hw_vblk(), cur, first,
                           *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn));

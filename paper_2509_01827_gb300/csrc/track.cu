@@ -750,7 +750,11 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
   }
 }
 
+// Launched as a programmatic dependent of the kernel before it in the
+// stream: its CTAs may be placed while that kernel's last wave still runs,
+// and wait here until it has completed and its writes are visible.
 __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   apply_plan(d, hw_vblk(), cur_next, mode);
 }
 
@@ -872,7 +876,18 @@ cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
 }
 
 cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st) {
-  k_apply<<<64, 256, 0, st>>>(d, cur_next, mode);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(64);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply, d, cur_next, mode);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

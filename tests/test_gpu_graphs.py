@@ -1,0 +1,44 @@
+"""Replaying steps in graphs of several steps (needs a GPU).
+
+cem_step replays groups of consecutive steps as one CUDA graph, with single
+steps wherever an energy record would fall inside a group.  The kernels and
+their order are the same either way, so a run taken in one call must be
+bit-identical to the same run taken one step per call (fields, masses,
+splits, energy records), in both precisions."""
+import numpy as np
+import pytest
+
+from paper_2509_01827_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_01827_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_call_equals_single_steps(precision):
+    from paper_2509_01827_gb300.cem import Solver
+    p = inputs.notched_plate(100, 40, traction=3e6, steps=0, phantom_cap=20000, crack_cap=4000)
+    p.energy_every = 10  # records at steps 0, 10, 20, ...: groups and single steps mix
+    a, b = Solver(p, precision=precision), Solver(p, precision=precision)
+    n = 237
+    a.step(n)
+    for _ in range(n):
+        b.step(1)
+    na, nb = a.nodes(), b.nodes()
+    for k in ("ux", "uy", "vx", "vy", "m"):
+        np.testing.assert_array_equal(na[k], nb[k], err_msg=k)
+    ca, cb = a.cracks(), b.cracks()
+    assert len(ca["elem"]) > 0  # the run splits elements
+    for k in ("elem", "ka", "kb", "step", "ud", "nodes"):
+        np.testing.assert_array_equal(ca[k], cb[k], err_msg=k)
+    ea, eb = a.energy(), b.energy()
+    for k in ("step", "KE", "SE", "W_ext", "W_dir", "U_d"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+    assert a.counts()["step"] == b.counts()["step"] == n
+    a.close()
+    b.close()
