@@ -717,8 +717,11 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
 template <bool ENERGY, int TY>
 __global__ void __launch_bounds__(BX * BY, 4) k_main32(DevState d, int cur,
                                                                       int first) {
-  // the split writes that follow may be placed once every tile CTA has
-  // started (they wait for this kernel's completion themselves)
+  // launched as a programmatic dependent of the kernel before it (the
+  // previous step's split writes): wait until that kernel has completed and
+  // its writes are visible; then let the split writes that follow be placed
+  // once every tile CTA has started (they wait for this kernel themselves)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ float4 smem_dyn[];
   main32_tile<ENERGY, TY>(d, hw_vblk(), cur, first,
@@ -871,8 +874,19 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
   constexpr size_t smem = sizeof(Tile<TYs>::Smem);
   cudaStream_t st = ss.main;
   auto main_kernel = [&](cudaStream_t s) {
-    if (energy) k_main32<true, TYs><<<grid, block, smem, s>>>(d, cur, first ? 1 : 0);
-    else k_main32<false, TYs><<<grid, block, smem, s>>>(d, cur, first ? 1 : 0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int f = first ? 1 : 0;
+    if (energy) cudaLaunchKernelEx(&cfg, k_main32<true, TYs>, d, cur, f);
+    else cudaLaunchKernelEx(&cfg, k_main32<false, TYs>, d, cur, f);
   };
   if (marks) {
     // the pieces' evaluation alone (its energy partials land past the

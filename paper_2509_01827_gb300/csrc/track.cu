@@ -752,9 +752,12 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
 
 // Launched as a programmatic dependent of the kernel before it in the
 // stream: its CTAs may be placed while that kernel's last wave still runs,
-// and wait here until it has completed and its writes are visible.
+// and wait here until it has completed and its writes are visible.  It lets
+// the next step's tile update be placed in turn (that kernel waits for this
+// one the same way).
 __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   apply_plan(d, hw_vblk(), cur_next, mode);
 }
 
