@@ -91,7 +91,8 @@ struct DevState {
   double *ck_ud;
   int *ck_step;
   double *pf;            // [ck_cap * 16] piece nodal forces (FP64 mode)
-  float *pff;            // [ck_cap * 16] piece nodal forces (FP32 mode)
+  float *pff;            // [ck_cap * 16] piece nodal forces (FP32 mode; written only by
+                         // the profiling path, the step evaluates pieces where used)
 
   // phantoms [ph_cap]
   int *ph_owner;

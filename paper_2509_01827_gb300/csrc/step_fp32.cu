@@ -2,8 +2,9 @@
 // displacement kept as a compensated pair of floats (hi + lo, ~48-bit
 // mantissa) and advanced with an error-free two-sum, FP64 energy sums.
 //
-// k_main32 is the bandwidth-bound kernel of the method: one pass over every
-// real node per step.  For each node it forms the strains at the midpoints of
+// k_main32 is the kernel that touches every real node each step (its HBM
+// floor is 54 bytes per node; the shared-memory stencil traffic bounds it in
+// practice).  For each node it forms the strains at the midpoints of
 // the 12 edges around it from node differences (Eq. 4 at the edge points):
 // along an edge the tangential derivative is the difference of its two
 // nodes, across it the normal derivative of each side is the sum of that
@@ -11,8 +12,10 @@
 // sides are averaged (Eqs. 1-2 with equal areas), otherwise each intact side
 // keeps its own strain; sigma = D eps per side (zero for split or missing
 // sides); the node force is B^T sigma A/4 (Eq. 6) summed over those edges
-// and sides, plus the forces of split-element pieces; then the
-// central-difference update.
+// and sides, plus the forces of split-element pieces (evaluated in the tile
+// from the pieces' nodes); then the central-difference update.  k_phantom32
+// updates the phantom nodes, evaluating each user piece at the phantom; the
+// two run side by side with the surface evaluation and the selection.
 #include <cuda_runtime.h>
 
 #include <cfloat>
