@@ -470,6 +470,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.pl_app0, (size_t)d.prop_cap) && dalloc_n(h, d.pl_alpha, (size_t)d.prop_cap * 2) &&
        dalloc_n(h, d.pl_mreal, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_mph, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.pl_mold, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_dm, (size_t)d.prop_cap * 4) &&
+       dalloc_n(h, d.pl_mireal, (size_t)d.prop_cap * 4) && dalloc_n(h, d.pl_miph, (size_t)d.prop_cap * 4) &&
        dalloc_n(h, d.pl_users, (size_t)d.prop_cap * 16) && dalloc_n(h, d.pl_upf, (size_t)d.prop_cap * 16) &&
        dalloc_n(h, d.pl_uap, (size_t)d.prop_cap * 16) &&
        dalloc_n(h, d.pl_nu, (size_t)d.prop_cap * 4) &&

@@ -128,6 +128,7 @@ struct DevState {
   // split, its phantom's mass after it, the phantom's mass before (-1: new),
   // the mass the phantom gains, and the phantom's complete user list
   double *pl_mreal, *pl_mph, *pl_mold, *pl_dm;  // [4]
+  double *pl_mireal, *pl_miph;  // [4] inverses of pl_mreal and pl_mph (0 for no mass)
   int *pl_users, *pl_upf;  // [16]: 4 users of the phantom of each local node
   double *pl_uap;          // [16]: their piece areas
   int *pl_nu;              // [4]

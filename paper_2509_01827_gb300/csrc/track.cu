@@ -82,9 +82,12 @@ __device__ int block_exscan(int v, int *total) {
   return pre;
 }
 
-__device__ void set_mass(const DevState &d, int N, double m) {
+__device__ __forceinline__ double inverse_mass(double m) { return m > 0.0 ? 1.0 / m : 0.0; }
+
+// a node's lumped mass and its inverse (planned by the selection, which runs
+// beside the node updates, so the split writes do no FP64 division for it)
+__device__ void set_mass(const DevState &d, int N, double m, double mi) {
   d.m[N] = m;
-  double mi = m > 0.0 ? 1.0 / m : 0.0;
   d.minv[N] = mi;
   if (d.precision == 1) d.minvf[N] = (float)mi;
 }
@@ -538,6 +541,7 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
           if (np.st[q] != ST_OUT) mreal = mreal + d.mat.rho * Ap * 0.25;
         }
         d.pl_mreal[w * 4 + a] = mreal;
+        d.pl_mireal[w * 4 + a] = inverse_mass(mreal);
         // the reused phantom's users (sorted by element) and their areas
         int us[4] = {u4.x, u4.y, u4.z, u4.w}, uf[4] = {f4.x, f4.y, f4.z, f4.w};
         double Au[4] = {A01.x, A01.y, A23.x, A23.y};
@@ -575,6 +579,7 @@ __device__ __forceinline__ void select_plan(const DevState &d, int mode,
         for (int q = 0; q < 4; ++q)
           if (q < nun) acc = acc + d.mat.rho * outA[q] * 0.25;
         d.pl_mph[w * 4 + a] = acc;
+        d.pl_miph[w * 4 + a] = inverse_mass(acc);
         d.pl_mold[w * 4 + a] = mold;
         d.pl_dm[w * 4 + a] = d.mat.rho * Anew * 0.25;
         d.pl_nu[w * 4 + a] = nu;  // users before the insertion (4: list full)
@@ -694,8 +699,8 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
         reinterpret_cast<double2 *>(d.ph_uap)[2 * t + 1] = ua[1];
         d.ph_nuser[t] = nu + 1;
       }
-      set_mass(d, N, mreal);
-      set_mass(d, P, mnew);
+      set_mass(d, N, mreal, d.pl_mireal[w * 4 + a]);
+      set_mass(d, P, mnew, d.pl_miph[w * 4 + a]);
     } else if (act) {
       // lanes 4-7: surface list at local edge k = lane - 4; lane 4 also
       // writes the split record
