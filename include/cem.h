@@ -218,9 +218,11 @@ cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip,
 /* Profiling: advances n steps like cem_step but with direct kernel launches,
  * one after the other, bracketed by CUDA events on the handle's stream, and
  * returns device milliseconds in ms[9]: [0] all n steps (first event to
- * last), [1] piece forces, [2] tile update of real nodes, [3] phantom
- * update, [4] surface evaluation, [5] tracking selection, [6] energy
- * records, [7] number of kernels, [8] split writes. */
+ * last), [1] piece forces (FP32: the pieces' evaluation timed on its own;
+ * the step itself evaluates them inside the tile and phantom updates),
+ * [2] tile update of real nodes, [3] phantom update, [4] surface
+ * evaluation, [5] tracking selection, [6] energy records, [7] number of
+ * kernels, [8] split writes. */
 cem_status cem_profile_steps(cem_handle *h, int n, double *ms);
 
 /* Testing hook for the tracking bookkeeping: runs the selection and split
