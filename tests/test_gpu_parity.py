@@ -133,3 +133,35 @@ def test_fragmentation_full_size_first_steps():
     p = inputs.fragmentation(2048, mode="neumann")
     o, g = run_pair(p, 4, chunks=[1, 3])
     compare_fp64(o, g)
+
+
+def test_bookkeeping_more_proposals_than_staged():
+    """A step with more proposals than the selection stages in shared memory
+    (1024): the sort, winners and plans run on the global scratch and still
+    match the oracle exactly.  A 64x64 mesh with a fifth of its elements
+    inactive has thousands of surface points."""
+    from oracle.oracle import from_problem
+    from paper_2509_01827_gb300.cem import Solver
+    rng = np.random.default_rng(11)
+    nx = ny = 64
+    act = (rng.random(nx * ny) >= 0.2).astype(np.uint8)
+    p = inputs.Problem(name="bk_many", nx=nx, ny=ny, hx=1e-3, hy=1e-3, active=act,
+                       phantom_cap=20 * nx * ny, crack_cap=nx * ny)
+    o = from_problem(p)
+    g = Solver(p)
+    n = o.counts()["nn"] + o.counts()["n_phantom"]
+    st = dict(vx=rng.standard_normal(n), vy=rng.standard_normal(n))
+    o.set_state(**st)
+    g.set_state(**st)
+    staged = 0
+    for rnd in range(3):
+        ev = o.eval_surface()
+        pick = np.nonzero(rng.random(len(ev["edge"])) < 0.8)[0]
+        staged = max(staged, len(pick))
+        edge, elem = ev["edge"][pick], ev["ahead"][pick]
+        k = np.array([rng.choice([q for q in range(4) if q != k0]) for k0 in ev["k0"][pick]])
+        G = rng.integers(1, 6, len(pick)).astype(np.float64)
+        o.apply_proposals(edge, elem, k, G)
+        g.debug_apply_proposals(edge, elem, k, G)
+        compare_fp64(o, g)
+    assert staged > 1024
