@@ -11,10 +11,11 @@
    channels, the last five zero): traction / 3 MPa, the notch (1 on the
    pre-cracked elements), (G_c - 3 J/m^2) / 0.36 J/m^2 (the Weibull field's
    standard deviation).
-3. Training: the U-Net of surrogate.py, weighted binary cross-entropy
-   (cracked elements weighted by the training set's intact/cracked ratio,
-   capped at 20), Adam with a linear warm-up over 5% of the steps and a
-   cosine learning-rate decay, batch 64.
+3. Training: the U-Net of surrogate.py (by default five levels, 32 .. 512
+   channels), weighted binary cross-entropy (cracked elements weighted by
+   the training set's intact/cracked ratio, capped at 20), Adam (peak rate
+   1e-3; the five-level net did not train at 2e-3) with a linear warm-up
+   over 5% of the steps and a cosine learning-rate decay, batch 64.
 4. Evaluation: mean Jaccard index of the predicted cracked set (logit >
    threshold, threshold chosen on held-out training runs) on the test runs,
    beside the no-learning floor of a straight crack along the notch row.
@@ -128,13 +129,13 @@ def mean_jaccard(Z, Y, thr):
     return float(j.mean().item()), j.cpu().numpy()
 
 
-def bench_steps(B, n):
+def bench_steps(B, n, chans=(32, 64, 128, 256, 512)):
     """Times forward, backward (loss included) and Adam of the surrogate on
     synthetic inputs (3 random channels, 7% cracked targets) after 3 warm-up
     steps; returns milliseconds per step and the FLOP rate of the convolutions."""
     import torch
     from .surrogate import UNet
-    net = UNet(B, H_EL, W_EL, pos_weight=12.0)
+    net = UNet(B, H_EL, W_EL, chans=list(chans), pos_weight=12.0)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(B * H_EL * W_EL, 8, device="cuda", generator=g)
     x[:, 3:] = 0
@@ -166,7 +167,7 @@ def bench_steps(B, n):
         f = 2.0 * B * h * w * 9 * p["cin"] * p["cout"]
         flops_f += f
         flops_b += f * (1 if name == "e0a" else 2)
-    return {"batch": B, "steps": n, "fwd_ms": fwd, "bwd_ms": bwd, "adam_ms": adam,
+    return {"batch": B, "chans": list(chans), "steps": n, "fwd_ms": fwd, "bwd_ms": bwd, "adam_ms": adam,
             "step_ms": fwd + bwd + adam, "conv_tflop_per_step": (flops_f + flops_b) / 1e12,
             "conv_tflops": (flops_f + flops_b) / ((fwd + bwd + adam) * 1e-3) / 1e12}
 
@@ -178,9 +179,12 @@ def main():
     ap.add_argument("--val", type=int, default=256, help="training runs held out for the threshold")
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--chans", default="32,64,128,256,512",
+                    help="channels per U-Net level (level 0 at most 32; H and W divisible "
+                         "by 2^(levels-1))")
     ap.add_argument("--bench-steps", type=int, default=0,
                     help="only time this many training steps of batch --batch on synthetic inputs")
     ap.add_argument("--save", default=None,
@@ -193,7 +197,8 @@ def main():
     torch.cuda.set_device(0)
     log = lambda m: print(m, flush=True)
     if args.bench_steps:
-        print(json.dumps(bench_steps(args.batch, args.bench_steps)))
+        print(json.dumps(bench_steps(args.batch, args.bench_steps,
+                                     [int(c) for c in args.chans.split(",")])))
         return
 
     t0 = time.perf_counter()
@@ -204,7 +209,9 @@ def main():
     ntr = args.train - nval
     frac = float(Ytr[:ntr].float().mean().item())
     pos_weight = float(min(20.0, (1.0 - frac) / max(frac, 1e-6)))
-    net = UNet(args.batch, H_EL, W_EL, pos_weight=pos_weight, lr=args.lr, seed=args.seed)
+    chans = [int(c) for c in args.chans.split(",")]
+    net = UNet(args.batch, H_EL, W_EL, chans=chans, pos_weight=pos_weight, lr=args.lr,
+               seed=args.seed)
     rng = np.random.default_rng(args.seed)
     steps_per_epoch = ntr // args.batch
     total = steps_per_epoch * args.epochs
@@ -250,7 +257,7 @@ def main():
     j_te0, _ = mean_jaccard(Zte, Yte, 0.0)
     out = {
         "workload": "surrogate_400x160", "train_runs": ntr, "val_runs": nval,
-        "test_runs": args.test, "epochs": args.epochs, "batch": args.batch,
+        "test_runs": args.test, "epochs": args.epochs, "batch": args.batch, "chans": chans,
         "params": int(sum(p["w"].numel() + p["b"].numel() for p in net.convs.values())
                       + net.head["w"].numel() + 1),
         "cracked_fraction_train": frac, "pos_weight": pos_weight,
@@ -266,7 +273,8 @@ def main():
     }
     if args.save:
         k = min(8, args.test)
-        np.savez_compressed(args.save, **net.params_numpy(),
+        np.savez_compressed(args.save, **net.params_numpy(), chans=np.array(chans),
+                            threshold=np.array(best_thr),
                             test_target=Yte[:k].cpu().numpy().reshape(k, H_EL, W_EL),
                             test_pred=(Zte[:k] > best_thr).cpu().numpy().reshape(k, H_EL, W_EL))
     print(json.dumps(out))

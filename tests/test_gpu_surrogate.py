@@ -326,7 +326,8 @@ def test_training_reduces_loss():
     assert losses[-1] < 0.5 * losses[0], losses[::10]
 
 
-@pytest.mark.parametrize("cin,cout", [(8, 32), (24, 40), (32, 64), (64, 128), (96, 32), (128, 256), (40, 96), (16, 18)])
+@pytest.mark.parametrize("cin,cout", [(8, 32), (24, 40), (32, 64), (64, 128), (96, 32), (128, 256), (40, 96),
+                                      (16, 18), (256, 512), (256, 768)])
 def test_tcgen05_and_mma_paths_agree(cin, cout):
     """The tcgen05 (TMEM) and mma.sync paths of the 3x3 convolution against the
     oracle, ragged pixel counts, every N tile width; no bounded wait gives up."""
@@ -357,7 +358,8 @@ def test_tcgen05_and_mma_paths_agree(cin, cout):
         assert _rel(out[path], mref) < 1e-2, path
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 24), (8, 32), (32, 64), (64, 128), (40, 96), (128, 256)])
+@pytest.mark.parametrize("cin,cout", [(16, 24), (8, 32), (32, 64), (64, 128), (40, 96), (128, 256),
+                                      (768, 256), (256, 512)])
 def test_weight_gradient_paths_agree(cin, cout):
     """Weight and bias gradients on the tcgen05 path and on the mma.sync path
     against the oracle (BF16 products are exact in FP32)."""
