@@ -597,11 +597,23 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
       fy = (2.f * rx) * (H1.y - H2.y) + hy2 * ((Hd0.x + Hd1.x) - (Hu0.x + Hu1.x)) +
            (2.f * ry) * (V1.x - V2.x) + hx2 * ((Vl0.y + Vl1.y) - (Vr0.y + Vr1.y));
     } else {
+      // the across-edge differences (B - A, L - R) of the node's own four
+      // edges are zero when the four elements around it are all intact or
+      // all not: those nodes skip the per-side loads of these edges
+      const int ey = ty + r * BY + 1, ex = tx + 1;
+      const bool i00 = sst[ey][ex] == ST_INTACT, i01 = sst[ey][ex + 1] == ST_INTACT;
+      const bool i10 = sst[ey + 1][ex] == ST_INTACT, i11 = sst[ey + 1][ex + 1] == ST_INTACT;
+      const bool mixed = !((i00 && i01 && i10 && i11) || !(i00 || i01 || i10 || i11));
       // h(i-1, j), h(i, j): N is the right / left node of both elements
       const float2 P1 = sHP[cj][ci - 1], P2 = sHP[cj][ci];
-      const float4 Q1 = sHAB[cj][ci - 1], Q2 = sHAB[cj][ci];
-      fx = rx * (P1.x - P2.x) + hy2 * ((Q1.w - Q1.y) + (Q2.w - Q2.y));
-      fy = rx * (P1.y - P2.y) + hy2 * ((Q1.z - Q1.x) + (Q2.z - Q2.x));
+      if (mixed) {
+        const float4 Q1 = sHAB[cj][ci - 1], Q2 = sHAB[cj][ci];
+        fx = rx * (P1.x - P2.x) + hy2 * ((Q1.w - Q1.y) + (Q2.w - Q2.y));
+        fy = rx * (P1.y - P2.y) + hy2 * ((Q1.z - Q1.x) + (Q2.z - Q2.x));
+      } else {
+        fx = rx * (P1.x - P2.x);
+        fy = rx * (P1.y - P2.y);
+      }
       // h(i-1, j+1), h(i, j+1): N is a lower node of their below element (B);
       // h(i-1, j-1), h(i, j-1): N is an upper node of their above element (A)
       const float2 Bu0 = hi2(sHAB[cj + 1][ci - 1]), Bu1 = hi2(sHAB[cj + 1][ci]);
@@ -610,9 +622,14 @@ __device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur,
       fy += hy2 * ((Ad0.x + Ad1.x) - (Bu0.x + Bu1.x));
       // v(i, j-1): N top node; v(i, j): N bottom node of both elements
       const float2 S1 = sVP[cj - 1][ci], S2 = sVP[cj][ci];
-      const float4 W1 = sVAB[cj - 1][ci], W2 = sVAB[cj][ci];
-      fx += ry * (S1.x - S2.x) + hx2 * ((W1.z - W1.x) + (W2.z - W2.x));
-      fy += ry * (S1.y - S2.y) + hx2 * ((W1.w - W1.y) + (W2.w - W2.y));
+      if (mixed) {
+        const float4 W1 = sVAB[cj - 1][ci], W2 = sVAB[cj][ci];
+        fx += ry * (S1.x - S2.x) + hx2 * ((W1.z - W1.x) + (W2.z - W2.x));
+        fy += ry * (S1.y - S2.y) + hx2 * ((W1.w - W1.y) + (W2.w - W2.y));
+      } else {
+        fx += ry * (S1.x - S2.x);
+        fy += ry * (S1.y - S2.y);
+      }
       // v(i-1, j-1), v(i-1, j): N is a right node of their right element (R);
       // v(i+1, j-1), v(i+1, j): N is a left node of their left element (L)
       const float2 Rl0 = lo2(sVAB[cj - 1][ci - 1]), Rl1 = lo2(sVAB[cj][ci - 1]);
