@@ -435,7 +435,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
                                     : 2 * (rim + 4L * d.ck_cap) + 8192;
   if (lc > (1L << 30)) lc = 1L << 30;
   d.list_cap = (int)lc;
-  d.prop_cap = 8192;
+  d.prop_cap = track_sort_capacity();
   d.ncap = d.g.nn + d.ph_cap;
   d.lam_cap = 4096;
   d.rec_cap = 65536;

@@ -258,6 +258,9 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st);
 cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
+// proposals one step can hold: the selection sorts (a power of two) that many
+// at most, in shared memory or in its global scratch of that size
+int track_sort_capacity();
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);
 cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st);
