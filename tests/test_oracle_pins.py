@@ -135,6 +135,157 @@ def test_internal_forces_sum_to_zero():
     assert abs(fy.sum()) < 1e-12 * np.abs(fy).sum()
 
 
+# ------------------------------------------------------------ a1-a3 quadrature and smoothing
+# Natural-coordinate derivatives of the bilinear shape functions
+# N_a = (1 + xi_a xi)(1 + eta_a eta)/4 at the four edge midpoints
+# k = 0 (0,-1), 1 (1,0), 2 (0,1), 3 (-1,0); rows a = 0..3, columns k.
+# dN/dxi_a = xi_a (1 + eta_a eta)/4, dN/deta_a = eta_a (1 + xi_a xi)/4.
+_P = np.array([[-0.5, -0.25, 0.0, -0.25], [0.5, 0.25, 0.0, 0.25],
+               [0.0, 0.25, 0.5, 0.25], [0.0, -0.25, -0.5, -0.25]])
+_Q = np.array([[-0.25, 0.0, -0.25, -0.5], [-0.25, -0.5, -0.25, 0.0],
+               [0.25, 0.5, 0.25, 0.0], [0.25, 0.0, 0.25, 0.5]])
+
+
+def _isolated_column_node1(hx, hy, dx, dy):
+    """Forces on the four nodes of one isolated hx x hy element when its local
+    node 1 moves by (dx, dy), from Eq. 6 with the four edge-midpoint points
+    each weighted A/4 (reading C1).
+
+    With dN/dx = 2P/hx, dN/dy = 2Q/hy and A/4 = hx hy/4, the 2x2 block
+    K_a1 = sum_k (A/4) B_a^T D B_1 reduces to sums of products of the tables
+    above, worked out by hand (r = hy/hx):
+      sum_k P_a P_1 = (-3/8, 3/8, 1/8, -1/8)   sum_k Q_a Q_1 = (1/8, 3/8, -3/8, -1/8)
+      sum_k Q_a P_1 = (-1/4, -1/4, 1/4, 1/4)   sum_k P_a Q_1 = (1/4, -1/4, -1/4, 1/4)
+      f_ax = (D11 r S_PP + D33/r S_QQ) dx + (D12 S_PQ + D33 S_QP) dy
+      f_ay = (D12 S_QP + D33 S_PQ) dx + (D11/r S_QQ + D33 r S_PP) dy
+    (2x2 Gauss quadrature would give S_PP(1,1) = 1/3 instead of 3/8.)"""
+    D11, D12, D33 = d_plane_strain()
+    r = hy / hx
+    spp = np.array([-3, 3, 1, -1]) / 8.0
+    sqq = np.array([1, 3, -3, -1]) / 8.0
+    sqp = np.array([-1, -1, 1, 1]) / 4.0
+    spq = np.array([1, -1, -1, 1]) / 4.0
+    fx = (D11 * r * spp + D33 / r * sqq) * dx + (D12 * spq + D33 * sqp) * dy
+    fy = (D12 * sqp + D33 * spq) * dx + (D11 / r * sqq + D33 * r * spp) * dy
+    return np.stack([fx, fy], 1)
+
+
+def test_shape_derivative_tables_are_the_bilinear_ones():
+    """The tables above are the bilinear derivatives (checked by central
+    differences of N_a at the edge midpoints), so the pins below rest on the
+    element's definition, not on a retyped table."""
+    xa = np.array([-1, 1, 1, -1.0])
+    ya = np.array([-1, -1, 1, 1.0])
+    pts = [(0, -1), (1, 0), (0, 1), (-1, 0)]
+    N = lambda a, x, y: (1 + xa[a] * x) * (1 + ya[a] * y) / 4
+    d = 1e-6
+    for a in range(4):
+        for k, (x, y) in enumerate(pts):
+            assert abs((N(a, x + d, y) - N(a, x - d, y)) / (2 * d) - _P[a, k]) < 1e-9
+            assert abs((N(a, x, y + d) - N(a, x, y - d)) / (2 * d) - _Q[a, k]) < 1e-9
+    # the closed-form sums of the column helper
+    assert np.allclose(_P @ _P[1], [-3 / 8, 3 / 8, 1 / 8, -1 / 8])
+    assert np.allclose(_Q @ _Q[1], [1 / 8, 3 / 8, -3 / 8, -1 / 8])
+    assert np.allclose(_Q @ _P[1], [-1 / 4, -1 / 4, 1 / 4, 1 / 4])
+    assert np.allclose(_P @ _Q[1], [1 / 4, -1 / 4, -1 / 4, 1 / 4])
+
+
+@pytest.mark.parametrize("hx,hy", [(1e-3, 1e-3), (0.7e-3, 0.3e-3)])
+@pytest.mark.parametrize("dx,dy", [(1e-6, 0.0), (0.0, 1e-6), (0.4e-6, -0.9e-6)])
+def test_single_element_stiffness_column(hx, hy, dx, dy):
+    """One element alone: every edge is a boundary edge (own strain), so the
+    nodal forces are the element stiffness column of the moved node under the
+    edge-midpoint rule (a non-linear field: the hourglass parts of a single
+    moved node are resisted, Sec. 2.1 Eq. 4 at the edge points)."""
+    s = make(1, 1, hx, hy)
+    ux, uy = np.zeros(4), np.zeros(4)
+    ux[1], uy[1] = dx, dy
+    s.set_state(ux=ux, uy=uy)
+    fx, fy = s.internal_force()
+    want = _isolated_column_node1(hx, hy, dx, dy)
+    glob = [0, 1, 3, 2]                                 # local node -> global node
+    scale = np.max(np.abs(want))
+    np.testing.assert_allclose(np.stack([fx[glob], fy[glob]], 1), want, rtol=0,
+                               atol=1e-13 * scale)
+
+
+@pytest.mark.parametrize("hx,hy", [(1e-3, 1e-3), (0.6e-3, 0.25e-3)])
+def test_edge_smoothing_couples_far_nodes_horizontal(hx, hy):
+    """2 x 1 mesh, node 0 (a corner of the left element only) moves by
+    (dx, dy).  The right element's own strain is zero everywhere, so its far
+    nodes (2 and 5) feel the move only through the area-weighted edge strain
+    of Eqs. 1-2 at the shared edge:
+      left element, right-edge point (xi = 1, eta = 0): dN_0/dx = -1/(2hx),
+        dN_0/dy = 0, so eps_own = (-dx/(2hx), 0, -dy/(2hx));
+      equal areas: eps_g = eps_own / 2, sigma_g = D eps_g
+        = (-D11 dx, -D12 dx, -D33 dy) / (4hx);
+      right element, left-edge point (xi = -1, eta = 0): its local nodes 1, 2
+        have dN/dx = 1/(2hx), dN/dy = 0, so f = (A/4)(1/(2hx)) (sxx, sxy)
+        = hy/8 (sxx, sxy) = (-D11 dx, -D33 dy) hy / (32 hx).
+    Using each element's own strain (no averaging) would give exactly zero
+    there, and pairing the wrong edge of the neighbour another value."""
+    D11, D12, D33 = d_plane_strain()
+    dx, dy = 1e-6, -0.7e-6
+    s = make(2, 1, hx, hy)
+    ux, uy = np.zeros(6), np.zeros(6)
+    ux[0], uy[0] = dx, dy
+    s.set_state(ux=ux, uy=uy)
+    fx, fy = s.internal_force()
+    want = np.array([-D11 * dx, -D33 * dy]) * hy / (32 * hx)
+    for n in (2, 5):
+        np.testing.assert_allclose([fx[n], fy[n]], want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("hx,hy", [(1e-3, 1e-3), (0.25e-3, 0.6e-3)])
+def test_edge_smoothing_couples_far_nodes_vertical(hx, hy):
+    """1 x 2 mesh (elements stacked), node 0 moves by (dx, dy).  Bottom
+    element, top-edge point (xi = 0, eta = 1): dN_0/dx = 0, dN_0/dy =
+    -1/(2hy), so eps_own = (0, -dy/(2hy), -dx/(2hy)); halved by the averaging;
+    sigma_g = (-D12 dy, -D11 dy, -D33 dx)/(4hy).  Top element, bottom-edge
+    point: its local nodes 2, 3 (global 5, 4) have dN/dx = 0, dN/dy = 1/(2hy):
+    f = (A/4)(1/(2hy)) (sxy, syy) = (-D33 dx, -D11 dy) hx / (32 hy)."""
+    D11, D12, D33 = d_plane_strain()
+    dx, dy = -0.8e-6, 1.1e-6
+    s = make(1, 2, hx, hy)
+    ux, uy = np.zeros(6), np.zeros(6)
+    ux[0], uy[0] = dx, dy
+    s.set_state(ux=ux, uy=uy)
+    fx, fy = s.internal_force()
+    want = np.array([-D33 * dx, -D11 * dy]) * hx / (32 * hy)
+    for n in (4, 5):
+        np.testing.assert_allclose([fx[n], fy[n]], want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("hx,hy", [(1e-3, 1e-3), (0.5e-3, 0.8e-3)])
+def test_no_smoothing_beside_a_split_element(hx, hy):
+    """Reading C4: smoothing is off on every edge touching a split element.
+    2 x 1 mesh with the left element pre-cut (left to right edge midpoint);
+    the right element's far node 2 (its local node 1) moves.  The left
+    element's pieces do not move, so the right element must act exactly as
+    if it were alone: its four nodes carry the isolated-element column
+    (hand form above).  With the left element intact the shared edge
+    averages the strains and the forces differ (control)."""
+    dx, dy = 0.9e-6, 0.5e-6
+    want = _isolated_column_node1(hx, hy, dx, dy)      # rows: e1 local 0..3
+    glob = [1, 2, 5, 4]                                 # e1 local -> global node
+    s = make(2, 1, hx, hy)
+    s.precrack([[0, 3, 1]])
+    n = s.counts()["nn"] + s.counts()["n_phantom"]
+    ux, uy = np.zeros(n), np.zeros(n)
+    ux[2], uy[2] = dx, dy
+    s.set_state(ux=ux, uy=uy)
+    fx, fy = s.internal_force()
+    scale = np.max(np.abs(want))
+    got = np.array([[fx[g], fy[g]] for g in glob])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * scale)
+    # phantoms and the left element's own real nodes feel nothing
+    assert np.all(fx[[0, 3]] == 0) and np.all(fx[6:] == 0) and np.all(fy[6:] == 0)
+    c = make(2, 1, hx, hy)
+    c.set_state(ux=ux[:6], uy=uy[:6])
+    cx, cy = c.internal_force()
+    assert np.max(np.abs(np.array([[cx[g], cy[g]] for g in glob]) - want)) > 1e-3 * scale
+
+
 # ------------------------------------------------------------ a5 dynamics
 def test_total_mass_equals_density_times_area():
     s, _ = _random_cracked_mesh(3)
