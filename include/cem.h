@@ -258,16 +258,17 @@ cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge,
 cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_end,
                             void *cuda_stream, cem_handle **out);
 
-/* Launch configuration of a batch: tile_rows (8 or 16) is the height of the
- * FP32 tile update's tiles (32 nodes wide; the FP64 tiles are fixed at
- * 32 x 8), grid_main the persistent grid of the tile update (1 .. 64 x SMs).
- * Results do not depend on it in FP64; in FP32 the grouping of some sums
- * changes with the tile height (last-bit differences).  Default 16, 3 x SMs. */
+/* Launch configuration of a batch: tile_rows (8 .. 64) is the height of the
+ * FP32 node update's tiles (28 nodes wide, one warp each; the FP64 tiles are
+ * fixed at 32 x 8), grid_main the persistent grid of the node update
+ * (1 .. 64 x SMs).  Nodal results do not depend on it; in FP32 the energy
+ * records group their partial sums by tile (last-bit differences).
+ * Default 16, 3 x SMs. */
 cem_status cem_batch_set_config(cem_handle *batch, int tile_rows, int grid_main);
 
 /* Autotuner: times steps_per_candidate real steps (after one untimed step)
- * for each candidate configuration -- tile heights {16, 8} (FP32 only) x
- * grids {1, 2, 3, 4} x SMs -- keeps the fastest and returns it.  The timed
+ * for each candidate configuration -- tile heights {16, 8, 32, 64} (FP32
+ * only) x grids {1, 2, 3, 4} x SMs -- keeps the fastest and returns it.  The timed
  * steps advance the simulation like cem_step. */
 cem_status cem_batch_autotune(cem_handle *batch, int steps_per_candidate, int *tile_rows,
                               int *grid_main);

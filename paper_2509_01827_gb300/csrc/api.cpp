@@ -204,7 +204,9 @@ void drop_graphs(cem_handle *h) {
   h->multi.clear();
 }
 
-int kernels_in_step(bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
+// kernels one step launches: the step kernels, selection and split writes,
+// the energy prologue and epilogue on record steps
+int kernels_in_step(const cem_handle *, bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
 
 // Enqueues one explicit step (buffers cur -> cur^1) on the stream.  With
 // marks (profiling) events are recorded after the energy prologue, after
@@ -447,7 +449,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
   } else {
     for (int b = 0; b < 2; ++b) ok = ok && dalloc_n(h, d.u4[b], nc);
     ok = ok && dalloc_n(h, d.v2, nc) && dalloc_n(h, d.minvf, nc) &&
-         dalloc_n(h, d.pff, (size_t)d.ck_cap * 16);
+         dalloc_n(h, d.pff, (size_t)d.ck_cap * 16) && dalloc_n(h, d.pfe, nec * 8) &&
+         dalloc_n(h, d.fsp, (size_t)nn);
   }
   ok = ok && dalloc_n(h, d.m, nc) && dalloc_n(h, d.minv, nc) && dalloc_n(h, d.Wn, nc) &&
        dalloc_n(h, d.Wd, nc) && dalloc_n(h, d.nflag, (size_t)nn) && dalloc_n(h, d.Fx, (size_t)nn) &&
@@ -720,8 +723,8 @@ cem_status cem_step(cem_handle *h, int n) {
       const int gm = group_mask(h->step, h->energy_every);
       if (h->step > 0 && chunk - q >= kGraphSteps && gm >= 0) {
         const unsigned mask = (unsigned)gm;
-        const long kernels = kGraphSteps * kernels_in_step(false) +
-                             (mask ? kernels_in_step(true) - kernels_in_step(false) : 0);
+        const long kernels = kGraphSteps * kernels_in_step(h, false) +
+                             (mask ? kernels_in_step(h, true) - kernels_in_step(h, false) : 0);
         cudaGraphExec_t gx;
         rc = multi_graph_for(h, h->cur, mask, &gx);
         if (rc != CEM_OK) return rc;
@@ -740,7 +743,7 @@ cem_status cem_step(cem_handle *h, int n) {
         if (rc != CEM_OK) return rc;
         CUDA_TRY(h, cudaGraphLaunch(gx, h->st));
       }
-      h->launches += kernels_in_step(energy);
+      h->launches += kernels_in_step(h, energy);
       h->cur ^= 1;
       h->step += 1;
       ++q;
@@ -770,7 +773,7 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
     bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
     cudaEventRecord(ev[(size_t)q * M], h->st);
     err = enqueue_step(h, h->cur, h->step == 0, energy, &ev[(size_t)q * M + 1]);
-    kernels += kernels_in_step(energy);
+    kernels += kernels_in_step(h, energy);
     h->cur ^= 1;
     h->step += 1;
   }
@@ -1088,7 +1091,7 @@ struct BatchPlan {
   int precision = 0;
   int energy_every = 0;
   long step = 0;           // batch step (equals every active member's step)
-  int tile_rows = 16;      // FP32 tile height (8 or 16)
+  int tile_rows = 16;      // FP32 tile height (8 .. 64 node rows)
   int grid_main = 0;       // persistent grid of the tile update
   int sms = 0;
   BatchDev bd{};
@@ -1121,20 +1124,19 @@ cem_status batch_upload(cem_handle *b) {
     d.step_end = (int)std::min<long>(p->step_end[s], (long)INT_MAX);
     d.cur_xor = m->cur ^ (int)(m->step & 1);
     ds[s] = d;
-    int gx, gy;
+    int tiles;
     if (p->precision == CEM_FP32_MIXED) {
-      gx = (d.g.nx + 1 + 31) / 32;
-      gy = (d.g.ny + 1 + p->tile_rows - 1) / p->tile_rows;
+      // FP32 node update: one item per group of eight warp tiles
+      const int ng = groups_fp32(d, p->tile_rows);
+      for (int q = 0; q < ng; ++q) wm.push_back(make_int4(s, q, 0, ng));
+      tiles = tiles_fp32(d, p->tile_rows);
     } else {
-      gx = (d.g.nx + 1 + 31) / 32;
-      gy = tiles_fp64(d) / gx;
+      const int gx = (d.g.nx + 1 + 31) / 32, gy = tiles_fp64(d) / gx;
+      for (int y = 0; y < gy; ++y)
+        for (int x = 0; x < gx; ++x) wm.push_back(make_int4(s, x, y, gx | (gy << 16)));
+      tiles = gx * gy;
     }
-    for (int y = 0; y < gy; ++y)
-      for (int x = 0; x < gx; ++x) wm.push_back(make_int4(s, x, y, gx | (gy << 16)));
-    // the FP32 step has no piece kernel: its tile and phantom updates
-    // evaluate the pieces themselves
-    const int tiles = gx * gy, gph = grid_phantoms(d);
-    const int gp = p->precision == CEM_FP32_MIXED ? 0 : grid_pieces(d);
+    const int gph = grid_phantoms(d), gp = grid_pieces(d);
     for (int q = 0; q < gp; ++q) wp.push_back(make_int4(s, q, tiles, gp));
     for (int q = 0; q < gph; ++q) wph.push_back(make_int4(s, q, tiles + gp, gph));
     // the evaluation has no energy partials: a few virtual blocks per member
@@ -1430,7 +1432,7 @@ cem_status cem_batch_set_config(cem_handle *b, int tile_rows, int grid_main) {
   if (!b) return CEM_ERR_ARG;
   if (!b->batch) return fail(b, CEM_ERR_STATE, "not a batch handle");
   BatchPlan *p = b->batch;
-  if (tile_rows != 8 && tile_rows != 16) return fail(b, CEM_ERR_ARG, "tile_rows must be 8 or 16");
+  if (tile_rows < 8 || tile_rows > 64) return fail(b, CEM_ERR_ARG, "tile_rows must be in 8 .. 64");
   if (grid_main < 1 || grid_main > 64 * p->sms) return fail(b, CEM_ERR_ARG, "1 <= grid_main <= 64 * SMs");
   CUDA_TRY(b, cudaSetDevice(b->device));
   const bool relist = p->precision == CEM_FP32_MIXED && tile_rows != p->tile_rows;
@@ -1449,8 +1451,8 @@ cem_status cem_batch_autotune(cem_handle *b, int steps_per_candidate, int *tile_
   if (steps_per_candidate < 1) return fail(b, CEM_ERR_ARG, "steps_per_candidate >= 1");
   CUDA_TRY(b, cudaSetDevice(b->device));
   std::vector<std::pair<int, int>> cand;
-  const int rows[2] = {16, 8};
-  for (int r = 0; r < (p->precision == CEM_FP32_MIXED ? 2 : 1); ++r)
+  const int rows[4] = {16, 8, 32, 64};
+  for (int r = 0; r < (p->precision == CEM_FP32_MIXED ? 4 : 1); ++r)
     for (int k = 1; k <= 4; ++k) cand.push_back({rows[r], k * p->sms});
   cudaEvent_t e0, e1;
   CUDA_TRY(b, cudaEventCreate(&e0));

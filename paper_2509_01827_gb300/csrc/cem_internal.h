@@ -91,8 +91,11 @@ struct DevState {
   double *ck_ud;
   int *ck_step;
   double *pf;            // [ck_cap * 16] piece nodal forces (FP64 mode)
-  float *pff;            // [ck_cap * 16] piece nodal forces (FP32 mode; written only by
-                         // the profiling path, the step evaluates pieces where used)
+  float *pff;            // [ck_cap * 16] piece nodal forces (FP32 mode)
+  float *pfe;            // [ne * 8] FP32 mode: forces of a split element's pieces at its
+                         // four real nodes (local node a: the piece on its side)
+  float2 *fsp;           // [nn] FP32 mode: internal force of a node with a load or a
+                         // prescribed velocity, handed from the march to its update
 
   // phantoms [ph_cap]
   int *ph_owner;
@@ -275,7 +278,8 @@ int energy_parts_step(const DevState &d);    // partials one step writes (alone)
 
 // batched counterparts (see BatchDev); tile_rows selects the FP32 tile
 // update's tile height (8 or 16 node rows), grid_main its persistent grid
-int tiles_fp32(const DevState &d, int tile_rows);
+int tiles_fp32(const DevState &d, int tile_rows);   // energy partials of the node update
+int groups_fp32(const DevState &d, int tile_rows);  // its CTAs (eight warp tiles each)
 int tiles_fp64(const DevState &d);
 int grid_pieces(const DevState &d);
 int grid_phantoms(const DevState &d);

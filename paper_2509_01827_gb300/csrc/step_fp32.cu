@@ -225,9 +225,10 @@ __device__ __forceinline__ double piece32_energy(const Piece32 &P) {
   return acc;
 }
 
-// Piece forces of split elements (the profiling path times the pieces'
-// evaluation on its own; the step itself has the tile and phantom kernels
-// evaluate them).
+// Piece forces of every split element, evaluated once per step before the
+// node updates: all eight nodal forces of each piece into pff (the phantom
+// update gathers them), and each real node's force (from the piece on its
+// side) into the element's pfe record (the node update adds them).
 __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
                                          int part_off) {
   const int n = 2 * d.cnt->n_ck;
@@ -236,516 +237,469 @@ __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, in
     const int c = t >> 1, p = t & 1;
     Piece32 P;
     piece32(d, c, p, cur, P);
-    float *o = d.pff + c * 16 + p * 8;
+    float4 *o = reinterpret_cast<float4 *>(d.pff + c * 16 + p * 8);
+    o[0] = make_float4(P.f[0], P.f[1], P.f[2], P.f[3]);
+    o[1] = make_float4(P.f[4], P.f[5], P.f[6], P.f[7]);
+    const int info = d.ck_info[c];
+    float2 *r = reinterpret_cast<float2 *>(d.pfe) + (size_t)d.ck_elem[c] * 4;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) o[q] = P.f[q];
+    for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
+      if (((info >> (4 + a)) & 1) == p) r[a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
     if (energy) se += piece32_energy(P);
   }
   if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + vb.x));
 }
 
 __global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
+  // a programmatic dependent of the previous step's split writes (see k_march32)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   pieces32(d, hw_vblk(), cur, energy, part_off);
 }
 
-// -------------------------------------------------------------- main tile
-// One CTA of 32 x 8 threads owns a tile of TX x TY real nodes, TX = 32 and
-// TY = 8 or 16 (TY / 8 rows per thread).  Shared memory holds, with a
-// two-node halo:
-//   sU  displacement pairs (x.hi, x.lo, y.hi, y.lo) of nodes [i0-2, i0+TX+1] x [j0-2, j0+TY+1]
-//   sD  node differences D(i,j) = (ux(i+1,j)-ux(i,j), uy(i+1,j)-uy(i,j),
-//       ux(i,j+1)-ux(i,j), uy(i,j+1)-uy(i,j)) of nodes [i0-2, i0+TX] x [j0-2, j0+TY],
-//       formed from the pairs as (hi_b - hi_a) + (lo_b - lo_a)
-//   sH  horizontal edges h(i,j), i in [i0-1, i0+TX), j in [j0-1, j0+TY]:
-//       with A the stress (xx, yy, xy) used by the element above and B the
-//       one used by the element below (zero where that element is not
-//       intact), AB = (A.yy, A.xy, B.yy, B.xy) and P = (A.xx + B.xx,
-//       A.xy + B.xy)
-//   sV  vertical edges v(i,j), i in [i0-1, i0+TX], j in [j0-1, j0+TY): with
-//       R the stress used by the element right and L by the element left,
-//       AB = (R.xx, R.xy, L.xx, L.xy) and P = (R.xy + L.xy, R.yy + L.yy)
-// Tiles whose halo holds only intact elements keep one stress per edge
-// instead.  sU is dead once sD is formed and shares its storage with sH;
-// sD is dead once the edge stresses are formed and then holds the forces
-// at real nodes of the split elements that touch the tile's nodes (the
-// window of elements [i0-1, i0+TX-1] x [j0-1, j0+TY-1]), KSLOT elements at
-// a time, with the window's split elements listed in increasing id.
-constexpr int TX = 32, BX = 32, BY = 8;
-
-// Rank of this thread's flag among the set flags of the block, in thread
-// order, and their total.  Every thread of the block calls it.
-__device__ __forceinline__ int block_rank(bool flag, int &total) {
-  constexpr int NWARP = BX * BY / 32;
-  __shared__ int s_cnt[NWARP];
-  const int tid = threadIdx.x + threadIdx.y * BX, lane = tid & 31, w = tid >> 5;
-  const unsigned b = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) s_cnt[w] = __popc(b);
-  __syncthreads();
-  int off = 0, tot = 0;
-#pragma unroll
-  for (int q = 0; q < NWARP; ++q) {
-    const int n = s_cnt[q];
-    off += q < w ? n : 0;
-    tot += n;
-  }
-  __syncthreads();
-  total = tot;
-  return off + __popc(b & ((1u << lane) - 1u));
+// -------------------------------------------------------------- warp march
+// One warp updates a tile of WX x TY real nodes by marching up its node
+// rows.  Lane l holds node column c = i0 - 2 + l (columns i0-2 .. i0+29);
+// lanes 2..29 own the tile's WX = 28 columns, the two lanes on each side only
+// supply the values the owned columns need from their neighbours.  Vertical
+// neighbours are the lane's own registers from earlier rows; horizontal ones
+// come from the adjacent lanes by warp shuffles, so the stencil uses no
+// shared memory.  Iteration t loads node row t and forms
+//   Dx(c,t)   = u(c+1,t) - u(c,t)    tangential difference of edge h(c,t)
+//   Dy(c,t-1) = u(c,t) - u(c,t-1)    tangential difference of edge v(c,t-1)
+// (compensated pairs: (hi_b - hi_a) + (lo_b - lo_a)), then the strain and
+// the stress used on each side of edges h(c,t-1) and v(c,t-1) (Eq. 4 at the
+// edge midpoints: the tangential derivative is the edge's own difference,
+// the normal derivative of a side the sum of that side's two across-edge
+// differences; with both sides intact they are averaged, Eqs. 1-2 with equal
+// areas; a side that is not intact uses nothing and gets nothing), and adds
+// each side's B^T sigma A/4 (Eq. 6) to the forces of the nodes it touches
+// (rows t-2 .. t of columns c-1, c, c+1), as well as the forces of the
+// pieces of split element (c,t-1) at its real nodes.  Node row t-2 then has
+// every contribution: its force is summed across the lanes and the node
+// takes its central-difference update.
+__device__ __forceinline__ Stress3 masked(const Stress3 &s, bool on) {
+  Stress3 r;
+  r.xx = on ? s.xx : 0.f;
+  r.yy = on ? s.yy : 0.f;
+  r.xy = on ? s.xy : 0.f;
+  return r;
 }
 
-// the low / high half of a float4 in shared memory (one 8-byte load)
-__device__ __forceinline__ float2 lo2(const float4 &v) {
-  return reinterpret_cast<const float2 *>(&v)[0];
-}
-__device__ __forceinline__ float2 hi2(const float4 &v) {
-  return reinterpret_cast<const float2 *>(&v)[1];
-}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-template <int TY>
-struct Tile {
-  static constexpr int RY = TY / BY;  // node rows per thread
-  static constexpr int UXn = TX + 4, UYn = TY + 4;
-  static constexpr int DXn = TX + 3, DYn = TY + 3;
-  static constexpr int EXn = TX + 3, EYn = TY + 3;
-  static constexpr int HXn = TX + 1, HYn = TY + 2;
-  static constexpr int VXn = TX + 2, VYn = TY + 1;
-  struct SmemA {
-    float4 U[UYn][UXn];
-  };
-  struct SmemB {
-    float4 AB[HYn][HXn];
-    float2 P[HYn][HXn];
-  };
-  union SmemMain {
-    SmemA a;
-    SmemB b;
-  };
-  struct SmemFastH {  // intact tiles: one stress per edge, as (xx, xy) and (yy, xy)
-    float2 P[HYn][HXn], Q[HYn][HXn];
-  };
-  struct SmemFastV {
-    float2 P[VYn][VXn], Q[VYn][VXn];
-  };
-  union SmemV {
-    struct {
-      float4 AB[VYn][VXn];
-      float2 P[VYn][VXn];
-    } gen;
-    SmemFastV fast;
-  };
-  static constexpr int WXn = TX + 1, WYn = TY + 1, NWIN = WXn * WYn;
-  static constexpr int KSLOT = (2 * DYn * DXn * (int)sizeof(float2) - 4 * NWIN) / 32;
-  struct SmemD {
-    float2 Dx[DYn][DXn], Dy[DYn][DXn];  // (dux, duy) along x and along y
-  };
-  struct SmemPieces {
-    float2 slot[KSLOT][4];  // force at local node a of split element slot
-    uint16_t list[NWIN];    // window index of the n-th split element
-    uint16_t map[NWIN];     // rank of a split element in the list
-  };
-  static_assert(sizeof(SmemPieces) <= sizeof(SmemD), "piece slots fit in sD");
-  struct Smem {  // > 48 KB for TY = 16: dynamic shared memory
-    union {
-      SmemMain ab;
-      SmemFastH fh;
-    } u1;
-    union {
-      SmemD d;
-      SmemPieces pc;
-    } u2;
-    SmemV v;
-    uint8_t st[EYn][EXn];
-  };
+// Node data in flight per warp: u, v and 1/m of node rows t-2 .. t+kAhead-1
+// sit in a shared-memory ring filled by asynchronous copies (cp.async),
+// issued kAhead rows ahead of their use, so that the march holds no
+// prefetch registers for them.
+constexpr int kRing = 4, kAhead = kRing - 2;
+// Node columns per lane: lane l holds columns c_k = i0 - kHalo*kCols +
+// kCols*l + k, k < kCols; the kHalo lanes on each side only supply the
+// values the owned columns need (two columns of neighbours on each side).
+constexpr int kCols = 2;
+constexpr int kHalo = (2 + kCols - 1) / kCols;
+constexpr int WX = (32 - 2 * kHalo) * kCols;  // owned columns of a tile
+struct MarchRing {
+  float4 u[kRing][kCols][32];
+  float2 v[kRing][kCols][32];
+  float mi[kRing][kCols][32];
 };
 
-template <bool ENERGY, int TY>
-__device__ __forceinline__ void main32_tile(const DevState &d, VBlk vb, int cur, int first,
-                                            typename Tile<TY>::Smem &T) {
-  using C = Tile<TY>;
-  constexpr int RY = C::RY, UXn = C::UXn, UYn = C::UYn, DXn = C::DXn, DYn = C::DYn;
-  constexpr int EXn = C::EXn, EYn = C::EYn, HXn = C::HXn, HYn = C::HYn, VXn = C::VXn,
-                VYn = C::VYn;
-  float4 (*sU)[UXn] = T.u1.ab.a.U;
-  float4 (*sHAB)[HXn] = T.u1.ab.b.AB;
-  float2 (*sHP)[HXn] = T.u1.ab.b.P;
-  float2 (*fHP)[HXn] = T.u1.fh.P, (*fHQ)[HXn] = T.u1.fh.Q;
-  float2 (*sDx)[DXn] = T.u2.d.Dx, (*sDy)[DXn] = T.u2.d.Dy;
-  float4 (*sVAB)[VXn] = T.v.gen.AB;
-  float2 (*sVP)[VXn] = T.v.gen.P;
-  float2 (*fVP)[VXn] = T.v.fast.P, (*fVQ)[VXn] = T.v.fast.Q;
-  uint8_t (*sst)[EXn] = T.st;
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, int valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "r"(valid)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void f2acc(float2 &a, float x, float y) { a.x += x; a.y += y; }
 
+// The tile height TY (node rows) is chosen at launch, at most 64.
+template <bool ENERGY>
+__device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int tile_y, int TY,
+                                             int cur, int first, double *part, MarchRing &ring) {
+  constexpr int K = kCols;
   const Geo &g = d.g;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = vb.x * TX, j0 = vb.y * TY;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int i0 = tile_x * WX, j0 = tile_y * TY;
+  const int c0 = i0 - kHalo * K + K * lane;  // column of k = 0
   const int stride = g.nx + 1;
+  const bool own_lane = lane >= kHalo && lane < 32 - kHalo;
   const float4 *__restrict__ u4 = d.u4[cur];
-
-  // own nodes (i, j0+ty+8r): issue their loads first
-  const int i = i0 + tx;
-  float2 own_v[RY];
-  float own_mi[RY];
-  int own_nf[RY];
-#pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    const int j = j0 + ty + r * BY;
-    if (i <= g.nx && j <= g.ny) {
-      const int N = j * stride + i;
-      own_v[r] = d.v2[N];
-      own_mi[r] = d.minvf[N];
-      own_nf[r] = d.nflag[N];
-    } else {
-      own_v[r] = make_float2(0.f, 0.f);
-      own_mi[r] = 0.f;
-      own_nf[r] = 0;
-    }
-  }
-  // stage displacements and element states: every load is issued before
-  // any shared store, so the block waits for one memory latency, not six
-  const int tid0 = tx + ty * BX;
-  constexpr int NU = (UXn * UYn + BX * BY - 1) / (BX * BY);
-  constexpr int NE = (EXn * EYn + BX * BY - 1) / (BX * BY);
-  float4 ureg[NU];
-  int sreg[NE];
-#pragma unroll
-  for (int k = 0; k < NU; ++k) {
-    const int q = tid0 + k * BX * BY;
-    const int ly = q / UXn, lx = q - ly * UXn;
-    const int jj = j0 - 2 + ly, ii = i0 - 2 + lx;
-    ureg[k] = (q < UXn * UYn && jj >= 0 && jj <= g.ny && ii >= 0 && ii <= g.nx)
-                  ? u4[jj * stride + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int k = 0; k < NE; ++k) {
-    const int q = tid0 + k * BX * BY;
-    const int ly = q / EXn, lx = q - ly * EXn;
-    const int jj = j0 - 2 + ly, ii = i0 - 2 + lx;
-    sreg[k] = (q < EXn * EYn && jj >= 0 && jj < g.ny && ii >= 0 && ii < g.nx)
-                  ? (int)d.estate[jj * g.nx + ii] : (int)ST_OUT;
-  }
-  int any_open = 0;  // some element of the halo is not intact
-#pragma unroll
-  for (int k = 0; k < NU; ++k) {
-    const int q = tid0 + k * BX * BY;
-    if (q < UXn * UYn) sU[q / UXn][q % UXn] = ureg[k];
-  }
-#pragma unroll
-  for (int k = 0; k < NE; ++k) {
-    const int q = tid0 + k * BX * BY;
-    if (q < EXn * EYn) {
-      sst[q / EXn][q % EXn] = (uint8_t)sreg[k];
-      any_open |= sreg[k] != ST_INTACT;
-    }
-  }
-  const bool general = __syncthreads_or(any_open) != 0;
-  // own displacement pairs, needed by the update after sU is overwritten
-  float4 own_u[RY];
-#pragma unroll
-  for (int r = 0; r < RY; ++r) own_u[r] = sU[ty + r * BY + 2][tx + 2];
-  const int tid = tx + ty * BX;
-  constexpr int NTH = BX * BY;
-  for (int q = tid; q < DXn * DYn; q += NTH) {
-    const int ly = q / DXn, lx = q - ly * DXn;
-    const float4 U0 = sU[ly][lx], Ux = sU[ly][lx + 1], Uy = sU[ly + 1][lx];
-    sDx[ly][lx] = make_float2((Ux.x - U0.x) + (Ux.y - U0.y), (Ux.z - U0.z) + (Ux.w - U0.w));
-    sDy[ly][lx] = make_float2((Uy.x - U0.x) + (Uy.y - U0.y), (Uy.z - U0.z) + (Uy.w - U0.w));
-  }
-  __syncthreads();
-
-  const Mat &m = d.mat;
   const float rx = g.rxf, ry = g.ryf;
-  const float hx2 = 0.5f * rx, hy2 = 0.5f * ry, hx4 = 0.25f * rx, hy4 = 0.25f * ry;
-  const float qA = g.qAf;
-  float se = 0.f;    // strain energy of this thread's edges / qA (energy steps)
-  double sep = 0.0;  // strain energy of the pieces of the split elements it owns
-
-  if (!general) {
-    // every element around the tile is intact: smoothed strain on every
-    // edge, one stress per edge (stored in the .a arrays)
-    for (int q = tid; q < HXn * HYn; q += NTH) {
-      {
-        const int ly = q / HXn, lx = q - ly * HXn;
-        const float2 X0 = sDx[ly + 1][lx + 1];
-        const float2 Y0 = sDy[ly + 1][lx + 1], Y1 = sDy[ly + 1][lx + 2];
-        const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];
-        const float exx = rx * X0.x;
-        const float eyy = hy4 * ((Y0.y + Y1.y) + (Z0.y + Z1.y));
-        const float gxy = fmaf(hy4, (Y0.x + Y1.x) + (Z0.x + Z1.x), rx * X0.y);
-        const Stress3 st = stress32(m, exx, eyy, gxy);
-        fHP[ly][lx] = make_float2(st.xx, st.xy);
-        fHQ[ly][lx] = make_float2(st.yy, st.xy);
-        if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
-          se += exx * st.xx + eyy * st.yy + gxy * st.xy;
-      }
-    }
-    for (int q = tid; q < VXn * VYn; q += NTH) {
-      {
-        const int ly = q / VXn, lx = q - ly * VXn;
-        const float2 Y0 = sDy[ly + 1][lx + 1];
-        const float2 X0 = sDx[ly + 1][lx + 1], X1 = sDx[ly + 2][lx + 1];
-        const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];
-        const float exx = hx4 * ((X0.x + X1.x) + (W0.x + W1.x));
-        const float eyy = ry * Y0.y;
-        const float gxy = fmaf(hx4, (X0.y + X1.y) + (W0.y + W1.y), ry * Y0.x);
-        const Stress3 st = stress32(m, exx, eyy, gxy);
-        fVP[ly][lx] = make_float2(st.xx, st.xy);
-        fVQ[ly][lx] = make_float2(st.yy, st.xy);
-        if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
-          se += exx * st.xx + eyy * st.yy + gxy * st.xy;
-      }
-    }
-  } else {
-    // horizontal edges h(ii,jj), ii = i0-1+lx, jj = j0-1+ly:
-    // below element (ii, jj-1) = sst[ly][lx+1], above (ii, jj) = sst[ly+1][lx+1]
-    for (int q = tid; q < HXn * HYn; q += NTH) {
-      {
-        const int ly = q / HXn, lx = q - ly * HXn;
-        const int sb = sst[ly][lx + 1], sa = sst[ly + 1][lx + 1];
-        float4 Ta = make_float4(0.f, 0.f, 0.f, 0.f), Tb = Ta;
-        if (sa == ST_INTACT || sb == ST_INTACT) {
-          const float2 X0 = sDx[ly + 1][lx + 1];                        // (ii,jj)
-          const float2 Y0 = sDy[ly + 1][lx + 1], Y1 = sDy[ly + 1][lx + 2];  // (ii,jj), (ii+1,jj)
-          const float exx = rx * X0.x, cdv = rx * X0.y;
-          float eyy, gxy, w;
-          if (sa == ST_INTACT && sb == ST_INTACT) {
-            const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];      // (ii,jj-1), (ii+1,jj-1)
-            eyy = hy4 * ((Y0.y + Y1.y) + (Z0.y + Z1.y));
-            gxy = fmaf(hy4, (Y0.x + Y1.x) + (Z0.x + Z1.x), cdv);
-            w = 1.f;
-          } else if (sa == ST_INTACT) {
-            eyy = hy2 * (Y0.y + Y1.y);
-            gxy = fmaf(hy2, Y0.x + Y1.x, cdv);
-            w = 0.5f;
-          } else {
-            const float2 Z0 = sDy[ly][lx + 1], Z1 = sDy[ly][lx + 2];
-            eyy = hy2 * (Z0.y + Z1.y);
-            gxy = fmaf(hy2, Z0.x + Z1.x, cdv);
-            w = 0.5f;
-          }
-          const Stress3 s = stress32(m, exx, eyy, gxy);
-          const float4 S = make_float4(s.xx, s.yy, s.xy, 0.f);
-          if (sa == ST_INTACT) Ta = S;
-          if (sb == ST_INTACT) Tb = S;
-          if (ENERGY && lx >= 1 && ly >= 1 && ly <= TY)
-            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
-        }
-        sHAB[ly][lx] = make_float4(Ta.y, Ta.z, Tb.y, Tb.z);
-        sHP[ly][lx] = make_float2(Ta.x + Tb.x, Ta.z + Tb.z);
-      }
-    }
-    // vertical edges v(ii,jj), ii = i0-1+lx, jj = j0-1+ly:
-    // left element (ii-1, jj) = sst[ly+1][lx], right (ii, jj) = sst[ly+1][lx+1]
-    for (int q = tid; q < VXn * VYn; q += NTH) {
-      {
-        const int ly = q / VXn, lx = q - ly * VXn;
-        const int sl = sst[ly + 1][lx], sr = sst[ly + 1][lx + 1];
-        float4 Ta = make_float4(0.f, 0.f, 0.f, 0.f), Tb = Ta;
-        if (sl == ST_INTACT || sr == ST_INTACT) {
-          const float2 Y0 = sDy[ly + 1][lx + 1];                        // (ii,jj)
-          const float2 X0 = sDx[ly + 1][lx + 1], X1 = sDx[ly + 2][lx + 1];  // (ii,jj), (ii,jj+1)
-          const float eyy = ry * Y0.y, cdu = ry * Y0.x;
-          float exx, gxy, w;
-          if (sl == ST_INTACT && sr == ST_INTACT) {
-            const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];      // (ii-1,jj), (ii-1,jj+1)
-            exx = hx4 * ((X0.x + X1.x) + (W0.x + W1.x));
-            gxy = fmaf(hx4, (X0.y + X1.y) + (W0.y + W1.y), cdu);
-            w = 1.f;
-          } else if (sr == ST_INTACT) {
-            exx = hx2 * (X0.x + X1.x);
-            gxy = fmaf(hx2, X0.y + X1.y, cdu);
-            w = 0.5f;
-          } else {
-            const float2 W0 = sDx[ly + 1][lx], W1 = sDx[ly + 2][lx];
-            exx = hx2 * (W0.x + W1.x);
-            gxy = fmaf(hx2, W0.y + W1.y, cdu);
-            w = 0.5f;
-          }
-          const Stress3 s = stress32(m, exx, eyy, gxy);
-          const float4 S = make_float4(s.xx, s.yy, s.xy, 0.f);
-          if (sr == ST_INTACT) Ta = S;
-          if (sl == ST_INTACT) Tb = S;
-          if (ENERGY && lx >= 1 && lx <= TX && ly >= 1)
-            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
-        }
-        sVAB[ly][lx] = make_float4(Ta.x, Ta.z, Tb.x, Tb.z);
-        sVP[ly][lx] = make_float2(Ta.z + Tb.z, Ta.y + Tb.y);
-      }
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-
-  // element forces of the own nodes
-  float fxr[RY], fyr[RY];
-#pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    // edge arrays: edge (i', j') at [j' - (j0-1)][i' - (i0-1)]
-    const int ci = tx + 1, cj = ty + r * BY + 1;
-    float fx, fy;
-    if (!general) {
-      // one stress per edge: the two sides of every edge carry the same sigma
-      // (xx, xy) of h(i-1,j), h(i,j); (yy, xy) of the rows above / below
-      const float2 H1 = fHP[cj][ci - 1], H2 = fHP[cj][ci];
-      const float2 Hu0 = fHQ[cj + 1][ci - 1], Hu1 = fHQ[cj + 1][ci];
-      const float2 Hd0 = fHQ[cj - 1][ci - 1], Hd1 = fHQ[cj - 1][ci];
-      // (yy, xy) of v(i,j-1), v(i,j); (xx, xy) of the columns left / right
-      const float2 V1 = fVQ[cj - 1][ci], V2 = fVQ[cj][ci];
-      const float2 Vl0 = fVP[cj - 1][ci - 1], Vl1 = fVP[cj][ci - 1];
-      const float2 Vr0 = fVP[cj - 1][ci + 1], Vr1 = fVP[cj][ci + 1];
-      fx = (2.f * rx) * (H1.x - H2.x) + hy2 * ((Hd0.y + Hd1.y) - (Hu0.y + Hu1.y)) +
-           (2.f * ry) * (V1.y - V2.y) + hx2 * ((Vl0.x + Vl1.x) - (Vr0.x + Vr1.x));
-      fy = (2.f * rx) * (H1.y - H2.y) + hy2 * ((Hd0.x + Hd1.x) - (Hu0.x + Hu1.x)) +
-           (2.f * ry) * (V1.x - V2.x) + hx2 * ((Vl0.y + Vl1.y) - (Vr0.y + Vr1.y));
-    } else {
-      // the across-edge differences (B - A, L - R) of the node's own four
-      // edges are zero when the four elements around it are all intact or
-      // all not: those nodes skip the per-side loads of these edges
-      const int ey = ty + r * BY + 1, ex = tx + 1;
-      const bool i00 = sst[ey][ex] == ST_INTACT, i01 = sst[ey][ex + 1] == ST_INTACT;
-      const bool i10 = sst[ey + 1][ex] == ST_INTACT, i11 = sst[ey + 1][ex + 1] == ST_INTACT;
-      const bool mixed = !((i00 && i01 && i10 && i11) || !(i00 || i01 || i10 || i11));
-      // h(i-1, j), h(i, j): N is the right / left node of both elements
-      const float2 P1 = sHP[cj][ci - 1], P2 = sHP[cj][ci];
-      if (mixed) {
-        const float4 Q1 = sHAB[cj][ci - 1], Q2 = sHAB[cj][ci];
-        fx = rx * (P1.x - P2.x) + hy2 * ((Q1.w - Q1.y) + (Q2.w - Q2.y));
-        fy = rx * (P1.y - P2.y) + hy2 * ((Q1.z - Q1.x) + (Q2.z - Q2.x));
-      } else {
-        fx = rx * (P1.x - P2.x);
-        fy = rx * (P1.y - P2.y);
-      }
-      // h(i-1, j+1), h(i, j+1): N is a lower node of their below element (B);
-      // h(i-1, j-1), h(i, j-1): N is an upper node of their above element (A)
-      const float2 Bu0 = hi2(sHAB[cj + 1][ci - 1]), Bu1 = hi2(sHAB[cj + 1][ci]);
-      const float2 Ad0 = lo2(sHAB[cj - 1][ci - 1]), Ad1 = lo2(sHAB[cj - 1][ci]);
-      fx += hy2 * ((Ad0.y + Ad1.y) - (Bu0.y + Bu1.y));
-      fy += hy2 * ((Ad0.x + Ad1.x) - (Bu0.x + Bu1.x));
-      // v(i, j-1): N top node; v(i, j): N bottom node of both elements
-      const float2 S1 = sVP[cj - 1][ci], S2 = sVP[cj][ci];
-      if (mixed) {
-        const float4 W1 = sVAB[cj - 1][ci], W2 = sVAB[cj][ci];
-        fx += ry * (S1.x - S2.x) + hx2 * ((W1.z - W1.x) + (W2.z - W2.x));
-        fy += ry * (S1.y - S2.y) + hx2 * ((W1.w - W1.y) + (W2.w - W2.y));
-      } else {
-        fx += ry * (S1.x - S2.x);
-        fy += ry * (S1.y - S2.y);
-      }
-      // v(i-1, j-1), v(i-1, j): N is a right node of their right element (R);
-      // v(i+1, j-1), v(i+1, j): N is a left node of their left element (L)
-      const float2 Rl0 = lo2(sVAB[cj - 1][ci - 1]), Rl1 = lo2(sVAB[cj][ci - 1]);
-      const float2 Lr0 = hi2(sVAB[cj - 1][ci + 1]), Lr1 = hi2(sVAB[cj][ci + 1]);
-      fx += hx2 * ((Rl0.x + Rl1.x) - (Lr0.x + Lr1.x));
-      fy += hx2 * ((Rl0.y + Rl1.y) - (Lr0.y + Lr1.y));
-    }
-    fxr[r] = fx * qA;
-    fyr[r] = fy * qA;
-  }
-
-  if (general) {
-    // forces of the pieces of split elements at the own nodes, added in
-    // increasing element id.  Window element (wx, wy) is (i0-1+wx, j0-1+wy),
-    // its state sst[wy+1][wx+1].  The pieces are evaluated here from their
-    // nodes' displacements, so the update does not wait for the piece kernel.
-    __syncthreads();  // sD is dead: its storage now holds the piece forces
-    constexpr int WXn = C::WXn, NWIN = C::NWIN, KSLOT = C::KSLOT;
-    uint16_t *wlist = T.u2.pc.list, *wmap = T.u2.pc.map;
-    float2 (*slot)[4] = T.u2.pc.slot;
-    int nl = 0;
-    for (int q0 = 0; q0 < NWIN; q0 += NTH) {
-      const int q = q0 + tid;
-      bool cr = false;
-      if (q < NWIN) {
-        const int wy = q / WXn, wx = q - wy * WXn;
-        cr = sst[wy + 1][wx + 1] == ST_CRACKED;
-      }
-      int tot;
-      const int rk = nl + block_rank(cr, tot);
-      if (q < NWIN) wmap[q] = cr ? (uint16_t)rk : (uint16_t)0xffff;
-      if (cr) wlist[rk] = (uint16_t)q;
-      nl += tot;
-    }
-    __syncthreads();
-    for (int base = 0; base < nl; base += KSLOT) {
-      const int nb = nl - base < KSLOT ? nl - base : KSLOT;
-      for (int t = tid; t < 2 * nb; t += NTH) {
-        const int li = base + (t >> 1), p = t & 1;
-        const int q = wlist[li];
-        const int wy = q / WXn, wx = q - wy * WXn;
-        const int c = d.crack_of[(j0 - 1 + wy) * g.nx + i0 - 1 + wx];
-        const int info = d.ck_info[c];
-        Piece32 P;
-        piece32(d, c, p, cur, P);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
-          if (((info >> (4 + a)) & 1) == p)
-            slot[li - base][a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
-        // the tile owns elements [i0, i0+TX) x [j0, j0+TY)
-        if (ENERGY && wx >= 1 && wx <= TX && wy >= 1 && wy <= TY) sep += piece32_energy(P);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < RY; ++r) {
-        // elements (i-1, j-1), (i, j-1), (i-1, j), (i, j) of node (i, j) and
-        // the node's local index in each
-        const int wy0 = ty + r * BY, wx0 = tx;
-        const int dwx[4] = {0, 1, 0, 1}, dwy[4] = {0, 0, 1, 1}, la[4] = {2, 3, 1, 0};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int q = (wy0 + dwy[k]) * WXn + wx0 + dwx[k];
-          if (sst[wy0 + dwy[k] + 1][wx0 + dwx[k] + 1] == ST_CRACKED) {
-            const int li = wmap[q];
-            if (li >= base && li < base + nb) {
-              const float2 F = slot[li - base][la[k]];
-              fxr[r] += F.x;
-              fyr[r] += F.y;
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-
-  double ke = 0.0;  // nodes with loads or prescribed velocities (FP64 path)
-  float ke2 = 0.f;  // 2 KE of the other nodes
-  const float dt = m.dtf;
+  const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
+  // D scaled by A/4: the stresses below are A/4 sigma, so that every edge
+  // term is a force and a piece force adds to it directly
+  Mat mq = d.mat;
+  mq.D11f *= g.qAf;
+  mq.D12f *= g.qAf;
+  mq.D33f *= g.qAf;
+  const float dt = d.mat.dtf;
   const float dtv = first ? 0.5f * dt : dt;
+
+  // stage node row r into ring slot r mod kRing (zeros outside the mesh; v
+  // and 1/m only for the owned nodes), one commit group per row
+  auto stage = [&](int r) {
+    const int q = (r + 4 * kRing) & (kRing - 1);
+    const bool rin = r >= 0 && r <= g.ny;
+    const bool rown = own_lane && r >= j0 && r < j0 + TY;
 #pragma unroll
-  for (int r = 0; r < RY; ++r) {
-    const int j = j0 + ty + r * BY;
-    if (i > g.nx || j > g.ny) continue;
-    const float fx = fxr[r], fy = fyr[r];
-    const int N = j * stride + i;
-    if (own_nf[r]) {
-      ke += update_special(d, N, cur, first, fx, fy, own_u[r], own_v[r], own_mi[r], own_nf[r],
-                           ENERGY ? 1 : 0);
-    } else {
-      const float2 vn = update_plain(d, N, cur, dtv, dt, fx, fy, own_u[r], own_v[r], own_mi[r]);
-      if (ENERGY && own_mi[r] > 0.f) {
-        // KE of the mid-step velocity, FP32 like the velocities themselves
-        const float bx = first ? own_v[r].x : 0.5f * (own_v[r].x + vn.x);
-        const float by = first ? own_v[r].y : 0.5f * (own_v[r].y + vn.y);
-        ke2 += __fdividef(fmaf(bx, bx, by * by), own_mi[r]);
+    for (int k = 0; k < K; ++k) {
+      const int c = c0 + k;
+      const bool in = rin && c >= 0 && c <= g.nx;
+      const int N = in ? r * stride + c : 0;
+      cp_async16(&ring.u[q][k][lane], u4 + N, in ? 16 : 0);
+      const bool mine = in && rown;
+      cp_async8(&ring.v[q][k][lane], d.v2 + N, mine ? 8 : 0);
+      cp_async4(&ring.mi[q][k][lane], d.minvf + N, mine ? 4 : 0);
+    }
+    cp_async_commit();
+  };
+  auto load_es = [&](int r, int k) -> int {  // state of element (c_k, r)
+    const int c = c0 + k;
+    return (c >= 0 && c < g.nx && r >= 0 && r < g.ny) ? (int)d.estate[r * g.nx + c] : (int)ST_OUT;
+  };
+  auto load_nf = [&](int r, int k) -> int {
+    const int c = c0 + k;
+    return (own_lane && c <= g.nx && r >= j0 && r < j0 + TY && r <= g.ny)
+               ? (int)d.nflag[r * stride + c] : 0;
+  };
+
+#pragma unroll
+  for (int q = 0; q <= kAhead; ++q) stage(j0 - 2 + q);  // rows j0-2 .. j0+kAhead-2
+  cp_async_wait<kAhead>();  // row j0 - 2 is in
+  const float2 z2 = make_float2(0.f, 0.f);
+  float4 U1[K];         // u(c_k, t-1)
+  int es1[K], esn[K];   // elements (c_k, t-2) and (c_k, t-1), the latter loaded a row ahead
+  int nf1[K], nf2[K];   // node flags of rows t-1, t-2
+  float2 Dx1[K], Dy2[K];  // Dx(c_k, t-1), Dy(c_k, t-2)
+  // force sums of nodes (c_k, t-2+q), q = 0..2
+  float2 own0[K], own1[K];
+  unsigned long long spmask[K];  // owned rows whose node has a load or prescribed velocity
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    U1[k] = ring.u[(j0 - 2 + 4 * kRing) & (kRing - 1)][k][lane];
+    es1[k] = load_es(j0 - 3, k);
+    esn[k] = load_es(j0 - 2, k);
+    nf1[k] = nf2[k] = 0;
+    Dx1[k] = Dy2[k] = own0[k] = own1[k] = z2;
+    spmask[k] = 0;
+  }
+  float2 DxL1 = z2, DyR2 = z2;  // Dx(c_0 - 1, t-1), Dy(c_{K-1} + 1, t-2)
+  // terms this lane adds for the column right of its last (ua) and left of
+  // its first (da), rows t-2 and t-1
+  float2 ua0 = z2, ua1 = z2, da0 = z2, da1 = z2;
+  unsigned pk_on = 0;  // bit k: element (c_k, t-2) is split; its piece forces come this row
+  bool bad = false;    // some updated velocity is not finite
+  float se = 0.f;      // A/4 eps.sigma of owned edges
+  double ke = 0.0;     // kinetic energy of special nodes
+  float ke2 = 0.f;     // 2 KE of the other nodes
+
+#pragma unroll 1
+  for (int t = j0 - 1; t <= j0 + TY + 1; ++t) {
+    cp_async_wait<kAhead - 1>();  // rows up to t are in
+    const int sl = (t + 4 * kRing) & (kRing - 1);
+    float4 U0[K];
+    int es0[K], nf0[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      U0[k] = ring.u[sl][k][lane];
+      es0[k] = esn[k];  // element (c_k, t-1)
+      esn[k] = load_es(t, k);
+      nf0[k] = load_nf(t, k);
+    }
+    const bool owned_row = ENERGY && t - 1 >= j0 && t - 1 < j0 + TY;
+    // ---- differences: Dx(c_k, t), Dy(c_k, t-1), and the lane's neighbours
+    float2 Dx0[K], Dy1[K];
+    {
+      float4 Ur;  // u(c_{K-1} + 1, t) from the next lane
+      Ur.x = __shfl_down_sync(FULL, U0[0].x, 1);
+      Ur.y = __shfl_down_sync(FULL, U0[0].y, 1);
+      Ur.z = __shfl_down_sync(FULL, U0[0].z, 1);
+      Ur.w = __shfl_down_sync(FULL, U0[0].w, 1);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float4 R = k < K - 1 ? U0[k < K - 1 ? k + 1 : k] : Ur;
+        Dx0[k] = make_float2(df_diff(U0[k].x, U0[k].y, R.x, R.y), df_diff(U0[k].z, U0[k].w, R.z, R.w));
+        Dy1[k] = make_float2(df_diff(U1[k].x, U1[k].y, U0[k].x, U0[k].y),
+                             df_diff(U1[k].z, U1[k].w, U0[k].z, U0[k].w));
       }
     }
+    float2 DyRl, DxLf;  // Dy(c_{K-1} + 1, t-1), Dx(c_0 - 1, t)
+    DyRl.x = __shfl_down_sync(FULL, Dy1[0].x, 1);
+    DyRl.y = __shfl_down_sync(FULL, Dy1[0].y, 1);
+    DxLf.x = __shfl_up_sync(FULL, Dx0[K - 1].x, 1);
+    DxLf.y = __shfl_up_sync(FULL, Dx0[K - 1].y, 1);
+    const int esLf = __shfl_up_sync(FULL, es0[K - 1], 1);  // element (c_0 - 1, t-1)
+    float2 own2[K], ua2 = z2, da2 = z2;  // row t
+#pragma unroll
+    for (int k = 0; k < K; ++k) own2[k] = z2;
+    bool intact = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) intact = intact && es0[k] == ST_INTACT && es1[k] == ST_INTACT;
+    intact = __all_sync(FULL, intact && esLf == ST_INTACT);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 DyR1 = k < K - 1 ? Dy1[k < K - 1 ? k + 1 : k] : DyRl;
+      const float2 DyR2k = k < K - 1 ? Dy2[k < K - 1 ? k + 1 : k] : DyR2;
+      const float2 DxL0 = k > 0 ? Dx0[k > 0 ? k - 1 : k] : DxLf;
+      const float2 DxL1k = k > 0 ? Dx1[k > 0 ? k - 1 : k] : DxL1;
+      const int esL0 = k > 0 ? es0[k > 0 ? k - 1 : k] : esLf;
+      const bool owned_edge = owned_row && own_lane && c0 + k <= g.nx;
+      // right neighbour column's sums (this lane's next column, or ua)
+      float2 &nr0 = k < K - 1 ? own0[k < K - 1 ? k + 1 : k] : ua0;
+      float2 &nr1 = k < K - 1 ? own1[k < K - 1 ? k + 1 : k] : ua1;
+      float2 &nr2 = k < K - 1 ? own2[k < K - 1 ? k + 1 : k] : ua2;
+      float2 &nl1 = k > 0 ? own1[k > 0 ? k - 1 : k] : da1;
+      float2 &nl2 = k > 0 ? own2[k > 0 ? k - 1 : k] : da2;
+      if (intact) {
+        // every element around the row's edges is intact: one averaged
+        // stress per edge (the same sums as below with both sides intact)
+        {  // h(c_k, t-1)
+          const float2 sY = f2add(f2add(Dy1[k], DyR1), f2add(Dy2[k], DyR2k));
+          const float q = 0.5f * hy2;
+          const float exx = rx * Dx1[k].x, eyy = q * sY.y, gxy = fmaf(q, sY.x, rx * Dx1[k].y);
+          const Stress3 s = stress32(mq, exx, eyy, gxy);
+          const float px = rx * (s.xx + s.xx), py = rx * (s.xy + s.xy);
+          f2acc(own1[k], -px, -py);
+          f2acc(nr1, px, py);
+          const float bx = hy2 * s.xy, by = hy2 * s.yy;
+          f2acc(own0[k], -bx, -by);
+          f2acc(nr0, -bx, -by);
+          f2acc(own2[k], bx, by);
+          f2acc(nr2, bx, by);
+          if (owned_edge) se += exx * s.xx + eyy * s.yy + gxy * s.xy;
+        }
+        {  // v(c_k, t-1)
+          const float2 sX = f2add(f2add(Dx1[k], Dx0[k]), f2add(DxL1k, DxL0));
+          const float q = 0.5f * hx2;
+          const float exx = q * sX.x, eyy = ry * Dy1[k].y, gxy = fmaf(q, sX.y, ry * Dy1[k].x);
+          const Stress3 s = stress32(mq, exx, eyy, gxy);
+          const float sx = ry * (s.xy + s.xy), sy = ry * (s.yy + s.yy);
+          f2acc(own1[k], -sx, -sy);
+          f2acc(own2[k], sx, sy);
+          const float rxx = hx2 * s.xx, rxy = hx2 * s.xy;
+          f2acc(nr1, rxx, rxy);
+          f2acc(nr2, rxx, rxy);
+          f2acc(nl1, -rxx, -rxy);
+          f2acc(nl2, -rxx, -rxy);
+          if (owned_edge) se += exx * s.xx + eyy * s.yy + gxy * s.xy;
+        }
+      } else {
+        {  // h(c_k, t-1): above element (c_k, t-1), below (c_k, t-2)
+          const bool ia = es0[k] == ST_INTACT, ib = es1[k] == ST_INTACT, both = ia && ib;
+          const float2 upv = f2add(Dy1[k], DyR1), dnv = f2add(Dy2[k], DyR2k);
+          const float2 sY = both ? f2add(upv, dnv) : (ia ? upv : dnv);
+          const float fy = both ? 0.5f * hy2 : hy2;
+          const float exx = rx * Dx1[k].x, eyy = fy * sY.y, gxy = fmaf(fy, sY.x, rx * Dx1[k].y);
+          const Stress3 s = stress32(mq, exx, eyy, gxy);
+          const Stress3 A = masked(s, ia), B = masked(s, ib);
+          // node (c_k, t-1) is the left node of h, its right neighbour the right node
+          const float tx = hy2 * (B.xy - A.xy), ty = hy2 * (B.yy - A.yy);
+          const float px = rx * (A.xx + B.xx), py = rx * (A.xy + B.xy);
+          f2acc(own1[k], tx - px, ty - py);
+          f2acc(nr1, tx + px, ty + py);
+          // upper nodes of the element below, lower nodes of the element above
+          const float bx = hy2 * B.xy, by = hy2 * B.yy, ax = hy2 * A.xy, ay = hy2 * A.yy;
+          f2acc(own0[k], -bx, -by);
+          f2acc(nr0, -bx, -by);
+          f2acc(own2[k], ax, ay);
+          f2acc(nr2, ax, ay);
+          if (owned_edge) {
+            const float w = both ? 1.f : ((ia || ib) ? 0.5f : 0.f);
+            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
+          }
+        }
+        {  // v(c_k, t-1): right element (c_k, t-1), left (c_k - 1, t-1)
+          const bool ir = es0[k] == ST_INTACT, il = esL0 == ST_INTACT, both = ir && il;
+          const float2 rt = f2add(Dx1[k], Dx0[k]), lt = f2add(DxL1k, DxL0);
+          const float2 sX = both ? f2add(rt, lt) : (ir ? rt : lt);
+          const float fx = both ? 0.5f * hx2 : hx2;
+          const float exx = fx * sX.x, eyy = ry * Dy1[k].y, gxy = fmaf(fx, sX.y, ry * Dy1[k].x);
+          const Stress3 s = stress32(mq, exx, eyy, gxy);
+          const Stress3 R = masked(s, ir), L = masked(s, il);
+          // node (c_k, t-1) is the lower node of v, node (c_k, t) its upper node
+          const float sx = ry * (R.xy + L.xy), sy = ry * (R.yy + L.yy);
+          const float wx = hx2 * (L.xx - R.xx), wy = hx2 * (L.xy - R.xy);
+          f2acc(own1[k], wx - sx, wy - sy);
+          f2acc(own2[k], wx + sx, wy + sy);
+          // left nodes of the element right, right nodes of the element left
+          const float rxx = hx2 * R.xx, rxy = hx2 * R.xy, lxx = hx2 * L.xx, lxy = hx2 * L.xy;
+          f2acc(nr1, rxx, rxy);
+          f2acc(nr2, rxx, rxy);
+          f2acc(nl1, -lxx, -lxy);
+          f2acc(nl2, -lxx, -lxy);
+          if (owned_edge) {
+            const float w = both ? 1.f : ((ir || il) ? 0.5f : 0.f);
+            se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
+          }
+        }
+      }
+    }
+    // ---- pieces of split elements (c_k, t-2), prefetched into L1 one row ago:
+    // local nodes 0 (c_k, t-2), 1 (c_k+1, t-2), 2 (c_k+1, t-1), 3 (c_k, t-1)
+    if (__any_sync(FULL, pk_on != 0)) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if ((pk_on >> k) & 1) {
+          const float4 *q = reinterpret_cast<const float4 *>(d.pfe) + (size_t)((t - 2) * g.nx + c0 + k) * 2;
+          const float4 p0 = q[0], p1 = q[1];
+          float2 &nr0 = k < K - 1 ? own0[k < K - 1 ? k + 1 : k] : ua0;
+          float2 &nr1 = k < K - 1 ? own1[k < K - 1 ? k + 1 : k] : ua1;
+          f2acc(own0[k], p0.x, p0.y);
+          f2acc(nr0, p0.z, p0.w);
+          f2acc(nr1, p1.x, p1.y);
+          f2acc(own1[k], p1.z, p1.w);
+        }
+      }
+    }
+    pk_on = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (es0[k] == ST_CRACKED) {
+        pk_on |= 1u << k;
+        prefetch_l1(d.pfe + (size_t)((t - 1) * g.nx + c0 + k) * 8);
+      }
+    // ---- nodes (c_k, t-2): every edge and piece touching them is in
+    {
+      const float ux = __shfl_up_sync(FULL, ua0.x, 1), uy = __shfl_up_sync(FULL, ua0.y, 1);
+      const float dx = __shfl_down_sync(FULL, da0.x, 1), dy = __shfl_down_sync(FULL, da0.y, 1);
+      own0[0].x += ux; own0[0].y += uy;
+      own0[K - 1].x += dx; own0[K - 1].y += dy;
+    }
+    const int r = t - 2;
+    if (own_lane && r >= j0 && r <= g.ny) {
+      const int s2 = (r + 4 * kRing) & (kRing - 1);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k;
+        if (c > g.nx) continue;
+        const int N = r * stride + c;
+        const float fx = own0[k].x, fy = own0[k].y;
+        if (nf2[k]) {
+          // nodes with loads or prescribed velocities are updated after the
+          // march (FP64 work, out of the loop's registers)
+          d.fsp[N] = make_float2(fx, fy);
+          spmask[k] |= 1ull << (r - j0);
+        } else {
+          const float4 Uo = ring.u[s2][k][lane];
+          const float2 vo = ring.v[s2][k][lane];
+          const float mio = ring.mi[s2][k][lane];
+          const float vxn = fmaf(dtv, -fx * mio, vo.x);
+          const float vyn = fmaf(dtv, -fy * mio, vo.y);
+          d.v2[N] = make_float2(vxn, vyn);
+          bad |= !(fabsf(vxn + vyn) <= FLT_MAX);  // NaN or Inf in either
+          float4 U = Uo;
+          df_add(U.x, U.y, dt * vxn);
+          df_add(U.z, U.w, dt * vyn);
+          d.u4[cur ^ 1][N] = U;
+          if (ENERGY && mio > 0.f) {
+            const float bx = first ? vo.x : 0.5f * (vo.x + vxn);
+            const float by = first ? vo.y : 0.5f * (vo.y + vyn);
+            ke2 += __fdividef(fmaf(bx, bx, by * by), mio);
+          }
+        }
+      }
+    }
+    // ---- the next row in flight, then advance the pipeline by one row
+    stage(t + kAhead);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      U1[k] = U0[k];
+      es1[k] = es0[k];
+      nf2[k] = nf1[k]; nf1[k] = nf0[k];
+      Dx1[k] = Dx0[k];
+      Dy2[k] = Dy1[k];
+      own0[k] = own1[k]; own1[k] = own2[k];
+    }
+    DxL1 = DxLf;
+    DyR2 = DyRl;
+    ua0 = ua1; ua1 = ua2;
+    da0 = da1; da1 = da2;
   }
-  if (ENERGY)
-    block_sum2(ke + 0.5 * (double)ke2, (double)qA * (double)se + sep,
-               d.e_part + 2 * (vb.y * vb.gx + vb.x));
+  cp_async_wait<0>();  // no copy into the ring outlives the tile
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    while (spmask[k]) {
+      const int r = j0 + __ffsll((long long)spmask[k]) - 1;
+      spmask[k] &= spmask[k] - 1;
+      const int N = r * stride + c0 + k;
+      const float2 F = d.fsp[N];
+      ke += update_special(d, N, cur, first, F.x, F.y, u4[N], d.v2[N], d.minvf[N],
+                           (int)d.nflag[N], ENERGY ? 1 : 0);
+    }
+  }
+  // a non-finite velocity (NaN or Inf) is reported through the status word
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(&d.cnt->status, STAT_NONFINITE);
+  if (ENERGY) {
+    double a = ke + 0.5 * (double)ke2, b = (double)se;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(FULL, a, o);
+      b += __shfl_down_sync(FULL, b, o);
+    }
+    if (lane == 0) {
+      part[0] = a;
+      part[1] = b;
+    }
+  }
 }
 
-template <bool ENERGY, int TY>
-__global__ void __launch_bounds__(BX * BY, 4) k_main32(DevState d, int cur,
-                                                                      int first) {
-  // launched as a programmatic dependent of the kernel before it (the
-  // previous step's split writes): wait until that kernel has completed and
-  // its writes are visible; then let the split writes that follow be placed
-  // once every tile CTA has started (they wait for this kernel themselves)
+// A CTA of eight warps takes a group of eight consecutive tiles (tile index
+// = tile row * tiles per row + tile column); warp w marches tile 8 g + w.
+// Neighbouring warps share their halo columns through L1.  Each tile writes
+// its own energy partial pair, tiles past the last write zeros.
+constexpr int kMarchWarps = 4;
+// tile heights: at least 8 node rows (the energy partials are sized for
+// that), at most 64 (one bit per owned row)
+constexpr int kMarchRowsMin = 8, kMarchRowsMax = 64;
+
+__host__ __device__ inline int march_tiles_x(int nx) { return (nx + 1 + WX - 1) / WX; }
+__host__ __device__ inline int march_tiles_y(int ny, int ty) { return (ny + 1 + ty - 1) / ty; }
+__host__ __device__ inline int march_groups(int nx, int ny, int ty) {
+  return (march_tiles_x(nx) * march_tiles_y(ny, ty) + kMarchWarps - 1) / kMarchWarps;
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ void march32_group(const DevState &d, int group, int ty, int cur,
+                                              int first, MarchRing *rings) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tix = group * kMarchWarps + w;
+  const int ntx = march_tiles_x(d.g.nx), nty = march_tiles_y(d.g.ny, ty);
+  double *part = d.e_part + 2 * tix;
+  if (tix < ntx * nty) {
+    march32_tile<ENERGY>(d, tix % ntx, tix / ntx, ty, cur, first, part, rings[w]);
+  } else if (ENERGY && lane == 0) {
+    part[0] = 0.0;
+    part[1] = 0.0;
+  }
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(32 * kMarchWarps, 4) k_march32(DevState d, int cur, int first,
+                                                                  int ty) {
+  // launched as a programmatic dependent of the kernel before it (the piece
+  // forces): wait until that kernel has completed and its writes are
+  // visible; then let the kernels that follow be placed once every CTA of
+  // this kernel has started (they wait for it themselves)
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
-  extern __shared__ float4 smem_dyn[];
-  main32_tile<ENERGY, TY>(d, hw_vblk(), cur, first,
-                          *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn));
+  __shared__ MarchRing rings[kMarchWarps];
+  march32_group<ENERGY>(d, blockIdx.x, ty, cur, first, rings);
 }
 
 // ---------------------------------------------------------------- phantoms
@@ -758,17 +712,14 @@ __device__ __forceinline__ void phantom32(const DevState &d, VBlk vb, int cur, i
   for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
     int N = d.g.nn + t;
     // users' piece-force indices c*16 + p*8 + 2a in increasing element id,
-    // -1 unused: the phantom is local node a of piece p of split c, whose
-    // force there is evaluated here
+    // -1 unused: the phantom is local node a of piece p of split c
     const int4 uf = reinterpret_cast<const int4 *>(d.ph_upf)[t];
     const int ufs[4] = {uf.x, uf.y, uf.z, uf.w};
     float fx = 0.f, fy = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (ufs[q] >= 0) {
-        Piece32 P;
-        piece32_state(d, ufs[q] >> 4, (ufs[q] >> 3) & 1, cur, P);
-        const float2 F = piece32_force(d.g, P, (ufs[q] >> 1) & 3);
+        const float2 F = *reinterpret_cast<const float2 *>(d.pff + ufs[q]);
         fx += F.x;
         fy += F.y;
       }
@@ -788,13 +739,13 @@ __global__ void k_phantom32(DevState d, int cur, int first, int energy, int part
 // ---------------------------------------------------------------- batched
 // One launch per kernel kind for every member of a batch.  The grids are
 // persistent: blocks walk the work list with a stride of the grid size.
-// 1-D items are (member, block, energy-partial offset, member's grid size).
-template <bool ENERGY, int TY>
-__global__ void __launch_bounds__(BX * BY, 4) k_main32_batch(BatchDev b,
-                                                                            int first) {
-  extern __shared__ float4 smem_dyn[];
-  auto &T = *reinterpret_cast<typename Tile<TY>::Smem *>(smem_dyn);
+// 1-D items are (member, block, energy-partial offset, member's grid size);
+// the node update's items are (member, tile group, 0, groups).
+template <bool ENERGY>
+__global__ void __launch_bounds__(32 * kMarchWarps, 4) k_march32_batch(BatchDev b, int first,
+                                                                        int ty) {
   __shared__ DevState sd;
+  __shared__ MarchRing rings[kMarchWarps];
   int held = -1, w0, w1;
   const int n = *b.bstep;
   block_range(b.n_main, w0, w1);
@@ -802,7 +753,21 @@ __global__ void __launch_bounds__(BX * BY, 4) k_main32_batch(BatchDev b,
     const int4 it = b.w_main[w];
     stage_member(b.ds, it.x, sd, held);
     if (!member_active(sd, n)) continue;
-    main32_tile<ENERGY, TY>(sd, item_vblk(it), member_cur(sd, n), first, T);
+    march32_group<ENERGY>(sd, it.y, ty, member_cur(sd, n), first, rings);
+  }
+}
+
+
+__global__ void k_pieces32_batch(BatchDev b, int energy) {
+  __shared__ DevState sd;
+  int held = -1, w0, w1;
+  const int n = *b.bstep;
+  block_range(b.n_pieces, w0, w1);
+  for (int w = w0; w < w1; ++w) {
+    const int4 it = b.w_pieces[w];
+    stage_member(b.ds, it.x, sd, held);
+    if (!member_active(sd, n)) continue;
+    pieces32(sd, VBlk{it.y, 0, it.w, 1}, member_cur(sd, n), energy, it.z);
     __syncthreads();
   }
 }
@@ -826,36 +791,23 @@ int grid_for(int n, int block, int maxb) {
   return b < 1 ? 1 : (b > maxb ? maxb : b);
 }
 
-template <bool ENERGY, int TY>
-cudaError_t set_smem_attr() {
+cudaError_t set_all_smem_attrs() {
   static bool done = false;
   if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(k_main32<ENERGY, TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(typename Tile<TY>::Smem));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_main32_batch<ENERGY, TY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(typename Tile<TY>::Smem));
+    // every kernel of the step asks for one shared-memory split, so that the
+    // side branches can share SMs with the node update
+    cudaError_t e = match_tile_carveout(k_phantom32);
+    if (e == cudaSuccess) e = match_tile_carveout(k_phantom32_batch);
+    if (e == cudaSuccess) e = match_tile_carveout(k_pieces32);
+    if (e == cudaSuccess) e = match_tile_carveout(k_pieces32_batch);
+    if (e == cudaSuccess) e = match_tile_carveout(k_march32<true>);
+    if (e == cudaSuccess) e = match_tile_carveout(k_march32<false>);
+    if (e == cudaSuccess) e = match_tile_carveout(k_march32_batch<true>);
+    if (e == cudaSuccess) e = match_tile_carveout(k_march32_batch<false>);
     if (e != cudaSuccess) return e;
     done = true;
   }
   return cudaSuccess;
-}
-
-cudaError_t set_all_smem_attrs() {
-  static bool side = false;
-  if (!side) {
-    cudaError_t e = match_tile_carveout(k_phantom32);
-    if (e == cudaSuccess) e = match_tile_carveout(k_phantom32_batch);
-    if (e != cudaSuccess) return e;
-    side = true;
-  }
-  cudaError_t e;
-  if ((e = set_smem_attr<true, 16>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<false, 16>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<true, 8>()) != cudaSuccess) return e;
-  return set_smem_attr<false, 8>();
 }
 
 }  // namespace
@@ -863,75 +815,85 @@ cudaError_t set_all_smem_attrs() {
 cudaError_t launch_eval32(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_eval32_batch(const BatchDev &b, cudaStream_t st);
 
+// Tile height of a mesh stepped alone: 8 node rows.  Many short tiles (3-4
+// waves of resident warps on the 2048 x 2048 plate) measured faster than
+// one wave of tall ones (2048^2 step: 65 us at 8 rows, 73 at 16, 96 at 32).
+int march_rows_solo(const DevState &) { return kMarchRowsMin; }
+
+// energy partials of the node update: one per tile, in groups of eight
 int tiles_fp32(const DevState &d, int tile_rows) {
-  return ((d.g.nx + 1 + TX - 1) / TX) * ((d.g.ny + 1 + tile_rows - 1) / tile_rows);
+  return march_groups(d.g.nx, d.g.ny, tile_rows) * kMarchWarps;
+}
+int groups_fp32(const DevState &d, int tile_rows) {
+  return march_groups(d.g.nx, d.g.ny, tile_rows);
 }
 
-// energy partials: tiles of the smallest tile height first, then the
-// phantom update's warps (at most 1216 blocks of kPhWarps)
-int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + kPhWarps * 1216 + 8; }
+// energy partials: tiles of the smallest tile height first, then the piece
+// blocks (at most 1216), then the phantom update's warps (at most 1216
+// blocks of kPhWarps)
+int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + kPhWarps * 1216 + 1216 + 8; }
 
 int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 1216); }
 // side-branch grids: two phantom blocks and one evaluation block per SM, so that
-// they start together with the tile update and share the SMs with it
+// they start together with the node update and share the SMs with it
 int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 304); }
 
 // energy partials one FP32 step writes with the given tile height
 int energy_parts_step_fp32(const DevState &d, int tile_rows) {
-  return tiles_fp32(d, tile_rows) + kPhWarps * grid_phantoms(d);
+  return tiles_fp32(d, tile_rows) + grid_pieces(d) + kPhWarps * grid_phantoms(d);
 }
 
 cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy,
                              const StepStreams &ss, cudaEvent_t *marks) {
-  constexpr int TYs = 16;  // tile height of a mesh stepped alone
-  const dim3 grid((d.g.nx + 1 + TX - 1) / TX, (d.g.ny + 1 + TYs - 1) / TYs);
-  const dim3 block(BX, BY);
-  const int tiles = grid.x * grid.y;  // energy partials of the tiles come first
+  const int ty = march_rows_solo(d);
+  const int groups = groups_fp32(d, ty);
+  const int tiles = groups * kMarchWarps;  // energy partials: tiles, piece blocks, phantom warps
   const int gp = grid_pieces(d);
   const int gph = grid_phantoms(d);
+  const int en = energy ? 1 : 0, f = first ? 1 : 0;
   cudaError_t e = set_all_smem_attrs();
   if (e != cudaSuccess) return e;
-  constexpr size_t smem = sizeof(Tile<TYs>::Smem);
   cudaStream_t st = ss.main;
-  auto main_kernel = [&](cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
+  auto node_update = [&]() {
+    // a programmatic dependent of the piece forces before it on the main stream
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(groups);
+    cfg.blockDim = dim3(32 * kMarchWarps);
+    cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const int f = first ? 1 : 0;
-    if (energy) cudaLaunchKernelEx(&cfg, k_main32<true, TYs>, d, cur, f);
-    else cudaLaunchKernelEx(&cfg, k_main32<false, TYs>, d, cur, f);
+    if (energy) cudaLaunchKernelEx(&cfg, k_march32<true>, d, cur, f, ty);
+    else cudaLaunchKernelEx(&cfg, k_march32<false>, d, cur, f, ty);
   };
   if (marks) {
-    // the pieces' evaluation alone (its energy partials land past the
-    // phantom update's and are not summed), then the step's own kernels
-    k_pieces32<<<gp, 256, 0, st>>>(d, cur, 0, tiles + gph);
+    // the step's kernels one after another
+    k_pieces32<<<gp, 256, 0, st>>>(d, cur, en, tiles);
     cudaEventRecord(marks[0], st);
-    main_kernel(st);
+    node_update();
     cudaEventRecord(marks[1], st);
-    k_phantom32<<<gph, 32 * kPhWarps, 0, st>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
+    k_phantom32<<<gph, 32 * kPhWarps, 0, st>>>(d, cur, f, en, tiles + gp);
     cudaEventRecord(marks[2], st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_eval32(d, cur, st);
   }
-  // the tile update and the phantom update evaluate the pieces they need
-  // themselves, so the three branches start together
+  // the surface evaluation and selection read only the state before the
+  // step (aux2); the piece forces come first on main, then the node update
+  // there and the phantom update (aux1) side by side
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
-  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   e = launch_eval32(d, cur, ss.aux2);
   if (e != cudaSuccess) return e;
   e = launch_select(d, TRACK_STEP, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_phantom32<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(d, cur, first ? 1 : 0, energy ? 1 : 0, tiles);
-  main_kernel(st);
+  k_pieces32<<<gp, 256, 0, st>>>(d, cur, en, tiles);
+  cudaEventRecord(ss.join1, st);
+  cudaStreamWaitEvent(ss.aux1, ss.join1, 0);
+  k_phantom32<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(d, cur, f, en, tiles + gp);
+  node_update();
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
   cudaStreamWaitEvent(st, ss.join1, 0);
@@ -945,28 +907,23 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
                                    int grid_main, const StepStreams &ss) {
   cudaError_t e = set_all_smem_attrs();
   if (e != cudaSuccess) return e;
-  const dim3 block(BX, BY);
   const int gm = grid_main < 1 ? 1 : grid_main;
-  const int gph = grid_for(b.n_ph, 1, 1216);
+  const int gp = grid_for(b.n_pieces, 1, 1216), gph = grid_for(b.n_ph, 1, 1216);
+  const int f = first ? 1 : 0, en = energy ? 1 : 0;
   cudaStream_t st = ss.main;
   cudaEventRecord(ss.fork, st);
   cudaStreamWaitEvent(ss.aux2, ss.fork, 0);
-  cudaStreamWaitEvent(ss.aux1, ss.fork, 0);
   e = launch_eval32_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
   e = launch_select_batch(b, ss.aux2);
   if (e != cudaSuccess) return e;
-  k_phantom32_batch<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(b, first ? 1 : 0, energy ? 1 : 0);
-  const int f = first ? 1 : 0;
-  if (tile_rows == 8) {
-    constexpr size_t sm = sizeof(Tile<8>::Smem);
-    if (energy) k_main32_batch<true, 8><<<gm, block, sm, st>>>(b, f);
-    else k_main32_batch<false, 8><<<gm, block, sm, st>>>(b, f);
-  } else {
-    constexpr size_t sm = sizeof(Tile<16>::Smem);
-    if (energy) k_main32_batch<true, 16><<<gm, block, sm, st>>>(b, f);
-    else k_main32_batch<false, 16><<<gm, block, sm, st>>>(b, f);
-  }
+  k_pieces32_batch<<<gp, 256, 0, st>>>(b, en);
+  cudaEventRecord(ss.join1, st);
+  cudaStreamWaitEvent(ss.aux1, ss.join1, 0);
+  k_phantom32_batch<<<gph, 32 * kPhWarps, 0, ss.aux1>>>(b, f, en);
+  const dim3 block(32 * kMarchWarps);
+  if (energy) k_march32_batch<true><<<gm, block, 0, st>>>(b, f, tile_rows);
+  else k_march32_batch<false><<<gm, block, 0, st>>>(b, f, tile_rows);
   cudaEventRecord(ss.join1, ss.aux1);
   cudaEventRecord(ss.join2, ss.aux2);
   cudaStreamWaitEvent(st, ss.join1, 0);

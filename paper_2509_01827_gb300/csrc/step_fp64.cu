@@ -465,9 +465,10 @@ int energy_parts_needed(const DevState &d) {
 }
 
 int energy_parts_step_fp32(const DevState &d, int tile_rows);
+int march_rows_solo(const DevState &d);
 
 int energy_parts_step(const DevState &d) {
-  if (d.precision == 1) return energy_parts_step_fp32(d, 16);
+  if (d.precision == 1) return energy_parts_step_fp32(d, march_rows_solo(d));
   return tiles_fp64(d) + grid_pieces(d) + grid_phantoms(d);
 }
 

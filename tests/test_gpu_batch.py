@@ -2,8 +2,11 @@
 
 A batch runs one launch per kernel kind for all its members.  Each member
 must end exactly where it ends when stepped alone: bit-identical in FP64
-(fields, masses, cracks, energy records) and, with the same tile height, in
-the FP32-mixed mode too; members stop at their own step limits."""
+(fields, masses, cracks, energy records); in the FP32-mixed mode fields,
+masses and cracks are bit-identical too (a node's arithmetic does not depend
+on the tiling), while the energy records sum FP32 partials per tile, and the
+tile height of a mesh stepped alone is sized to the GPU, so they agree to
+1e-6; members stop at their own step limits."""
 import numpy as np
 import pytest
 
@@ -36,14 +39,19 @@ def _state(s):
     return n, c, e
 
 
-def _assert_same(a, b):
+def _assert_same(a, b, energy_rtol=0.0):
     (na, ca, ea), (nb, cb, eb) = a, b
     for k in ("ux", "uy", "vx", "vy", "m"):
         np.testing.assert_array_equal(na[k], nb[k], err_msg=k)
     for k in ("elem", "ka", "kb", "step", "ud", "nodes"):
         np.testing.assert_array_equal(ca[k], cb[k], err_msg=k)
-    for k in ("step", "KE", "SE", "W_ext", "W_dir", "U_d"):
-        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+    np.testing.assert_array_equal(ea["step"], eb["step"])
+    for k in ("KE", "SE", "W_ext", "W_dir", "U_d"):
+        if energy_rtol:
+            scale = max(np.max(np.abs(eb[k])), 1e-300)
+            np.testing.assert_allclose(ea[k], eb[k], rtol=0, atol=energy_rtol * scale, err_msg=k)
+        else:
+            np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -64,27 +72,30 @@ def test_batch_equals_solo_runs(precision):
     assert b.counts()["step"] == 450
     for m, lim, ref in zip(members, limits, solo):
         assert m.counts()["step"] == lim
-        _assert_same(_state(m), ref)
+        _assert_same(_state(m), ref, energy_rtol=1e-6 if precision == 1 else 0.0)
     assert sum(len(r[1]["elem"]) for r in solo) > 3 * 50  # the notches grew
     b.close()
 
 
-def test_fp32_tile_rows_8_within_tolerance():
-    """Tile height 8 groups some FP32 sums differently: the fields agree with
-    the tile-16 run to the FP32-mixed tolerance before initiation."""
+def test_fp32_tile_rows_give_identical_fields():
+    """The node update's tile height changes which warp marches a node, not
+    the node's arithmetic: FP32-mixed fields are bit-identical for tile
+    heights 8, 16, 32 and 64, through crack initiation."""
     from paper_2509_01827_gb300.cem import CEM_FP32_MIXED, Batch, Solver
     probs = _specimens()
     runs = []
-    for rows in (16, 8):
+    for rows in (16, 8, 32, 64):
         members = [Solver(p, precision=CEM_FP32_MIXED) for p in probs]
         b = Batch(members)
         b.set_config(rows, 152)
-        b.step(120)
-        runs.append([m.nodes() for m in members])
+        b.step(260)
+        runs.append([(m.nodes(), m.cracks()) for m in members])
         b.close()
-    for a, c in zip(*runs):
-        for k in ("ux", "uy"):
-            assert np.max(np.abs(a[k] - c[k])) <= 1e-5 * np.max(np.abs(a[k]))
+    for other in runs[1:]:
+        for (a, ca), (c, cc) in zip(runs[0], other):
+            for k in ("ux", "uy", "vx", "vy", "m"):
+                np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+            np.testing.assert_array_equal(ca["elem"], cc["elem"])
 
 
 def test_autotune_keeps_results_fp64():
