@@ -212,45 +212,45 @@ def fragments(cracks, nx, ny, active=None):
     belong to one fragment when a chain of pieces joins them in which each
     consecutive pair shares a node, real or phantom: shared nodes are shared
     degrees of freedom, so such pieces move together.  Returns (count,
-    labels) with labels a dict piece -> fragment id, ids numbered in order of
-    each fragment's lowest piece."""
-    elem = np.asarray(cracks["elem"])
-    nodes = np.asarray(cracks["nodes"]).reshape(len(elem), 2, 4)
-    split = {int(e): c for c, e in enumerate(elem)}
-    parent = {}
-
-    def find(x):
-        while parent[x] != x:
-            parent[x] = parent[parent[x]]
-            x = parent[x]
-        return x
-
-    def union(x, y):
-        rx, ry = find(x), find(y)
-        if rx != ry:
-            if ry < rx:
-                rx, ry = ry, rx
-            parent[ry] = rx
-
-    pieces = []
-    for e in range(nx * ny):
-        if active is not None and not active[e]:
-            continue
-        i, j = e % nx, e // nx
-        if e in split:
-            lists = [(p, [int(n) for n in nodes[split[e]][p]]) for p in (0, 1)]
-        else:
-            lists = [(0, [(j + _DJ[a]) * (nx + 1) + i + _DI[a] for a in range(4)])]
-        for p, ns in lists:
-            key = ("p", e, p)
-            parent.setdefault(key, key)
-            pieces.append(key)
-            for n in ns:
-                nk = ("n", n)
-                parent.setdefault(nk, nk)
-                union(key, nk)
-    roots = {}
-    labels = {}
-    for key in pieces:
-        labels[(key[1], key[2])] = roots.setdefault(find(key), len(roots))
-    return len(roots), labels
+    labels): labels is an int array of shape (nx*ny, 2), the fragment id of
+    piece (e, p) or -1 where there is no such piece; ids are numbered in
+    increasing order of each fragment's lowest (element, piece)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    ne = nx * ny
+    nn = (nx + 1) * (ny + 1)
+    elem = np.asarray(cracks["elem"], np.int64)
+    nodes = np.asarray(cracks["nodes"], np.int64).reshape(len(elem), 2, 4)
+    act = np.ones(ne, bool) if active is None else np.asarray(active, bool)
+    is_split = np.zeros(ne, bool)
+    is_split[elem] = True
+    e = np.arange(ne)
+    i, j = e % nx, e // nx
+    real = np.stack([j * (nx + 1) + i, j * (nx + 1) + i + 1, (j + 1) * (nx + 1) + i + 1,
+                     (j + 1) * (nx + 1) + i], 1)
+    # piece (e, p) -> vertex 2e + p; node n -> vertex 2 ne + n
+    intact = np.nonzero(act & ~is_split)[0]
+    rows = [np.repeat(2 * intact, 4)]
+    cols = [real[intact].reshape(-1)]
+    live = act[elem]
+    for p in (0, 1):
+        rows.append(np.repeat(2 * elem[live] + p, 4))
+        cols.append(nodes[live, p].reshape(-1))
+    r = np.concatenate(rows)
+    c = 2 * ne + np.concatenate(cols)
+    nv = 2 * ne + max(nn, int(c.max()) - 2 * ne + 1 if len(c) else nn)
+    g = coo_matrix((np.ones(len(r), np.int8), (r, c)), shape=(nv, nv))
+    _, comp = connected_components(g, directed=False)
+    has = np.zeros(2 * ne, bool)
+    has[2 * intact] = True
+    has[2 * elem[live]] = True
+    has[2 * elem[live] + 1] = True
+    pv = np.nonzero(has)[0]                      # piece vertices in (e, p) order
+    ids = np.full(2 * ne, -1, np.int64)
+    _, inv = np.unique(comp[pv], return_inverse=True)
+    # renumber components in order of their lowest piece
+    _, first = np.unique(inv, return_index=True)
+    rank = np.empty(len(first), np.int64)
+    rank[np.argsort(first)] = np.arange(len(first))
+    ids[pv] = rank[inv]
+    return int(len(first)), ids.reshape(ne, 2)
