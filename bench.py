@@ -3,14 +3,21 @@
 
 Workload (default): the 2048 x 2048 Q4 fragmentation plate -- 0.1 m square,
 central hole of radius 5 mm, 50 MPa internal pressure pulse, Weibull G_c
-(mean 3 J/m^2, shape 10, seed 2509) -- run from t = 0.  A "step" is one
-whole explicit step: piece forces, tile update of every real node, phantom
-update, surface evaluation, multi-tip tracking, and an energy record every
-50 steps.  Metric: element-updates/s = active elements * steps / time.
+(mean 3 J/m^2, shape 10, seed 2509).  A "step" is one whole explicit step:
+piece forces, node update of every real node, phantom update, surface
+evaluation, multi-tip tracking, and an energy record every 50 steps.
+Metric: element-updates/s = active elements * steps / time.
 
---impl ours (default): the CUDA library; value from CUDA events around the
-  timed steps (graph replays), roofline of the dominant kernel from a
-  profiled window of the same run, oracle CPU baseline on a bounded sample.
+--impl ours (default): the CUDA library.  After --warmup steps the run is
+  advanced, untimed, past crack initiation until the tip list holds
+  --min-tips tips; the --steps steps that follow are timed with CUDA events
+  (graph replays).  The roofline of the node update comes from a profiled
+  window right after (per-kernel CUDA events), 53 B per element-update
+  (FP32-mixed) over its average launch time.  Beside it: the whole run from
+  t = 0 to 60 us in both precisions (throughput of each, and the FP32 crack
+  pattern against the FP64 one: Jaccard over time, fragments, branching
+  time), one-call-per-step end-to-end throughput, and the CPU oracle on a
+  bounded sample.
 --impl reference: the CPU oracle as it stands (the only reference this
   method has), timed on a bounded sample on this host.
 Multi-GPU (torchrun): one independent replica per GPU (the path does not
@@ -157,12 +164,78 @@ def replica_throughput(units_per_rank, ms_per_rank, world, device="cuda"):
 
 # ------------------------------------------------------------------ ours
 def bytes_per_update(precision):
-    """Algorithmic bytes of the tile kernel per (real node, element) pair."""
+    """Algorithmic bytes per element-update: the state one step must read and
+    write per (real node, element) pair of the structured mesh."""
     if precision == "fp32":
-        # u hi+lo read+write 32, v read+write 16, 1/m 4, node flag 1, element state 1
-        return 54.0
-    # u read+write 32, v read+write 32, 1/m 8, node flag 1, element state 1
-    return 74.0
+        # u hi+lo read+write 32, v read+write 16, 1/m 4; element state 1
+        return 53.0
+    # u read+write 32, v read+write 32, 1/m 8; element state 1
+    return 73.0
+
+
+def measured_traffic(kernel_source):
+    """DRAM bytes (read + write) of one node-update launch from the committed
+    ncu summary, if it was taken on the current kernel source (its SHA-256
+    is recorded beside the figure); None otherwise."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_march32_fragmentation_2048.md")
+    try:
+        text = open(path).read()
+        src = open(kernel_source, "rb").read()
+    except OSError:
+        return None, None
+    vals = {}
+    for line in text.splitlines():
+        for key in ("traffic_bytes_per_launch:", "source_sha256:", "window:"):
+            if line.strip().startswith(key):
+                vals[key] = line.split(":", 1)[1].strip()
+    if vals.get("source_sha256:") != hashlib.sha256(src).hexdigest():
+        return None, None
+    try:
+        return float(vals["traffic_bytes_per_launch:"]), vals.get("window:")
+    except (KeyError, ValueError):
+        return None, None
+
+
+def timed_steps(sol, n, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sol.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def advance_to_tips(sol, min_tips, max_steps, chunk=100):
+    """Steps (untimed) until the tip list holds min_tips tips."""
+    done = 0
+    while done < max_steps and sol.counts()["n_tips"] < min_tips:
+        sol.step(chunk)
+        done += chunk
+    return done
+
+
+def accuracy_block(c32, c64, prob, dt, series_us=(5, 10, 20, 30, 40, 50, 60)):
+    """FP32-mixed against FP64 crack patterns of the same run (Jaccard of the
+    cracked-element sets over time, fragments, branching step)."""
+    from paper_2509_01827_gb300 import metrics
+    out = {"jaccard_end": metrics.jaccard(c32["elem"], c64["elem"]),
+           "cracked_fp32": int(len(c32["elem"])), "cracked_fp64": int(len(c64["elem"]))}
+    ser = []
+    for tus in series_us:
+        s_ = int(round(tus * 1e-6 / dt))
+        a = c32["elem"][c32["step"] <= s_]
+        b = c64["elem"][c64["step"] <= s_]
+        ser.append([tus, round(metrics.jaccard(a, b), 4)])
+    out["jaccard_vs_time_us"] = ser
+    out["fragments_fp32"] = metrics.fragments(c32, prob.nx, prob.ny, prob.active)[0]
+    out["fragments_fp64"] = metrics.fragments(c64, prob.nx, prob.ny, prob.active)[0]
+    for tag, c in (("fp32", c32), ("fp64", c64)):
+        s_ = metrics.branching_step(c, prob.nx, prob.ny, prob.hx, prob.hy, prob.active)
+        out[f"branching_t_us_{tag}"] = None if s_ is None else round(s_ * dt * 1e6, 3)
+    return out
 
 
 def run_ours(args, rank, world):
@@ -181,8 +254,10 @@ def run_ours(args, rank, world):
     sol = Solver(prob, precision=prec, device=dev)
     stream = sol._stream
     nact = prob.n_active
-    # warm-up (also builds the CUDA graphs)
+    # warm-up (also builds the CUDA graphs), then the run is advanced, untimed,
+    # past crack initiation until the tip list holds --min-tips tips
     sol.step(args.warmup)
+    adv = advance_to_tips(sol, args.min_tips, args.max_advance) if args.min_tips > 0 else 0
     torch.cuda.synchronize()
     c0 = sol.counts()
     uuid = None
@@ -212,7 +287,8 @@ def run_ours(args, rank, world):
     c1 = sol.counts()
     launches = c1["kernel_launches"] - c0["kernel_launches"]
 
-    # per-kernel device time over a profiled window of the same run
+    # per-kernel device time over a profiled window right after the timed one
+    # (kernels one after another, CUDA events on the launching stream)
     nprof = max(1, min(args.profile_steps, 4000))
     prof = sol.profile_steps(nprof)
     peaks = measured_peaks()
@@ -220,11 +296,16 @@ def run_ours(args, rank, world):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or HBM_FALLBACK_GBS
     bpu = bytes_per_update(args.precision)
-    units = prob.n_nodes  # one tile-kernel launch updates every real node once
-    bytes_launch = units * bpu
+    bytes_launch = nact * bpu  # one node-update launch advances every active element once
     main_ms = prof["main"] / nprof
     achieved = bytes_launch / (main_ms * 1e-3) / 1e9
     share = prof["main"] / prof["total"] if prof["total"] > 0 else None
+    traffic, traffic_window = (None, None)
+    if args.precision == "fp32":
+        traffic, traffic_window = measured_traffic(
+            os.path.join(ROOT, "paper_2509_01827_gb300", "csrc", "step_fp32.cu"))
+    if args.traffic is not None:
+        traffic, traffic_window = args.traffic, "given on the command line"
 
     # end to end through the C ABI: one cem_step(1) per step from the host,
     # load factors uploaded from pinned host memory and the status word read
@@ -235,47 +316,67 @@ def run_ours(args, rank, world):
     for _ in range(ne2e):
         sol.step(1)
     e2e_val, _ = replica_throughput(nact * ne2e, (time.perf_counter() - t0) * 1e3, world)
-
-    companion = None
-    if args.companion and rank == 0 and world == 1:
-        other = CEM_FP64 if prec == CEM_FP32_MIXED else CEM_FP32_MIXED
-        s2 = Solver(make_problem(args.workload), precision=other, device=dev)
-        s2.step(args.warmup)
-        torch.cuda.synchronize()
-        n2 = args.companion_steps
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(s2._stream)
-        s2.step(n2)
-        f1.record(s2._stream)
-        torch.cuda.synchronize()
-        companion = {"precision": "fp64" if other == CEM_FP64 else "fp32",
-                     "value": nact * n2 / (f0.elapsed_time(f1) * 1e-3), "unit": METRIC,
-                     "steps": n2, "warmup": args.warmup}
-        s2.close()
-
     counts = sol.counts()
     sol.close()
+
+    whole = companion = accuracy = None
+    if args.whole_run and rank == 0 and world == 1:
+        # the whole run from t = 0 to the workload's end time, in this
+        # precision and in the other one (same inputs): throughput of each and
+        # the crack-pattern agreement of the two
+        other = CEM_FP64 if prec == CEM_FP32_MIXED else CEM_FP32_MIXED
+        tabs = {}
+        for pr in (prec, other):
+            s2 = Solver(make_problem(args.workload), precision=pr, device=dev)
+            s2.step(1)
+            n2 = prob.steps - 1
+            ms2 = timed_steps(s2, n2, s2._stream)
+            rate = nact * n2 / (ms2 * 1e-3)
+            tabs[pr] = s2.cracks()
+            dt = s2.counts()["dt"]
+            entry = {"precision": "fp64" if pr == CEM_FP64 else "fp32", "value": rate,
+                     "unit": METRIC, "steps": n2, "t_end_us": round(s2.counts()["t"] * 1e6, 3),
+                     "ms_per_step": ms2 / n2}
+            if pr == prec:
+                whole = entry
+            else:
+                companion = entry
+            s2.close()
+        if args.precision == "fp32":
+            accuracy = accuracy_block(tabs[prec], tabs[other], prob, dt)
+            accuracy["reference"] = ("the FP64 mode of this library on the same run "
+                                     "(bit-identical to the CPU oracle in the parity tests)")
+
     if rank != 0:
         return None
+    cfg = {"workload": args.workload, "mesh": f"{prob.nx}x{prob.ny} Q4",
+           "active_elements": nact, "nodes": prob.n_nodes,
+           "precision": "fp32-mixed (FP32 element math, compensated FP32 displacement)"
+           if args.precision == "fp32" else "fp64",
+           "energy_every": prob.energy_every,
+           "l2": f"inputs larger than L2: state {bpu * nact / 1e6:.0f} MB > 129 MB",
+           "parallelism": f"replicas x{world}",
+           "timed_window": f"{args.steps} steps after the run was advanced untimed past "
+                           f"initiation to >= {args.min_tips} tips",
+           "t_start_us": round(c0["t"] * 1e6, 3), "tips_start": c0["n_tips"],
+           "cracked_start": c0["n_cracked"], "advanced_steps": adv,
+           "t_end_us": round(c1["t"] * 1e6, 3), "tips_end": c1["n_tips"],
+           "cracked_elements_end": c1["n_cracked"]}
+    if accuracy:
+        cfg["crack_pattern_accuracy"] = accuracy
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "mesh": f"{prob.nx}x{prob.ny} Q4",
-                   "active_elements": nact, "nodes": prob.n_nodes,
-                   "precision": "fp32-mixed (FP32 element math, compensated FP32 displacement)"
-                   if args.precision == "fp32" else "fp64",
-                   "energy_every": prob.energy_every,
-                   "l2": f"inputs larger than L2: state {bpu * prob.n_nodes / 1e6:.0f} MB > 129 MB",
-                   "parallelism": f"replicas x{world}",
-                   "cracked_elements_end": counts["n_cracked"], "tips_end": counts["n_tips"],
-                   "t_end_us": counts["t"] * 1e6},
+        "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": args.traffic,
-                     "kernel": "tile update (k_main)", "peak_source": peak_src,
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "traffic_window": traffic_window,
+                     "kernel": "node update (k_march32)" if args.precision == "fp32"
+                     else "tile update (k_main64)", "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_launch,
+                     "bytes_per_element_update": bpu,
                      "avg_launch_ms": main_ms, "share_of_step": share,
                      "profiled_steps": nprof, "per_kernel_ms": prof},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 16,
@@ -286,9 +387,12 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    del counts
     if args.precision == "fp64":
         line["roofline"]["note"] = ("the FP64 tile kernel is bound by the FP64 pipe, "
                                     "not by HBM")
+    if whole:
+        line["whole_run"] = whole
     if companion:
         line["companion"] = companion
     if not args.no_cpu_baseline:
@@ -459,22 +563,26 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=9000)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="fragmentation_2048_neumann")
     ap.add_argument("--profile-steps", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=300)
-    ap.add_argument("--companion", type=int, default=1)
-    ap.add_argument("--companion-steps", type=int, default=100)
+    ap.add_argument("--whole-run", type=int, default=1,
+                    help="also time the whole run in both precisions and compare crack patterns")
+    ap.add_argument("--min-tips", type=int, default=100,
+                    help="advance the run untimed until the tip list holds this many tips")
+    ap.add_argument("--max-advance", type=int, default=6000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--steps-reference", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune-steps", type=int, default=5)
     ap.add_argument("--solo-sample", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu DRAM bytes per launch of the tile kernel, when known")
+                    help="ncu DRAM bytes per launch of the node update, overriding the "
+                         "committed summary")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

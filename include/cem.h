@@ -58,7 +58,10 @@ typedef enum {
   CEM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
   CEM_ERR_CAPACITY = -3,  /* a phantom/crack/list/winner capacity was exceeded */
   CEM_ERR_NONFINITE = -4, /* a displacement or velocity became NaN or Inf */
-  CEM_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  CEM_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up; the solver has no
+                             device-side waits and never returns it (the surrogate
+                             kernels of cem_surrogate.h report theirs through
+                             cem_sg_timeouts) */
   CEM_ERR_STATE = -6      /* call out of order (e.g. stepping before material) */
 } cem_status;
 
@@ -303,7 +306,9 @@ cem_status cem_batch_autotune(cem_handle *batch, int steps_per_candidate, int *t
  * device that loads the library holds until the process exits.  Meshes with
  * ny > CEM_NOALLOC_MAX_NY are rejected with CEM_ERR_ARG.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current); make that first call before any stream capture.  All
+ * the device current); make that first call before any stream capture.  A
+ * cudaDeviceReset unloads the array: the next call finds its cached address
+ * stale and looks it up again (so make that call outside a capture too).  All
  * calls on a device share the array: calls whose work overlaps on the GPU
  * (different streams or host threads without an order between them) race
  * and corrupt each other's results, so order them.  Nothing in the array

@@ -125,8 +125,12 @@ int cem_sg_adam(float *w, const float *g, float *m, float *v, long n, float lr, 
 int cem_sg_set_gemm_path(int use_tcgen05);
 
 /* Number of tcgen05 CTAs whose bounded wait for their MMAs gave up since the
- * library was loaded (their output tile is left unwritten; 0 in a healthy
- * run).  Synchronises with the device. */
+ * library was loaded (0 in a healthy run).  Such a CTA leaves its output
+ * tile unwritten, waits (bounded) for the MMAs it had issued, and frees its
+ * tensor memory only if they finished: the results of any call during which
+ * the count grew are invalid, and the binding's training and inference
+ * check the count around each epoch and evaluation and fail when it grows.
+ * Synchronises with the device. */
 int cem_sg_timeouts(int *count);
 
 /* y = BF16(x), n elements. */

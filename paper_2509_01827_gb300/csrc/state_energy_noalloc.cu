@@ -215,6 +215,12 @@ extern "C" cem_status cem_state_energy_noalloc(int nx, int ny, double hx, double
   double *rows = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_na_mutex);
+    // A cached address that no longer maps to this device's memory (after a
+    // cudaDeviceReset, which unloads the module) is looked up again.
+    if (g_na_rows[dev] && na_check_ptr(g_na_rows[dev], dev)) {
+      cudaGetLastError();
+      g_na_rows[dev] = nullptr;
+    }
     if (!g_na_rows[dev]) {
       // First call on this device: look up the scratch's device address
       // (this device is current).

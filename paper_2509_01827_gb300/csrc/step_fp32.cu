@@ -226,26 +226,33 @@ __device__ __forceinline__ double piece32_energy(const Piece32 &P) {
 }
 
 // Piece forces of every split element, evaluated once per step before the
-// node updates: all eight nodal forces of each piece into pff (the phantom
-// update gathers them), and each real node's force (from the piece on its
-// side) into the element's pfe record (the node update adds them).
+// node updates, one thread per split element: all eight nodal forces of each
+// piece into pff (the phantom update gathers them), and each real node's
+// force (from the piece on its side) into the element's pfe record (the node
+// update adds them).
 __device__ __forceinline__ void pieces32(const DevState &d, VBlk vb, int cur, int energy,
                                          int part_off) {
-  const int n = 2 * d.cnt->n_ck;
+  const int n = d.cnt->n_ck;
   double se = 0.0;
-  for (int t = vb.x * blockDim.x + threadIdx.x; t < n; t += vb.gx * blockDim.x) {
-    const int c = t >> 1, p = t & 1;
-    Piece32 P;
-    piece32(d, c, p, cur, P);
-    float4 *o = reinterpret_cast<float4 *>(d.pff + c * 16 + p * 8);
-    o[0] = make_float4(P.f[0], P.f[1], P.f[2], P.f[3]);
-    o[1] = make_float4(P.f[4], P.f[5], P.f[6], P.f[7]);
+  for (int c = vb.x * blockDim.x + threadIdx.x; c < n; c += vb.gx * blockDim.x) {
     const int info = d.ck_info[c];
-    float2 *r = reinterpret_cast<float2 *>(d.pfe) + (size_t)d.ck_elem[c] * 4;
+    const int e = d.ck_elem[c];
+    float2 fr[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
-      if (((info >> (4 + a)) & 1) == p) r[a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
-    if (energy) se += piece32_energy(P);
+    for (int p = 0; p < 2; ++p) {
+      Piece32 P;
+      piece32(d, c, p, cur, P);
+      float4 *o = reinterpret_cast<float4 *>(d.pff + c * 16 + p * 8);
+      o[0] = make_float4(P.f[0], P.f[1], P.f[2], P.f[3]);
+      o[1] = make_float4(P.f[4], P.f[5], P.f[6], P.f[7]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)  // piece p holds the real nodes of side p
+        if (((info >> (4 + a)) & 1) == p) fr[a] = make_float2(P.f[2 * a], P.f[2 * a + 1]);
+      if (energy) se += piece32_energy(P);
+    }
+    float4 *r = reinterpret_cast<float4 *>(d.pfe) + (size_t)e * 2;
+    r[0] = make_float4(fr[0].x, fr[0].y, fr[1].x, fr[1].y);
+    r[1] = make_float4(fr[2].x, fr[2].y, fr[3].x, fr[3].y);
   }
   if (energy) block_sum2(0.0, se, d.e_part + 2 * (part_off + vb.x));
 }
@@ -665,8 +672,8 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
 // its own energy partial pair, tiles past the last write zeros.
 constexpr int kMarchWarps = 4;
 // tile heights: at least 8 node rows (the energy partials are sized for
-// that), at most 64 (one bit per owned row)
-constexpr int kMarchRowsMin = 8, kMarchRowsMax = 64;
+// that), at most 64 (one bit per owned row; cem_batch_set_config checks it)
+constexpr int kMarchRowsMin = 8;
 
 __host__ __device__ inline int march_tiles_x(int nx) { return (nx + 1 + WX - 1) / WX; }
 __host__ __device__ inline int march_tiles_y(int ny, int ty) { return (ny + 1 + ty - 1) / ty; }
@@ -833,7 +840,10 @@ int groups_fp32(const DevState &d, int tile_rows) {
 // blocks of kPhWarps)
 int energy_parts_fp32(const DevState &d) { return tiles_fp32(d, 8) + kPhWarps * 1216 + 1216 + 8; }
 
-int grid_pieces(const DevState &d) { return grid_for(2 * d.ck_cap, 256, 1216); }
+// piece-force blocks: one thread per split element in FP32, per piece in FP64
+int grid_pieces(const DevState &d) {
+  return grid_for(d.precision == 1 ? d.ck_cap : 2 * d.ck_cap, 256, 1216);
+}
 // side-branch grids: two phantom blocks and one evaluation block per SM, so that
 // they start together with the node update and share the SMs with it
 int grid_phantoms(const DevState &d) { return grid_for(d.ph_cap, 256, 304); }

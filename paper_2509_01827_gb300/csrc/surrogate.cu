@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256) k_conv3x3(ConvArgs a) {
 // reading it are done, which frees the stage for the next copies.  The
 // epilogue reads TMEM with tcgen05.ld (warp w: rows 32w .. 32w+31).  Every
 // mbarrier wait is bounded; a wait that gives up records a timeout
-// (cem_sg_timeouts) and the CTA stops issuing work and frees its TMEM.
+// (cem_sg_timeouts), and the CTA stops issuing work, waits (bounded) for the
+// MMAs already issued, and frees its TMEM only once they are done.
 constexpr int TCM = 128, TCK = 64, TCS = 4;
 constexpr long TC_SPIN = 1L << 24;  // mbarrier polls (with a short sleep) before a wait gives up
 
@@ -322,6 +323,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_tc(ConvArgs a) {
 
   constexpr uint32_t idesc = tc_idesc(TCM, BN);
   bool failed = false;
+  int last_kb = -1;  // the last stage whose MMAs were issued
 #pragma unroll
   for (int s = 0; s < TCS - 1; ++s) {
     if (s < KB) load_stage(s, s);
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_tc(ConvArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_u32(&T.mma_bar[s])));
     }
+    last_kb = kb;
     const int nk = kb + TCS - 1;
     if (nk < KB) {
       if (kb >= 1 && !mbar_wait(&T.mma_bar[(kb - 1) % TCS], ((kb - 1) / TCS) & 1)) {
@@ -437,9 +440,16 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_tc(ConvArgs a) {
   } else if (tid == 0) {
     atomicAdd(&g_tc_timeouts, 1);
   }
+  // After a wait gave up, MMAs may still be in flight: wait (bounded) for the
+  // last issued commit, which tracks every earlier MMA, before the TMEM is
+  // freed; if that wait gives up too, the CTA exits without freeing it (the
+  // results of the call are invalid in either case; cem_sg_timeouts says so).
+  bool drained = true;
+  if (failed && last_kb >= 0)
+    drained = __syncthreads_and(mbar_wait(&T.mma_bar[last_kb % TCS], (last_kb / TCS) & 1)) != 0;
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
-  if (warp == 0)
+  if (warp == 0 && drained)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
 }
 
@@ -712,6 +722,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_wgrad_tc(WgradArgs a) {
 
   constexpr uint32_t idesc = tc_idesc_mn(WTM, BN);
   bool failed = false;
+  int last_kb = -1;  // the last stage whose MMAs were issued
 #pragma unroll
   for (int s = 0; s < TCS - 1; ++s) {
     if (s < KB) load_stage(s, s);
@@ -739,6 +750,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_wgrad_tc(WgradArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_u32(&T.mma_bar[s])));
     }
+    last_kb = kb;
     const int nk = kb + TCS - 1;
     if (nk < KB) {
       if (kb >= 1 && !mbar_wait(&T.mma_bar[(kb - 1) % TCS], ((kb - 1) / TCS) & 1)) failed = true;
@@ -786,9 +798,16 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3_wgrad_tc(WgradArgs a) {
   } else if (tid == 0) {
     atomicAdd(&g_tc_timeouts, 1);
   }
+  // After a wait gave up, MMAs may still be in flight: wait (bounded) for the
+  // last issued commit, which tracks every earlier MMA, before the TMEM is
+  // freed; if that wait gives up too, the CTA exits without freeing it (the
+  // results of the call are invalid in either case; cem_sg_timeouts says so).
+  bool drained = true;
+  if (failed && last_kb >= 0)
+    drained = __syncthreads_and(mbar_wait(&T.mma_bar[last_kb % TCS], (last_kb / TCS) & 1)) != 0;
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
-  if (warp == 0)
+  if (warp == 0 && drained)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
 }
 

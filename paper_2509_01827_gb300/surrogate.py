@@ -65,6 +65,24 @@ def _ok(rc, what):
         raise RuntimeError(f"{what} failed with {rc}")
 
 
+def timeouts() -> int:
+    """Tensor-core CTAs whose bounded MMA wait gave up since the library was
+    loaded (their outputs are invalid).  Synchronises with the device."""
+    n = C.c_int(0)
+    _ok(sg().cem_sg_timeouts(C.byref(n)), "cem_sg_timeouts")
+    return n.value
+
+
+def check_timeouts(before: int, what: str) -> int:
+    """Raises if the time-out count grew past `before` during `what`; returns
+    the current count."""
+    now = timeouts()
+    if now != before:
+        raise RuntimeError(f"{now - before} tensor-core wait(s) gave up during {what}: "
+                           "its results are invalid")
+    return now
+
+
 def _p(t, off_elems=0):
     """Device address of tensor t, plus an element offset."""
     return t.data_ptr() + off_elems * t.element_size()

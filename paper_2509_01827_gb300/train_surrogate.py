@@ -105,8 +105,11 @@ def generate(seeds, chunk=256, device=0, log=print):
 
 
 def predict(net, X, B):
-    """Logits of every run of X (padded to whole batches)."""
+    """Logits of every run of X (padded to whole batches); fails if a
+    tensor-core wait gave up meanwhile."""
     import torch
+    from .surrogate import check_timeouts, timeouts
+    t0 = timeouts()
     n = X.shape[0]
     out = torch.empty((n, X.shape[1]), dtype=torch.float32, device=X.device)
     for c0 in range(0, n, B):
@@ -116,6 +119,7 @@ def predict(net, X, B):
             net.x8[k * X.shape[1]:].zero_()
         net.forward()
         out[c0:c0 + k].copy_(net.z[: k * X.shape[1]].reshape(k, -1))
+    check_timeouts(t0, "inference")
     return out
 
 
@@ -192,7 +196,7 @@ def main():
     args = ap.parse_args()
     import torch
     from . import build as _build
-    from .surrogate import UNet
+    from .surrogate import UNet, check_timeouts, timeouts
     _build.build()
     torch.cuda.set_device(0)
     log = lambda m: print(m, flush=True)
@@ -220,6 +224,7 @@ def main():
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     it = 0
+    tmo = timeouts()
     for ep in range(args.epochs):
         perm = torch.from_numpy(rng.permutation(ntr)).to(Xtr.device)
         ep_loss = torch.zeros((), dtype=torch.float32, device=Xtr.device)
@@ -238,6 +243,7 @@ def main():
             ep_loss += loss[0]
             it += 1
         hist.append(float(ep_loss.item()) / steps_per_epoch)
+        tmo = check_timeouts(tmo, f"training epoch {ep}")
         log(f"epoch {ep}: loss {hist[-1]:.4f}")
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1

@@ -77,6 +77,32 @@ def test_batch_equals_solo_runs(precision):
     b.close()
 
 
+def test_batch_members_equal_the_oracle_fp64():
+    """Each FP64 member of a batch against the CPU oracle directly (not only
+    against its own solo run): fields, masses, crack and phantom tables and
+    energies identical.  One member is drawn at the 400 x 160 end of the
+    64-specimen batch's size range (the largest mesh that batch holds)."""
+    from tests._parity import compare_energy, compare_fp64
+    from oracle.oracle import from_problem
+    from paper_2509_01827_gb300.cem import Batch, Solver
+    probs = _specimens()[:2]
+    big = inputs.notched_plate(400, 160, notch_len=0.04, traction=2.5e6, steps=0,
+                               phantom_cap=40000, crack_cap=16000)
+    big.energy_every = 10
+    probs.append(big)
+    limits = [300, 220, 420]
+    members = [Solver(p) for p in probs]
+    b = Batch(members, step_end=limits)
+    b.step(max(limits))
+    for p, m, lim in zip(probs, members, limits):
+        o = from_problem(p)
+        o.step(lim)
+        compare_fp64(o, m)
+        compare_energy(o, m)
+    assert members[2].counts()["n_cracked"] > 170  # the notch row plus growth
+    b.close()
+
+
 def test_fp32_tile_rows_give_identical_fields():
     """The node update's tile height changes which warp marches a node, not
     the node's arithmetic: FP32-mixed fields are bit-identical for tile

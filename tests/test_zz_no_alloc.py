@@ -1,14 +1,19 @@
-"""The allocation-free energy entry point against the handle API (needs a GPU).
+"""The allocation-free energy entry point against the CPU oracle (needs a GPU).
 
 cem_state_energy_noalloc serves callers that cannot allocate device memory
 (an application whose device memory all belongs to its own fixed arena, or a
 monitor that must not call cudaMalloc / cudaFree, which synchronise the
 device, while other streams run).  It keeps its scratch in one fixed device
-array shared by every call.  Here two calls in a row, on meshes of different
-sizes (the second smaller, so stale rows of the first call stay in the
-scratch), must give the KE and SE that the handle API records at step 0 for
-the same state, to 1e-12 relative (the same FP64 arithmetic, partial sums
-grouped differently).
+array shared by every call.  Here calls in a row, on meshes of different
+sizes (each smaller than the one before, so stale rows of the earlier call
+stay in the scratch), must give the oracle's strain energy of the state
+(orc_strain_energy: ES-FEM edge strains, A/4 of each edge point per element)
+and its kinetic energy 1/2 sum m |v|^2 with the oracle's lumped masses, to
+1e-12 relative (the same FP64 arithmetic, partial sums grouped differently),
+and the KE and SE the handle API records at step 0 for the same state.  The
+last case is a 3 x 2 mesh with a hole at the boundary, where the lumped
+mass of a node and the edges that are smoothed depend on which neighbours
+are missing.
 
 This file is named so that pytest collects it last."""
 import numpy as np
@@ -49,6 +54,17 @@ def _handle_energy(p, u, v):
     return e["KE"][0], e["SE"][0]
 
 
+def _oracle_energy(p, u, v):
+    """The oracle's SE of u and 1/2 sum m |v|^2 with its lumped masses."""
+    from oracle.oracle import from_problem
+    o = from_problem(p)
+    n = p.n_nodes
+    o.set_state(ux=u[:n], uy=u[n:], vx=v[:n], vy=v[n:])
+    m = o.nodes()["m"]
+    ke = 0.5 * float(np.sum(m * (v[:n] ** 2 + v[n:] ** 2)))
+    return ke, o.strain_energy()
+
+
 def _noalloc_energy(p, u, v):
     import torch
     from paper_2509_01827_gb300 import cem
@@ -70,22 +86,28 @@ def _noalloc_energy(p, u, v):
 
 
 @pytest.mark.gpu
-def test_two_calls_in_a_row_match_the_handle_api(_built):
+def test_calls_in_a_row_match_the_oracle_and_the_handle_api(_built):
     import torch
     torch.cuda.init()
+    edge_hole = np.ones(6, np.uint8)
+    edge_hole[2] = 0                                                 # corner element out
     cases = [
         _case(40, 40, inputs.hole_mask(40, 0.04, 0.008), True, 11),  # plate with a hole
         _case(20, 13, None, False, 12),                              # fewer rows, plane stress
+        _case(3, 2, edge_hole, True, 13),                            # hole at the boundary
     ]
-    expected = [_handle_energy(*c) for c in cases]
-    got = [_noalloc_energy(*c) for c in cases]  # two calls in a row
-    for (ke_h, se_h), (ke, se, grown) in zip(expected, got):
-        assert ke_h > 0 and se_h > 0
+    oracle = [_oracle_energy(*c) for c in cases]
+    handle = [_handle_energy(*c) for c in cases]
+    got = [_noalloc_energy(*c) for c in cases]  # calls in a row
+    for (ke_o, se_o), (ke_h, se_h), (ke, se, grown) in zip(oracle, handle, got):
+        assert ke_o > 0 and se_o > 0
+        assert abs(ke - ke_o) <= REL * ke_o, (ke, ke_o)
+        assert abs(se - se_o) <= REL * se_o, (se, se_o)
         assert abs(ke - ke_h) <= REL * ke_h, (ke, ke_h)
         assert abs(se - se_h) <= REL * se_h, (se, se_h)
-    # the second call found the scratch already set up: device memory in use
-    # did not grow during it
-    assert got[1][2] == 0
+    # later calls found the scratch already set up: device memory in use did
+    # not grow during them
+    assert got[1][2] == 0 and got[2][2] == 0
 
 
 def test_rejects_meshes_beyond_the_scratch_limit(_built):
