@@ -230,8 +230,6 @@ def accuracy_block(c32, c64, prob, dt, series_us=(5, 10, 20, 30, 40, 50, 60)):
         b = c64["elem"][c64["step"] <= s_]
         ser.append([tus, round(metrics.jaccard(a, b), 4)])
     out["jaccard_vs_time_us"] = ser
-    out["fragments_fp32"] = metrics.fragments(c32, prob.nx, prob.ny, prob.active)[0]
-    out["fragments_fp64"] = metrics.fragments(c64, prob.nx, prob.ny, prob.active)[0]
     for tag, c in (("fp32", c32), ("fp64", c64)):
         s_ = metrics.branching_step(c, prob.nx, prob.ny, prob.hx, prob.hy, prob.active)
         out[f"branching_t_us_{tag}"] = None if s_ is None else round(s_ * dt * 1e6, 3)
@@ -334,9 +332,15 @@ def run_ours(args, rank, world):
             rate = nact * n2 / (ms2 * 1e-3)
             tabs[pr] = s2.cracks()
             dt = s2.counts()["dt"]
+            en = s2.energy()
+            nfrag, _ = s2.fragments(labels=False)
             entry = {"precision": "fp64" if pr == CEM_FP64 else "fp32", "value": rate,
                      "unit": METRIC, "steps": n2, "t_end_us": round(s2.counts()["t"] * 1e6, 3),
-                     "ms_per_step": ms2 / n2}
+                     "ms_per_step": ms2 / n2, "fragments_end": nfrag,
+                     # dissipated energy U_d (J/m) and KE, SE, W_ext over time
+                     "energy_series": [[round(float(en["t"][q]) * 1e6, 2)] +
+                                       [float(en[k][q]) for k in ("U_d", "KE", "SE", "W_ext")]
+                                       for q in range(0, len(en["t"]), max(1, len(en["t"]) // 12))]}
             if pr == prec:
                 whole = entry
             else:
@@ -344,6 +348,8 @@ def run_ours(args, rank, world):
             s2.close()
         if args.precision == "fp32":
             accuracy = accuracy_block(tabs[prec], tabs[other], prob, dt)
+            accuracy["fragments_fp32"] = whole["fragments_end"]
+            accuracy["fragments_fp64"] = companion["fragments_end"]
             accuracy["reference"] = ("the FP64 mode of this library on the same run "
                                      "(bit-identical to the CPU oracle in the parity tests)")
 

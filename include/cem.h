@@ -138,7 +138,15 @@ typedef enum {
   CEM_FIELD_MASS = 2,    /* double[n_nodes_total] (get only) */
   CEM_FIELD_STATE = 3,   /* uint8[nx*ny]: 0 intact, 1 split, 2 inactive (get only) */
   CEM_FIELD_ENERGY = 4,  /* double[7 * n_energy]: step, t, KE, SE, W_ext, W_dir, U_d */
-  CEM_FIELD_GC = 5       /* float[nx*ny] (get only) */
+  CEM_FIELD_GC = 5,      /* float[nx*ny] (get only) */
+  CEM_FIELD_SIGMA = 6,   /* double[3 * nx*ny]: element mean stress sxx[ne], syy[ne],
+                            sxy[ne] (Pa; get only): an intact element averages over its
+                            four edge points the stress its internal force uses there
+                            (Eqs. 1-2 smoothing applied); a split element weights its
+                            pieces' means by their areas; inactive elements 0 */
+  CEM_FIELD_SIGMA1 = 7   /* double[nx*ny]: largest principal value of that stress,
+                            (sxx+syy)/2 + sqrt(((sxx-syy)/2)^2 + sxy^2) (the stress
+                            contours of Sec. 4; get only) */
 } cem_field;
 
 /* Sets initial u or v of all current nodes before the first step.
@@ -323,6 +331,42 @@ cem_status cem_state_energy_noalloc(int nx, int ny, double hx, double hy,
                                     double nu, double rho, int plane_strain,
                                     const double *u, const double *v, double *out,
                                     void *cuda_stream, char *err, int err_len);
+
+/* Fragments of the cracked body (Sec. 4.4 reports fragment counts, Table
+ * 1).  A piece is an intact active element, or one side of a split element
+ * (its node list: real nodes on that side, phantom copies of the others);
+ * pieces that share a node, real or phantom, move together, and a fragment
+ * is a connected set of pieces under that relation.  *n_fragments = their
+ * number; piece_fragment (host, may be NULL; cap >= 2 * nx * ny entries)
+ * receives the fragment of piece 2 e + p (p = 0 for an intact element, p =
+ * side for a split one; -1 where there is no such piece), fragments numbered
+ * in increasing order of their lowest piece.  Computed on the device by a
+ * union-find over the nodes.  Errors: CEM_ERR_ARG (cap too small),
+ * CEM_ERR_STATE (batch handle), CEM_ERR_CUDA. */
+cem_status cem_get_fragments(cem_handle *h, int *n_fragments, int *piece_fragment, long cap);
+
+/* Checkpoint and restart of a run (the paper has none: a library service,
+ * so that a long explicit run can be stopped and resumed).  The state blob
+ * holds the step counter and every quantity that carries over from one step
+ * to the next: displacements and velocities of real and phantom nodes (the
+ * current buffer), lumped masses and their inverses, boundary-work
+ * accumulators, element states, the split-element table, the phantom table,
+ * the surface / tip list, and the energy records.  The mesh, material and
+ * loads are not in it: load into a handle built with the same descriptor,
+ * material and loads.  A run of 2N steps and a run of N steps, saved,
+ * loaded into a fresh handle and run N more steps end bit-identical.
+ *
+ * cem_state_size: *n_bytes = the blob size at the current step (it grows
+ * with the splits).  cem_save_state: writes the blob into the caller's host
+ * buffer blob of n_bytes (>= the size).  cem_load_state: replaces the
+ * handle's state by the blob's (copied; the caller keeps the buffer).
+ * Errors: CEM_ERR_ARG (buffer too small, not a blob, another mesh, precision
+ * or time step), CEM_ERR_CAPACITY (the blob's phantoms, splits, list entries
+ * or records exceed the handle's capacities), CEM_ERR_STATE (no material,
+ * or a batch / batch member), CEM_ERR_CUDA. */
+cem_status cem_state_size(cem_handle *h, long *n_bytes);
+cem_status cem_save_state(cem_handle *h, void *blob, long n_bytes);
+cem_status cem_load_state(cem_handle *h, const void *blob, long n_bytes);
 
 /* Message of the last failure on h (or of the last failed create when h is
  * NULL).  Valid until the next call on h. */

@@ -69,6 +69,8 @@ int orc_eval_surface(orc_sim *s, int *edge, int *ahead, int *k0, double *G4,
 int orc_apply_proposals(orc_sim *s, int n, const int *edge, const int *elem,
                         const int *k, const double *G);
 int orc_strain_energy(orc_sim *s, double *se);
+/* mean stress of each element (see the definition in cem_oracle.c) */
+int orc_element_stress(orc_sim *s, double *sxx, double *syy, double *sxy);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,7 @@ def lib():
         L.orc_get_energy.argtypes = [C.c_void_p, _dp]
         L.orc_internal_force.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_strain_energy.argtypes = [C.c_void_p, _dp]
+        L.orc_element_stress.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.orc_eval_surface.argtypes = [C.c_void_p, _ip, _ip, _ip, _dp, _ip]
         L.orc_apply_proposals.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _ip, _dp]
         _LIB = L
@@ -184,6 +185,13 @@ class OracleSim:
         se = np.zeros(1)
         self._chk(lib().orc_strain_energy(self._h, _p(se, _dp)))
         return float(se[0])
+
+    def element_stress(self):
+        """Mean stress (sxx, syy, sxy) of every element, shape (ne, 3)."""
+        ne = self.nx * self.ny
+        out = [np.zeros(ne) for _ in range(3)]
+        self._chk(lib().orc_element_stress(self._h, *[_p(a, _dp) for a in out]))
+        return np.stack(out, 1)
 
     def eval_surface(self):
         n = self.counts()["n_surface"]

@@ -26,6 +26,7 @@ UNITS = [
     ("eval_fp32.cu", ["-fmad=false"]),
     ("state_energy_noalloc.cu", ["-fmad=false"]),
     ("surrogate.cu", []),
+    ("fragments.cu", []),
     ("api.cpp", []),
 ]
 HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh"]

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libcem.so")
 CEM_OK, CEM_ERR_ARG, CEM_ERR_CUDA, CEM_ERR_CAPACITY = 0, -1, -2, -3
 CEM_ERR_NONFINITE, CEM_ERR_TIMEOUT, CEM_ERR_STATE = -4, -5, -6
 CEM_FP64, CEM_FP32_MIXED = 0, 1
-CEM_FIELD_U, CEM_FIELD_V, CEM_FIELD_MASS, CEM_FIELD_STATE, CEM_FIELD_ENERGY, CEM_FIELD_GC = range(6)
+(CEM_FIELD_U, CEM_FIELD_V, CEM_FIELD_MASS, CEM_FIELD_STATE, CEM_FIELD_ENERGY, CEM_FIELD_GC,
+ CEM_FIELD_SIGMA, CEM_FIELD_SIGMA1) = range(8)
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -92,6 +93,10 @@ SIGNATURES = {
                                            C.c_double, C.c_double, C.c_double, C.c_int,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_char_p, C.c_int]),
+    "cem_get_fragments": (C.c_int, [_h, _ip, _ip, C.c_long]),
+    "cem_state_size": (C.c_int, [_h, C.POINTER(C.c_long)]),
+    "cem_save_state": (C.c_int, [_h, C.c_void_p, C.c_long]),
+    "cem_load_state": (C.c_int, [_h, C.c_void_p, C.c_long]),
     "cem_last_error": (C.c_char_p, [_h]),
     "cem_mesh_destroy": (None, [_h]),
 }
@@ -178,6 +183,10 @@ def cem_get_fields(h, which, n_nodes_total=None, n_elems=None, n_energy=None):
         out = np.empty(7 * n_energy)
     elif which == CEM_FIELD_GC:
         out = np.empty(n_elems, np.float32)
+    elif which == CEM_FIELD_SIGMA:
+        out = np.empty(3 * n_elems)
+    elif which == CEM_FIELD_SIGMA1:
+        out = np.empty(n_elems)
     else:
         raise ValueError(which)
     _chk(h, lib().cem_get_fields(h, which, out.ctypes.data, out.nbytes, 0))
@@ -263,6 +272,33 @@ def cem_state_energy_noalloc(nx, ny, hx, hy, elem_active_ptr, E, nu, rho, plane_
                                         stream_ptr or None, err, len(err))
     if rc != CEM_OK:
         raise CemError(rc, err.value.decode())
+
+
+def cem_get_fragments(h, n_elems, labels=True):
+    """(number of fragments, labels of the pieces 2 e + p or None)."""
+    n = C.c_int()
+    lab = np.empty(2 * n_elems, np.int32) if labels else None
+    _chk(h, lib().cem_get_fragments(h, C.byref(n), _p(lab, _ip), 0 if lab is None else len(lab)))
+    return n.value, lab
+
+
+def cem_state_size(h) -> int:
+    n = C.c_long()
+    _chk(h, lib().cem_state_size(h, C.byref(n)))
+    return n.value
+
+
+def cem_save_state(h) -> bytes:
+    """The run's state blob (include/cem.h: cem_save_state)."""
+    n = cem_state_size(h)
+    buf = (C.c_char * n)()
+    _chk(h, lib().cem_save_state(h, buf, n))
+    return bytes(buf)
+
+
+def cem_load_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _chk(h, lib().cem_load_state(h, buf, len(blob)))
 
 
 def cem_mesh_destroy(h):
@@ -395,6 +431,15 @@ class Solver:
     def state(self):
         return cem_get_fields(self.h, CEM_FIELD_STATE, n_elems=self.prob.nx * self.prob.ny)
 
+    def element_stress(self):
+        """Element mean stress, shape (ne, 3): sxx, syy, sxy."""
+        ne = self.prob.nx * self.prob.ny
+        return cem_get_fields(self.h, CEM_FIELD_SIGMA, n_elems=ne).reshape(3, ne).T.copy()
+
+    def sigma1(self):
+        """Largest principal value of the element mean stress, shape (ne,)."""
+        return cem_get_fields(self.h, CEM_FIELD_SIGMA1, n_elems=self.prob.nx * self.prob.ny)
+
     def energy(self):
         n = self.counts()["n_energy"]
         rec = cem_get_fields(self.h, CEM_FIELD_ENERGY, n_energy=n).reshape(n, 7)
@@ -434,6 +479,17 @@ class Solver:
 
     def profile_steps(self, n):
         return cem_profile_steps(self.h, n)
+
+    def fragments(self, labels=True):
+        """(number of fragments, piece labels of shape (ne, 2) or None)."""
+        n, lab = cem_get_fragments(self.h, self.prob.nx * self.prob.ny, labels)
+        return n, None if lab is None else lab.reshape(-1, 2)
+
+    def save_state(self) -> bytes:
+        return cem_save_state(self.h)
+
+    def load_state(self, blob: bytes):
+        cem_load_state(self.h, blob)
 
     def debug_apply_proposals(self, edge, elem, k, G):
         cem_debug_apply_proposals(self.h, edge, elem, k, G)

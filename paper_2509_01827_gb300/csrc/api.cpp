@@ -857,6 +857,8 @@ cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int
     case CEM_FIELD_STATE: need = d.g.ne; break;
     case CEM_FIELD_ENERGY: need = 56L * h->h_cnt->n_rec; break;
     case CEM_FIELD_GC: need = 4L * d.g.ne; break;
+    case CEM_FIELD_SIGMA: need = 24L * d.g.ne; break;
+    case CEM_FIELD_SIGMA1: need = 8L * d.g.ne; break;
     default: return fail(h, CEM_ERR_ARG, "unknown field %d", which);
   }
   if (n_bytes < need) return fail(h, CEM_ERR_ARG, "buffer too small: need %ld bytes", need);
@@ -882,10 +884,215 @@ cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int
     CUDA_TRY(h, cudaMemcpyAsync(o, d.estate, d.g.ne, kind, h->st));
   } else if (which == CEM_FIELD_ENERGY) {
     if (need) CUDA_TRY(h, cudaMemcpyAsync(o, d.erec, need, kind, h->st));
+  } else if (which == CEM_FIELD_SIGMA || which == CEM_FIELD_SIGMA1) {
+    double *tmp = (double *)scratch(h, (size_t)d.g.ne * 32);
+    if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+    CUDA_TRY(h, launch_element_stress(d, h->cur, tmp, h->st));
+    const double *src = which == CEM_FIELD_SIGMA ? tmp : tmp + 3 * (size_t)d.g.ne;
+    CUDA_TRY(h, cudaMemcpyAsync(o, src, need, kind, h->st));
   } else {
     CUDA_TRY(h, cudaMemcpyAsync(o, d.gc, need, kind, h->st));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+// ------------------------------------------------------------- checkpoint
+// The state blob: a header, the counters, then every array that evolves from
+// step to step, each cut to the entries in use, in a fixed order.  Arrays
+// that a step recomputes before it reads them (piece forces, proposals,
+// plans, energy partials) are not saved.
+namespace {
+
+constexpr unsigned kBlobMagic = 0x53454d43u;  // "CEMS"
+constexpr int kBlobVersion = 1;
+
+struct BlobHeader {
+  unsigned magic;
+  int version, precision, nx, ny, nn, ne, ned;
+  int n_ph, n_ck, n_S, n_rec;
+  long step;
+  double dt;
+  int pad[6];
+};
+
+struct BlobPart {
+  void *dev;
+  size_t bytes;
+};
+
+// the arrays of the blob, in order, sized by the counts c
+std::vector<BlobPart> blob_parts(const cem_handle *h, const Counters &c) {
+  const DevState &d = h->d;
+  const size_t N = (size_t)d.g.nn + c.n_ph, ne = d.g.ne, nck = c.n_ck, nph = c.n_ph;
+  std::vector<BlobPart> p;
+  if (d.precision == CEM_FP64) {
+    p.push_back({d.ux[h->cur], N * 8});
+    p.push_back({d.uy[h->cur], N * 8});
+    p.push_back({d.vx, N * 8});
+    p.push_back({d.vy, N * 8});
+  } else {
+    p.push_back({d.u4[h->cur], N * 16});
+    p.push_back({d.v2, N * 8});
+    p.push_back({d.minvf, N * 4});
+  }
+  p.push_back({d.m, N * 8});
+  p.push_back({d.minv, N * 8});
+  p.push_back({d.Wn, N * 8});
+  p.push_back({d.Wd, N * 8});
+  p.push_back({d.estate, ne});
+  p.push_back({d.crack_of, ne * 4});
+  p.push_back({d.ck_elem, nck * 4});
+  p.push_back({d.ck_info, nck * 4});
+  p.push_back({d.ck_node, nck * 32});
+  p.push_back({d.ck_Ap, nck * 16});
+  p.push_back({d.ck_ud, nck * 8});
+  p.push_back({d.ck_step, nck * 4});
+  p.push_back({d.ph_owner, nph * 4});
+  p.push_back({d.ph_creator, nph * 4});
+  p.push_back({d.ph_nuser, nph * 4});
+  p.push_back({d.ph_users, nph * 16});
+  p.push_back({d.ph_upf, nph * 16});
+  p.push_back({d.ph_uap, nph * 32});
+  p.push_back({d.S, (size_t)c.n_S * 4});
+  p.push_back({d.S_info, (size_t)c.n_S * 4});
+  p.push_back({d.S_G, (size_t)c.n_S * 8});
+  p.push_back({d.spos, (size_t)d.g.ned * 4});
+  p.push_back({d.erec, (size_t)c.n_rec * 56});
+  return p;
+}
+
+size_t blob_bytes(const std::vector<BlobPart> &parts) {
+  size_t b = sizeof(BlobHeader) + sizeof(Counters);
+  for (const auto &q : parts) b += q.bytes;
+  return b;
+}
+
+cem_status blob_usable(cem_handle *h) {
+  if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
+  if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
+  return CEM_OK;
+}
+
+}  // namespace
+
+cem_status cem_state_size(cem_handle *h, long *n_bytes) {
+  if (!h || !n_bytes) return CEM_ERR_ARG;
+  cem_status rc = blob_usable(h);
+  if (rc != CEM_OK) return rc;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  rc = sync_status(h);
+  if (rc != CEM_OK) return rc;
+  *n_bytes = (long)blob_bytes(blob_parts(h, *h->h_cnt));
+  return CEM_OK;
+}
+
+cem_status cem_save_state(cem_handle *h, void *blob, long n_bytes) {
+  if (!h || !blob) return CEM_ERR_ARG;
+  cem_status rc = blob_usable(h);
+  if (rc != CEM_OK) return rc;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  rc = sync_status(h);
+  if (rc != CEM_OK) return rc;
+  const Counters c = *h->h_cnt;
+  const auto parts = blob_parts(h, c);
+  const size_t need = blob_bytes(parts);
+  if ((size_t)n_bytes < need) return fail(h, CEM_ERR_ARG, "blob needs %zu bytes", need);
+  BlobHeader hd{};
+  hd.magic = kBlobMagic;
+  hd.version = kBlobVersion;
+  hd.precision = h->d.precision;
+  hd.nx = h->d.g.nx;
+  hd.ny = h->d.g.ny;
+  hd.nn = h->d.g.nn;
+  hd.ne = h->d.g.ne;
+  hd.ned = h->d.g.ned;
+  hd.n_ph = c.n_ph;
+  hd.n_ck = c.n_ck;
+  hd.n_S = c.n_S;
+  hd.n_rec = c.n_rec;
+  hd.step = h->step;
+  hd.dt = h->d.mat.dt;
+  char *o = static_cast<char *>(blob);
+  memcpy(o, &hd, sizeof hd);
+  memcpy(o + sizeof hd, &c, sizeof c);
+  size_t off = sizeof hd + sizeof c;
+  for (const auto &q : parts) {
+    if (q.bytes) CUDA_TRY(h, cudaMemcpyAsync(o + off, q.dev, q.bytes, cudaMemcpyDeviceToHost, h->st));
+    off += q.bytes;
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+cem_status cem_load_state(cem_handle *h, const void *blob, long n_bytes) {
+  if (!h || !blob) return CEM_ERR_ARG;
+  cem_status rc = blob_usable(h);
+  if (rc != CEM_OK) return rc;
+  if ((size_t)n_bytes < sizeof(BlobHeader) + sizeof(Counters))
+    return fail(h, CEM_ERR_ARG, "blob too short");
+  BlobHeader hd;
+  Counters c;
+  const char *in = static_cast<const char *>(blob);
+  memcpy(&hd, in, sizeof hd);
+  memcpy(&c, in + sizeof hd, sizeof c);
+  const DevState &d = h->d;
+  if (hd.magic != kBlobMagic || hd.version != kBlobVersion)
+    return fail(h, CEM_ERR_ARG, "not a state blob of this library version");
+  if (hd.precision != d.precision || hd.nx != d.g.nx || hd.ny != d.g.ny || hd.nn != d.g.nn ||
+      hd.ne != d.g.ne || hd.ned != d.g.ned)
+    return fail(h, CEM_ERR_ARG, "blob of another mesh or precision");
+  if (hd.dt != d.mat.dt) return fail(h, CEM_ERR_ARG, "blob of another time step (material)");
+  if (c.n_ph > d.ph_cap || c.n_ck > d.ck_cap || c.n_S > d.list_cap || c.n_rec > d.rec_cap ||
+      c.n_ph < 0 || c.n_ck < 0 || c.n_S < 0 || c.n_rec < 0 || hd.step < 0)
+    return fail(h, CEM_ERR_CAPACITY, "the blob's phantoms, splits, list or records exceed "
+                                     "this handle's capacities");
+  const auto parts = blob_parts(h, c);
+  if ((size_t)n_bytes < blob_bytes(parts)) return fail(h, CEM_ERR_ARG, "blob truncated");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  size_t off = sizeof hd + sizeof c;
+  for (const auto &q : parts) {
+    if (q.bytes) CUDA_TRY(h, cudaMemcpyAsync(q.dev, in + off, q.bytes, cudaMemcpyHostToDevice, h->st));
+    off += q.bytes;
+  }
+  // counters of the saved step; the transient ones (plans of a step in
+  // flight) start clear, and the load-factor table is rebuilt at the next step
+  Counters k = c;
+  k.n_prop = 0;
+  k.pend_nwin = 0;
+  k.lam_base = (int)hd.step;
+  *h->h_cnt = k;
+  CUDA_TRY(h, cudaMemcpyAsync(d.cnt, h->h_cnt, sizeof(Counters), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->step = hd.step;
+  h->lam_lo = 0;
+  h->lam_n = 0;
+  return check_status(h);
+}
+
+cem_status cem_get_fragments(cem_handle *h, int *n_fragments, int *piece_fragment, long cap) {
+  if (!h || !n_fragments) return CEM_ERR_ARG;
+  if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  cem_status rc = sync_status(h);
+  if (rc != CEM_OK) return rc;
+  const DevState &d = h->d;
+  const long nq = 2L * d.g.ne;
+  if (piece_fragment && cap < nq) return fail(h, CEM_ERR_ARG, "need room for %ld pieces", nq);
+  const int n_nodes = d.g.nn + h->h_cnt->n_ph;
+  const size_t sb = fragments_scratch_bytes(d, n_nodes);
+  char *tmp = (char *)scratch(h, sb + (size_t)nq * 4 + 256);
+  if (!tmp) return fail(h, CEM_ERR_CUDA, "temporary allocation failed");
+  int *labels = reinterpret_cast<int *>(tmp + ((sb + 255) & ~(size_t)255));
+  int *count = reinterpret_cast<int *>(tmp) + sb / 4 - 1;
+  CUDA_TRY(h, launch_fragments(d, n_nodes, tmp, labels, count, h->st));
+  int c = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&c, count, 4, cudaMemcpyDeviceToHost, h->st));
+  if (piece_fragment)
+    CUDA_TRY(h, cudaMemcpyAsync(piece_fragment, labels, (size_t)nq * 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  *n_fragments = c;
   return CEM_OK;
 }
 

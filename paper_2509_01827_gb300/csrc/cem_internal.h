@@ -267,6 +267,14 @@ int track_sort_capacity();
 cudaError_t launch_surface_info(const DevState &d, int *out3, cudaStream_t st);
 cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st);
+// element mean stress (sxx, syy, sxy) and largest principal stress into
+// out4[0..ne), [ne..2ne), [2ne..3ne), [3ne..4ne)
+cudaError_t launch_element_stress(const DevState &d, int cur, double *out4, cudaStream_t st);
+// fragments: labels[2 e + p] of every piece (-1: none), *count fragments;
+// device scratch of fragments_scratch_bytes
+size_t fragments_scratch_bytes(const DevState &d, int n_nodes);
+cudaError_t launch_fragments(const DevState &d, int n_nodes, void *scratch, int *labels,
+                             int *count, cudaStream_t st);
 cudaError_t launch_energy_post(const DevState &d, int nparts, cudaStream_t st);
 cudaError_t launch_fp32_to_fp64(const DevState &d, int cur, double *ux, double *uy,
                                 double *vx, double *vy, int n, cudaStream_t st);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "cem_internal.h"
+#include "q4_fp64.cuh"
 
 namespace cem {
 
@@ -172,12 +173,101 @@ __global__ void k_f64_to_f32(DevState d, int cur, const double *ux, const double
   }
 }
 
+// ---------------------------------------------------------- element stress
+// Mean stress of every element, for the stress contour outputs of Sec. 4: an
+// intact element averages over its four edge points the stress its internal
+// force uses there (Eqs. 1-2: the own strains of both elements beside an
+// edge averaged when both are intact, Eq. 4 at the edge midpoints); a split
+// element weights its pieces' mean stresses by the piece areas; an inactive
+// element gets 0.  Also the largest principal stress
+// sigma1 = (sxx + syy)/2 + sqrt(((sxx - syy)/2)^2 + sxy^2).  FP64 in both
+// precisions (the FP32-mixed displacement pairs are summed to doubles).
+__device__ __forceinline__ void node_u(const DevState &d, int cur, int N, double &x, double &y) {
+  if (d.precision == 0) {
+    x = d.ux[cur][N];
+    y = d.uy[cur][N];
+  } else {
+    const float4 U = d.u4[cur][N];
+    x = (double)U.x + (double)U.y;
+    y = (double)U.z + (double)U.w;
+  }
+}
+
+__device__ __forceinline__ void elem_u(const DevState &d, int cur, int e, double u[4], double v[4]) {
+  const int i = e % d.g.nx, j = e / d.g.nx, r = d.g.nx + 1;
+  const int n4[4] = {j * r + i, j * r + i + 1, (j + 1) * r + i + 1, (j + 1) * r + i};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) node_u(d, cur, n4[a], u[a], v[a]);
+}
+
+__global__ void k_element_stress(DevState d, int cur, double *sx, double *sy, double *sxy,
+                                 double *s1) {
+  const Geo &g = d.g;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.ne; e += gridDim.x * blockDim.x) {
+    double m[3] = {0.0, 0.0, 0.0};
+    const int st = d.estate[e];
+    if (st == ST_INTACT) {
+      double u[4], v[4], sig[4][3];
+      elem_u(d, cur, e, u, v);
+      const int i = e % g.nx, j = e / g.nx;
+      for (int k = 0; k < 4; ++k) {
+        double own[3];
+        strain64_rt(g, k, u, v, own);
+        const int f = k == 0 ? (j > 0 ? e - g.nx : -1)
+                    : k == 1 ? (i < g.nx - 1 ? e + 1 : -1)
+                    : k == 2 ? (j < g.ny - 1 ? e + g.nx : -1)
+                             : (i > 0 ? e - 1 : -1);
+        double ep[3];
+        if (f >= 0 && d.estate[f] == ST_INTACT) {
+          double uf[4], vf[4], of[3];
+          elem_u(d, cur, f, uf, vf);
+          strain64_rt(g, (k + 2) % 4, uf, vf, of);
+          const double *p1 = e < f ? own : of, *p2 = e < f ? of : own;
+          for (int c = 0; c < 3; ++c) ep[c] = 0.5 * p1[c] + 0.5 * p2[c];
+        } else {
+          for (int c = 0; c < 3; ++c) ep[c] = own[c];
+        }
+        stress64(d.mat, ep, sig[k]);
+      }
+      for (int c = 0; c < 3; ++c) m[c] = (((sig[0][c] + sig[1][c]) + sig[2][c]) + sig[3][c]) * 0.25;
+    } else if (st == ST_CRACKED) {
+      const int ck = d.crack_of[e];
+      double mp[2][3];
+      for (int p = 0; p < 2; ++p) {
+        double u[4], v[4], sig[4][3];
+        for (int a = 0; a < 4; ++a) node_u(d, cur, d.ck_node[ck * 8 + p * 4 + a], u[a], v[a]);
+        for (int k = 0; k < 4; ++k) {
+          double ep[3];
+          strain64_rt(g, k, u, v, ep);
+          stress64(d.mat, ep, sig[k]);
+        }
+        for (int c = 0; c < 3; ++c)
+          mp[p][c] = (((sig[0][c] + sig[1][c]) + sig[2][c]) + sig[3][c]) * 0.25;
+      }
+      const double A0 = d.ck_Ap[ck * 2], A1 = d.ck_Ap[ck * 2 + 1];
+      for (int c = 0; c < 3; ++c) m[c] = (A0 * mp[0][c] + A1 * mp[1][c]) / (A0 + A1);
+    }
+    sx[e] = m[0];
+    sy[e] = m[1];
+    sxy[e] = m[2];
+    const double h = 0.5 * (m[0] - m[1]);
+    s1[e] = 0.5 * (m[0] + m[1]) + sqrt(h * h + m[2] * m[2]);
+  }
+}
+
 int grid_for(int n, int block, int maxb) {
   int b = (n + block - 1) / block;
   return b < 1 ? 1 : (b > maxb ? maxb : b);
 }
 
 }  // namespace
+
+cudaError_t launch_element_stress(const DevState &d, int cur, double *out4, cudaStream_t st) {
+  const int ne = d.g.ne;
+  k_element_stress<<<grid_for(ne, 256, 4864), 256, 0, st>>>(d, cur, out4, out4 + ne, out4 + 2 * ne,
+                                                           out4 + 3 * (size_t)ne);
+  return cudaGetLastError();
+}
 
 cudaError_t energy_carveouts() {
   static bool done = false;

@@ -165,3 +165,22 @@ def test_bookkeeping_more_proposals_than_staged():
         g.debug_apply_proposals(edge, elem, k, G)
         compare_fp64(o, g)
     assert staged > 1024
+
+
+@pytest.mark.parametrize("precision,steps,tol", [(0, 260, 1e-12), (1, 150, 1e-4)])
+def test_element_stress_and_sigma1(precision, steps, tol):
+    """Element mean stress and its largest principal value (the stress
+    contour outputs, CEM_FIELD_SIGMA / CEM_FIELD_SIGMA1) against the oracle's
+    element stresses: FP64 after splits to 1e-12 of the largest stress, FP32
+    before initiation to 1e-4."""
+    p = inputs.notched_plate(100, 40, steps=steps)
+    o, g = run_pair(p, steps, precision=precision)
+    want = o.element_stress()
+    got = g.element_stress()
+    scale = np.max(np.abs(want))
+    np.testing.assert_allclose(got, want, rtol=0, atol=tol * scale)
+    h = 0.5 * (want[:, 0] - want[:, 1])
+    s1 = 0.5 * (want[:, 0] + want[:, 1]) + np.sqrt(h * h + want[:, 2] ** 2)
+    np.testing.assert_allclose(g.sigma1(), s1, rtol=0, atol=tol * scale)
+    if precision == 0:
+        assert g.counts()["n_cracked"] > len(p.precracks)  # split elements are covered

@@ -286,6 +286,49 @@ def test_no_smoothing_beside_a_split_element(hx, hy):
     assert np.max(np.abs(np.array([[cx[g], cy[g]] for g in glob]) - want)) > 1e-3 * scale
 
 
+def test_element_stress_of_a_linear_field_and_a_rotation():
+    """Element mean stress (the contour output): a linear field gives
+    D eps_exact in every element -- intact or split (phantoms carry the
+    field at their real node's position) -- and a rigid rotation gives 0."""
+    nx, ny, hx, hy = 7, 5, 1e-3, 0.6e-3
+    s = make(nx, ny, hx, hy)
+    s.precrack([[2 * nx + i, 3, 1] for i in range(4)] + [[4 * nx + 5, 3, 0]])
+    c = s.counts()
+    nn = c["nn"]
+    x, y = node_xy(nx, ny, hx, hy)
+    owner = s.phantoms()["owner"]
+    X = np.concatenate([x, x[owner]])
+    Y = np.concatenate([y, y[owner]])
+    a, b, cc, d = 1.0e-4, -0.4e-4, 0.7e-4, -2.0e-4
+    s.set_state(ux=a * X + b * Y, uy=cc * X + d * Y)
+    D11, D12, D33 = d_plane_strain()
+    want = np.array([D11 * a + D12 * d, D12 * a + D11 * d, D33 * (b + cc)])
+    got = s.element_stress()
+    np.testing.assert_allclose(got, np.broadcast_to(want, got.shape), rtol=1e-11,
+                               atol=1e-11 * np.max(np.abs(want)))
+    w = 1e-3
+    s2 = make(nx, ny, hx, hy)
+    s2.set_state(ux=-w * y, uy=w * x)
+    assert np.max(np.abs(s2.element_stress())) < 1e-12 * D11 * w
+    del nn
+
+
+def test_element_stress_uses_the_smoothed_edge_stress():
+    """2 x 1 mesh, node 0 moved by dx: the right element's own strain is 0;
+    at the shared edge the smoothing gives half of the left element's
+    eps_xx = -dx/(2hx) there, so its mean stress over four edge points is
+    (D11, D12) * (-dx/(4hx)) / 4."""
+    hx, hy, dx = 1e-3, 0.5e-3, 1e-6
+    s = make(2, 1, hx, hy)
+    ux = np.zeros(6)
+    ux[0] = dx
+    s.set_state(ux=ux)
+    D11, D12, _ = d_plane_strain()
+    got = s.element_stress()[1]
+    np.testing.assert_allclose(got[:2], np.array([D11, D12]) * (-dx / (4 * hx)) / 4, rtol=1e-13)
+    assert got[2] == 0.0
+
+
 # ------------------------------------------------------------ a5 dynamics
 def test_total_mass_equals_density_times_area():
     s, _ = _random_cracked_mesh(3)
