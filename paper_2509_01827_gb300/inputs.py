@@ -252,6 +252,33 @@ def fragmentation(n=2048, L=0.1, r=0.005, mode="neumann", p0=50e6, v0=2.0, seed=
     return prob
 
 
+def kalthoff(n=200, L=0.1, notch_y=0.025, notch_len=0.05, v0=16.5, t0=1e-6, t_end=90e-6,
+             scope=SCOPE_NBHD, steps=None, name=None, phantom_cap=None, crack_cap=None):
+    """Upper half of the Kalthoff-Winkler plate (Sec. 4.1): an L x L square
+    (the plate's symmetry line is the bottom edge, held at v_y = 0), a notch
+    from the left edge along y = notch_y of length notch_len, and the impact
+    on the left edge below the notch: v_x = v0 t/t0 (t <= t0), v0 after.
+    Steel of Sec. 4.1: E = 190 GPa, nu = 0.3, rho = 8000 kg/m^3,
+    G_c = 2.213e4 J/m^2, plane strain.  The notch is a row of pattern-II
+    pre-cracks in the element row just below y = notch_y (a node line); the
+    tracking scope is MCT (node neighbourhoods) or SCT (tips only)."""
+    h = L / n
+    mat = Material(E=190e9, nu=0.3, rho=8000.0, gc_uniform=2.213e4, scope=scope)
+    jn = int(round(notch_y / h)) - 1
+    nnotch = int(round(notch_len / h))
+    pre = np.array([[jn * n + i, 3, 1] for i in range(nnotch)], np.int32).reshape(-1, 3)
+    left = [node_id(n, 0, j) for j in range(jn + 1)]  # left-edge nodes below the notch
+    bcs = [BC(VELOCITY, np.array(left, np.int32), 1, LAW_RAMP, v0, t0),
+           BC(VELOCITY, boundary_nodes(n, n, "bottom"), 2, LAW_RAMP, 0.0, t0)]
+    prob = Problem(name=name or f"kalthoff_{n}x{n}_{'sct' if scope == SCOPE_TIPS else 'mct'}",
+                   nx=n, ny=n, hx=h, hy=h, material=mat, bcs=bcs, precracks=pre,
+                   phantom_cap=phantom_cap or max(8192, n * n), crack_cap=crack_cap or max(4096, n * n // 2))
+    if steps is None:
+        steps = int(math.ceil(t_end / estimate_dt(prob)))
+    prob.steps = steps
+    return prob
+
+
 def estimate_dt(prob: Problem) -> float:
     """Half the plane-strain CFL limit, for sizing step counts only."""
     m = prob.material

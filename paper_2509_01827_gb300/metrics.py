@@ -23,6 +23,9 @@ them; the definitions are this library's own:
   `radius` of b and ahead of it ((c - b) . d > 0) form two branches, one on
   each side of d; the angle is the one between the vectors from b's centroid
   to each branch's mean centroid.
+* Crack angle: the direction, from a crack's origin (a notch tip), of the
+  mean offset of the elements split within a ring of radii r_min .. r_max
+  around it.
 * Fragments: connected pieces of material after splitting.  Every intact
   element is one piece and every split element two (the pieces on each side
   of its cut); pieces that share a node, real or phantom, are joined (they
@@ -201,6 +204,24 @@ def branch_angle(cracks, nx, ny, hx, hy, active=None, radius=5e-3, min_sep=3.0):
     u, v = np.mean(left, axis=0), np.mean(right, axis=0)
     c = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
     return math.degrees(math.acos(max(-1.0, min(1.0, c)))), b
+
+
+def crack_angle(cracks, nx, hx, hy, origin, r_min, r_max, grown_only=True):
+    """Direction (degrees from +x) of the crack grown from `origin`: the
+    angle of the mean offset from origin of the split elements whose
+    centroids lie between r_min and r_max from it (split during the run,
+    not pre-cracks, when grown_only).  None when no element qualifies."""
+    elem = np.asarray(cracks["elem"])
+    st = np.asarray(cracks["step"])
+    sel = st >= 0 if grown_only else np.ones(len(elem), bool)
+    e = elem[sel]
+    cx = (e % nx + 0.5) * hx - origin[0]
+    cy = (e // nx + 0.5) * hy - origin[1]
+    r = np.hypot(cx, cy)
+    m = (r >= r_min) & (r <= r_max)
+    if not np.any(m):
+        return None
+    return math.degrees(math.atan2(float(np.mean(cy[m])), float(np.mean(cx[m]))))
 
 
 def fragments(cracks, nx, ny, active=None):

@@ -184,3 +184,15 @@ def test_element_stress_and_sigma1(precision, steps, tol):
     np.testing.assert_allclose(g.sigma1(), s1, rtol=0, atol=tol * scale)
     if precision == 0:
         assert g.counts()["n_cracked"] > len(p.precracks)  # split elements are covered
+
+
+@pytest.mark.parametrize("scope", [inputs.SCOPE_NBHD, inputs.SCOPE_TIPS])
+def test_kalthoff_plate(scope):
+    """Upper half of the Kalthoff-Winkler plate (Sec. 4.1 steel, impact ramp
+    on the left edge below the notch, symmetry line held at v_y = 0) in the
+    multiple-tips (MCT) and single-tip (SCT) scopes, to 90 us on a 2 mm
+    mesh: bit-identical to the oracle; the crack starts at the notch tip."""
+    p = inputs.kalthoff(50, scope=scope)
+    o, g = run_pair(p, p.steps, chunks=[250, p.steps - 250])
+    compare_fp64(o, g)
+    assert g.counts()["n_cracked"] > len(p.precracks)

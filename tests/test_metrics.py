@@ -201,3 +201,22 @@ def test_fragments_of_random_scripted_cracking_match_brute_force():
     n, _ = metrics.fragments(cr, nx, ny)
     assert n == _brute_fragments(cr, nx, ny, None)
     assert n > 1
+
+
+@pytest.mark.parametrize("slope_deg", [70.0, 45.0, 20.0])
+def test_crack_angle_of_a_staircase(slope_deg):
+    """Elements along a straight line from the origin at a known angle (their
+    centroids within half an element of it) give that angle back."""
+    nx, ny, h = 300, 300, 0.5e-3
+    ox, oy = 50e-3, 25e-3
+    t = math.radians(slope_deg)
+    elems = []
+    for q in range(1, 2000):
+        x, y = ox + q * 0.1 * h * math.cos(t), oy + q * 0.1 * h * math.sin(t)
+        e = int(y // h) * nx + int(x // h)
+        if e not in elems:
+            elems.append(e)
+    cr = dict(elem=np.array(elems), step=np.arange(len(elems)))
+    a = metrics.crack_angle(cr, nx, h, h, (ox, oy), 5e-3, 40e-3)
+    assert abs(a - slope_deg) < 1.5, a
+    assert metrics.crack_angle(cr, nx, h, h, (ox, oy), 200e-3, 300e-3) is None
