@@ -47,6 +47,7 @@ struct cem_handle {
   int neu_law = 0, dir_law = 0;
   double neu_t0 = 0, neu_tau = 0, dir_t0 = 0, dir_tau = 0;
   int cur = 0;
+  bool mrow_stale = true;  // the FP32 node update's row flags need a rebuild
   long step = 0;
   int energy_every = 0;
   cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][energy]
@@ -192,7 +193,19 @@ cem_status upload_loads(cem_handle *h) {
   if (!bc.empty())
     CUDA_TRY(h, cudaMemcpyAsync(h->d.bc_nodes, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice, h->st));
   h->d.n_bc = (int)bc.size();
+  h->mrow_stale = true;
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return CEM_OK;
+}
+
+// Row flags of the FP32 node update, rebuilt before a step whenever the
+// node flags or element states were written from the host (the apply kernel
+// keeps them current as elements split).
+cem_status ensure_march_rows(cem_handle *h) {
+  if (!h->mrow_stale || h->d.precision != CEM_FP32_MIXED) return CEM_OK;
+  CUDA_TRY(h, launch_march_rows(h->d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));  // a batch steps its members on its own stream
+  h->mrow_stale = false;
   return CEM_OK;
 }
 
@@ -456,6 +469,7 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
        dalloc_n(h, d.Wd, nc) && dalloc_n(h, d.nflag, (size_t)nn) && dalloc_n(h, d.Fx, (size_t)nn) &&
        dalloc_n(h, d.Fy, (size_t)nn) && dalloc_n(h, d.Vx, (size_t)nn) && dalloc_n(h, d.Vy, (size_t)nn) &&
        dalloc_n(h, d.bc_nodes, (size_t)nn) && dalloc_n(h, d.estate, nec) &&
+       dalloc_n(h, d.mrow, (size_t)(d.g.ny + 1) * march_tiles_x_of(d.g.nx)) &&
        dalloc_n(h, d.crack_of, nec) && dalloc_n(h, d.gc, nec) &&
        dalloc_n(h, d.ck_elem, (size_t)d.ck_cap) && dalloc_n(h, d.ck_info, (size_t)d.ck_cap) &&
        dalloc_n(h, d.ck_node, (size_t)d.ck_cap * 8) && dalloc_n(h, d.ck_Ap, (size_t)d.ck_cap * 2) &&
@@ -600,6 +614,7 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
   }
   CUDA_TRY(h, launch_build_surface(d, h->st));
   h->material = true;
+  h->mrow_stale = true;
   return sync_status(h);
 }
 
@@ -707,6 +722,8 @@ cem_status cem_step(cem_handle *h, int n) {
   if (n < 0) return fail(h, CEM_ERR_ARG, "negative step count");
   if (n == 0) return CEM_OK;
   CUDA_TRY(h, cudaSetDevice(h->device));
+  cem_status rs = ensure_march_rows(h);
+  if (rs != CEM_OK) return rs;
   const DevState &d = h->d;
   int done = 0;
   while (done < n) {
@@ -762,7 +779,9 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
   if (n < 1 || n > h->d.lam_cap) return fail(h, CEM_ERR_ARG, "1 <= n <= %d", h->d.lam_cap);
   CUDA_TRY(h, cudaSetDevice(h->device));
   for (int q = 0; q < 9; ++q) ms[q] = 0.0;
-  cem_status rc = upload_load_factors(h, n);
+  cem_status rc = ensure_march_rows(h);
+  if (rc != CEM_OK) return rc;
+  rc = upload_load_factors(h, n);
   if (rc != CEM_OK) return rc;
   const int M = 9;  // events per step: start + 8 marks
   std::vector<cudaEvent_t> ev((size_t)n * M);
@@ -1068,6 +1087,7 @@ cem_status cem_load_state(cem_handle *h, const void *blob, long n_bytes) {
   h->step = hd.step;
   h->lam_lo = 0;
   h->lam_n = 0;
+  h->mrow_stale = true;
   return check_status(h);
 }
 
@@ -1327,6 +1347,7 @@ cem_status batch_upload(cem_handle *b) {
   std::vector<int> nparts((size_t)n);
   for (int s = 0; s < n; ++s) {
     cem_handle *m = p->members[s];
+    if (ensure_march_rows(m) != CEM_OK) return fail(b, CEM_ERR_CUDA, "member %d: row flags", s);
     DevState d = m->d;
     d.step_end = (int)std::min<long>(p->step_end[s], (long)INT_MAX);
     d.cur_xor = m->cur ^ (int)(m->step & 1);

@@ -15,6 +15,12 @@ enum : uint8_t { NF_LOADED = 1, NF_DIRX = 2, NF_DIRY = 4 };
 // device status bits
 enum : int { STAT_CAPACITY = 1, STAT_NONFINITE = 2, STAT_TIMEOUT = 4 };
 
+// FP32 node-update tiles: tile column tx owns node columns
+// [tx * kMarchWX, tx * kMarchWX + kMarchWX) and its lanes read element
+// columns [tx * kMarchWX - kMarchLeft, tx * kMarchWX - kMarchLeft + kMarchSpan).
+constexpr int kMarchWX = 60, kMarchLeft = 2, kMarchSpan = 64;
+__host__ __device__ inline int march_tiles_x_of(int nx) { return (nx + kMarchWX) / kMarchWX; }
+
 // Counters live in device memory so that captured graphs can be replayed.
 struct Counters {
   int n_ph;       // phantom nodes in use
@@ -96,6 +102,12 @@ struct DevState {
                          // four real nodes (local node a: the piece on its side)
   float2 *fsp;           // [nn] FP32 mode: internal force of a node with a load or a
                          // prescribed velocity, handed from the march to its update
+  // [(ny + 1) * march_tiles_x_of(nx)] row flags of the FP32 node update, per
+  // node row r and tile column: low byte 1 when no owned node of the tile in
+  // row r has a load or a prescribed velocity, high byte 1 when every
+  // element of row r that the tile's lanes read is intact (cleared by the
+  // apply kernel when it splits one of them)
+  uint16_t *mrow;
 
   // phantoms [ph_cap]
   int *ph_owner;
@@ -269,6 +281,8 @@ cudaError_t launch_debug_filter(const DevState &d, int n, cudaStream_t st);
 cudaError_t launch_energy_pre(const DevState &d, cudaStream_t st);
 // element mean stress (sxx, syy, sxy) and largest principal stress into
 // out4[0..ne), [ne..2ne), [2ne..3ne), [3ne..4ne)
+// rebuilds the node update's row flags from nflag and estate
+cudaError_t launch_march_rows(const DevState &d, cudaStream_t st);
 cudaError_t launch_element_stress(const DevState &d, int cur, double *out4, cudaStream_t st);
 // fragments: labels[2 e + p] of every piece (-1: none), *count fragments;
 // device scratch of fragments_scratch_bytes

@@ -18,6 +18,7 @@
 // two run side by side with the surface evaluation and the selection.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "cem_internal.h"
@@ -293,7 +294,41 @@ __device__ __forceinline__ Stress3 masked(const Stress3 &s, bool on) {
   return r;
 }
 
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// Packed FP32 pairs (add/sub/mul .rn.f32x2): one instruction works on both
+// lanes of a float2, each lane rounded as the scalar operation would be and
+// never contracted with a neighbouring multiply, so every force sum below is
+// the same in the all-intact branch and the general one.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+// (b - a) of two compensated pairs per component: (b.hi - a.hi) + (b.lo - a.lo)
+__device__ __forceinline__ float2 pdiff(const float4 &a, const float4 &b) {
+  const float2 tx = psub(make_float2(b.x, b.y), make_float2(a.x, a.y));
+  const float2 ty = psub(make_float2(b.z, b.w), make_float2(a.z, a.w));
+  return make_float2(tx.x + tx.y, ty.x + ty.y);
+}
 
 // Node data in flight per warp: u, v and 1/m of node rows t-2 .. t+kAhead-1
 // sit in a shared-memory ring filled by asynchronous copies (cp.async),
@@ -306,6 +341,8 @@ constexpr int kRing = 4, kAhead = kRing - 2;
 constexpr int kCols = 2;
 constexpr int kHalo = (2 + kCols - 1) / kCols;
 constexpr int WX = (32 - 2 * kHalo) * kCols;  // owned columns of a tile
+static_assert(WX == kMarchWX && kHalo * kCols == kMarchLeft && 32 * kCols == kMarchSpan,
+              "the row flags describe these tiles");
 struct MarchRing {
   float4 u[kRing][kCols][32];
   float2 v[kRing][kCols][32];
@@ -333,10 +370,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ void prefetch_l1(const void *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
-__device__ __forceinline__ void f2acc(float2 &a, float x, float y) { a.x += x; a.y += y; }
 
-// The tile height TY (node rows) is chosen at launch, at most 64.
-template <bool ENERGY>
+// The tile height TY (node rows) is chosen at launch, at most 64.  CLEAN:
+// every element the tile reads is intact and no node it updates has a load
+// or a prescribed velocity (the general branch, the pieces and the special
+// updates drop out at compile time).
+template <bool ENERGY, bool CLEAN>
 __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int tile_y, int TY,
                                              int cur, int first, double *part, MarchRing &ring) {
   constexpr int K = kCols;
@@ -350,6 +389,8 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
   const float4 *__restrict__ u4 = d.u4[cur];
   const float rx = g.rxf, ry = g.ryf;
   const float hx2 = 0.5f * rx, hy2 = 0.5f * ry;
+  const float2 RX = make_float2(rx, rx), RY = make_float2(ry, ry);
+  const float2 HX2 = make_float2(hx2, hx2), HY2 = make_float2(hy2, hy2);
   // D scaled by A/4: the stresses below are A/4 sigma, so that every edge
   // term is a force and a piece force adds to it directly
   Mat mq = d.mat;
@@ -377,11 +418,14 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
     }
     cp_async_commit();
   };
+  // a clean tile reads no element state and no node flag: they are known
   auto load_es = [&](int r, int k) -> int {  // state of element (c_k, r)
+    if (CLEAN) return (int)ST_INTACT;
     const int c = c0 + k;
     return (c >= 0 && c < g.nx && r >= 0 && r < g.ny) ? (int)d.estate[r * g.nx + c] : (int)ST_OUT;
   };
   auto load_nf = [&](int r, int k) -> int {
+    if (CLEAN) return 0;
     const int c = c0 + k;
     return (own_lane && c <= g.nx && r >= j0 && r < j0 + TY && r <= g.ny)
                ? (int)d.nflag[r * stride + c] : 0;
@@ -442,9 +486,8 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float4 R = k < K - 1 ? U0[k < K - 1 ? k + 1 : k] : Ur;
-        Dx0[k] = make_float2(df_diff(U0[k].x, U0[k].y, R.x, R.y), df_diff(U0[k].z, U0[k].w, R.z, R.w));
-        Dy1[k] = make_float2(df_diff(U1[k].x, U1[k].y, U0[k].x, U0[k].y),
-                             df_diff(U1[k].z, U1[k].w, U0[k].z, U0[k].w));
+        Dx0[k] = pdiff(U0[k], R);
+        Dy1[k] = pdiff(U1[k], U0[k]);
       }
     }
     float2 DyRl, DxLf;  // Dy(c_{K-1} + 1, t-1), Dx(c_0 - 1, t)
@@ -459,7 +502,10 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
     bool intact = true;
 #pragma unroll
     for (int k = 0; k < K; ++k) intact = intact && es0[k] == ST_INTACT && es1[k] == ST_INTACT;
-    intact = __all_sync(FULL, intact && esLf == ST_INTACT);
+    intact = CLEAN || __all_sync(FULL, intact && esLf == ST_INTACT);
+    // the edges of row j0 - 2 only touch node rows below the tile: the first
+    // row marched only forms its differences
+    if (t >= j0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const float2 DyR1 = k < K - 1 ? Dy1[k < K - 1 ? k + 1 : k] : DyRl;
@@ -476,57 +522,64 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
       float2 &nl2 = k > 0 ? own2[k > 0 ? k - 1 : k] : da2;
       if (intact) {
         // every element around the row's edges is intact: one averaged
-        // stress per edge (the same sums as below with both sides intact)
+        // stress per edge (the general branch with both sides intact, term
+        // for term: its zero differences drop out exactly)
         {  // h(c_k, t-1)
-          const float2 sY = f2add(f2add(Dy1[k], DyR1), f2add(Dy2[k], DyR2k));
+          const float2 sY = padd(padd(Dy1[k], DyR1), padd(Dy2[k], DyR2k));
           const float q = 0.5f * hy2;
-          const float exx = rx * Dx1[k].x, eyy = q * sY.y, gxy = fmaf(q, sY.x, rx * Dx1[k].y);
+          const float2 mD = pmul(RX, Dx1[k]);
+          const float exx = mD.x, eyy = q * sY.y, gxy = fmaf(q, sY.x, mD.y);
           const Stress3 s = stress32(mq, exx, eyy, gxy);
-          const float px = rx * (s.xx + s.xx), py = rx * (s.xy + s.xy);
-          f2acc(own1[k], -px, -py);
-          f2acc(nr1, px, py);
-          const float bx = hy2 * s.xy, by = hy2 * s.yy;
-          f2acc(own0[k], -bx, -by);
-          f2acc(nr0, -bx, -by);
-          f2acc(own2[k], bx, by);
-          f2acc(nr2, bx, by);
+          const float2 sxp = make_float2(s.xx, s.xy);
+          const float2 P = pmul(RX, padd(sxp, sxp));
+          own1[k] = psub(own1[k], P);
+          nr1 = padd(nr1, P);
+          const float2 Bv = make_float2(hy2 * s.xy, hy2 * s.yy);
+          own0[k] = psub(own0[k], Bv);
+          nr0 = psub(nr0, Bv);
+          own2[k] = padd(own2[k], Bv);
+          nr2 = padd(nr2, Bv);
           if (owned_edge) se += exx * s.xx + eyy * s.yy + gxy * s.xy;
         }
         {  // v(c_k, t-1)
-          const float2 sX = f2add(f2add(Dx1[k], Dx0[k]), f2add(DxL1k, DxL0));
+          const float2 sX = padd(padd(Dx1[k], Dx0[k]), padd(DxL1k, DxL0));
           const float q = 0.5f * hx2;
-          const float exx = q * sX.x, eyy = ry * Dy1[k].y, gxy = fmaf(q, sX.y, ry * Dy1[k].x);
+          const float2 mD = pmul(RY, Dy1[k]);
+          const float exx = q * sX.x, eyy = mD.y, gxy = fmaf(q, sX.y, mD.x);
           const Stress3 s = stress32(mq, exx, eyy, gxy);
-          const float sx = ry * (s.xy + s.xy), sy = ry * (s.yy + s.yy);
-          f2acc(own1[k], -sx, -sy);
-          f2acc(own2[k], sx, sy);
-          const float rxx = hx2 * s.xx, rxy = hx2 * s.xy;
-          f2acc(nr1, rxx, rxy);
-          f2acc(nr2, rxx, rxy);
-          f2acc(nl1, -rxx, -rxy);
-          f2acc(nl2, -rxx, -rxy);
+          const float2 syp = make_float2(s.xy, s.yy);
+          const float2 S = pmul(RY, padd(syp, syp));
+          own1[k] = psub(own1[k], S);
+          own2[k] = padd(own2[k], S);
+          const float2 Rv = make_float2(hx2 * s.xx, hx2 * s.xy);
+          nr1 = padd(nr1, Rv);
+          nr2 = padd(nr2, Rv);
+          nl1 = psub(nl1, Rv);
+          nl2 = psub(nl2, Rv);
           if (owned_edge) se += exx * s.xx + eyy * s.yy + gxy * s.xy;
         }
       } else {
         {  // h(c_k, t-1): above element (c_k, t-1), below (c_k, t-2)
           const bool ia = es0[k] == ST_INTACT, ib = es1[k] == ST_INTACT, both = ia && ib;
-          const float2 upv = f2add(Dy1[k], DyR1), dnv = f2add(Dy2[k], DyR2k);
-          const float2 sY = both ? f2add(upv, dnv) : (ia ? upv : dnv);
+          const float2 upv = padd(Dy1[k], DyR1), dnv = padd(Dy2[k], DyR2k);
+          const float2 sY = both ? padd(upv, dnv) : (ia ? upv : dnv);
           const float fy = both ? 0.5f * hy2 : hy2;
-          const float exx = rx * Dx1[k].x, eyy = fy * sY.y, gxy = fmaf(fy, sY.x, rx * Dx1[k].y);
+          const float2 mD = pmul(RX, Dx1[k]);
+          const float exx = mD.x, eyy = fy * sY.y, gxy = fmaf(fy, sY.x, mD.y);
           const Stress3 s = stress32(mq, exx, eyy, gxy);
           const Stress3 A = masked(s, ia), B = masked(s, ib);
           // node (c_k, t-1) is the left node of h, its right neighbour the right node
-          const float tx = hy2 * (B.xy - A.xy), ty = hy2 * (B.yy - A.yy);
-          const float px = rx * (A.xx + B.xx), py = rx * (A.xy + B.xy);
-          f2acc(own1[k], tx - px, ty - py);
-          f2acc(nr1, tx + px, ty + py);
+          const float2 T = pmul(HY2, psub(make_float2(B.xy, B.yy), make_float2(A.xy, A.yy)));
+          const float2 P = pmul(RX, padd(make_float2(A.xx, A.xy), make_float2(B.xx, B.xy)));
+          own1[k] = padd(own1[k], psub(T, P));
+          nr1 = padd(nr1, padd(T, P));
           // upper nodes of the element below, lower nodes of the element above
-          const float bx = hy2 * B.xy, by = hy2 * B.yy, ax = hy2 * A.xy, ay = hy2 * A.yy;
-          f2acc(own0[k], -bx, -by);
-          f2acc(nr0, -bx, -by);
-          f2acc(own2[k], ax, ay);
-          f2acc(nr2, ax, ay);
+          const float2 Bv = make_float2(hy2 * B.xy, hy2 * B.yy);
+          const float2 Av = make_float2(hy2 * A.xy, hy2 * A.yy);
+          own0[k] = psub(own0[k], Bv);
+          nr0 = psub(nr0, Bv);
+          own2[k] = padd(own2[k], Av);
+          nr2 = padd(nr2, Av);
           if (owned_edge) {
             const float w = both ? 1.f : ((ia || ib) ? 0.5f : 0.f);
             se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
@@ -534,23 +587,25 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
         }
         {  // v(c_k, t-1): right element (c_k, t-1), left (c_k - 1, t-1)
           const bool ir = es0[k] == ST_INTACT, il = esL0 == ST_INTACT, both = ir && il;
-          const float2 rt = f2add(Dx1[k], Dx0[k]), lt = f2add(DxL1k, DxL0);
-          const float2 sX = both ? f2add(rt, lt) : (ir ? rt : lt);
+          const float2 rt = padd(Dx1[k], Dx0[k]), lt = padd(DxL1k, DxL0);
+          const float2 sX = both ? padd(rt, lt) : (ir ? rt : lt);
           const float fx = both ? 0.5f * hx2 : hx2;
-          const float exx = fx * sX.x, eyy = ry * Dy1[k].y, gxy = fmaf(fx, sX.y, ry * Dy1[k].x);
+          const float2 mD = pmul(RY, Dy1[k]);
+          const float exx = fx * sX.x, eyy = mD.y, gxy = fmaf(fx, sX.y, mD.x);
           const Stress3 s = stress32(mq, exx, eyy, gxy);
           const Stress3 R = masked(s, ir), L = masked(s, il);
           // node (c_k, t-1) is the lower node of v, node (c_k, t) its upper node
-          const float sx = ry * (R.xy + L.xy), sy = ry * (R.yy + L.yy);
-          const float wx = hx2 * (L.xx - R.xx), wy = hx2 * (L.xy - R.xy);
-          f2acc(own1[k], wx - sx, wy - sy);
-          f2acc(own2[k], wx + sx, wy + sy);
+          const float2 S = pmul(RY, padd(make_float2(R.xy, R.yy), make_float2(L.xy, L.yy)));
+          const float2 W = pmul(HX2, psub(make_float2(L.xx, L.xy), make_float2(R.xx, R.xy)));
+          own1[k] = padd(own1[k], psub(W, S));
+          own2[k] = padd(own2[k], padd(W, S));
           // left nodes of the element right, right nodes of the element left
-          const float rxx = hx2 * R.xx, rxy = hx2 * R.xy, lxx = hx2 * L.xx, lxy = hx2 * L.xy;
-          f2acc(nr1, rxx, rxy);
-          f2acc(nr2, rxx, rxy);
-          f2acc(nl1, -lxx, -lxy);
-          f2acc(nl2, -lxx, -lxy);
+          const float2 Rv = make_float2(hx2 * R.xx, hx2 * R.xy);
+          const float2 Lv = make_float2(hx2 * L.xx, hx2 * L.xy);
+          nr1 = padd(nr1, Rv);
+          nr2 = padd(nr2, Rv);
+          nl1 = psub(nl1, Lv);
+          nl2 = psub(nl2, Lv);
           if (owned_edge) {
             const float w = both ? 1.f : ((ir || il) ? 0.5f : 0.f);
             se += w * (exx * s.xx + eyy * s.yy + gxy * s.xy);
@@ -558,9 +613,10 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
         }
       }
     }
+    }
     // ---- pieces of split elements (c_k, t-2), prefetched into L1 one row ago:
     // local nodes 0 (c_k, t-2), 1 (c_k+1, t-2), 2 (c_k+1, t-1), 3 (c_k, t-1)
-    if (__any_sync(FULL, pk_on != 0)) {
+    if (!CLEAN && __any_sync(FULL, pk_on != 0)) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if ((pk_on >> k) & 1) {
@@ -568,10 +624,10 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
           const float4 p0 = q[0], p1 = q[1];
           float2 &nr0 = k < K - 1 ? own0[k < K - 1 ? k + 1 : k] : ua0;
           float2 &nr1 = k < K - 1 ? own1[k < K - 1 ? k + 1 : k] : ua1;
-          f2acc(own0[k], p0.x, p0.y);
-          f2acc(nr0, p0.z, p0.w);
-          f2acc(nr1, p1.x, p1.y);
-          f2acc(own1[k], p1.z, p1.w);
+          own0[k] = padd(own0[k], make_float2(p0.x, p0.y));
+          nr0 = padd(nr0, make_float2(p0.z, p0.w));
+          nr1 = padd(nr1, make_float2(p1.x, p1.y));
+          own1[k] = padd(own1[k], make_float2(p1.z, p1.w));
         }
       }
     }
@@ -586,8 +642,8 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
     {
       const float ux = __shfl_up_sync(FULL, ua0.x, 1), uy = __shfl_up_sync(FULL, ua0.y, 1);
       const float dx = __shfl_down_sync(FULL, da0.x, 1), dy = __shfl_down_sync(FULL, da0.y, 1);
-      own0[0].x += ux; own0[0].y += uy;
-      own0[K - 1].x += dx; own0[K - 1].y += dy;
+      own0[0] = padd(own0[0], make_float2(ux, uy));
+      own0[K - 1] = padd(own0[K - 1], make_float2(dx, dy));
     }
     const int r = t - 2;
     if (own_lane && r >= j0 && r <= g.ny) {
@@ -681,6 +737,21 @@ __host__ __device__ inline int march_groups(int nx, int ny, int ty) {
   return (march_tiles_x(nx) * march_tiles_y(ny, ty) + kMarchWarps - 1) / kMarchWarps;
 }
 
+// Warp-uniform: every element of rows j0-2 .. j0+TY that the tile's lanes
+// read is intact, and no owned node of rows j0 .. j0+TY-1 has a load or a
+// prescribed velocity (from the row flags; tiles at the mesh edge are never
+// clean).
+__device__ __forceinline__ bool tile_clean(const DevState &d, int tile_x, int j0, int TY) {
+  const int ntx = march_tiles_x_of(d.g.nx), lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int q = lane; q < TY + 3; q += 32) {
+    const int r = j0 - 2 + q;
+    const int f = (r >= 0 && r <= d.g.ny) ? (int)d.mrow[(size_t)r * ntx + tile_x] : 0;
+    ok = ok && (f & 0x100) && (r < j0 || r >= j0 + TY || (f & 1));
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 template <bool ENERGY>
 __device__ __forceinline__ void march32_group(const DevState &d, int group, int ty, int cur,
                                               int first, MarchRing *rings) {
@@ -689,7 +760,11 @@ __device__ __forceinline__ void march32_group(const DevState &d, int group, int 
   const int ntx = march_tiles_x(d.g.nx), nty = march_tiles_y(d.g.ny, ty);
   double *part = d.e_part + 2 * tix;
   if (tix < ntx * nty) {
-    march32_tile<ENERGY>(d, tix % ntx, tix / ntx, ty, cur, first, part, rings[w]);
+    const int tile_x = tix % ntx, tile_y = tix / ntx;
+    if (tile_clean(d, tile_x, tile_y * ty, ty))
+      march32_tile<ENERGY, true>(d, tile_x, tile_y, ty, cur, first, part, rings[w]);
+    else
+      march32_tile<ENERGY, false>(d, tile_x, tile_y, ty, cur, first, part, rings[w]);
   } else if (ENERGY && lane == 0) {
     part[0] = 0.0;
     part[1] = 0.0;
@@ -826,6 +901,32 @@ cudaError_t launch_eval32_batch(const BatchDev &b, cudaStream_t st);
 // waves of resident warps on the 2048 x 2048 plate) measured faster than
 // one wave of tall ones (2048^2 step: 65 us at 8 rows, 73 at 16, 96 at 32).
 int march_rows_solo(const DevState &) { return kMarchRowsMin; }
+
+namespace {
+// one thread per (node row, tile column) entry of the row flags
+__global__ void k_march_rows(DevState d) {
+  const Geo &g = d.g;
+  const int ntx = march_tiles_x_of(g.nx), stride = g.nx + 1;
+  const long n = (long)(g.ny + 1) * ntx;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(q / ntx), tx = (int)(q % ntx);
+    bool quiet = true;
+    for (int c = tx * kMarchWX; c < tx * kMarchWX + kMarchWX && c <= g.nx; ++c)
+      quiet = quiet && d.nflag[r * stride + c] == 0;
+    bool intact = r < g.ny;
+    for (int c = tx * kMarchWX - kMarchLeft; intact && c < tx * kMarchWX - kMarchLeft + kMarchSpan; ++c)
+      intact = c >= 0 && c < g.nx && d.estate[r * g.nx + c] == ST_INTACT;
+    d.mrow[q] = (uint16_t)((quiet ? 1 : 0) | (intact ? 0x100 : 0));
+  }
+}
+}  // namespace
+
+cudaError_t launch_march_rows(const DevState &d, cudaStream_t st) {
+  const long n = (long)(d.g.ny + 1) * march_tiles_x_of(d.g.nx);
+  const int grid = (int)std::min<long>((n + 255) / 256, 4096);
+  k_march_rows<<<grid, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
 
 // energy partials of the node update: one per tile, in groups of eight
 int tiles_fp32(const DevState &d, int tile_rows) {

@@ -36,6 +36,19 @@ namespace cem {
 
 namespace {
 
+// Element e is split: the tiles of the FP32 node update whose lanes read its
+// column lose the all-intact flag of its row (every tile column tx with
+// tx * W - L <= i < tx * W - L + S).
+__device__ __forceinline__ void march_rows_split(const DevState &d, int e) {
+  if (!d.mrow) return;
+  const int i = e % d.g.nx, j = e / d.g.nx, ntx = march_tiles_x_of(d.g.nx);
+  const int a = i + kMarchLeft - kMarchSpan;
+  const int lo = a < 0 ? 0 : a / kMarchWX + 1;
+  const int hi = min((i + kMarchLeft) / kMarchWX, ntx - 1);
+  for (int tx = lo; tx <= hi; ++tx)
+    reinterpret_cast<uint8_t *>(d.mrow + (size_t)j * ntx + tx)[1] = 0;
+}
+
 // The selection CTA is sized to fit in the SM resources one tile-update CTA
 // frees (256 threads x 64 registers, under 48 KB of shared memory), so that
 // it runs beside the tile update.
@@ -741,6 +754,7 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
         }
         d.crack_of[e] = c;
         d.estate[e] = ST_CRACKED;
+        march_rows_split(d, e);
       }
     }
   }
