@@ -279,6 +279,40 @@ def kalthoff(n=200, L=0.1, notch_y=0.025, notch_len=0.05, v0=16.5, t0=1e-6, t_en
     return prob
 
 
+def compact_tension(n=100, L=0.25, notch_len=0.125, v0=3.993, t0=100e-6, t_end=200e-6, gc=100.0,
+                    scope=SCOPE_NBHD, steps=None, name=None, phantom_cap=None, crack_cap=None):
+    """Dirichlet compact-tension plate (our approximation of Sec. 4.3, whose
+    dimensions are given only in a figure): an L x L square, a vertical
+    notch from the middle of the top edge down to depth notch_len, driven by
+    velocities on the notch faces: the nodes of the right face get
+    v_x = v0 t/t0 (t <= t0), v0 after (the ramp-then-constant law of Sec.
+    4.3; v0 = 1.375, 3.318 or 3.993 m/s there, t0 = 100 us), the nodes of the
+    left face are held at v_x = 0.  The notch is a column of pattern-II
+    pre-cracks (bottom-edge midpoint to top-edge midpoint) in element column
+    n/2; the face nodes are those of its elements above the tip element's
+    lower edge.  The material is the concrete-like one of Sec. 4.2
+    (E = 32 GPa, nu = 0.2, rho = 2450 kg/m^3, G_c = 3 J/m^2), plane strain."""
+    h = L / n
+    mat = Material(E=32e9, nu=0.2, rho=2450.0, gc_uniform=gc, scope=scope)
+    i0 = n // 2
+    nnotch = max(1, int(round(notch_len / h)))
+    rows = range(n - nnotch, n)
+    pre = np.array([[j * n + i0, 0, 2] for j in reversed(rows)], np.int32).reshape(-1, 3)
+    face = range(n - nnotch + 1, n + 1)
+    left = np.array([node_id(n, i0, j) for j in face], np.int32)
+    right = np.array([node_id(n, i0 + 1, j) for j in face], np.int32)
+    bcs = [BC(VELOCITY, right, 1, LAW_RAMP, v0, t0),
+           BC(VELOCITY, left, 1, LAW_RAMP, 0.0, t0)]
+    prob = Problem(name=name or f"compact_tension_{n}x{n}_v{v0:g}", nx=n, ny=n, hx=h, hy=h,
+                   material=mat, bcs=bcs, precracks=pre,
+                   phantom_cap=phantom_cap or max(8192, 2 * n * n),
+                   crack_cap=crack_cap or max(4096, n * n // 2))
+    if steps is None:
+        steps = int(math.ceil(t_end / estimate_dt(prob)))
+    prob.steps = steps
+    return prob
+
+
 def estimate_dt(prob: Problem) -> float:
     """Half the plane-strain CFL limit, for sizing step counts only."""
     m = prob.material

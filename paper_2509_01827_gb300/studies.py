@@ -1,0 +1,105 @@
+"""Crack-pattern studies of Sec. 4 on the solver, one JSON line per case.
+
+    python -m paper_2509_01827_gb300.studies compact_tension [--n 100]
+    python -m paper_2509_01827_gb300.studies kalthoff [--n 200,400]
+
+compact_tension: the Dirichlet compact-tension plate (Sec. 4.3) at the three
+loading rates of Sec. 4.3, FP64 and FP32-mixed, with the dissipated energy U_d
+(Figs. of Sec. 4.3 plot it against time), the grown splits, the branching
+time, the fragments and the FP32-vs-FP64 Jaccard of the cracked sets.
+
+kalthoff: the upper half of the Kalthoff-Winkler plate (Sec. 4.1) in the
+multiple-tips and single-tip scopes, with the direction of the crack grown
+from the notch tip in three rings around it (Sec. 4.1 compares crack angles).
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs, metrics
+
+
+def _run(p, precision, chunk=1000):
+    from .cem import Solver
+    import torch
+    g = Solver(p, precision=precision)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    left = p.steps
+    while left:
+        n = min(chunk, left)
+        g.step(n)
+        left -= n
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out = dict(cracks=g.cracks(), counts=g.counts(), seconds=el, fragments=g.fragments(labels=False)[0],
+               energy=g.energy())
+    g.close()
+    return out
+
+
+def _summary(p, r, dt):
+    c = r["cracks"]
+    grown = c["step"] >= 0
+    bs = metrics.branching_step(c, p.nx, p.ny, p.hx, p.hy, p.active)
+    return dict(steps=p.steps, seconds=round(r["seconds"], 3), grown=int(np.sum(grown)),
+                tips_end=int(r["counts"]["n_tips"]), U_d=float(np.sum(c["ud"])),
+                branching_t_us=None if bs is None else round(bs * dt * 1e6, 3),
+                fragments=int(r["fragments"]))
+
+
+def compact_tension(n=100):
+    from .cem import CEM_FP32_MIXED, CEM_FP64
+    for v0 in (1.375, 3.318, 3.993):
+        p = inputs.compact_tension(n, v0=v0)
+        p.energy_every = 0
+        dt = inputs.estimate_dt(p)
+        r64 = _run(p, CEM_FP64)
+        r32 = _run(p, CEM_FP32_MIXED)
+        line = dict(study="compact_tension", n=n, v0=v0, t_end_us=round(p.steps * dt * 1e6, 2),
+                    fp64=_summary(p, r64, dt), fp32=_summary(p, r32, dt),
+                    jaccard_fp32_fp64=metrics.jaccard(r64["cracks"]["elem"], r32["cracks"]["elem"]))
+        print(json.dumps(line), flush=True)
+
+
+def kalthoff(ns=(200, 400)):
+    from .cem import CEM_FP32_MIXED, CEM_FP64
+    L, notch_y, notch_len = 0.1, 0.025, 0.05
+    rings = ((2e-3, 10e-3), (5e-3, 25e-3), (10e-3, 40e-3))
+    for n in ns:
+        for scope, name in ((inputs.SCOPE_NBHD, "mct"), (inputs.SCOPE_TIPS, "sct")):
+            p = inputs.kalthoff(n, L=L, notch_y=notch_y, notch_len=notch_len, scope=scope)
+            p.energy_every = 0
+            dt = inputs.estimate_dt(p)
+            line = dict(study="kalthoff", n=n, scope=name, t_end_us=round(p.steps * dt * 1e6, 2))
+            for tag, prec in (("fp64", CEM_FP64), ("fp32", CEM_FP32_MIXED)):
+                r = _run(p, prec)
+                s = _summary(p, r, dt)
+                tip = ((notch_len), notch_y)  # the notch tip: end of the pre-cracked row
+                s["angles_deg"] = [None if a is None else round(a, 1) for a in
+                                   (metrics.crack_angle(r["cracks"], p.nx, p.hx, p.hy, tip, r0, r1)
+                                    for r0, r1 in rings)]
+                s["first_growth_us"] = (None if s["grown"] == 0 else
+                                        round(float(np.min(r["cracks"]["step"][r["cracks"]["step"] >= 0]))
+                                              * dt * 1e6, 2))
+                line[tag] = s
+            print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["compact_tension", "kalthoff"])
+    ap.add_argument("--n", default=None)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    if a.study == "compact_tension":
+        compact_tension(int(a.n or 100))
+    else:
+        kalthoff(tuple(int(x) for x in (a.n or "200,400").split(",")))
+
+
+if __name__ == "__main__":
+    main()

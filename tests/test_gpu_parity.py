@@ -196,3 +196,16 @@ def test_kalthoff_plate(scope):
     o, g = run_pair(p, p.steps, chunks=[250, p.steps - 250])
     compare_fp64(o, g)
     assert g.counts()["n_cracked"] > len(p.precracks)
+
+
+@pytest.mark.parametrize("v0", [1.375, 3.993])
+def test_compact_tension_plate(v0):
+    """Dirichlet compact-tension plate (Sec. 4.3 velocity law on the notch
+    faces, our square approximation of its geometry) at the slowest and the
+    fastest loading rate of Sec. 4.3, 40 x 40 mesh to 200 us: bit-identical
+    to the oracle, with the crack grown from the notch."""
+    p = inputs.compact_tension(40, v0=v0)
+    p.energy_every = 25
+    o, g = run_pair(p, p.steps, chunks=[100, p.steps - 100])
+    compare_fp64(o, g)
+    assert g.counts()["n_cracked"] > len(p.precracks)
