@@ -1354,7 +1354,7 @@ cem_status batch_upload(cem_handle *b) {
     ds[s] = d;
     int tiles;
     if (p->precision == CEM_FP32_MIXED) {
-      // FP32 node update: one item per group of eight warp tiles
+      // FP32 node update: one item per group of four warp tiles
       const int ng = groups_fp32(d, p->tile_rows);
       for (int q = 0; q < ng; ++q) wm.push_back(make_int4(s, q, 0, ng));
       tiles = tiles_fp32(d, p->tile_rows);

@@ -301,7 +301,7 @@ int energy_parts_step(const DevState &d);    // partials one step writes (alone)
 // batched counterparts (see BatchDev); tile_rows selects the FP32 tile
 // update's tile height (8 or 16 node rows), grid_main its persistent grid
 int tiles_fp32(const DevState &d, int tile_rows);   // energy partials of the node update
-int groups_fp32(const DevState &d, int tile_rows);  // its CTAs (eight warp tiles each)
+int groups_fp32(const DevState &d, int tile_rows);  // its CTAs (four warp tiles each)
 int tiles_fp64(const DevState &d);
 int grid_pieces(const DevState &d);
 int grid_phantoms(const DevState &d);

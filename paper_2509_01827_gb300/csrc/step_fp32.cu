@@ -2,20 +2,23 @@
 // displacement kept as a compensated pair of floats (hi + lo, ~48-bit
 // mantissa) and advanced with an error-free two-sum, FP64 energy sums.
 //
-// k_main32 is the kernel that touches every real node each step (its HBM
-// floor is 54 bytes per node; the shared-memory stencil traffic bounds it in
-// practice).  For each node it forms the strains at the midpoints of
-// the 12 edges around it from node differences (Eq. 4 at the edge points):
-// along an edge the tangential derivative is the difference of its two
-// nodes, across it the normal derivative of each side is the sum of that
-// side's two across-edge differences; with two intact neighbours the two
-// sides are averaged (Eqs. 1-2 with equal areas), otherwise each intact side
-// keeps its own strain; sigma = D eps per side (zero for split or missing
-// sides); the node force is B^T sigma A/4 (Eq. 6) summed over those edges
-// and sides, plus the forces of split-element pieces (evaluated in the tile
-// from the pieces' nodes); then the central-difference update.  k_phantom32
-// updates the phantom nodes, evaluating each user piece at the phantom; the
-// two run side by side with the surface evaluation and the selection.
+// One step is four kernels: k_pieces32 evaluates the pieces of every split
+// element (their forces at all eight nodes for the phantom update, and at
+// each element's real nodes for the node update); k_march32 updates every
+// real node (its HBM floor is 53 bytes per active element: u read and
+// written as 16-byte compensated pairs, v read and written as float2, 1/m
+// read, one element-state byte); k_phantom32 updates the phantom nodes from
+// the piece forces; the surface evaluation and the selection run beside them.
+// k_march32 forms, for each node, the strains at the midpoints of the edges
+// around it from node differences (Eq. 4 at the edge points): along an edge
+// the tangential derivative is the difference of its two nodes, across it the
+// normal derivative of each side is the sum of that side's two across-edge
+// differences; with two intact neighbours the two sides are averaged (Eqs.
+// 1-2 with equal areas), otherwise each intact side keeps its own strain;
+// sigma = D eps per side (zero for split or missing sides); the node force is
+// B^T sigma A/4 (Eq. 6) summed over those edges and sides, plus the piece
+// forces of the split elements it belongs to; then the central-difference
+// update.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -267,12 +270,13 @@ __global__ void k_pieces32(DevState d, int cur, int energy, int part_off) {
 
 // -------------------------------------------------------------- warp march
 // One warp updates a tile of WX x TY real nodes by marching up its node
-// rows.  Lane l holds node column c = i0 - 2 + l (columns i0-2 .. i0+29);
-// lanes 2..29 own the tile's WX = 28 columns, the two lanes on each side only
-// supply the values the owned columns need from their neighbours.  Vertical
-// neighbours are the lane's own registers from earlier rows; horizontal ones
-// come from the adjacent lanes by warp shuffles, so the stencil uses no
-// shared memory.  Iteration t loads node row t and forms
+// rows.  Lane l holds the two node columns c_k = i0 - 2 + 2 l + k (columns
+// i0-2 .. i0+61); lanes 1..30 own the tile's WX = 60 columns, lanes 0 and 31
+// only supply the values the owned columns need from their neighbours.
+// Vertical neighbours are the lane's own registers from earlier rows;
+// horizontal ones are the lane's other column or come from the adjacent lanes
+// by warp shuffles (shared memory only stages the rows in flight).  Iteration
+// t loads node row t and forms
 //   Dx(c,t)   = u(c+1,t) - u(c,t)    tangential difference of edge h(c,t)
 //   Dy(c,t-1) = u(c,t) - u(c,t-1)    tangential difference of edge v(c,t-1)
 // (compensated pairs: (hi_b - hi_a) + (lo_b - lo_a)), then the strain and
@@ -722,8 +726,8 @@ __device__ __forceinline__ void march32_tile(const DevState &d, int tile_x, int 
   }
 }
 
-// A CTA of eight warps takes a group of eight consecutive tiles (tile index
-// = tile row * tiles per row + tile column); warp w marches tile 8 g + w.
+// A CTA of four warps takes a group of four consecutive tiles (tile index
+// = tile row * tiles per row + tile column); warp w marches tile 4 g + w.
 // Neighbouring warps share their halo columns through L1.  Each tile writes
 // its own energy partial pair, tiles past the last write zeros.
 constexpr int kMarchWarps = 4;
@@ -928,7 +932,7 @@ cudaError_t launch_march_rows(const DevState &d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// energy partials of the node update: one per tile, in groups of eight
+// energy partials of the node update: one per tile, in groups of four
 int tiles_fp32(const DevState &d, int tile_rows) {
   return march_groups(d.g.nx, d.g.ny, tile_rows) * kMarchWarps;
 }
