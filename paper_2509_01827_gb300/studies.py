@@ -2,6 +2,7 @@
 
     python -m paper_2509_01827_gb300.studies compact_tension [--n 100]
     python -m paper_2509_01827_gb300.studies kalthoff [--n 200,400]
+    python -m paper_2509_01827_gb300.studies ceiling [--n 64]
 
 compact_tension: the Dirichlet compact-tension plate (Sec. 4.3) at the three
 loading rates of Sec. 4.3, FP64 and FP32-mixed, with the dissipated energy U_d
@@ -11,6 +12,12 @@ time, the fragments and the FP32-vs-FP64 Jaccard of the cracked sets.
 kalthoff: the upper half of the Kalthoff-Winkler plate (Sec. 4.1) in the
 multiple-tips and single-tip scopes, with the direction of the crack grown
 from the notch tip in three rings around it (Sec. 4.1 compares crack angles).
+
+ceiling: how far the crack map the surrogate learns is fixed by its input.
+On n runs of the surrogate's data set (test seeds 10^6 + q), the Jaccard
+index at 80 us of the FP32-mixed map (the training target) against the FP64
+map, and of the FP64 and FP32 maps against runs whose G_c field is raised by
+one FP32 ulp everywhere.
 """
 import argparse
 import json
@@ -88,15 +95,40 @@ def kalthoff(ns=(200, 400)):
             print(json.dumps(line), flush=True)
 
 
+def ceiling(n=64):
+    from .cem import CEM_FP32_MIXED, CEM_FP64
+    J = {"fp32_vs_fp64": [], "fp64_vs_gc_ulp": [], "fp32_vs_gc_ulp": []}
+    for q in range(n):
+        seed = 10**6 + q
+        p, _ = inputs.surrogate_run(seed)
+        u, _ = inputs.surrogate_run(seed)
+        u.gc = np.nextafter(u.gc, np.float32(np.inf)).astype(np.float32)
+        c64 = _run(p, CEM_FP64)["cracks"]["elem"]
+        c32 = _run(p, CEM_FP32_MIXED)["cracks"]["elem"]
+        u64 = _run(u, CEM_FP64)["cracks"]["elem"]
+        u32 = _run(u, CEM_FP32_MIXED)["cracks"]["elem"]
+        line = dict(study="ceiling", seed=seed, n64=len(c64), n32=len(c32),
+                    fp32_vs_fp64=metrics.jaccard(c64, c32), fp64_vs_gc_ulp=metrics.jaccard(c64, u64),
+                    fp32_vs_gc_ulp=metrics.jaccard(c32, u32))
+        for k in J:
+            J[k].append(line[k])
+        print(json.dumps(line), flush=True)
+    print(json.dumps(dict(study="ceiling_summary", runs=n,
+                          **{k: dict(mean=float(np.mean(v)), min=float(np.min(v)),
+                                     p10=float(np.percentile(v, 10))) for k, v in J.items()})), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["compact_tension", "kalthoff"])
+    ap.add_argument("study", choices=["compact_tension", "kalthoff", "ceiling"])
     ap.add_argument("--n", default=None)
     a = ap.parse_args()
     from . import build
     build.build()
     if a.study == "compact_tension":
         compact_tension(int(a.n or 100))
+    elif a.study == "ceiling":
+        ceiling(int(a.n or 64))
     else:
         kalthoff(tuple(int(x) for x in (a.n or "200,400").split(",")))
 
