@@ -8,6 +8,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "cem_oracle.c")
+SRC_CST = os.path.join(HERE, "cst_oracle.c")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcem_oracle.so")
 
@@ -15,13 +16,13 @@ LIB = os.path.join(OUT_DIR, "libcem_oracle.so")
 def build(force: bool = False) -> str:
     """Compile the oracle shared library if it is missing or stale; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    deps = [SRC, os.path.join(HERE, "cem_oracle.h")]
+    deps = [SRC, SRC_CST, os.path.join(HERE, "cem_oracle.h"), os.path.join(HERE, "cst_oracle.h")]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
-           "-o", tmp, SRC, "-lm"]
+           "-o", tmp, SRC, SRC_CST, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -361,3 +361,112 @@ CONFIGS = {
     "fragmentation_2048_neumann": lambda: fragmentation(2048, mode="neumann"),
     "fragmentation_2048_dirichlet": lambda: fragmentation(2048, mode="dirichlet"),
 }
+
+
+# ------------------------------------------------ unstructured triangles
+@dataclass
+class TriProblem:
+    """An unstructured mesh of constant-strain triangles (the paper's own
+    element, Sec. 2.1): node coordinates X (nn, 2), counter-clockwise
+    connectivity conn (ne, 3); loads as for Problem, with Neumann items given
+    as edge ids of ``tri_edges`` and Dirichlet items as node ids; an optional
+    initial state init = (ux, uy, vx, vy)."""
+    name: str
+    X: np.ndarray
+    conn: np.ndarray
+    material: Material = field(default_factory=Material)
+    bcs: List[BC] = field(default_factory=list)
+    dt_factor: float = 0.5
+    dt: Optional[float] = None
+    steps: int = 0
+    energy_every: int = 0
+    init: Optional[tuple] = None
+
+    @property
+    def n_nodes(self):
+        return len(self.X)
+
+    @property
+    def n_elems(self):
+        return len(self.conn)
+
+
+def tri_edges(conn):
+    """The edges of a triangle mesh: the distinct node pairs {a, b} of the
+    elements' sides, numbered in increasing (min, max); for each, its nodes
+    n1 < n2 and its elements e1 < e2 (e2 = -1 on the boundary)."""
+    conn = np.asarray(conn, np.int64)
+    ne = len(conn)
+    a = conn.reshape(-1)
+    b = conn[:, [1, 2, 0]].reshape(-1)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    el = np.repeat(np.arange(ne), 3)
+    order = np.lexsort((el, hi, lo))
+    lo, hi, el = lo[order], hi[order], el[order]
+    first = np.ones(len(lo), bool)
+    first[1:] = (lo[1:] != lo[:-1]) | (hi[1:] != hi[:-1])
+    idx = np.flatnonzero(first)
+    n1, n2, e1 = lo[idx], hi[idx], el[idx]
+    e2 = np.full(len(idx), -1, np.int64)
+    two = np.append(idx[1:], len(lo)) - idx == 2
+    e2[two] = el[idx[two] + 1]
+    return dict(n1=n1.astype(np.int32), n2=n2.astype(np.int32), e1=e1.astype(np.int32),
+                e2=e2.astype(np.int32))
+
+
+def tri_plate(nx=40, ny=16, lx=0.1, ly=0.04, jitter=0.25, seed=11, traction=1e6, v0=0.0,
+              t0=1e-6, t_end=20e-6, random_state=0.0, steps=None, name=None,
+              material=None):
+    """A rectangular plate meshed by triangles: an (nx+1) x (ny+1) grid whose
+    interior nodes are moved by up to jitter x the cell size (Philox streams
+    0 and 1 of seed), each cell split along a diagonal that alternates with
+    the cell's parity.  Loads: normal traction on the top and bottom edges
+    (top +y, bottom -y, from t = 0) and, if v0 != 0, a prescribed
+    x-velocity ramped to v0 over t0 on the left edge.  random_state > 0 adds
+    a seeded initial displacement and velocity field of that amplitude
+    (streams 2-5), to exercise every term of the stiffness."""
+    hx, hy = lx / nx, ly / ny
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1))
+    x = ii.reshape(-1) * hx
+    y = jj.reshape(-1) * hy
+    nn = (nx + 1) * (ny + 1)
+    interior = ((ii > 0) & (ii < nx) & (jj > 0) & (jj < ny)).reshape(-1)
+    if jitter:
+        dx = (uniform01(nn, seed, stream=0) - 0.5) * 2.0 * jitter * hx
+        dy = (uniform01(nn, seed, stream=1) - 0.5) * 2.0 * jitter * hy
+        x = np.where(interior, x + dx, x)
+        y = np.where(interior, y + dy, y)
+    X = np.stack([x, y], axis=1)
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            n00, n10 = j * (nx + 1) + i, j * (nx + 1) + i + 1
+            n01, n11 = n00 + nx + 1, n10 + nx + 1
+            if (i + j) % 2 == 0:
+                tris += [(n00, n10, n11), (n00, n11, n01)]
+            else:
+                tris += [(n00, n10, n01), (n10, n11, n01)]
+    conn = np.array(tris, np.int32)
+    ed = tri_edges(conn)
+    yb = ed["e2"] < 0
+    top = np.flatnonzero(yb & (np.abs(y[ed["n1"]] - ly) < 1e-12 * ly) & (np.abs(y[ed["n2"]] - ly) < 1e-12 * ly))
+    bot = np.flatnonzero(yb & (np.abs(y[ed["n1"]]) < 1e-12 * ly) & (np.abs(y[ed["n2"]]) < 1e-12 * ly))
+    bcs = []
+    if traction:
+        bcs += [BC(TRACTION, top.astype(np.int32), 2, LAW_CONST, traction),
+                BC(TRACTION, bot.astype(np.int32), 2, LAW_CONST, -traction)]
+    if v0:
+        left = np.flatnonzero(np.abs(x) < 1e-12 * lx).astype(np.int32)
+        bcs.append(BC(VELOCITY, left, 1, LAW_RAMP, v0, t0))
+    init = None
+    if random_state:
+        r = [(uniform01(nn, seed, stream=q) - 0.5) * random_state for q in (2, 3, 4, 5)]
+        init = (r[0] * hx, r[1] * hy, r[2], r[3])
+    prob = TriProblem(name=name or f"tri_plate_{nx}x{ny}", X=X, conn=conn,
+                      material=material or Material(), bcs=bcs, init=init)
+    if steps is None:
+        m = prob.material
+        cd = math.sqrt(m.E * (1 - m.nu) / (m.rho * (1 + m.nu) * (1 - 2 * m.nu)))
+        steps = int(math.ceil(t_end / (0.5 * 0.5 * min(hx, hy) / cd)))
+    prob.steps = steps
+    return prob
