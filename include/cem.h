@@ -100,6 +100,40 @@ typedef struct {
  * Errors: CEM_ERR_ARG (sizes, capacities, pre-crack triples), CEM_ERR_CUDA. */
 cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out);
 
+/* Unstructured mesh of constant-strain triangles, the paper's own element
+ * (Sec. 2.1): ES-FEM edge strains, the area-weighted average of the two
+ * triangles beside an edge (Eqs. 1, 3), and internal forces B_j^T sigma
+ * A_j / 3 from every triangle j of every edge (Eq. 5); lumped masses
+ * rho A / 3 per node; FP64.  The triangles do not crack on this path.
+ * Edges are the distinct node pairs {a, b} of the triangles' sides,
+ * numbered in increasing (min(a,b), max(a,b)): cem_set_bc's traction and
+ * pressure items are these edge ids (boundary edges only, outward normal
+ * from the counter-clockwise triangle), its velocity items node ids.
+ * On such a handle cem_set_material (G_c, gamma and scope are ignored),
+ * cem_set_bc, cem_set_fields (U, V), cem_step, cem_get_fields (U, V, MASS,
+ * ENERGY with U_d = 0), cem_get_counts, cem_last_error and cem_mesh_destroy
+ * work; every other call returns CEM_ERR_STATE. */
+typedef struct {
+  int n_nodes, n_elems;              /* >= 3, >= 1 */
+  const double *X;                   /* [2*n_nodes]: x, y of node N at X[2N], X[2N+1] (m); copied */
+  const int *conn;                   /* [3*n_elems]: nodes of element e at conn[3e..3e+2],
+                                        counter-clockwise; copied */
+  double dt_factor;                  /* dt = dt_factor * h_min / c_d (0 -> 0.5), h_min the
+                                        smallest altitude 2A / longest side */
+  double dt;                         /* > 0 overrides dt_factor */
+  int energy_every;                  /* record energies every K steps (0 = never) */
+  void *cuda_stream;                 /* cudaStream_t, NULL = a stream of the library's own */
+  int device;                        /* CUDA device ordinal */
+  cem_alloc_fn alloc;                /* optional device allocator */
+  cem_free_fn free;                  /* required when alloc is given */
+  void *alloc_ctx;
+} cem_tri_mesh_desc;
+
+/* Builds the triangle mesh (geometry, edge list, per-node gather lists) and
+ * its device state.  Errors: CEM_ERR_ARG (sizes, node ids, a clockwise or
+ * degenerate triangle, an edge of more than two triangles), CEM_ERR_CUDA. */
+cem_status cem_tri_mesh_create(const cem_tri_mesh_desc *desc, cem_handle **out);
+
 /* Linear elastic material (E > 0, -1 < nu < 0.5, rho > 0), per-element
  * critical energy release rate G_c (gc_per_elem[nx*ny], FP32, or NULL for
  * gc_uniform), plane strain (1) or plane stress (0), the split ratio gamma

@@ -27,9 +27,10 @@ UNITS = [
     ("state_energy_noalloc.cu", ["-fmad=false"]),
     ("surrogate.cu", []),
     ("fragments.cu", []),
+    ("tri.cu", ["-fmad=false"]),
     ("api.cpp", []),
 ]
-HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh"]
+HEADERS = ["cem_internal.h", "q4_fp64.cuh", "eval_common.cuh", "tri_internal.h"]
 
 
 def _stale(obj, deps):

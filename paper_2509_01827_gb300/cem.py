@@ -38,6 +38,13 @@ class cem_mesh_desc(C.Structure):
                 ("free", _FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
+class cem_tri_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("n_elems", C.c_int), ("X", C.POINTER(C.c_double)),
+                ("conn", C.POINTER(C.c_int)), ("dt_factor", C.c_double), ("dt", C.c_double),
+                ("energy_every", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
 class cem_counts(C.Structure):
     _fields_ = [("n_nodes", C.c_long), ("n_phantoms", C.c_long), ("n_elems", C.c_long),
                 ("n_active", C.c_long), ("n_cracked", C.c_long), ("n_surface", C.c_long),
@@ -71,6 +78,7 @@ _h = C.c_void_p
 # name -> (restype, argtypes); every entry point of include/cem.h
 SIGNATURES = {
     "cem_mesh_create": (C.c_int, [C.POINTER(cem_mesh_desc), C.POINTER(C.c_void_p)]),
+    "cem_tri_mesh_create": (C.c_int, [C.POINTER(cem_tri_mesh_desc), C.POINTER(C.c_void_p)]),
     "cem_set_material": (C.c_int, [_h, C.c_double, C.c_double, C.c_double, _fp, C.c_double,
                                    C.c_int, C.c_double, C.c_int, C.c_int]),
     "cem_set_bc": (C.c_int, [_h, C.c_int, C.c_int, _ip, C.c_int, C.c_int, C.c_double,
@@ -131,6 +139,14 @@ def _p(a, t):
 def cem_mesh_create(desc: cem_mesh_desc) -> int:
     h = C.c_void_p()
     rc = lib().cem_mesh_create(C.byref(desc), C.byref(h))
+    if rc != CEM_OK:
+        raise CemError(rc, lib().cem_last_error(None).decode())
+    return h.value
+
+
+def cem_tri_mesh_create(desc: cem_tri_mesh_desc) -> int:
+    h = C.c_void_p()
+    rc = lib().cem_tri_mesh_create(C.byref(desc), C.byref(h))
     if rc != CEM_OK:
         raise CemError(rc, lib().cem_last_error(None).decode())
     return h.value
@@ -530,3 +546,91 @@ class Batch:
 
     def autotune(self, steps_per_candidate=5):
         return cem_batch_autotune(self.h, steps_per_candidate)
+
+
+class TriSolver:
+    """One FP64 run of a ``paper_2509_01827_gb300.inputs.TriProblem`` (an
+    unstructured mesh of constant-strain triangles) on a GPU."""
+
+    def __init__(self, prob: _inputs.TriProblem, device: int = 0, use_torch: bool = True,
+                 stream=None, energy_every: Optional[int] = None):
+        self.prob = prob
+        self.h = None
+        self._mem = None
+        if use_torch:
+            import torch
+            self._mem = TorchDeviceMemory(device)
+            if stream is None:
+                stream = torch.cuda.Stream(device=device)
+            self._stream = stream
+            stream_ptr = stream.cuda_stream
+        else:
+            self._stream = None
+            stream_ptr = 0 if stream is None else int(stream)
+        X = np.ascontiguousarray(prob.X, np.float64).reshape(-1)
+        conn = np.ascontiguousarray(prob.conn, np.int32).reshape(-1)
+        self._keep = [X, conn]
+        d = cem_tri_mesh_desc()
+        d.n_nodes, d.n_elems = len(X) // 2, len(conn) // 3
+        d.X = X.ctypes.data_as(_dp)
+        d.conn = conn.ctypes.data_as(_ip)
+        d.dt_factor = prob.dt_factor
+        d.dt = prob.dt if prob.dt is not None else 0.0
+        d.energy_every = prob.energy_every if energy_every is None else energy_every
+        d.cuda_stream = stream_ptr
+        d.device = device
+        if self._mem is not None:
+            d.alloc = self._mem.alloc_cb
+            d.free = self._mem.free_cb
+        else:
+            d.alloc = _ALLOC_FN()
+            d.free = _FREE_FN()
+        self.h = cem_tri_mesh_create(d)
+        m = prob.material
+        cem_set_material(self.h, m.E, m.nu, m.rho, None, m.gc_uniform, m.plane_strain,
+                         m.gamma, m.gamma_mode, m.scope)
+        for bc in prob.bcs:
+            cem_set_bc(self.h, bc.kind, bc.items, bc.comp_mask, bc.law, bc.a0, bc.t0, bc.tau)
+        if prob.init is not None:
+            self.set_state(*prob.init)
+
+    def close(self):
+        if self.h:
+            cem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        cem_step(self.h, n)
+
+    def counts(self):
+        return cem_get_counts(self.h)
+
+    def set_state(self, ux=None, uy=None, vx=None, vy=None):
+        n = self.prob.n_nodes
+        for which, (a, b) in ((CEM_FIELD_U, (ux, uy)), (CEM_FIELD_V, (vx, vy))):
+            if a is not None or b is not None:
+                f = np.zeros(2 * n)
+                if a is not None:
+                    f[:n] = a
+                if b is not None:
+                    f[n:] = b
+                cem_set_fields(self.h, which, f)
+
+    def nodes(self):
+        n = self.prob.n_nodes
+        u = cem_get_fields(self.h, CEM_FIELD_U, n)
+        v = cem_get_fields(self.h, CEM_FIELD_V, n)
+        m = cem_get_fields(self.h, CEM_FIELD_MASS, n)
+        return dict(ux=u[:n], uy=u[n:], vx=v[:n], vy=v[n:], m=m)
+
+    def energy(self):
+        n = self.counts()["n_energy"]
+        rec = cem_get_fields(self.h, CEM_FIELD_ENERGY, n_energy=n).reshape(n, 7)
+        return dict(step=rec[:, 0].astype(np.int64), t=rec[:, 1], KE=rec[:, 2], SE=rec[:, 3],
+                    W_ext=rec[:, 4], W_dir=rec[:, 5], U_d=rec[:, 6])

@@ -21,6 +21,7 @@
 
 #include "../../include/cem.h"
 #include "cem_internal.h"
+#include "tri_internal.h"
 
 using namespace cem;
 
@@ -64,6 +65,7 @@ struct cem_handle {
   std::string err;
   BatchPlan *batch = nullptr;   // set on a batch handle (cem_batch_create)
   cem_handle *in_batch = nullptr;  // set on a member of a batch
+  TriMesh *tri = nullptr;          // set on an unstructured triangle mesh (tri.cu)
 };
 
 namespace {
@@ -79,6 +81,17 @@ cem_status fail(cem_handle *h, cem_status code, const char *fmt, ...) {
   if (h) h->err = buf; else g_create_error = buf;
   return code;
 }
+
+// a triangle-mesh call's status, its message kept on the handle
+cem_status tri_rc(cem_handle *h, cem_status rc, const std::string &e) {
+  if (rc != CEM_OK) h->err = e;
+  return rc;
+}
+
+#define TRI_NOT_AVAILABLE(h)                                                          \
+  do {                                                                                \
+    if ((h)->tri) return fail((h), CEM_ERR_STATE, "not available on a triangle mesh"); \
+  } while (0)
 
 #define CUDA_TRY(h, expr)                                                               \
   do {                                                                                  \
@@ -352,6 +365,20 @@ const char *cem_last_error(const cem_handle *h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+cem_status cem_tri_mesh_create(const cem_tri_mesh_desc *desc, cem_handle **out) {
+  if (!desc || !out) return fail(nullptr, CEM_ERR_ARG, "null argument");
+  *out = nullptr;
+  std::string e;
+  TriMesh *t = tri_create(desc, e);
+  if (!t) return fail(nullptr, e.rfind("CUDA", 0) == 0 || e.rfind("device", 0) == 0 ? CEM_ERR_CUDA : CEM_ERR_ARG,
+                      "%s", e.c_str());
+  cem_handle *h = new cem_handle();
+  h->tri = t;
+  h->device = desc->device;
+  *out = h;
+  return CEM_OK;
+}
+
 cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
   if (!desc || !out) return fail(nullptr, CEM_ERR_ARG, "null argument");
   *out = nullptr;
@@ -525,6 +552,11 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
 
 void cem_mesh_destroy(cem_handle *h) {
   if (!h) return;
+  if (h->tri) {
+    tri_destroy(h->tri);
+    delete h;
+    return;
+  }
   cudaSetDevice(h->device);
   if (h->batch) batch_release(h);
   if (h->in_batch) batch_detach(h);
@@ -550,6 +582,10 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
                             const float *gc_per_elem, double gc_uniform, int plane_strain,
                             double gamma, int gamma_mode, int mct_scope) {
   if (!h) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_set_material(h->tri, E, nu, rho, plane_strain, e), e);
+  }
   if (h->batch) return fail(h, CEM_ERR_STATE, "not valid on a batch handle");
   if (h->material) return fail(h, CEM_ERR_STATE, "material already set");
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(rho > 0)) return fail(h, CEM_ERR_ARG, "bad material");
@@ -621,6 +657,10 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
 cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items, int comp_mask,
                       int law, double a0, double t0, double tau) {
   if (!h) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_set_bc(h->tri, kind, n_items, items, comp_mask, law, a0, t0, tau, e), e);
+  }
   if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (h->step != 0) return fail(h, CEM_ERR_STATE, "loads must be set before the first step");
   if (n_items < 0 || (n_items > 0 && !items)) return fail(h, CEM_ERR_ARG, "bad items");
@@ -686,6 +726,10 @@ cem_status cem_set_bc(cem_handle *h, int kind, int n_items, const int *items, in
 
 cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_bytes, int on_device) {
   if (!h || !data) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_set_fields(h->tri, which, data, n_bytes, on_device, e), e);
+  }
   if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (h->step != 0) return fail(h, CEM_ERR_STATE, "fields can only be set before the first step");
   if (which != CEM_FIELD_U && which != CEM_FIELD_V) return fail(h, CEM_ERR_ARG, "field not settable");
@@ -716,6 +760,10 @@ cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_byt
 
 cem_status cem_step(cem_handle *h, int n) {
   if (!h) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_step(h->tri, n, e), e);
+  }
   if (h->batch) return batch_step(h, n);
   if (h->in_batch) return fail(h, CEM_ERR_STATE, "a member of a batch is stepped by the batch");
   if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
@@ -774,6 +822,7 @@ cem_status cem_step(cem_handle *h, int n) {
 
 cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
   if (!h || !ms) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
   if (n < 1 || n > h->d.lam_cap) return fail(h, CEM_ERR_ARG, "1 <= n <= %d", h->d.lam_cap);
@@ -825,6 +874,10 @@ cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {
 
 cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
   if (!h || !out) return CEM_ERR_ARG;
+  if (h->tri) {
+    tri_counts(h->tri, out);
+    return CEM_OK;
+  }
   if (h->batch) return batch_counts(h, out);
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
@@ -861,6 +914,10 @@ cem_status cem_get_counts(cem_handle *h, cem_counts *out) {
 
 cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes, int on_device) {
   if (!h || !out) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_get_fields(h->tri, which, out, n_bytes, on_device, e), e);
+  }
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
@@ -997,6 +1054,7 @@ cem_status blob_usable(cem_handle *h) {
 
 cem_status cem_state_size(cem_handle *h, long *n_bytes) {
   if (!h || !n_bytes) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   cem_status rc = blob_usable(h);
   if (rc != CEM_OK) return rc;
   CUDA_TRY(h, cudaSetDevice(h->device));
@@ -1008,6 +1066,7 @@ cem_status cem_state_size(cem_handle *h, long *n_bytes) {
 
 cem_status cem_save_state(cem_handle *h, void *blob, long n_bytes) {
   if (!h || !blob) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   cem_status rc = blob_usable(h);
   if (rc != CEM_OK) return rc;
   CUDA_TRY(h, cudaSetDevice(h->device));
@@ -1046,6 +1105,7 @@ cem_status cem_save_state(cem_handle *h, void *blob, long n_bytes) {
 
 cem_status cem_load_state(cem_handle *h, const void *blob, long n_bytes) {
   if (!h || !blob) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   cem_status rc = blob_usable(h);
   if (rc != CEM_OK) return rc;
   if ((size_t)n_bytes < sizeof(BlobHeader) + sizeof(Counters))
@@ -1093,6 +1153,7 @@ cem_status cem_load_state(cem_handle *h, const void *blob, long n_bytes) {
 
 cem_status cem_get_fragments(cem_handle *h, int *n_fragments, int *piece_fragment, long cap) {
   if (!h || !n_fragments) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   cem_status rc = sync_status(h);
@@ -1118,6 +1179,7 @@ cem_status cem_get_fragments(cem_handle *h, int *n_fragments, int *piece_fragmen
 
 cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
@@ -1157,6 +1219,7 @@ cem_status cem_get_cracks(cem_handle *h, cem_crack *out, int cap, int *n_out) {
 
 cem_status cem_get_phantoms(cem_handle *h, cem_phantom *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
@@ -1213,6 +1276,7 @@ static cem_status surface_rows(cem_handle *h, std::vector<int> &rows) {
 
 cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   std::vector<int> rows;
   cem_status rc = surface_rows(h, rows);
@@ -1230,6 +1294,7 @@ cem_status cem_get_surface(cem_handle *h, int *edge, int *ahead, int *is_tip, in
 
 cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out) {
   if (!h || !n_out) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch) return fail(h, CEM_ERR_STATE, "batch handle: query its members");
   std::vector<int> rows;
   cem_status rc = surface_rows(h, rows);
@@ -1275,6 +1340,7 @@ cem_status cem_get_crack_tips(cem_handle *h, cem_tip *out, int cap, int *n_out) 
 cem_status cem_debug_apply_proposals(cem_handle *h, int n, const int *edge, const int *elem,
                                      const int *k, const double *G) {
   if (!h) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(h);
   if (h->batch || h->in_batch) return fail(h, CEM_ERR_STATE, "not valid on a batch or its members");
   if (!h->material) return fail(h, CEM_ERR_STATE, "material first");
   if (n < 0 || n > h->d.prop_cap) return fail(h, CEM_ERR_ARG, "bad proposal count");
@@ -1583,6 +1649,7 @@ cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_
   for (int s = 0; s < n; ++s) {
     cem_handle *m = members[s];
     if (!m || m->batch) return fail(nullptr, CEM_ERR_ARG, "member %d is not a mesh handle", s);
+    if (m->tri) return fail(nullptr, CEM_ERR_STATE, "member %d is a triangle mesh", s);
     if (m->in_batch) return fail(nullptr, CEM_ERR_STATE, "member %d is already in a batch", s);
     if (!m->material) return fail(nullptr, CEM_ERR_STATE, "member %d has no material", s);
     for (int r = 0; r < s; ++r)
@@ -1658,6 +1725,7 @@ cem_status cem_batch_create(cem_handle *const *members, int n, const long *step_
 
 cem_status cem_batch_set_config(cem_handle *b, int tile_rows, int grid_main) {
   if (!b) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(b);
   if (!b->batch) return fail(b, CEM_ERR_STATE, "not a batch handle");
   BatchPlan *p = b->batch;
   if (tile_rows < 8 || tile_rows > 64) return fail(b, CEM_ERR_ARG, "tile_rows must be in 8 .. 64");
@@ -1674,6 +1742,7 @@ cem_status cem_batch_set_config(cem_handle *b, int tile_rows, int grid_main) {
 cem_status cem_batch_autotune(cem_handle *b, int steps_per_candidate, int *tile_rows,
                               int *grid_main) {
   if (!b) return CEM_ERR_ARG;
+  TRI_NOT_AVAILABLE(b);
   if (!b->batch) return fail(b, CEM_ERR_STATE, "not a batch handle");
   BatchPlan *p = b->batch;
   if (steps_per_candidate < 1) return fail(b, CEM_ERR_ARG, "steps_per_candidate >= 1");
