@@ -13,9 +13,12 @@
 //                 velocities.
 // The gather lists are built once on the host.  Compiled with -fmad=false
 // and summed in the oracle's order, so the fields are bit-identical to it.
-// HBM per step: about 3 x 56 B per element (strain pass: 3 node reads and a
-// 32-byte strain write; the records), 64 B per edge, and per node its
-// incidence list (~6 x (8 + 32 + 24) B) plus 80 B of node state.
+// HBM per step (FP64): per element its record (64 B) and node ids (16 B),
+// three node gathers and a 32-byte strain write; per edge its elements and
+// weights (32 B), two strain gathers and a 32-byte stress write; per node
+// its gather list (32 B per incidence, ~18 incidences: the node's b, c and
+// the triangle's A/3 stored with the edge id, so a node streams its list and
+// gathers only the edge stresses) and ~90 B of node state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,6 +40,13 @@ struct alignas(32) Dbl4 {
   double x, y, z, w;
 };
 
+// one (edge, triangle, local node) incidence of a node's gather list: the
+// edge whose stress it takes and the node's b, c and the triangle's A/3
+struct alignas(32) TriInc {
+  int g, pad;
+  double b, c, q3;
+};
+
 // element record: shape-function derivatives and the area's third
 struct alignas(64) TriElem {
   double b[3], c[3];
@@ -51,8 +61,10 @@ struct TriDev {
   const int2 *edge_el;     // [ned] elements (e2 = -1 on the boundary)
   const double2 *edge_w;   // [ned] (w1, w2) area weights
   const double *edge_a;    // [ned] smoothing-domain area (A1 + A2) / 3
-  const int *inc_ptr;      // [nn + 1]
-  const int2 *inc;         // (edge, 3 e + local node) per incidence
+  const int *inc_deg;      // [nn] incidences of each node
+  const long *slice_off;   // [ceil(nn / 32)] first record of each 32-node slice
+  const TriInc *inc;       // gather lists, sliced: record k of node 32 s + l at
+                           // slice_off[s] + 32 k + l (a warp's loads coalesce)
   Dbl4 *eps;            // [ne]
   Dbl4 *sig;            // [ned]
   double2 *u, *v;          // [nn]
@@ -133,14 +145,14 @@ __global__ void k_tri_node(TriDev d, double lamN, double lamD, double dt, double
   bool bad = false;
   for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < d.nn; N += gridDim.x * blockDim.x) {
     double fx = 0.0, fy = 0.0;
-    for (int q = d.inc_ptr[N]; q < d.inc_ptr[N + 1]; ++q) {
-      const int2 it = d.inc[q];
-      const Dbl4 s = d.sig[it.x];
-      const int e = it.y / 3, i = it.y - 3 * e;
-      const TriElem &r = d.el[e];
-      const double bi = r.b[i], ci = r.c[i], q3 = r.q3;
-      fx = fx + (bi * s.x + ci * s.z) * q3;
-      fy = fy + (ci * s.y + bi * s.z) * q3;
+    const int deg = d.inc_deg[N];
+    const TriInc *rec = d.inc + d.slice_off[N >> 5] + (N & 31);
+#pragma unroll 4
+    for (int k = 0; k < deg; ++k) {
+      const TriInc r = rec[32L * k];
+      const Dbl4 s = d.sig[r.g];
+      fx = fx + (r.b * s.x + r.c * s.z) * r.q3;
+      fy = fy + (r.c * s.y + r.b * s.z) * r.q3;
     }
     const int loaded = d.lflag[N];
     const int dm = d.dmask[N];
@@ -429,14 +441,30 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
       for (int i = 0; i < 3; ++i) cnt[t->conn[3L * e + i] + 1]++;
     }
   for (int N = 0; N < nn; ++N) cnt[N + 1] += cnt[N];
-  std::vector<int2> inc(cnt[nn]);
-  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  // sliced layout: the nodes of slice s = N / 32 store their k-th records
+  // side by side, 32 per row, as many rows as the slice's largest list
+  const int nsl = (nn + 31) / 32;
+  std::vector<int> deg(nn);
+  std::vector<long> soff(nsl + 1, 0);
+  for (int N = 0; N < nn; ++N) deg[N] = cnt[N + 1] - cnt[N];
+  for (int sl = 0; sl < nsl; ++sl) {
+    int dmax = 0;
+    for (int N = 32 * sl; N < std::min(nn, 32 * sl + 32); ++N) dmax = std::max(dmax, deg[N]);
+    soff[sl + 1] = soff[sl] + 32L * dmax;
+  }
+  std::vector<TriInc> inc(std::max(1L, soff[nsl]), TriInc{0, 0, 0.0, 0.0, 0.0});
+  std::vector<int> fill(nn, 0);
   for (int g = 0; g < t->ned; ++g)
     for (int side = 0; side < 2; ++side) {
       const int e = side ? t->ee2[g] : t->ee1[g];
       if (e < 0) continue;
-      for (int i = 0; i < 3; ++i) inc[fill[t->conn[3L * e + i]]++] = make_int2(g, 3 * e + i);
+      for (int i = 0; i < 3; ++i) {
+        const int N = t->conn[3L * e + i];
+        inc[soff[N >> 5] + (N & 31) + 32L * fill[N]++] =
+            TriInc{g, 0, t->el[e].b[i], t->el[e].c[i], t->el[e].q3};
+      }
     }
+  soff.pop_back();
   t->ge = grid_of(t->ned);
   t->gn = grid_of(nn);
   TriDev &d = t->d;
@@ -445,14 +473,17 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
   d.ned = t->ned;
   int4 *dconn;
   TriElem *del;
-  int2 *deel, *dinc;
+  int2 *deel;
+  TriInc *dinc;
   double2 *dew, *dF, *dVp;
   double *dea, *dm, *dminv;
-  int *dptr;
+  int *ddeg;
+  long *dsoff;
   unsigned char *dlf, *ddm;
   bool ok = tri_alloc_n(t, dconn, ne) && tri_alloc_n(t, del, ne) && tri_alloc_n(t, deel, t->ned) &&
             tri_alloc_n(t, dew, t->ned) && tri_alloc_n(t, dea, t->ned) &&
-            tri_alloc_n(t, dptr, (size_t)nn + 1) && tri_alloc_n(t, dinc, inc.size()) &&
+            tri_alloc_n(t, ddeg, (size_t)nn) && tri_alloc_n(t, dsoff, soff.size()) &&
+            tri_alloc_n(t, dinc, inc.size()) &&
             tri_alloc_n(t, d.eps, ne) && tri_alloc_n(t, d.sig, t->ned) &&
             tri_alloc_n(t, d.u, nn) && tri_alloc_n(t, d.v, nn) && tri_alloc_n(t, dm, nn) &&
             tri_alloc_n(t, dminv, nn) && tri_alloc_n(t, dF, nn) && tri_alloc_n(t, dVp, nn) &&
@@ -463,14 +494,14 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
   t->rec_cap = 1024;
   ok = ok && tri_alloc_n(t, d.rec, (size_t)t->rec_cap * 7);
   ok = ok && upload(t, dconn, c4) && upload(t, del, t->el) && upload(t, deel, eel) &&
-       upload(t, dew, ew) && upload(t, dea, ea) && upload(t, dptr, cnt) && upload(t, dinc, inc);
+       upload(t, dew, ew) && upload(t, dea, ea) && upload(t, ddeg, deg) && upload(t, dsoff, soff) && upload(t, dinc, inc);
   if (!ok || cudaStreamSynchronize(t->st) != cudaSuccess) {
     err = "device allocation or upload failed";
     tri_destroy(t);
     return nullptr;
   }
   d.conn = dconn; d.el = del; d.edge_el = deel; d.edge_w = dew; d.edge_a = dea;
-  d.inc_ptr = dptr; d.inc = dinc; d.m = dm; d.minv = dminv; d.F = dF; d.Vp = dVp;
+  d.inc_deg = ddeg; d.slice_off = dsoff; d.inc = dinc; d.m = dm; d.minv = dminv; d.F = dF; d.Vp = dVp;
   d.lflag = dlf; d.dmask = ddm;
   return t;
 }

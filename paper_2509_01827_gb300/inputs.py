@@ -414,17 +414,21 @@ def tri_edges(conn):
                 e2=e2.astype(np.int32))
 
 
-def tri_plate(nx=40, ny=16, lx=0.1, ly=0.04, jitter=0.25, seed=11, traction=1e6, v0=0.0,
+def tri_plate(nx=40, ny=16, lx=0.1, ly=0.04, jitter=0.2, seed=11, traction=1e6, v0=0.0,
               t0=1e-6, t_end=20e-6, random_state=0.0, steps=None, name=None,
               material=None):
     """A rectangular plate meshed by triangles: an (nx+1) x (ny+1) grid whose
     interior nodes are moved by up to jitter x the cell size (Philox streams
-    0 and 1 of seed), each cell split along a diagonal that alternates with
-    the cell's parity.  Loads: normal traction on the top and bottom edges
+    0 and 1 of seed; jitter <= 0.2 keeps every triangle counter-clockwise:
+    two nodes then move at most 0.57 of the 0.71 cell-size altitude towards
+    each other), each cell split along a diagonal that alternates with the
+    cell's parity.  Loads: normal traction on the top and bottom edges
     (top +y, bottom -y, from t = 0) and, if v0 != 0, a prescribed
     x-velocity ramped to v0 over t0 on the left edge.  random_state > 0 adds
     a seeded initial displacement and velocity field of that amplitude
     (streams 2-5), to exercise every term of the stiffness."""
+    if not 0 <= jitter <= 0.2:
+        raise ValueError("jitter must be in [0, 0.2]")
     hx, hy = lx / nx, ly / ny
     ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1))
     x = ii.reshape(-1) * hx

@@ -3,6 +3,7 @@
     python -m paper_2509_01827_gb300.studies compact_tension [--n 100]
     python -m paper_2509_01827_gb300.studies kalthoff [--n 200,400]
     python -m paper_2509_01827_gb300.studies ceiling [--n 64]
+    python -m paper_2509_01827_gb300.studies tri_throughput [--n 1024]
 
 compact_tension: the Dirichlet compact-tension plate (Sec. 4.3) at the three
 loading rates of Sec. 4.3, FP64 and FP32-mixed, with the dissipated energy U_d
@@ -18,6 +19,11 @@ On n runs of the surrogate's data set (test seeds 10^6 + q), the Jaccard
 index at 80 us of the FP32-mixed map (the training target) against the FP64
 map, and of the FP64 and FP32 maps against runs whose G_c field is raised by
 one FP32 ulp everywhere.
+
+tri_throughput: FP64 element-updates/s of the unstructured constant-strain
+triangle path (cem_tri_mesh_create) on an n x n jittered plate of 2 n^2
+triangles with tractions and a random initial state, CUDA events around
+repeated cem_step calls, and the mesh's sizes for the roofline.
 """
 import argparse
 import json
@@ -118,9 +124,32 @@ def ceiling(n=64):
                                      p10=float(np.percentile(v, 10))) for k, v in J.items()})), flush=True)
 
 
+def tri_throughput(n=1024, steps=200, warmup=10):
+    import torch
+    from .cem import TriSolver
+    p = inputs.tri_plate(n, n, lx=0.1, ly=0.1, jitter=0.2, traction=1e6, random_state=1e-3,
+                         steps=steps)
+    g = TriSolver(p)
+    g.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(g._stream)
+    g.step(steps)
+    e1.record(g._stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ed = inputs.tri_edges(p.conn)
+    line = dict(study="tri_throughput", n=n, nodes=int(p.n_nodes), elements=int(p.n_elems),
+                edges=int(len(ed["n1"])), incidences=int(3 * len(ed["n1"]) * 2 - 3 * int(np.sum(ed["e2"] < 0))),
+                steps=steps, ms_per_step=ms, element_updates_per_s=p.n_elems / (ms * 1e-3))
+    g.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["compact_tension", "kalthoff", "ceiling"])
+    ap.add_argument("study", choices=["compact_tension", "kalthoff", "ceiling", "tri_throughput"])
     ap.add_argument("--n", default=None)
     a = ap.parse_args()
     from . import build
@@ -129,6 +158,8 @@ def main():
         compact_tension(int(a.n or 100))
     elif a.study == "ceiling":
         ceiling(int(a.n or 64))
+    elif a.study == "tri_throughput":
+        tri_throughput(int(a.n or 1024))
     else:
         kalthoff(tuple(int(x) for x in (a.n or "200,400").split(",")))
 
