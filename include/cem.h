@@ -104,7 +104,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out);
  * (Sec. 2.1): ES-FEM edge strains, the area-weighted average of the two
  * triangles beside an edge (Eqs. 1, 3), and internal forces B_j^T sigma
  * A_j / 3 from every triangle j of every edge (Eq. 5); lumped masses
- * rho A / 3 per node; FP64.  The triangles do not crack on this path.
+ * rho A / 3 per node; FP64 or FP32-mixed.  The triangles do not crack on
+ * this path.
  * Edges are the distinct node pairs {a, b} of the triangles' sides,
  * numbered in increasing (min(a,b), max(a,b)): cem_set_bc's traction and
  * pressure items are these edge ids (boundary edges only, outward normal
@@ -118,6 +119,9 @@ typedef struct {
   const double *X;                   /* [2*n_nodes]: x, y of node N at X[2N], X[2N+1] (m); copied */
   const int *conn;                   /* [3*n_elems]: nodes of element e at conn[3e..3e+2],
                                         counter-clockwise; copied */
+  int precision;                     /* cem_precision: CEM_FP64, or CEM_FP32_MIXED (FP32
+                                        element arithmetic, displacement as compensated
+                                        float pairs, FP64 energies) */
   double dt_factor;                  /* dt = dt_factor * h_min / c_d (0 -> 0.5), h_min the
                                         smallest altitude 2A / longest side */
   double dt;                         /* > 0 overrides dt_factor */

@@ -40,7 +40,8 @@ class cem_mesh_desc(C.Structure):
 
 class cem_tri_mesh_desc(C.Structure):
     _fields_ = [("n_nodes", C.c_int), ("n_elems", C.c_int), ("X", C.POINTER(C.c_double)),
-                ("conn", C.POINTER(C.c_int)), ("dt_factor", C.c_double), ("dt", C.c_double),
+                ("conn", C.POINTER(C.c_int)), ("precision", C.c_int), ("dt_factor", C.c_double),
+                ("dt", C.c_double),
                 ("energy_every", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
                 ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p)]
 
@@ -549,11 +550,12 @@ class Batch:
 
 
 class TriSolver:
-    """One FP64 run of a ``paper_2509_01827_gb300.inputs.TriProblem`` (an
-    unstructured mesh of constant-strain triangles) on a GPU."""
+    """One run of a ``paper_2509_01827_gb300.inputs.TriProblem`` (an
+    unstructured mesh of constant-strain triangles) on a GPU, FP64 or
+    FP32-mixed."""
 
-    def __init__(self, prob: _inputs.TriProblem, device: int = 0, use_torch: bool = True,
-                 stream=None, energy_every: Optional[int] = None):
+    def __init__(self, prob: _inputs.TriProblem, precision: int = CEM_FP64, device: int = 0,
+                 use_torch: bool = True, stream=None, energy_every: Optional[int] = None):
         self.prob = prob
         self.h = None
         self._mem = None
@@ -574,6 +576,7 @@ class TriSolver:
         d.n_nodes, d.n_elems = len(X) // 2, len(conn) // 3
         d.X = X.ctypes.data_as(_dp)
         d.conn = conn.ctypes.data_as(_ip)
+        d.precision = precision
         d.dt_factor = prob.dt_factor
         d.dt = prob.dt if prob.dt is not None else 0.0
         d.energy_every = prob.energy_every if energy_every is None else energy_every

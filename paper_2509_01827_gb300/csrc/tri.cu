@@ -1,5 +1,6 @@
 // tri.cu -- ES-FEM constant-strain triangles on an unstructured mesh, FP64
-// (Sec. 2.1, Eqs. 1, 3 and 5; the paper's own element).  No cracking.
+// or FP32-mixed (Sec. 2.1, Eqs. 1, 3 and 5; the paper's own element).  No
+// cracking.
 //
 // One step is three kernels:
 //   k_tri_strain  element strain eps_e = B_e u_e (constant on the triangle);
@@ -12,7 +13,11 @@
 //                 central-difference update with loads and prescribed
 //                 velocities.
 // The gather lists are built once on the host.  Compiled with -fmad=false
-// and summed in the oracle's order, so the fields are bit-identical to it.
+// and summed in the oracle's order, so the FP64 fields are bit-identical to
+// it.  The FP32-mixed kernels (suffix 32) keep the displacement as
+// compensated float pairs (error-free two-sum), form element strains from
+// node differences, and do the rest in FP32 with FP64 energy sums: the FP64
+// pipe of this GPU is 1/74 of its FP32 rate, and the FP64 path is bound by it.
 // HBM per step (FP64): per element its record (64 B) and node ids (16 B),
 // three node gathers and a 32-byte strain write; per edge its elements and
 // weights (32 B), two strain gathers and a 32-byte stress write; per node
@@ -54,6 +59,16 @@ struct alignas(64) TriElem {
   double A;
 };
 
+// FP32-mixed mode: the same records in single precision
+struct alignas(32) TriElem32 {
+  float b[3], c[3];
+  float q3, A;
+};
+struct alignas(16) TriInc32 {
+  int g;
+  float b, c, q3;
+};
+
 struct TriDev {
   int nn, ne, ned;
   const int4 *conn;        // [ne] node ids, .w unused
@@ -75,6 +90,14 @@ struct TriDev {
   double *Wn, *Wd;         // [nn]
   double D11, D12, D33;
   double *part;            // energy partials: [grid_edge] SE, then [grid_node] x 3
+  // FP32-mixed mode (u as compensated pairs x.hi, x.lo, y.hi, y.lo)
+  int precision;
+  const TriElem32 *el32;
+  const float2 *edge_w32;
+  const TriInc32 *inc32;
+  float4 *eps32, *sig32, *u4;
+  float2 *v2;
+  const float *minvf;
   double *rec;             // energy records, 7 doubles each
   int *status;             // non-finite flag
 };
@@ -200,6 +223,125 @@ __global__ void k_tri_node(TriDev d, double lamN, double lamD, double dt, double
   }
 }
 
+// ------------------------------------------------------ FP32-mixed mode
+// (hi, lo) += x, error-free (Knuth's two-sum) with renormalisation: the
+// displacement keeps about 48 significant bits without FP64 arithmetic
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  const float l = __fadd_rn(lo, er);
+  const float h = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h, s));
+  hi = h;
+}
+
+// element strain from the differences of nodes 1 and 2 to node 0, each a
+// difference of compensated pairs: b_0 = -(b_1 + b_2), so sum_i b_i u_i =
+// b_1 (u_1 - u_0) + b_2 (u_2 - u_0), free of the cancellation of a large
+// common displacement
+__global__ void k_tri_strain32(TriDev d) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.ne; e += gridDim.x * blockDim.x) {
+    const int4 n = d.conn[e];
+    const TriElem32 &r = d.el32[e];
+    const float4 U0 = d.u4[n.x], U1 = d.u4[n.y], U2 = d.u4[n.z];
+    const float d1x = (U1.x - U0.x) + (U1.y - U0.y), d1y = (U1.z - U0.z) + (U1.w - U0.w);
+    const float d2x = (U2.x - U0.x) + (U2.y - U0.y), d2y = (U2.z - U0.z) + (U2.w - U0.w);
+    const float exx = r.b[1] * d1x + r.b[2] * d2x;
+    const float eyy = r.c[1] * d1y + r.c[2] * d2y;
+    const float gxy = (r.c[1] * d1x + r.c[2] * d2x) + (r.b[1] * d1y + r.b[2] * d2y);
+    d.eps32[e] = make_float4(exx, eyy, gxy, 0.f);
+  }
+}
+
+__global__ void k_tri_edge32(TriDev d, int energy) {
+  double se = 0.0;
+  const float D11 = (float)d.D11, D12 = (float)d.D12, D33 = (float)d.D33;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.ned; g += gridDim.x * blockDim.x) {
+    const int2 el = d.edge_el[g];
+    const float4 e1 = d.eps32[el.x];
+    float ep0 = e1.x, ep1 = e1.y, ep2 = e1.z;
+    if (el.y >= 0) {
+      const float2 w = d.edge_w32[g];
+      const float4 e2 = d.eps32[el.y];
+      ep0 = w.x * e1.x + w.y * e2.x;
+      ep1 = w.x * e1.y + w.y * e2.y;
+      ep2 = w.x * e1.z + w.y * e2.z;
+    }
+    const float s0 = D11 * ep0 + D12 * ep1;
+    const float s1 = D12 * ep0 + D11 * ep1;
+    const float s2 = D33 * ep2;
+    d.sig32[g] = make_float4(s0, s1, s2, 0.f);
+    if (energy) se += 0.5 * (d.edge_a[g] * (double)(ep0 * s0 + ep1 * s1 + ep2 * s2));
+  }
+  if (energy) block_sum_to(se, d.part);
+}
+
+__global__ void k_tri_node32(TriDev d, double lamN, double lamD, double dtd, double dtvd,
+                             int first, int energy, int part_off) {
+  double ke = 0.0, wn = 0.0, wd = 0.0;
+  bool bad = false;
+  const float dt = (float)dtd, dtv = (float)dtvd;
+  for (int N = blockIdx.x * blockDim.x + threadIdx.x; N < d.nn; N += gridDim.x * blockDim.x) {
+    float fx = 0.f, fy = 0.f;
+    const int deg = d.inc_deg[N];
+    const TriInc32 *rec = d.inc32 + d.slice_off[N >> 5] + (N & 31);
+#pragma unroll 4
+    for (int k = 0; k < deg; ++k) {
+      const TriInc32 r = rec[32L * k];
+      const float4 s = d.sig32[r.g];
+      fx = fx + (r.b * s.x + r.c * s.z) * r.q3;
+      fy = fy + (r.c * s.y + r.b * s.z) * r.q3;
+    }
+    const int loaded = d.lflag[N];
+    const int dm = d.dmask[N];
+    float fex = 0.f, fey = 0.f;
+    if (loaded) {
+      const double2 F = d.F[N];
+      fex = (float)(lamN * F.x);
+      fey = (float)(lamN * F.y);
+    }
+    const float mi = d.minvf[N];
+    const float2 vo = d.v2[N];
+    float vxn = vo.x + dtv * ((fex - fx) * mi);
+    float vyn = vo.y + dtv * ((fey - fy) * mi);
+    if (dm) {
+      const double2 V = d.Vp[N];
+      if (dm & 1) vxn = (float)(lamD * V.x);
+      if (dm & 2) vyn = (float)(lamD * V.y);
+    }
+    const double vbx = first ? (double)vo.x : 0.5 * ((double)vo.x + (double)vxn);
+    const double vby = first ? (double)vo.y : 0.5 * ((double)vo.y + (double)vyn);
+    if (energy) {
+      wn += d.Wn[N];
+      wd += d.Wd[N];
+    }
+    if (loaded) d.Wn[N] = d.Wn[N] + dtd * ((double)fex * vbx + (double)fey * vby);
+    if (dm) {
+      const double m = d.m[N], dv = dtvd;
+      const double Rx = m * (((double)vxn - (double)vo.x) / dv) - ((double)fex - (double)fx);
+      const double Ry = m * (((double)vyn - (double)vo.y) / dv) - ((double)fey - (double)fy);
+      double w = 0.0;
+      if (dm & 1) w = w + Rx * vbx;
+      if (dm & 2) w = w + Ry * vby;
+      d.Wd[N] = d.Wd[N] + dtd * w;
+    }
+    if (energy) ke += 0.5 * (d.m[N] * (vbx * vbx + vby * vby));
+    d.v2[N] = make_float2(vxn, vyn);
+    float4 U = d.u4[N];
+    two_sum_acc(U.x, U.y, dt * vxn);
+    two_sum_acc(U.z, U.w, dt * vyn);
+    d.u4[N] = U;
+    bad |= !(fabsf(vxn) <= FLT_MAX) || !(fabsf(vyn) <= FLT_MAX);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.status, 1);
+  if (energy) {
+    block_sum_to(ke, d.part + part_off);
+    block_sum_to(wn, d.part + part_off + gridDim.x);
+    block_sum_to(wd, d.part + part_off + 2 * gridDim.x);
+  }
+}
+
 // one thread: the record (step, t, KE, SE, W_ext, W_dir, U_d = 0) from the
 // partials, summed in block order
 __global__ void k_tri_record(TriDev d, int ge, int gn, int part_off, int slot, double step,
@@ -261,6 +403,7 @@ struct TriMesh {
   int ge = 1, gn = 1;
   TriDev d{};
   int *h_status = nullptr;
+  int precision = CEM_FP64;
 };
 
 namespace {
@@ -392,6 +535,12 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
   t->Vp.assign(nn, make_double2(0.0, 0.0));
   t->lflag.assign(nn, 0);
   t->dmask.assign(nn, 0);
+  if (desc->precision != CEM_FP64 && desc->precision != CEM_FP32_MIXED) {
+    err = "bad precision";
+    delete t;
+    return nullptr;
+  }
+  t->precision = desc->precision;
   t->dt_factor = desc->dt_factor > 0 ? desc->dt_factor : 0.5;
   t->dt_explicit = desc->dt > 0 ? desc->dt : 0.0;
   t->energy_every = desc->energy_every > 0 ? desc->energy_every : 0;
@@ -453,6 +602,7 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
     soff[sl + 1] = soff[sl] + 32L * dmax;
   }
   std::vector<TriInc> inc(std::max(1L, soff[nsl]), TriInc{0, 0, 0.0, 0.0, 0.0});
+  std::vector<TriInc32> inc32(t->precision == CEM_FP32_MIXED ? inc.size() : 0, TriInc32{0, 0.f, 0.f, 0.f});
   std::vector<int> fill(nn, 0);
   for (int g = 0; g < t->ned; ++g)
     for (int side = 0; side < 2; ++side) {
@@ -460,8 +610,10 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
       if (e < 0) continue;
       for (int i = 0; i < 3; ++i) {
         const int N = t->conn[3L * e + i];
-        inc[soff[N >> 5] + (N & 31) + 32L * fill[N]++] =
-            TriInc{g, 0, t->el[e].b[i], t->el[e].c[i], t->el[e].q3};
+        const long at = soff[N >> 5] + (N & 31) + 32L * fill[N]++;
+        inc[at] = TriInc{g, 0, t->el[e].b[i], t->el[e].c[i], t->el[e].q3};
+        if (!inc32.empty())
+          inc32[at] = TriInc32{g, (float)t->el[e].b[i], (float)t->el[e].c[i], (float)t->el[e].q3};
       }
     }
   soff.pop_back();
@@ -491,6 +643,26 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
             tri_alloc_n(t, d.Wd, nn) &&
             tri_alloc_n(t, d.part, (size_t)t->ge + 3 * (size_t)t->gn) &&
             tri_alloc_n(t, d.status, 1);
+  if (ok && t->precision == CEM_FP32_MIXED) {
+    std::vector<TriElem32> e32(ne);
+    for (int e = 0; e < ne; ++e) {
+      for (int i = 0; i < 3; ++i) { e32[e].b[i] = (float)t->el[e].b[i]; e32[e].c[i] = (float)t->el[e].c[i]; }
+      e32[e].q3 = (float)t->el[e].q3;
+      e32[e].A = (float)t->el[e].A;
+    }
+    std::vector<float2> w32(t->ned);
+    for (int g = 0; g < t->ned; ++g) w32[g] = make_float2((float)ew[g].x, (float)ew[g].y);
+    TriElem32 *de32;
+    float2 *dw32;
+    TriInc32 *di32;
+    float *dmf;
+    ok = tri_alloc_n(t, de32, ne) && tri_alloc_n(t, dw32, t->ned) && tri_alloc_n(t, di32, inc32.size()) &&
+         tri_alloc_n(t, d.eps32, ne) && tri_alloc_n(t, d.sig32, t->ned) && tri_alloc_n(t, d.u4, nn) &&
+         tri_alloc_n(t, d.v2, nn) && tri_alloc_n(t, dmf, nn) && upload(t, de32, e32) &&
+         upload(t, dw32, w32) && upload(t, di32, inc32);
+    d.el32 = de32; d.edge_w32 = dw32; d.inc32 = di32; d.minvf = dmf;
+  }
+  d.precision = t->precision;
   t->rec_cap = 1024;
   ok = ok && tri_alloc_n(t, d.rec, (size_t)t->rec_cap * 7);
   ok = ok && upload(t, dconn, c4) && upload(t, del, t->el) && upload(t, deel, eel) &&
@@ -537,7 +709,11 @@ cem_status tri_set_material(TriMesh *t, double E, double nu, double rho, int pla
   }
   for (int N = 0; N < t->nn; ++N) mi[N] = m[N] > 0 ? 1.0 / m[N] : 0.0;
   cudaSetDevice(t->device);
+  std::vector<float> mif;
+  if (t->precision == CEM_FP32_MIXED)
+    for (double x : mi) mif.push_back((float)x);
   if (!upload(t, const_cast<double *>(t->d.m), m) || !upload(t, const_cast<double *>(t->d.minv), mi) ||
+      (!mif.empty() && !upload(t, const_cast<float *>(t->d.minvf), mif)) ||
       cudaStreamSynchronize(t->st) != cudaSuccess) {
     err = "mass upload failed";
     return CEM_ERR_CUDA;
@@ -631,9 +807,29 @@ cem_status tri_set_fields(TriMesh *t, int which, const void *data, long n_bytes,
     return CEM_ERR_CUDA;
   }
   for (long N = 0; N < n; ++N) { il[2 * N] = h[N]; il[2 * N + 1] = h[n + N]; }
-  double2 *dst = which == CEM_FIELD_U ? t->d.u : t->d.v;
-  if (cudaMemcpyAsync(dst, il.data(), 16 * n, cudaMemcpyHostToDevice, t->st) != cudaSuccess ||
-      cudaStreamSynchronize(t->st) != cudaSuccess) {
+  cudaError_t ce;
+  if (t->precision == CEM_FP32_MIXED) {
+    if (which == CEM_FIELD_U) {
+      // compensated pairs: hi = the nearest float, lo = the rest
+      std::vector<float4> u4(n);
+      for (long N = 0; N < n; ++N) {
+        const float xh = (float)il[2 * N], yh = (float)il[2 * N + 1];
+        u4[N] = make_float4(xh, (float)(il[2 * N] - (double)xh), yh, (float)(il[2 * N + 1] - (double)yh));
+      }
+      ce = cudaMemcpyAsync(t->d.u4, u4.data(), 16 * n, cudaMemcpyHostToDevice, t->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+    } else {
+      std::vector<float2> v2(n);
+      for (long N = 0; N < n; ++N) v2[N] = make_float2((float)il[2 * N], (float)il[2 * N + 1]);
+      ce = cudaMemcpyAsync(t->d.v2, v2.data(), 8 * n, cudaMemcpyHostToDevice, t->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+    }
+  } else {
+    double2 *dst = which == CEM_FIELD_U ? t->d.u : t->d.v;
+    ce = cudaMemcpyAsync(dst, il.data(), 16 * n, cudaMemcpyHostToDevice, t->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+  }
+  if (ce != cudaSuccess) {
     err = "upload failed";
     return CEM_ERR_CUDA;
   }
@@ -663,9 +859,15 @@ cem_status tri_step(TriMesh *t, int n, std::string &err) {
     const double lamN = t->neu_set ? law_eval(t->neu_law, tt, t->neu_t0, t->neu_tau) : 0.0;
     const double lamD = t->dir_set ? law_eval(t->dir_law, ((double)s + 0.5) * dt, t->dir_t0, t->dir_tau) : 0.0;
     const double dtv = s == 0 ? 0.5 * dt : dt;
-    k_tri_strain<<<gs, kTB, 0, t->st>>>(t->d);
-    k_tri_edge<<<ge, kTB, 0, t->st>>>(t->d, energy ? 1 : 0);
-    k_tri_node<<<gn, kTB, 0, t->st>>>(t->d, lamN, lamD, dt, dtv, s == 0 ? 1 : 0, energy ? 1 : 0, ge);
+    if (t->precision == CEM_FP32_MIXED) {
+      k_tri_strain32<<<gs, kTB, 0, t->st>>>(t->d);
+      k_tri_edge32<<<ge, kTB, 0, t->st>>>(t->d, energy ? 1 : 0);
+      k_tri_node32<<<gn, kTB, 0, t->st>>>(t->d, lamN, lamD, dt, dtv, s == 0 ? 1 : 0, energy ? 1 : 0, ge);
+    } else {
+      k_tri_strain<<<gs, kTB, 0, t->st>>>(t->d);
+      k_tri_edge<<<ge, kTB, 0, t->st>>>(t->d, energy ? 1 : 0);
+      k_tri_node<<<gn, kTB, 0, t->st>>>(t->d, lamN, lamD, dt, dtv, s == 0 ? 1 : 0, energy ? 1 : 0, ge);
+    }
     t->launches += 3;
     if (energy) {
       if (t->n_rec == t->rec_cap) {
@@ -701,9 +903,26 @@ cem_status tri_get_fields(TriMesh *t, int which, void *out, long n_bytes, int on
   if (which == CEM_FIELD_U || which == CEM_FIELD_V) {
     if (n_bytes < 16 * n) { err = "buffer too small"; return CEM_ERR_ARG; }
     std::vector<double> il(2 * n);
-    if (cudaMemcpyAsync(il.data(), which == CEM_FIELD_U ? t->d.u : t->d.v, 16 * n,
-                        cudaMemcpyDeviceToHost, t->st) != cudaSuccess ||
-        cudaStreamSynchronize(t->st) != cudaSuccess) {
+    cudaError_t ce;
+    if (t->precision == CEM_FP32_MIXED && which == CEM_FIELD_U) {
+      std::vector<float4> u4(n);
+      ce = cudaMemcpyAsync(u4.data(), t->d.u4, 16 * n, cudaMemcpyDeviceToHost, t->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+      for (long N = 0; N < n; ++N) {
+        il[2 * N] = (double)u4[N].x + (double)u4[N].y;
+        il[2 * N + 1] = (double)u4[N].z + (double)u4[N].w;
+      }
+    } else if (t->precision == CEM_FP32_MIXED) {
+      std::vector<float2> v2(n);
+      ce = cudaMemcpyAsync(v2.data(), t->d.v2, 8 * n, cudaMemcpyDeviceToHost, t->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+      for (long N = 0; N < n; ++N) { il[2 * N] = v2[N].x; il[2 * N + 1] = v2[N].y; }
+    } else {
+      ce = cudaMemcpyAsync(il.data(), which == CEM_FIELD_U ? t->d.u : t->d.v, 16 * n,
+                           cudaMemcpyDeviceToHost, t->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+    }
+    if (ce != cudaSuccess) {
       err = "copy failed";
       return CEM_ERR_CUDA;
     }

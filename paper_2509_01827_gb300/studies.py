@@ -20,8 +20,8 @@ index at 80 us of the FP32-mixed map (the training target) against the FP64
 map, and of the FP64 and FP32 maps against runs whose G_c field is raised by
 one FP32 ulp everywhere.
 
-tri_throughput: FP64 element-updates/s of the unstructured constant-strain
-triangle path (cem_tri_mesh_create) on an n x n jittered plate of 2 n^2
+tri_throughput: FP64 and FP32-mixed element-updates/s of the unstructured
+constant-strain triangle path (cem_tri_mesh_create) on an n x n jittered plate of 2 n^2
 triangles with tractions and a random initial state, CUDA events around
 repeated cem_step calls, and the mesh's sizes for the roofline.
 """
@@ -126,25 +126,27 @@ def ceiling(n=64):
 
 def tri_throughput(n=1024, steps=200, warmup=10):
     import torch
-    from .cem import TriSolver
+    from .cem import CEM_FP32_MIXED, CEM_FP64, TriSolver
     p = inputs.tri_plate(n, n, lx=0.1, ly=0.1, jitter=0.2, traction=1e6, random_state=1e-3,
                          steps=steps)
-    g = TriSolver(p)
-    g.step(warmup)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(g._stream)
-    g.step(steps)
-    e1.record(g._stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
     ed = inputs.tri_edges(p.conn)
-    line = dict(study="tri_throughput", n=n, nodes=int(p.n_nodes), elements=int(p.n_elems),
-                edges=int(len(ed["n1"])), incidences=int(3 * len(ed["n1"]) * 2 - 3 * int(np.sum(ed["e2"] < 0))),
-                steps=steps, ms_per_step=ms, element_updates_per_s=p.n_elems / (ms * 1e-3))
-    g.close()
-    print(json.dumps(line), flush=True)
+    for name, prec in (("fp64", CEM_FP64), ("fp32", CEM_FP32_MIXED)):
+        g = TriSolver(p, precision=prec)
+        g.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(g._stream)
+        g.step(steps)
+        e1.record(g._stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        line = dict(study="tri_throughput", precision=name, n=n, nodes=int(p.n_nodes),
+                    elements=int(p.n_elems), edges=int(len(ed["n1"])),
+                    incidences=int(6 * len(ed["n1"]) - 3 * int(np.sum(ed["e2"] < 0))),
+                    steps=steps, ms_per_step=ms, element_updates_per_s=p.n_elems / (ms * 1e-3))
+        g.close()
+        print(json.dumps(line), flush=True)
 
 
 def main():

@@ -111,3 +111,31 @@ def test_argument_and_state_errors():
         cem_set_bc(g.h, inputs.TRACTION, interior, 2, inputs.LAW_CONST, 1.0, 0.0, 0.0)
     assert ei.value.code == CEM_ERR_ARG
     g.close()
+
+
+@pytest.mark.parametrize("case", ["traction_random_state", "velocity"])
+def test_fp32_mixed_against_the_oracle(case):
+    """FP32-mixed triangles (FP32 element arithmetic, compensated float-pair
+    displacement) against the FP64 oracle: displacement error
+    max|u32 - u64| / max|u64| below 1e-5 and energy records within 1e-4 of
+    the largest, over 400 steps."""
+    from oracle.cst_oracle import from_problem
+    from paper_2509_01827_gb300.cem import CEM_FP32_MIXED, TriSolver
+    if case == "traction_random_state":
+        p = inputs.tri_plate(30, 12, jitter=0.2, traction=1e6, random_state=1e-3, steps=400)
+    else:
+        p = inputs.tri_plate(24, 10, jitter=0.2, traction=2e6, v0=0.5, t0=2e-6, steps=400)
+    p.energy_every = 20
+    o = from_problem(p)
+    g = TriSolver(p, precision=CEM_FP32_MIXED)
+    o.step(p.steps)
+    g.step(p.steps)
+    a, b = o.nodes(), g.nodes()
+    for k in ("ux", "uy"):
+        err = np.max(np.abs(b[k] - a[k])) / np.max(np.abs(a[k]))
+        assert err < 1e-5, (k, err)
+    np.testing.assert_array_equal(a["m"], b["m"])
+    ea, eb = o.energy(), g.energy()
+    for k in ("KE", "SE", "W_ext", "W_dir"):
+        scale = max(1e-300, np.max(np.abs(ea[k])))
+        np.testing.assert_allclose(eb[k], ea[k], rtol=0, atol=1e-4 * scale, err_msg=k)
