@@ -645,9 +645,27 @@ __global__ void __launch_bounds__(TB, 4) k_select_batch(BatchDev b) {
 }
 
 // Split writes: eight threads per planned winner (lanes 0-3: local nodes,
-// 4-7: their phantoms / the split record), winners in parallel.  Runs after
-// the node updates of the step, so new phantoms copy u^{n+1} and v^{n+1/2}.
-__device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_next, int mode) {
+// 4-7: their phantoms / the split record), winners in parallel, in two
+// phases.  Phase 1 writes what no kernel of the step reads or writes: the
+// split record, the node lists, new phantoms' tables and work accumulators,
+// the phantom user lists and the surface list (the piece, phantom,
+// evaluation and selection kernels have finished).  Phase 2 writes what the
+// node update reads or produces: new phantoms copy u^{n+1} and v^{n+1/2} of
+// their real node, shared phantoms take the momentum-conserving merge, the
+// masses, the element state and the node update's row flags, and the counter
+// commit.  k_apply runs phase 1 before its grid-dependency wait, beside the
+// node update's last wave.
+__device__ __forceinline__ int apply_phantom(const DevState &d, int w, int a) {
+  int P = d.pl_reuse[w * 4 + a];
+  if (P < 0) {
+    int rank = 0;
+    for (int q = 0; q < a; ++q) rank += d.pl_reuse[w * 4 + q] < 0;
+    P = d.pl_ph0[w] + rank;
+  }
+  return P;
+}
+
+__device__ __forceinline__ void apply_tables(const DevState &d, VBlk vb, int mode) {
   Counters *cnt = d.cnt;
   const Geo &g = d.g;
   const int nw = cnt->pend_nwin;
@@ -660,60 +678,31 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
     const bool act = w < nw;
     const int a = lane & 3;
     if (act && lane < 4) {
-      // local node a: its phantom (new or shared), node lists, user list,
-      // masses; the momentum-conserving merge into a shared phantom
+      // local node a: its phantom (new or shared), node lists, user list
       const int e = d.pl_e[w], info = d.pl_info[w], c = d.pl_c[w];
       const int sd = (info >> (4 + a)) & 1;
       const int N = elem_node(g, e, a);
-      int P = d.pl_reuse[w * 4 + a];
-      const double mold = d.pl_mold[w * 4 + a], mnew = d.pl_mph[w * 4 + a];
-      const int nu = d.pl_nu[w * 4 + a];
-      const int4 us = reinterpret_cast<const int4 *>(d.pl_users)[w * 4 + a];
-      const int4 uf = reinterpret_cast<const int4 *>(d.pl_upf)[w * 4 + a];
-      const double mreal = d.pl_mreal[w * 4 + a], dm = d.pl_dm[w * 4 + a];
-      if (P < 0) {
-        int rank = 0;
-        for (int q = 0; q < a; ++q) rank += d.pl_reuse[w * 4 + q] < 0;
-        P = d.pl_ph0[w] + rank;
-        const int t = P - g.nn;
+      const int P = apply_phantom(d, w, a);
+      const int t = P - g.nn;
+      if (d.pl_reuse[w * 4 + a] < 0) {
         d.ph_owner[t] = N;
         d.ph_creator[t] = e * 4 + a;
         d.Wn[P] = 0.0;
         d.Wd[P] = 0.0;
-        if (d.precision == 1) {
-          d.u4[cur_next][P] = d.u4[cur_next][N];
-          d.v2[P] = d.v2[N];
-        } else {
-          d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
-          d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
-        }
-      } else if (mold >= 0.0) {
-        // merge: the phantom gains mass dm moving with its real node
-        if (d.precision == 1) {
-          const float2 vp = d.v2[P], vn = d.v2[N];
-          const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
-          const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
-          d.v2[P] = make_float2((float)vx, (float)vy);
-        } else {
-          d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
-          d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
-        }
       }
       d.ck_node[c * 8 + sd * 4 + a] = N;
       d.ck_node[c * 8 + (1 - sd) * 4 + a] = P;
-      const int t = P - g.nn;
+      const int nu = d.pl_nu[w * 4 + a];
       if (nu >= 4) {
         atomicOr(&cnt->status, STAT_CAPACITY);
       } else {
-        reinterpret_cast<int4 *>(d.ph_users)[t] = us;
-        reinterpret_cast<int4 *>(d.ph_upf)[t] = uf;
+        reinterpret_cast<int4 *>(d.ph_users)[t] = reinterpret_cast<const int4 *>(d.pl_users)[w * 4 + a];
+        reinterpret_cast<int4 *>(d.ph_upf)[t] = reinterpret_cast<const int4 *>(d.pl_upf)[w * 4 + a];
         const double2 *ua = reinterpret_cast<const double2 *>(d.pl_uap + w * 16 + a * 4);
         reinterpret_cast<double2 *>(d.ph_uap)[2 * t] = ua[0];
         reinterpret_cast<double2 *>(d.ph_uap)[2 * t + 1] = ua[1];
         d.ph_nuser[t] = nu + 1;
       }
-      set_mass(d, N, mreal, d.pl_mireal[w * 4 + a]);
-      set_mass(d, P, mnew, d.pl_miph[w * 4 + a]);
     } else if (act) {
       // lanes 4-7: surface list at local edge k = lane - 4; lane 4 also
       // writes the split record
@@ -753,9 +742,57 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
           d.ck_ud[c] = (double)d.gc[e] * L;
         }
         d.crack_of[e] = c;
-        d.estate[e] = ST_CRACKED;
-        march_rows_split(d, e);
       }
+    }
+  }
+}
+
+__device__ __forceinline__ void apply_nodes(const DevState &d, VBlk vb, int cur_next, int mode) {
+  Counters *cnt = d.cnt;
+  const Geo &g = d.g;
+  const int nw = cnt->pend_nwin;
+  const int step = cnt->pend_step;
+  const int lane32 = threadIdx.x & 31, lane = lane32 & 7, grp = lane32 >> 3;
+  const int warp = (vb.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (vb.gx * blockDim.x) >> 5;
+  for (int wb = warp * 4; wb < nw; wb += nwarps * 4) {
+    const int w = wb + grp;
+    const bool act = w < nw;
+    const int a = lane & 3;
+    if (act && lane < 4) {
+      // local node a: the new phantom's state, or the momentum-conserving
+      // merge into a shared phantom; the masses after the split
+      const int e = d.pl_e[w];
+      const int N = elem_node(g, e, a);
+      const int P = apply_phantom(d, w, a);
+      const double mold = d.pl_mold[w * 4 + a], mnew = d.pl_mph[w * 4 + a];
+      const double mreal = d.pl_mreal[w * 4 + a], dm = d.pl_dm[w * 4 + a];
+      if (d.pl_reuse[w * 4 + a] < 0) {
+        if (d.precision == 1) {
+          d.u4[cur_next][P] = d.u4[cur_next][N];
+          d.v2[P] = d.v2[N];
+        } else {
+          d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
+          d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
+        }
+      } else if (mold >= 0.0) {
+        // merge: the phantom gains mass dm moving with its real node
+        if (d.precision == 1) {
+          const float2 vp = d.v2[P], vn = d.v2[N];
+          const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
+          const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
+          d.v2[P] = make_float2((float)vx, (float)vy);
+        } else {
+          d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
+          d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
+        }
+      }
+      set_mass(d, N, mreal, d.pl_mireal[w * 4 + a]);
+      set_mass(d, P, mnew, d.pl_miph[w * 4 + a]);
+    } else if (act && lane == 4) {
+      const int e = d.pl_e[w];
+      d.estate[e] = ST_CRACKED;
+      march_rows_split(d, e);
     }
   }
   // the commit changes no value that another block of this kernel reads
@@ -769,15 +806,21 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
   }
 }
 
+__device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_next, int mode) {
+  apply_tables(d, vb, mode);
+  apply_nodes(d, vb, cur_next, mode);
+}
+
 // Launched as a programmatic dependent of the kernel before it in the
 // stream: its CTAs may be placed while that kernel's last wave still runs,
 // and wait here until it has completed and its writes are visible.  It lets
 // the next step's tile update be placed in turn (that kernel waits for this
 // one the same way).
 __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+  apply_tables(d, hw_vblk(), mode);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
-  apply_plan(d, hw_vblk(), cur_next, mode);
+  apply_nodes(d, hw_vblk(), cur_next, mode);
 }
 
 // APPLY_VB virtual CTAs per member of a batch; the last CTA to finish
