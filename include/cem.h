@@ -199,6 +199,21 @@ cem_status cem_set_fields(cem_handle *h, int which, const void *data,
  * before cem_set_material. */
 cem_status cem_step(cem_handle *h, int n);
 
+/* Pipelined stepping of a structured mesh handle: enqueues n steps like
+ * cem_step and an asynchronous copy of their status word into pinned host
+ * memory, then waits for the previous cem_step_async call's steps to finish
+ * and returns that call's status (the first call returns CEM_OK).  The
+ * host's wait overlaps the steps just enqueued, so back-to-back calls keep
+ * the GPU busy; each call's errors (CEM_ERR_NONFINITE, CEM_ERR_CAPACITY)
+ * are reported by the call after it, or by cem_sync.  cem_step drains
+ * pending asynchronous calls first.  CEM_ERR_STATE on a batch or triangle
+ * handle. */
+cem_status cem_step_async(cem_handle *h, int n);
+
+/* Waits for every pending cem_step_async call of the handle and returns the
+ * first error among them (CEM_OK if none or nothing is pending). */
+cem_status cem_sync(cem_handle *h);
+
 /* Copies a field into out (host, or device pointer when on_device = 1).
  * n_bytes must be at least the field size (see cem_get_counts). */
 cem_status cem_get_fields(cem_handle *h, int which, void *out, long n_bytes,

@@ -86,6 +86,8 @@ SIGNATURES = {
                              C.c_double, C.c_double]),
     "cem_set_fields": (C.c_int, [_h, C.c_int, C.c_void_p, C.c_long, C.c_int]),
     "cem_step": (C.c_int, [_h, C.c_int]),
+    "cem_step_async": (C.c_int, [_h, C.c_int]),
+    "cem_sync": (C.c_int, [_h]),
     "cem_get_fields": (C.c_int, [_h, C.c_int, C.c_void_p, C.c_long, C.c_int]),
     "cem_get_counts": (C.c_int, [_h, C.POINTER(cem_counts)]),
     "cem_get_crack_tips": (C.c_int, [_h, C.POINTER(cem_tip), C.c_int, _ip]),
@@ -151,6 +153,14 @@ def cem_tri_mesh_create(desc: cem_tri_mesh_desc) -> int:
     if rc != CEM_OK:
         raise CemError(rc, lib().cem_last_error(None).decode())
     return h.value
+
+
+def cem_step_async(h, n):
+    _chk(h, lib().cem_step_async(h, int(n)))
+
+
+def cem_sync(h):
+    _chk(h, lib().cem_sync(h))
 
 
 def cem_last_error(h) -> str:
@@ -413,6 +423,13 @@ class Solver:
 
     def step(self, n=1):
         cem_step(self.h, n)
+
+    def step_async(self, n=1):
+        """Enqueues n steps; raises the previous call's error, if any."""
+        cem_step_async(self.h, n)
+
+    def sync(self):
+        cem_sync(self.h)
 
     def counts(self):
         return cem_get_counts(self.h)

@@ -66,6 +66,11 @@ struct cem_handle {
   BatchPlan *batch = nullptr;   // set on a batch handle (cem_batch_create)
   cem_handle *in_batch = nullptr;  // set on a member of a batch
   TriMesh *tri = nullptr;          // set on an unstructured triangle mesh (tri.cu)
+  // cem_step_async: two pinned status slots, their events, which are pending
+  Counters *h_async = nullptr;
+  cudaEvent_t async_ev[2] = {nullptr, nullptr};
+  int async_next = 0;
+  unsigned async_pending = 0;
 };
 
 namespace {
@@ -175,17 +180,18 @@ int local_edge_host(const cem_handle *h, int e, int g) {
 }
 
 // Status word of the counters mirrored in h->h_cnt.
-cem_status check_status(cem_handle *h) {
-  int s = h->h_cnt->status;
+cem_status check_counters(cem_handle *h, const Counters &c) {
+  int s = c.status;
   if (s & STAT_CAPACITY)
     return fail(h, CEM_ERR_CAPACITY,
                 "capacity exceeded (phantoms %d/%d, cracks %d/%d, list %d/%d, proposals cap %d)",
-                h->h_cnt->n_ph, h->d.ph_cap, h->h_cnt->n_ck, h->d.ck_cap, h->h_cnt->n_S,
-                h->d.list_cap, h->d.prop_cap);
+                c.n_ph, h->d.ph_cap, c.n_ck, h->d.ck_cap, c.n_S, h->d.list_cap, h->d.prop_cap);
   if (s & STAT_NONFINITE) return fail(h, CEM_ERR_NONFINITE, "non-finite displacement or velocity");
   if (s & STAT_TIMEOUT) return fail(h, CEM_ERR_TIMEOUT, "device wait timed out");
   return CEM_OK;
 }
+
+cem_status check_status(cem_handle *h) { return check_counters(h, *h->h_cnt); }
 
 cem_status sync_status(cem_handle *h) {
   CUDA_TRY(h, cudaMemcpyAsync(h->h_cnt, h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
@@ -569,6 +575,9 @@ void cem_mesh_destroy(cem_handle *h) {
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->h_lam) cudaFreeHost(h->h_lam);
+  if (h->h_async) cudaFreeHost(h->h_async);
+  for (cudaEvent_t ev : h->async_ev)
+    if (ev) cudaEventDestroy(ev);
   if (h->ss.aux1) cudaStreamDestroy(h->ss.aux1);
   if (h->ss.aux2) cudaStreamDestroy(h->ss.aux2);
   if (h->ss.fork) cudaEventDestroy(h->ss.fork);
@@ -758,17 +767,10 @@ cem_status cem_set_fields(cem_handle *h, int which, const void *data, long n_byt
   return CEM_OK;
 }
 
-cem_status cem_step(cem_handle *h, int n) {
-  if (!h) return CEM_ERR_ARG;
-  if (h->tri) {
-    std::string e;
-    return tri_rc(h, tri_step(h->tri, n, e), e);
-  }
-  if (h->batch) return batch_step(h, n);
-  if (h->in_batch) return fail(h, CEM_ERR_STATE, "a member of a batch is stepped by the batch");
-  if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
-  if (n < 0) return fail(h, CEM_ERR_ARG, "negative step count");
-  if (n == 0) return CEM_OK;
+// Enqueues n steps of a mesh handle on its stream (graph replays) without
+// waiting for them; the load-factor staging is rewritten only after the
+// copies that read it have finished.
+cem_status enqueue_steps(cem_handle *h, int n) {
   CUDA_TRY(h, cudaSetDevice(h->device));
   cem_status rs = ensure_march_rows(h);
   if (rs != CEM_OK) return rs;
@@ -815,9 +817,89 @@ cem_status cem_step(cem_handle *h, int n) {
     }
     done += chunk;
   }
+  return CEM_OK;
+}
+
+// The status of the oldest pending cem_step_async call, after waiting for it.
+cem_status async_collect(cem_handle *h) {
+  const int slot = h->async_next ^ 1;
+  int first = (h->async_pending & (1u << h->async_next)) ? h->async_next : slot;
+  if (!(h->async_pending & (1u << first))) return CEM_OK;
+  CUDA_TRY(h, cudaEventSynchronize(h->async_ev[first]));
+  h->async_pending &= ~(1u << first);
+  return check_counters(h, h->h_async[first]);
+}
+
+// waits for every pending cem_step_async call; the first error
+cem_status async_drain(cem_handle *h) {
+  cem_status rc = CEM_OK;
+  while (h->async_pending) {
+    cem_status r = async_collect(h);
+    if (rc == CEM_OK) rc = r;
+  }
+  return rc;
+}
+
+cem_status step_checks(cem_handle *h, int n) {
+  if (h->in_batch) return fail(h, CEM_ERR_STATE, "a member of a batch is stepped by the batch");
+  if (!h->material) return fail(h, CEM_ERR_STATE, "cem_set_material must come first");
+  if (n < 0) return fail(h, CEM_ERR_ARG, "negative step count");
+  return CEM_OK;
+}
+
+cem_status cem_step(cem_handle *h, int n) {
+  if (!h) return CEM_ERR_ARG;
+  if (h->tri) {
+    std::string e;
+    return tri_rc(h, tri_step(h->tri, n, e), e);
+  }
+  if (h->batch) return batch_step(h, n);
+  cem_status rc = step_checks(h, n);
+  if (rc != CEM_OK) return rc;
+  rc = async_drain(h);
+  if (rc != CEM_OK) return rc;
+  if (n == 0) return CEM_OK;
+  rc = enqueue_steps(h, n);
+  if (rc != CEM_OK) return rc;
   // one read-back of the status word (non-finite velocities and capacity
   // overflows are flagged by the kernels themselves)
   return sync_status(h);
+}
+
+cem_status cem_step_async(cem_handle *h, int n) {
+  if (!h) return CEM_ERR_ARG;
+  if (h->tri || h->batch) return fail(h, CEM_ERR_STATE, "cem_step_async steps a structured mesh handle");
+  cem_status rc = step_checks(h, n);
+  if (rc != CEM_OK) return rc;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  if (!h->h_async) {
+    CUDA_TRY(h, cudaHostAlloc((void **)&h->h_async, 2 * sizeof(Counters), cudaHostAllocDefault));
+    for (auto &ev : h->async_ev) CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  // a slot still pending from two calls ago is collected first
+  if (h->async_pending & (1u << h->async_next)) {
+    rc = async_collect(h);
+    if (rc != CEM_OK) return rc;
+  }
+  if (n > 0) {
+    rc = enqueue_steps(h, n);
+    if (rc != CEM_OK) return rc;
+  }
+  const int slot = h->async_next;
+  CUDA_TRY(h, cudaMemcpyAsync(&h->h_async[slot], h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaEventRecord(h->async_ev[slot], h->st));
+  h->async_pending |= 1u << slot;
+  h->async_next ^= 1;
+  // the previous call's status, while this call's steps run
+  if (h->async_pending & (1u << h->async_next)) return async_collect(h);
+  return CEM_OK;
+}
+
+cem_status cem_sync(cem_handle *h) {
+  if (!h) return CEM_ERR_ARG;
+  if (h->tri || h->batch) return CEM_OK;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  return async_drain(h);
 }
 
 cem_status cem_profile_steps(cem_handle *h, int n, double *ms) {

@@ -42,3 +42,54 @@ def test_one_call_equals_single_steps(precision):
     assert a.counts()["step"] == b.counts()["step"] == n
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_async_steps_equal_blocking_steps(precision):
+    """cem_step_async, one step per call with each call collecting the
+    previous call's status, then cem_sync, ends bit-identical to cem_step."""
+    from paper_2509_01827_gb300.cem import Solver
+    p = inputs.notched_plate(100, 40, traction=3e6, steps=0, phantom_cap=20000, crack_cap=4000)
+    p.energy_every = 10
+    a, b = Solver(p, precision=precision), Solver(p, precision=precision)
+    n = 237
+    a.step(n)
+    for _ in range(n):
+        b.step_async(1)
+    b.sync()
+    na, nb = a.nodes(), b.nodes()
+    for k in ("ux", "uy", "vx", "vy", "m"):
+        np.testing.assert_array_equal(na[k], nb[k], err_msg=k)
+    ca, cb = a.cracks(), b.cracks()
+    assert len(ca["elem"]) > 0
+    for k in ("elem", "ka", "kb", "step", "nodes"):
+        np.testing.assert_array_equal(ca[k], cb[k], err_msg=k)
+    ea, eb = a.energy(), b.energy()
+    for k in ("step", "KE", "SE", "W_ext", "W_dir", "U_d"):
+        np.testing.assert_array_equal(ea[k], eb[k], err_msg=k)
+    assert b.counts()["step"] == n
+    a.close()
+    b.close()
+
+
+def test_async_errors_come_one_call_late():
+    """A non-finite state makes the steps of one cem_step_async call fail:
+    that call returns, and the next call (or cem_sync) reports the error."""
+    from paper_2509_01827_gb300.cem import CEM_ERR_NONFINITE, CemError, Solver
+    p = inputs.notched_plate(37, 19, steps=0)
+    s = Solver(p, precision=1)
+    vx = np.zeros(s.n_total())
+    vx[5] = np.nan
+    s.set_state(vx=vx)
+    s.step_async(3)
+    with pytest.raises(CemError) as ei:
+        s.sync()
+    assert ei.value.code == CEM_ERR_NONFINITE
+    s.close()
+    s = Solver(p, precision=1)
+    s.set_state(vx=vx)
+    s.step_async(3)
+    with pytest.raises(CemError) as ei:
+        s.step_async(1)
+    assert ei.value.code == CEM_ERR_NONFINITE
+    s.close()
