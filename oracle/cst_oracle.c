@@ -43,6 +43,9 @@ struct ocst {
   unsigned char *lflag, *dmask;
   int neu_set, neu_law, dir_set, dir_law;
   double neu_t0, neu_tau, dir_t0, dir_tau;
+  float *gc;             /* [ne] critical energy release rate */
+  double gamma;
+  int gamma_mode;
   int step, energy_every, nrec, reccap;
   double *erec;
   char err[256];
@@ -76,7 +79,7 @@ static int cmp_half(const void *p, const void *q) {
 
 void ocst_destroy(ocst *s) {
   if (!s) return;
-  void *p[] = {s->X, s->conn, s->A, s->b, s->c, s->en1, s->en2, s->ee1, s->ee2, s->ux, s->uy,
+  void *p[] = {s->gc, s->X, s->conn, s->A, s->b, s->c, s->en1, s->en2, s->ee1, s->ee2, s->ux, s->uy,
                s->vx, s->vy, s->m, s->minv, s->fx, s->fy, s->eps_e, s->eps_g, s->sig_g, s->Fx,
                s->Fy, s->Vx, s->Vy, s->Wn, s->Wd, s->lflag, s->dmask, s->erec};
   for (size_t q = 0; q < sizeof p / sizeof p[0]; ++q) free(p[q]);
@@ -179,7 +182,18 @@ ocst *ocst_create(int nn, int ne, const double *X, const int *conn) {
   s->sig_g = (double *)zalloc((size_t)ned * 3 * 8);
   s->reccap = 64;
   s->erec = (double *)zalloc((size_t)s->reccap * 7 * 8);
+  s->gc = (float *)zalloc((size_t)ne * 4);
+  for (int e = 0; e < ne; ++e) s->gc[e] = 3.0f;
+  s->gamma = 1.0;
   return s;
+}
+
+int ocst_set_fracture(ocst *s, const float *gc, double gc_uniform, double gamma, int gamma_mode) {
+  if (gamma_mode < 0 || gamma_mode > 1) return fail(s, -1, "bad gamma mode");
+  for (int e = 0; e < s->ne; ++e) s->gc[e] = gc ? gc[e] : (float)gc_uniform;
+  s->gamma = gamma;
+  s->gamma_mode = gamma_mode;
+  return 0;
 }
 
 int ocst_n_edges(const ocst *s) { return s->ned; }
@@ -488,5 +502,75 @@ int ocst_strain_energy(ocst *s, double *se) {
   if (!s->mat_set) return fail(s, -6, "material first");
   compute_forces(s);
   *se = strain_energy(s);
+  return 0;
+}
+
+/* ------------------------------------------------------ crack evaluation */
+
+/* Sec. 2.2, CST: the point is the midpoint g0 of local edge k0 of the intact
+ * triangle e (nodes N1 = conn[k0], N2 = conn[k0+1], counter-clockwise).
+ *   delta_d = (u_N2 - u_N1) H, H = 1 iff |x_N2 - x_N1|^2 > |X_N2 - X_N1|^2;
+ *   candidate j: the segment from g0 to the midpoint g of local edge
+ *   k = k0 + 1 + j, unit normal n oriented so that n . (X_N2 - X_N1) > 0,
+ *   sigma the stress of edge g as the triangle uses it (the smoothed edge
+ *   stress), G_j = delta_d . (sigma n) / 2.
+ * Decision: candidates with G > G_c(e); one such wins; with two, the path p
+ * wins if G_p > gamma (G_p - G_q) (ratio mode: G_p > gamma G_q), the larger G
+ * (the lower local edge on a tie) when both pass, none when neither does. */
+int ocst_eval_surface(ocst *s, int n, const int *edge, const int *elem, double *G, int *choice) {
+  if (!s->mat_set) return fail(s, -6, "material first");
+  compute_forces(s);
+  for (int q = 0; q < n; ++q) {
+    const int g0 = edge[q], e = elem[q];
+    if (g0 < 0 || g0 >= s->ned || e < 0 || e >= s->ne || (s->ee1[g0] != e && s->ee2[g0] != e))
+      return fail(s, -1, "point %d: edge %d is not an edge of element %d", q, g0, e);
+    const int *cn = s->conn + 3 * e;
+    int k0 = -1;
+    for (int k = 0; k < 3; ++k) {
+      const int a = cn[k], b = cn[(k + 1) % 3];
+      if ((a == s->en1[g0] && b == s->en2[g0]) || (a == s->en2[g0] && b == s->en1[g0])) k0 = k;
+    }
+    const int N1 = cn[k0], N2 = cn[(k0 + 1) % 3];
+    const double X1 = s->X[2 * N1], Y1 = s->X[2 * N1 + 1], X2 = s->X[2 * N2], Y2 = s->X[2 * N2 + 1];
+    const double dX = X2 - X1, dY = Y2 - Y1;
+    const double dux = s->ux[N2] - s->ux[N1], duy = s->uy[N2] - s->uy[N1];
+    const double lx = dX + dux, ly = dY + duy;
+    const int H = lx * lx + ly * ly > dX * dX + dY * dY;
+    const double ddx = H ? dux : 0.0, ddy = H ? duy : 0.0;
+    const double mx0 = 0.5 * (X1 + X2), my0 = 0.5 * (Y1 + Y2);
+    double Gj[2];
+    int kj[2];
+    for (int j = 0; j < 2; ++j) {
+      const int k = (k0 + 1 + j) % 3;
+      kj[j] = k;
+      const int a = cn[k], b = cn[(k + 1) % 3];
+      const double mx = 0.5 * (s->X[2 * a] + s->X[2 * b]), my = 0.5 * (s->X[2 * a + 1] + s->X[2 * b + 1]);
+      const double tx = mx - mx0, ty = my - my0;
+      const double L = sqrt(tx * tx + ty * ty);
+      double nx = -ty / L, ny = tx / L;
+      if (nx * dX + ny * dY < 0) { nx = -nx; ny = -ny; }
+      /* the edge of the triangle's local edge k */
+      int g = -1;
+      for (int h = 0; h < s->ned; ++h)
+        if ((s->en1[h] == (a < b ? a : b)) && (s->en2[h] == (a < b ? b : a))) { g = h; break; }
+      const double *sg = s->sig_g + 3 * g;
+      const double snx = sg[0] * nx + sg[2] * ny, sny = sg[2] * nx + sg[1] * ny;
+      Gj[j] = 0.5 * (ddx * snx + ddy * sny);
+      G[2 * q + j] = Gj[j];
+    }
+    const double gc = (double)s->gc[e];
+    const int a0 = Gj[0] > gc, a1 = Gj[1] > gc;
+    int pick = -1;
+    if (a0 && !a1) pick = 0;
+    else if (a1 && !a0) pick = 1;
+    else if (a0 && a1) {
+      const int p0 = s->gamma_mode ? Gj[0] > s->gamma * Gj[1] : Gj[0] > s->gamma * (Gj[0] - Gj[1]);
+      const int p1 = s->gamma_mode ? Gj[1] > s->gamma * Gj[0] : Gj[1] > s->gamma * (Gj[1] - Gj[0]);
+      if (p0 && p1) pick = Gj[1] > Gj[0] ? 1 : (Gj[0] > Gj[1] ? 0 : (kj[0] < kj[1] ? 0 : 1));
+      else if (p0) pick = 0;
+      else if (p1) pick = 1;
+    }
+    choice[q] = pick < 0 ? -1 : kj[pick];
+  }
   return 0;
 }

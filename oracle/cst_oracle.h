@@ -33,6 +33,10 @@ int ocst_n_edges(const ocst *s);
 int ocst_edges(const ocst *s, int *n1, int *n2, int *e1, int *e2);
 
 int ocst_set_material(ocst *s, double E, double nu, double rho, int plane_strain);
+/* critical energy release rate per element (gc NULL: gc_uniform) and the
+ * split ratio of the CST decision rule (gamma_mode 0: G_p > gamma (G_p - G_q),
+ * 1: G_p > gamma G_q) */
+int ocst_set_fracture(ocst *s, const float *gc, double gc_uniform, double gamma, int gamma_mode);
 /* dt = dt_factor * h_min / c_d, h_min the smallest element altitude
  * (2 A / longest edge), unless dt_explicit > 0. */
 int ocst_set_dt(ocst *s, double dt_factor, double dt_explicit);
@@ -52,6 +56,12 @@ int ocst_n_energy(const ocst *s);
 int ocst_get_energy(const ocst *s, double *rec);
 int ocst_internal_force(ocst *s, double *fx, double *fy);
 int ocst_strain_energy(ocst *s, double *se);
+/* Crack evaluation at n surface points (Sec. 2.2, CST): point q is edge
+ * edge[q] of its intact element elem[q] (the element ahead).  G[2q + j]
+ * is the energy release rate of the path from the point to the midpoint of
+ * the element's j-th other edge (its local edges k0+1, k0+2 mod 3, k0 the
+ * point's own); choice[q] the local edge of the chosen path, -1 for none. */
+int ocst_eval_surface(ocst *s, int n, const int *edge, const int *elem, double *G, int *choice);
 
 #ifdef __cplusplus
 }

@@ -41,6 +41,9 @@ def lib():
         L.ocst_get_energy.argtypes = [C.c_void_p, _dp]
         L.ocst_internal_force.argtypes = [C.c_void_p, _dp, _dp]
         L.ocst_strain_energy.argtypes = [C.c_void_p, _dp]
+        L.ocst_set_fracture.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_double, C.c_double,
+                                        C.c_int]
+        L.ocst_eval_surface.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _dp, _ip]
         _READY = True
     return L
 
@@ -122,6 +125,20 @@ class CstOracle:
         self._chk(lib().ocst_internal_force(self._h, _p(fx, _dp), _p(fy, _dp)))
         return fx, fy
 
+    def set_fracture(self, gc=None, gc_uniform=3.0, gamma=1.0, gamma_mode=0):
+        g = None if gc is None else np.ascontiguousarray(gc, np.float32)
+        self._chk(lib().ocst_set_fracture(self._h, None if g is None else g.ctypes.data_as(
+            C.POINTER(C.c_float)), gc_uniform, gamma, gamma_mode))
+
+    def eval_surface(self, edge, elem):
+        e = np.ascontiguousarray(edge, np.int32)
+        el = np.ascontiguousarray(elem, np.int32)
+        G = np.zeros(2 * len(e))
+        ch = np.zeros(len(e), np.int32)
+        self._chk(lib().ocst_eval_surface(self._h, len(e), _p(e, _ip), _p(el, _ip), _p(G, _dp),
+                                          _p(ch, _ip)))
+        return G.reshape(-1, 2), ch
+
     def strain_energy(self):
         se = np.zeros(1)
         self._chk(lib().ocst_strain_energy(self._h, _p(se, _dp)))
@@ -133,6 +150,7 @@ def from_problem(prob):
     s = CstOracle(prob.X, prob.conn)
     m = prob.material
     s.set_material(m.E, m.nu, m.rho, m.plane_strain)
+    s.set_fracture(getattr(prob, "gc", None), m.gc_uniform, m.gamma, m.gamma_mode)
     if prob.dt is not None:
         s.set_dt(0.0, prob.dt)
     else:

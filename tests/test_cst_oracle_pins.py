@@ -197,3 +197,51 @@ def test_work_balance_with_traction_and_velocity():
     work = e["W_ext"] + e["W_dir"]
     assert work[-1] > 0
     assert np.max(np.abs(tot - work)) < 2e-2 * np.max(np.abs(work))
+
+
+def _eyy_triangle(e, gc, gamma=1.0, gamma_mode=0, nu=0.25):
+    """The triangle (0,0), (1,0), (0,1) under u_y = e y (uniform eps_yy = e),
+    plane strain E = 1."""
+    s = CstOracle(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]), np.array([[0, 1, 2]]))
+    s.set_material(1.0, nu, 1.0, plane_strain=True)
+    s.set_fracture(None, gc, gamma, gamma_mode)
+    s.set_state(uy=np.array([0.0, 0.0, e]))
+    D11 = (1 - nu) / ((1 + nu) * (1 - 2 * nu))
+    return s, D11
+
+
+def test_G_hand_computation_uniform_eyy():
+    """Sec. 2.2, CST.  The point is the midpoint (0, 1/2) of the left edge
+    (local edge 2, N1 = node 2 at (0,1), N2 = node 0 at (0,0); edge id 1 of
+    the pairs (0,1), (0,2), (1,2)).  delta_d = u_N2 - u_N1 = (0, -e), the edge
+    stretches (H = 1).  Candidate local edge 0 (midpoint (1/2, 0)): the
+    segment's normal along X_N2 - X_N1 = (0, -1) is n = -(1, 1)/sqrt 2, the
+    stress (D12 e, D11 e, 0) gives sigma n = -(D12, D11) e/sqrt 2, so
+    G = D11 e^2 / (2 sqrt 2).  Candidate local edge 1 (midpoint (1/2, 1/2)):
+    the segment is horizontal, n = (0, -1), sigma n = (0, -D11 e), so
+    G = D11 e^2 / 2.  Both above G_c: the larger (local edge 1) wins."""
+    e = 1e-3
+    s, D11 = _eyy_triangle(e, gc=1e-9)
+    G, ch = s.eval_surface([1], [0])
+    assert G[0, 0] == pytest.approx(D11 * e * e / (2 * np.sqrt(2)), rel=1e-12)
+    assert G[0, 1] == pytest.approx(D11 * e * e / 2, rel=1e-12)
+    assert ch[0] == 1
+    # G_c between the two: only local edge 1 qualifies; above both: none
+    s.set_fracture(None, 0.4 * D11 * e * e, 1.0, 0)
+    assert s.eval_surface([1], [0])[1][0] == 1
+    s.set_fracture(None, 0.6 * D11 * e * e, 1.0, 0)
+    assert s.eval_surface([1], [0])[1][0] == -1
+
+
+def test_G_ratio_mode_and_compression():
+    """Ratio mode (G_p > gamma G_q): G_1 / G_0 = sqrt 2, so gamma = 1.2 picks
+    local edge 1 and gamma = 2 picks none.  Under compression (e < 0) the
+    edge shortens, H = 0 and both G vanish."""
+    e = 1e-3
+    s, D11 = _eyy_triangle(e, gc=1e-9, gamma=1.2, gamma_mode=1)
+    assert s.eval_surface([1], [0])[1][0] == 1
+    s.set_fracture(None, 1e-9, 2.0, 1)
+    assert s.eval_surface([1], [0])[1][0] == -1
+    s2, _ = _eyy_triangle(-e, gc=1e-12)
+    G, ch = s2.eval_surface([1], [0])
+    assert np.all(G == 0.0) and ch[0] == -1
