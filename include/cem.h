@@ -110,7 +110,8 @@ cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out);
  * numbered in increasing (min(a,b), max(a,b)): cem_set_bc's traction and
  * pressure items are these edge ids (boundary edges only, outward normal
  * from the counter-clockwise triangle), its velocity items node ids.
- * On such a handle cem_set_material (G_c, gamma and scope are ignored),
+ * On such a handle cem_set_material (G_c and gamma serve cem_tri_eval_surface;
+ * the scope is ignored),
  * cem_set_bc, cem_set_fields (U, V), cem_step, cem_get_fields (U, V, MASS,
  * ENERGY with U_d = 0), cem_get_counts, cem_last_error and cem_mesh_destroy
  * work; every other call returns CEM_ERR_STATE. */
@@ -137,6 +138,26 @@ typedef struct {
  * its device state.  Errors: CEM_ERR_ARG (sizes, node ids, a clockwise or
  * degenerate triangle, an edge of more than two triangles), CEM_ERR_CUDA. */
 cem_status cem_tri_mesh_create(const cem_tri_mesh_desc *desc, cem_handle **out);
+
+/* Crack evaluation of constant-strain triangles at n surface points (Sec.
+ * 2.2, the CST rules), FP64 from the current displacement (in FP32-mixed
+ * mode the float pairs are summed first).  Point q is edge edge[q] of
+ * element elem[q] (the element ahead), with nodes N1, N2 in the element's
+ * counter-clockwise order.  delta_d = (u_N2 - u_N1) when the edge is
+ * stretched (|x_N2 - x_N1|^2 > |X_N2 - X_N1|^2), else 0.  G[2q + j], j = 0,
+ * 1, is the energy release rate delta_d . (sigma n) / 2 of the path from the
+ * edge's midpoint to the midpoint of the element's local edge k0 + 1 + j
+ * (mod 3), k0 the point's own local edge: n the segment's unit normal with
+ * n . (X_N2 - X_N1) > 0, sigma that edge's smoothed stress.  choice[q] is
+ * the local edge of the chosen path or -1: paths with G above the element's
+ * G_c qualify; of two, path p wins if G_p > gamma (G_p - G_q) (ratio mode:
+ * G_p > gamma G_q), the larger G when both pass (the lower local edge on a
+ * tie); G_c, gamma and its mode come from cem_set_material.  Host arrays:
+ * edge, elem [n]; G [2n]; choice [n].  Errors: CEM_ERR_ARG (an edge that is
+ * not an edge of its element), CEM_ERR_STATE (not a triangle mesh, or before
+ * cem_set_material). */
+cem_status cem_tri_eval_surface(cem_handle *h, int n, const int *edge, const int *elem,
+                                double *G, int *choice);
 
 /* Linear elastic material (E > 0, -1 < nu < 0.5, rho > 0), per-element
  * critical energy release rate G_c (gc_per_elem[nx*ny], FP32, or NULL for

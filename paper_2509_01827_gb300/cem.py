@@ -80,6 +80,7 @@ _h = C.c_void_p
 SIGNATURES = {
     "cem_mesh_create": (C.c_int, [C.POINTER(cem_mesh_desc), C.POINTER(C.c_void_p)]),
     "cem_tri_mesh_create": (C.c_int, [C.POINTER(cem_tri_mesh_desc), C.POINTER(C.c_void_p)]),
+    "cem_tri_eval_surface": (C.c_int, [_h, C.c_int, _ip, _ip, _dp, _ip]),
     "cem_set_material": (C.c_int, [_h, C.c_double, C.c_double, C.c_double, _fp, C.c_double,
                                    C.c_int, C.c_double, C.c_int, C.c_int]),
     "cem_set_bc": (C.c_int, [_h, C.c_int, C.c_int, _ip, C.c_int, C.c_int, C.c_double,
@@ -607,8 +608,8 @@ class TriSolver:
             d.free = _FREE_FN()
         self.h = cem_tri_mesh_create(d)
         m = prob.material
-        cem_set_material(self.h, m.E, m.nu, m.rho, None, m.gc_uniform, m.plane_strain,
-                         m.gamma, m.gamma_mode, m.scope)
+        cem_set_material(self.h, m.E, m.nu, m.rho, getattr(prob, "gc", None), m.gc_uniform,
+                         m.plane_strain, m.gamma, m.gamma_mode, m.scope)
         for bc in prob.bcs:
             cem_set_bc(self.h, bc.kind, bc.items, bc.comp_mask, bc.law, bc.a0, bc.t0, bc.tau)
         if prob.init is not None:
@@ -654,3 +655,14 @@ class TriSolver:
         rec = cem_get_fields(self.h, CEM_FIELD_ENERGY, n_energy=n).reshape(n, 7)
         return dict(step=rec[:, 0].astype(np.int64), t=rec[:, 1], KE=rec[:, 2], SE=rec[:, 3],
                     W_ext=rec[:, 4], W_dir=rec[:, 5], U_d=rec[:, 6])
+
+    def eval_surface(self, edge, elem):
+        """G of the two candidate paths and the chosen local edge (-1: none)
+        at surface points (edge[q] of element elem[q])."""
+        e = np.ascontiguousarray(edge, np.int32)
+        el = np.ascontiguousarray(elem, np.int32)
+        G = np.zeros(2 * len(e))
+        ch = np.zeros(len(e), np.int32)
+        _chk(self.h, lib().cem_tri_eval_surface(self.h, len(e), _p(e, _ip), _p(el, _ip),
+                                                _p(G, _dp), _p(ch, _ip)))
+        return G.reshape(-1, 2), ch

@@ -385,6 +385,14 @@ cem_status cem_tri_mesh_create(const cem_tri_mesh_desc *desc, cem_handle **out) 
   return CEM_OK;
 }
 
+cem_status cem_tri_eval_surface(cem_handle *h, int n, const int *edge, const int *elem, double *G,
+                                int *choice) {
+  if (!h) return CEM_ERR_ARG;
+  if (!h->tri) return fail(h, CEM_ERR_STATE, "not a triangle mesh");
+  std::string e;
+  return tri_rc(h, tri_eval_surface(h->tri, n, edge, elem, G, choice, e), e);
+}
+
 cem_status cem_mesh_create(const cem_mesh_desc *desc, cem_handle **out) {
   if (!desc || !out) return fail(nullptr, CEM_ERR_ARG, "null argument");
   *out = nullptr;
@@ -593,7 +601,8 @@ cem_status cem_set_material(cem_handle *h, double E, double nu, double rho,
   if (!h) return CEM_ERR_ARG;
   if (h->tri) {
     std::string e;
-    return tri_rc(h, tri_set_material(h->tri, E, nu, rho, plane_strain, e), e);
+    return tri_rc(h, tri_set_material(h->tri, E, nu, rho, plane_strain, gc_per_elem, gc_uniform,
+                                      gamma, gamma_mode, e), e);
   }
   if (h->batch) return fail(h, CEM_ERR_STATE, "not valid on a batch handle");
   if (h->material) return fail(h, CEM_ERR_STATE, "material already set");

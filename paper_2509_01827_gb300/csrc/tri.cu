@@ -90,6 +90,10 @@ struct TriDev {
   double *Wn, *Wd;         // [nn]
   double D11, D12, D33;
   double *part;            // energy partials: [grid_edge] SE, then [grid_node] x 3
+  // crack evaluation: node coordinates, edge nodes, each element's edges
+  const double2 *X;        // [nn]
+  const int2 *edge_nodes;  // [ned] (min, max)
+  const int4 *elem_edges;  // [ne] edge ids of local edges 0, 1, 2
   // FP32-mixed mode (u as compensated pairs x.hi, x.lo, y.hi, y.lo)
   int precision;
   const TriElem32 *el32;
@@ -342,6 +346,106 @@ __global__ void k_tri_node32(TriDev d, double lamN, double lamD, double dtd, dou
   }
 }
 
+// ------------------------------------------------------- crack evaluation
+// FP64 displacement of node N in either precision
+__device__ __forceinline__ double2 node_u64(const TriDev &d, int N) {
+  if (d.precision == CEM_FP32_MIXED) {
+    const float4 U = d.u4[N];
+    return make_double2((double)U.x + (double)U.y, (double)U.z + (double)U.w);
+  }
+  return d.u[N];
+}
+
+// strain of element e from the current displacement, in the oracle's order
+__device__ __forceinline__ void elem_strain64(const TriDev &d, int e, double ep[3]) {
+  const int4 n = d.conn[e];
+  const int nd[3] = {n.x, n.y, n.z};
+  const TriElem &r = d.el[e];
+  double exx = 0.0, eyy = 0.0, gxy = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double2 u = node_u64(d, nd[i]);
+    exx = exx + r.b[i] * u.x;
+    eyy = eyy + r.c[i] * u.y;
+    gxy = gxy + (r.c[i] * u.x + r.b[i] * u.y);
+  }
+  ep[0] = exx; ep[1] = eyy; ep[2] = gxy;
+}
+
+// Sec. 2.2 for triangles, one thread per surface point (edge g0 of element
+// e): delta_d over the point's edge with the stretch test, the energy
+// release rate of the path to the midpoint of each of the element's two
+// other edges (the edge's smoothed stress on the segment's normal), and the
+// decision rule; FP64 in either precision.
+__global__ void k_tri_eval(TriDev d, int n, const int *edge, const int *elem, const float *gc,
+                           double gamma, int gamma_mode, double *G, int *choice) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int g0 = edge[q], e = elem[q];
+    const int4 cn4 = d.conn[e];
+    const int cn[3] = {cn4.x, cn4.y, cn4.z};
+    const int2 en = d.edge_nodes[g0];
+    int k0 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const int a = cn[k], b = cn[(k + 1) % 3];
+      if ((a == en.x && b == en.y) || (a == en.y && b == en.x)) k0 = k;
+    }
+    const int N1 = cn[k0], N2 = cn[(k0 + 1) % 3];
+    const double2 P1 = d.X[N1], P2 = d.X[N2];
+    const double dX = P2.x - P1.x, dY = P2.y - P1.y;
+    const double2 u1 = node_u64(d, N1), u2 = node_u64(d, N2);
+    const double dux = u2.x - u1.x, duy = u2.y - u1.y;
+    const double lx = dX + dux, ly = dY + duy;
+    const bool H = lx * lx + ly * ly > dX * dX + dY * dY;
+    const double ddx = H ? dux : 0.0, ddy = H ? duy : 0.0;
+    const double mx0 = 0.5 * (P1.x + P2.x), my0 = 0.5 * (P1.y + P2.y);
+    const int4 ee = d.elem_edges[e];
+    const int eds[3] = {ee.x, ee.y, ee.z};
+    double Gj[2];
+    int kj[2];
+    for (int j = 0; j < 2; ++j) {
+      const int k = (k0 + 1 + j) % 3;
+      kj[j] = k;
+      const double2 A = d.X[cn[k]], B = d.X[cn[(k + 1) % 3]];
+      const double mx = 0.5 * (A.x + B.x), my = 0.5 * (A.y + B.y);
+      const double tx = mx - mx0, ty = my - my0;
+      const double L = sqrt(tx * tx + ty * ty);
+      double nx = -ty / L, ny = tx / L;
+      if (nx * dX + ny * dY < 0) { nx = -nx; ny = -ny; }
+      const int g = eds[k];
+      const int2 el = d.edge_el[g];
+      double ep[3], e1[3], e2[3];
+      elem_strain64(d, el.x, e1);
+      if (el.y >= 0) {
+        elem_strain64(d, el.y, e2);
+        const double2 w = d.edge_w[g];
+        for (int c = 0; c < 3; ++c) ep[c] = w.x * e1[c] + w.y * e2[c];
+      } else {
+        for (int c = 0; c < 3; ++c) ep[c] = e1[c];
+      }
+      const double s0 = d.D11 * ep[0] + d.D12 * ep[1];
+      const double s1 = d.D12 * ep[0] + d.D11 * ep[1];
+      const double s2 = d.D33 * ep[2];
+      const double snx = s0 * nx + s2 * ny, sny = s2 * nx + s1 * ny;
+      Gj[j] = 0.5 * (ddx * snx + ddy * sny);
+      G[2 * q + j] = Gj[j];
+    }
+    const double gce = (double)gc[e];
+    const bool a0 = Gj[0] > gce, a1 = Gj[1] > gce;
+    int pick = -1;
+    if (a0 && !a1) {
+      pick = 0;
+    } else if (a1 && !a0) {
+      pick = 1;
+    } else if (a0 && a1) {
+      const bool p0 = gamma_mode ? Gj[0] > gamma * Gj[1] : Gj[0] > gamma * (Gj[0] - Gj[1]);
+      const bool p1 = gamma_mode ? Gj[1] > gamma * Gj[0] : Gj[1] > gamma * (Gj[1] - Gj[0]);
+      if (p0 && p1) pick = Gj[1] > Gj[0] ? 1 : (Gj[0] > Gj[1] ? 0 : (kj[0] < kj[1] ? 0 : 1));
+      else if (p0) pick = 0;
+      else if (p1) pick = 1;
+    }
+    choice[q] = pick < 0 ? -1 : kj[pick];
+  }
+}
+
 // one thread: the record (step, t, KE, SE, W_ext, W_dir, U_d = 0) from the
 // partials, summed in block order
 __global__ void k_tri_record(TriDev d, int ge, int gn, int part_off, int slot, double step,
@@ -404,6 +508,10 @@ struct TriMesh {
   TriDev d{};
   int *h_status = nullptr;
   int precision = CEM_FP64;
+  std::vector<float> gc;  // per element
+  double gamma = 1.0;
+  int gamma_mode = 0;
+  float *d_gc = nullptr;
 };
 
 namespace {
@@ -672,6 +780,38 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
     tri_destroy(t);
     return nullptr;
   }
+  // crack-evaluation tables: coordinates, edge nodes, each element's edges
+  {
+    std::vector<double2> X2(nn);
+    for (int N = 0; N < nn; ++N) X2[N] = make_double2(t->X[2L * N], t->X[2L * N + 1]);
+    std::vector<int2> enod(t->ned);
+    for (int g = 0; g < t->ned; ++g) enod[g] = make_int2(t->en1[g], t->en2[g]);
+    std::vector<int4> eed(ne, make_int4(-1, -1, -1, -1));
+    // each element's local edge k is the node pair (conn[k], conn[k+1])
+    for (int g = 0; g < t->ned; ++g)
+      for (int side = 0; side < 2; ++side) {
+        const int e = side ? t->ee2[g] : t->ee1[g];
+        if (e < 0) continue;
+        for (int k = 0; k < 3; ++k) {
+          const int a = t->conn[3L * e + k], b = t->conn[3L * e + (k + 1) % 3];
+          if (std::min(a, b) == t->en1[g] && std::max(a, b) == t->en2[g]) (&eed[e].x)[k] = g;
+        }
+      }
+    double2 *dX;
+    int2 *dEn;
+    int4 *dEe;
+    float *dgc;
+    t->gc.assign(ne, 3.0f);
+    if (!tri_alloc_n(t, dX, nn) || !tri_alloc_n(t, dEn, t->ned) || !tri_alloc_n(t, dEe, ne) ||
+        !tri_alloc_n(t, dgc, ne) || !upload(t, dX, X2) || !upload(t, dEn, enod) ||
+        !upload(t, dEe, eed) || !upload(t, dgc, t->gc) || cudaStreamSynchronize(t->st) != cudaSuccess) {
+      err = "device allocation or upload failed";
+      tri_destroy(t);
+      return nullptr;
+    }
+    d.X = dX; d.edge_nodes = dEn; d.elem_edges = dEe;
+    t->d_gc = dgc;
+  }
   d.conn = dconn; d.el = del; d.edge_el = deel; d.edge_w = dew; d.edge_a = dea;
   d.inc_deg = ddeg; d.slice_off = dsoff; d.inc = dinc; d.m = dm; d.minv = dminv; d.F = dF; d.Vp = dVp;
   d.lflag = dlf; d.dmask = ddm;
@@ -681,9 +821,15 @@ TriMesh *tri_create(const cem_tri_mesh_desc *desc, std::string &err) {
 int tri_n_edges(const TriMesh *t) { return t->ned; }
 
 cem_status tri_set_material(TriMesh *t, double E, double nu, double rho, int plane_strain,
+                            const float *gc, double gc_uniform, double gamma, int gamma_mode,
                             std::string &err) {
   if (t->material) { err = "material already set"; return CEM_ERR_STATE; }
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(rho > 0)) { err = "bad material"; return CEM_ERR_ARG; }
+  if (gamma_mode < 0 || gamma_mode > 1) { err = "bad gamma mode"; return CEM_ERR_ARG; }
+  for (int e = 0; e < t->ne; ++e) t->gc[e] = gc ? gc[e] : (float)gc_uniform;
+  t->gamma = gamma;
+  t->gamma_mode = gamma_mode;
+  if (!upload(t, t->d_gc, t->gc)) { err = "upload failed"; return CEM_ERR_CUDA; }
   t->E = E; t->nu = nu; t->rho = rho;
   double cd;
   if (plane_strain) {
@@ -954,6 +1100,45 @@ cem_status tri_get_fields(TriMesh *t, int which, void *out, long n_bytes, int on
     err = "copy failed";
     return CEM_ERR_CUDA;
   }
+  return CEM_OK;
+}
+
+cem_status tri_eval_surface(TriMesh *t, int n, const int *edge, const int *elem, double *G,
+                            int *choice, std::string &err) {
+  if (!t->material) { err = "cem_set_material must come first"; return CEM_ERR_STATE; }
+  if (n < 0 || (n > 0 && (!edge || !elem || !G || !choice))) { err = "bad arguments"; return CEM_ERR_ARG; }
+  if (n == 0) return CEM_OK;
+  for (int q = 0; q < n; ++q) {
+    const int g = edge[q], e = elem[q];
+    if (g < 0 || g >= t->ned || e < 0 || e >= t->ne || (t->ee1[g] != e && t->ee2[g] != e)) {
+      err = "point " + std::to_string(q) + ": not an edge of its element";
+      return CEM_ERR_ARG;
+    }
+  }
+  cudaSetDevice(t->device);
+  int *dedge = nullptr, *delem = nullptr, *dch = nullptr;
+  double *dG = nullptr;
+  cudaError_t ce = cudaMallocAsync((void **)&dedge, 4L * n, t->st);
+  if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&delem, 4L * n, t->st);
+  if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&dch, 4L * n, t->st);
+  if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&dG, 16L * n, t->st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dedge, edge, 4L * n, cudaMemcpyHostToDevice, t->st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(delem, elem, 4L * n, cudaMemcpyHostToDevice, t->st);
+  if (ce == cudaSuccess) {
+    k_tri_eval<<<grid_of(n), kTB, 0, t->st>>>(t->d, n, dedge, delem, t->d_gc, t->gamma,
+                                              t->gamma_mode, dG, dch);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(G, dG, 16L * n, cudaMemcpyDeviceToHost, t->st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(choice, dch, 4L * n, cudaMemcpyDeviceToHost, t->st);
+  for (void *p : {(void *)dedge, (void *)delem, (void *)dch, (void *)dG})
+    if (p) cudaFreeAsync(p, t->st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(t->st);
+  if (ce != cudaSuccess) {
+    err = std::string("evaluation failed: ") + cudaGetErrorString(ce);
+    return CEM_ERR_CUDA;
+  }
+  t->launches += 1;
   return CEM_OK;
 }
 

@@ -381,6 +381,7 @@ class TriProblem:
     steps: int = 0
     energy_every: int = 0
     init: Optional[tuple] = None
+    gc: Optional[np.ndarray] = None          # float32 per element, None = uniform
 
     @property
     def n_nodes(self):

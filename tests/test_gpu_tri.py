@@ -139,3 +139,40 @@ def test_fp32_mixed_against_the_oracle(case):
     for k in ("KE", "SE", "W_ext", "W_dir"):
         scale = max(1e-300, np.max(np.abs(ea[k])))
         np.testing.assert_allclose(eb[k], ea[k], rtol=0, atol=1e-4 * scale, err_msg=k)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_crack_evaluation_against_the_oracle(precision):
+    """G of the two candidate paths and the CST decision rule (Sec. 2.2) at
+    every boundary edge and a set of interior (edge, element) points after
+    120 steps, with a per-element G_c field around the median G: FP64
+    bit-identical to the oracle; FP32-mixed G within 1e-4 of the largest and
+    the same decisions wherever G is not within 1e-3 of G_c."""
+    from oracle.cst_oracle import from_problem
+    from paper_2509_01827_gb300.cem import TriSolver
+    p = inputs.tri_plate(30, 12, jitter=0.2, traction=5e6, random_state=1e-3, steps=120)
+    ed = inputs.tri_edges(p.conn)
+    bnd = np.flatnonzero(ed["e2"] < 0)
+    inner = np.flatnonzero(ed["e2"] >= 0)[::7]
+    edge = np.concatenate([bnd, inner, inner]).astype(np.int32)
+    elem = np.concatenate([ed["e1"][bnd], ed["e1"][inner], ed["e2"][inner]]).astype(np.int32)
+    pre = from_problem(p)
+    pre.step(p.steps)
+    Gpre, _ = pre.eval_surface(edge, elem)
+    scale = float(np.median(np.abs(Gpre[Gpre != 0]))) if np.any(Gpre != 0) else 1.0
+    p.gc = (scale * (0.5 + inputs.uniform01(len(p.conn), 5))).astype(np.float32)
+    o = from_problem(p)
+    g = TriSolver(p, precision=precision)
+    o.step(p.steps)
+    g.step(p.steps)
+    Go, co = o.eval_surface(edge, elem)
+    Gg, cg = g.eval_surface(edge, elem)
+    assert np.any(co >= 0) and np.any(co < 0)
+    if precision == 0:
+        np.testing.assert_array_equal(Gg, Go)
+        np.testing.assert_array_equal(cg, co)
+    else:
+        np.testing.assert_allclose(Gg, Go, rtol=0, atol=1e-4 * np.max(np.abs(Go)))
+        gce = p.gc[elem].astype(np.float64)[:, None]
+        near = np.any(np.abs(Go / gce - 1.0) < 1e-3, axis=1)
+        np.testing.assert_array_equal(cg[~near], co[~near])
