@@ -4,10 +4,11 @@
  * The surrogate learns the map from a notched-plate run's inputs -- the
  * traction, the notch and the critical energy release rate field G_c of the
  * explicit solver (include/cem.h) -- to the run's cracked-element map at the
- * end time.  It is a 4-level U-Net: per level two 3x3 convolutions with
- * ReLU, 2x2 max pooling down, nearest 2x upsampling and channel
- * concatenation of the skip up, a 1x1 head to one logit per element, and a
- * class-weighted binary cross-entropy, trained with Adam.  The paper has no
+ * end time.  It is a U-Net (levels set by the caller): per level two 3x3
+ * convolutions with ReLU, 2x2 max pooling down, nearest 2x upsampling and
+ * channel concatenation of the skip up, a 1x1 head to one logit per element,
+ * and a class-weighted binary cross-entropy (optionally plus a soft Dice
+ * term), trained with Adam.  The paper has no
  * such network; the solver's runs supply its training data.
  *
  * Conventions:
@@ -105,6 +106,20 @@ long cem_sg_bce_workspace(long n);
  * (uint8), and dz = d loss / d z. */
 int cem_sg_bce(const float *z, const unsigned char *t, long n, float pos_weight, float *dz,
                float *loss, void *ws, long ws_bytes, void *stream);
+
+/* Workspace bytes cem_sg_dice needs (0 for bad sizes). */
+long cem_sg_dice_workspace(int B, long n_per);
+
+/* Soft Dice loss of B samples of n_per logits each (z, t sample-major,
+ * t in {0, 1}), weighted by `weight`: with p = sigmoid(z), per sample
+ * D_b = (2 sum p t + eps) / (sum p + sum t + eps), and
+ *   loss[0] = weight (1 - mean_b D_b)       (overwritten),
+ *   dz     += weight d(1 - mean_b D_b)/dz   (added, e.g. to the BCE gradient).
+ * The overlap of the predicted and the target cracked sets is what the
+ * surrogate is judged by (the Jaccard index J = D / (2 - D) on hard maps);
+ * this term trains for it directly.  eps > 0; sums in a fixed order. */
+int cem_sg_dice(const float *z, const unsigned char *t, int B, long n_per, float weight, float eps,
+                float *dz, float *loss, void *ws, long ws_bytes, void *stream);
 
 /* One Adam step (Kingma and Ba, bias-corrected, step >= 1) on n FP32
  * weights w with gradient g and moments m, v; writes the BF16 copy w_bf16

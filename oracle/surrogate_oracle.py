@@ -107,6 +107,29 @@ def bce_logits(z, t, pos_weight):
     return loss.mean(), dz
 
 
+def soft_dice(z, t, eps=1.0):
+    """Soft Dice loss of each sample's probability map against its target,
+    averaged over the samples (z, t [n, ...]; p = sigmoid(z)):
+        D_b = (2 sum p t + eps) / (sum p + sum t + eps),  loss = 1 - mean_b D_b,
+    and its gradient with respect to z,
+        d loss / d z_i = -(1/n) (2 t_i (S_b + eps) - (2 I_b + eps)) / (S_b + eps)^2
+                         * p_i (1 - p_i),
+    I_b = sum p t and S_b = sum p + sum t of the sample b that holds i."""
+    z = z.astype(np.float64)
+    t = t.astype(np.float64)
+    n = z.shape[0]
+    p = 1.0 / (1.0 + np.exp(-z))
+    ax = tuple(range(1, z.ndim))
+    inter = (p * t).sum(axis=ax)
+    s = p.sum(axis=ax) + t.sum(axis=ax)
+    d = (2.0 * inter + eps) / (s + eps)
+    shape = (n,) + (1,) * (z.ndim - 1)
+    S, I = (s + eps).reshape(shape), inter.reshape(shape)
+    dd_dp = (2.0 * t * S - (2.0 * I + eps)) / (S * S)
+    dz = -dd_dp * p * (1.0 - p) / n
+    return 1.0 - d.mean(), dz
+
+
 def adam(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma and Ba) with bias correction; step counts from 1."""
     m = b1 * m + (1.0 - b1) * g

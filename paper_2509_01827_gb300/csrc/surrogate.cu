@@ -1074,6 +1074,90 @@ __global__ void k_bce(const float *z, const uint8_t *t, long n, float pw, float 
   if (threadIdx.x == 0) ws[blockIdx.x] = red[0];
 }
 
+// soft Dice over B samples of n_per logits each: per-(sample, chunk) partial
+// sums of p t, p and t (p = sigma(z)), block (c, b) covering elements
+// [c * chunk, (c + 1) * chunk) of sample b
+constexpr int kDiceChunk = 4096;
+
+__device__ __forceinline__ float block_sum256(float v, float *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const float s = red[0];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_dice_partial(const float *z, const uint8_t *t, long n_per,
+                                                      float *ws) {
+  __shared__ float red[256];
+  const int c = blockIdx.x, b = blockIdx.y, nchunk = gridDim.x;
+  const long lo = (long)c * kDiceChunk, hi = min(n_per, lo + kDiceChunk);
+  const float *zb = z + (size_t)b * n_per;
+  const uint8_t *tb = t + (size_t)b * n_per;
+  float spt = 0.f, sp = 0.f, st = 0.f;
+  for (long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float p = 1.f / (1.f + expf(-zb[i]));
+    const float tt = tb[i] ? 1.f : 0.f;
+    spt += p * tt;
+    sp += p;
+    st += tt;
+  }
+  spt = block_sum256(spt, red);
+  sp = block_sum256(sp, red);
+  st = block_sum256(st, red);
+  if (threadIdx.x == 0) {
+    float *o = ws + ((size_t)b * nchunk + c) * 3;
+    o[0] = spt;
+    o[1] = sp;
+    o[2] = st;
+  }
+}
+
+// dz += -(w / B) (2 t (S + eps) - (2 I + eps)) / (S + eps)^2 p (1 - p), the
+// sample's sums I = sum p t, S = sum p + sum t added in chunk order
+__global__ void __launch_bounds__(256) k_dice_grad(const float *z, const uint8_t *t, long n_per,
+                                                   int B, float w, float eps, const float *ws,
+                                                   float *dz) {
+  const int c = blockIdx.x, b = blockIdx.y, nchunk = gridDim.x;
+  float I = 0.f, S = 0.f;
+  for (int q = 0; q < nchunk; ++q) {
+    const float *o = ws + ((size_t)b * nchunk + q) * 3;
+    I += o[0];
+    S += o[1] + o[2];
+  }
+  const float Se = S + eps, num = 2.f * I + eps, scale = -w / ((float)B * Se * Se);
+  const long lo = (long)c * kDiceChunk, hi = min(n_per, lo + kDiceChunk);
+  const float *zb = z + (size_t)b * n_per;
+  const uint8_t *tb = t + (size_t)b * n_per;
+  float *db = dz + (size_t)b * n_per;
+  for (long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float p = 1.f / (1.f + expf(-zb[i]));
+    const float tt = tb[i] ? 1.f : 0.f;
+    db[i] += scale * (2.f * tt * Se - num) * p * (1.f - p);
+  }
+}
+
+// loss = w (1 - mean_b D_b), D_b = (2 I_b + eps) / (S_b + eps), in sample order
+__global__ void k_dice_loss(const float *ws, int nchunk, int B, float w, float eps, float *loss) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float dsum = 0.f;
+    for (int b = 0; b < B; ++b) {
+      float I = 0.f, S = 0.f;
+      for (int q = 0; q < nchunk; ++q) {
+        const float *o = ws + ((size_t)b * nchunk + q) * 3;
+        I += o[0];
+        S += o[1] + o[2];
+      }
+      dsum += (2.f * I + eps) / (S + eps);
+    }
+    loss[0] = w * (1.f - dsum / (float)B);
+  }
+}
+
 __global__ void k_sum_scaled(const float *ws, int m, float scale, float *out) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     float s = 0.f;
@@ -1298,6 +1382,25 @@ int cem_sg_bce(const float *z, const unsigned char *t, long n, float pos_weight,
   const int g = grid_1d(n, 256);
   k_bce<<<g, 256, 0, st>>>(z, t, n, pos_weight, dz, (float *)ws);
   k_sum_scaled<<<1, 32, 0, st>>>((const float *)ws, g, 1.f / (float)n, loss);
+  return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
+}
+
+long cem_sg_dice_workspace(int B, long n_per) {
+  if (B < 1 || n_per < 1) return 0;
+  return (long)B * ((n_per + kDiceChunk - 1) / kDiceChunk) * 3 * 4;
+}
+
+int cem_sg_dice(const float *z, const unsigned char *t, int B, long n_per, float weight, float eps,
+                float *dz, float *loss, void *ws, long ws_bytes, void *stream) {
+  if (!z || !t || !dz || !loss || !ws || B < 1 || n_per < 1 || !(eps > 0.f)) return CEM_SG_ERR_ARG;
+  if (ws_bytes < cem_sg_dice_workspace(B, n_per)) return CEM_SG_ERR_ARG;
+  const long nchunk = (n_per + kDiceChunk - 1) / kDiceChunk;
+  if (nchunk > 65535 || B > 65535) return CEM_SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const dim3 grid((unsigned)nchunk, (unsigned)B);
+  k_dice_partial<<<grid, 256, 0, st>>>(z, t, n_per, (float *)ws);
+  k_dice_grad<<<grid, 256, 0, st>>>(z, t, n_per, B, weight, eps, (const float *)ws, dz);
+  k_dice_loss<<<1, 32, 0, st>>>((const float *)ws, (int)nchunk, B, weight, eps, loss);
   return cudaGetLastError() == cudaSuccess ? CEM_SG_OK : CEM_SG_ERR_CUDA;
 }
 

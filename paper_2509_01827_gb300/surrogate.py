@@ -5,7 +5,8 @@ happen here; PyTorch supplies device memory and the stream.
 Network (per level l with C_l channels): two 3x3 convolutions with ReLU,
 2x2 max pooling down; up: nearest 2x upsampling of level l+1 concatenated
 with the level-l skip, two 3x3 convolutions with ReLU; a 1x1 head to one
-logit; class-weighted binary cross-entropy; Adam.  Activations NHWC BF16;
+logit; class-weighted binary cross-entropy, optionally plus a weighted soft
+Dice term per image; Adam.  Activations NHWC BF16;
 the input's 3 channels are padded to 8.
 """
 from __future__ import annotations
@@ -38,6 +39,8 @@ SG_SIGNATURES = {
     "cem_sg_head_bwd": (_i, [_v, _i, _i, _v, _v, _v, _v, _v, _v, _l, _v]),
     "cem_sg_bce_workspace": (_l, [_l]),
     "cem_sg_bce": (_i, [_v, _v, _l, _f, _v, _v, _v, _l, _v]),
+    "cem_sg_dice_workspace": (_l, [_i, _l]),
+    "cem_sg_dice": (_i, [_v, _v, _i, _l, _f, _f, _v, _v, _v, _l, _v]),
     "cem_sg_adam": (_i, [_v, _v, _v, _v, _l, _f, _f, _f, _f, _i, _v, _v, _i, _i, _v]),
     "cem_sg_to_bf16": (_i, [_v, _l, _v, _v]),
     "cem_sg_set_gemm_path": (_i, [_i]),
@@ -92,7 +95,8 @@ class UNet:
     """U-Net with its buffers for one batch shape (B, H, W)."""
 
     def __init__(self, B: int, H: int, W: int, chans: Sequence[int] = (32, 64, 128, 256),
-                 seed: int = 0, device: int = 0, pos_weight: float = 1.0, lr: float = 1e-3):
+                 seed: int = 0, device: int = 0, pos_weight: float = 1.0, lr: float = 1e-3,
+                 dice: float = 0.0, dice_eps: float = 1.0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -104,6 +108,7 @@ class UNet:
             raise ValueError("channels must be multiples of 8, level 0 at most 32")
         self.B, self.H, self.W = B, H, W
         self.pos_weight = float(pos_weight)
+        self.dice, self.dice_eps = float(dice), float(dice_eps)
         self.lr = lr
         self.step_count = 0
         self.cin = 8
@@ -166,9 +171,10 @@ class UNet:
         self.gpool = [e(self.P[l + 1], ch[l]) for l in range(L - 1)]
         self.z = torch.empty(self.P[0], dtype=torch.float32, device=self.dev)
         self.dz = torch.empty_like(self.z)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=self.dev)
         L_ = sg()
-        need = [L_.cem_sg_head_workspace(self.P[0], ch[0]), L_.cem_sg_bce_workspace(self.P[0])]
+        need = [L_.cem_sg_head_workspace(self.P[0], ch[0]), L_.cem_sg_bce_workspace(self.P[0]),
+                L_.cem_sg_dice_workspace(B, self.P[0] // B)]
         for name, p in self.convs.items():
             l = int(name[1])
             h, w = self.dims[l]
@@ -292,10 +298,16 @@ class UNet:
 
     # ----------------------------------------------------------------- loss
     def loss_and_grad(self, target_u8):
-        """Weighted BCE of self.z against target (device uint8 [B*H*W]);
-        leaves d loss / d z in self.dz.  Returns the loss tensor (device)."""
+        """Weighted BCE of self.z against target (device uint8 [B*H*W]), plus
+        dice * (1 - mean soft Dice of the B images) when dice > 0; leaves
+        d loss / d z in self.dz.  Returns the loss tensor (device; [0] the
+        BCE, [1] the Dice term, zero without it)."""
         _ok(sg().cem_sg_bce(_p(self.z), _p(target_u8), self.P[0], self.pos_weight, _p(self.dz),
                             _p(self.loss), _p(self.ws), self.ws_bytes, self._stream()), "bce")
+        if self.dice > 0:
+            _ok(sg().cem_sg_dice(_p(self.z), _p(target_u8), self.B, self.P[0] // self.B,
+                                 self.dice, self.dice_eps, _p(self.dz), _p(self.loss, 1),
+                                 _p(self.ws), self.ws_bytes, self._stream()), "dice")
         return self.loss
 
     def adam_step(self, lr=None, b1=0.9, b2=0.999, eps=1e-8):

@@ -133,6 +133,66 @@ def mean_jaccard(Z, Y, thr):
     return float(j.mean().item()), j.cpu().numpy()
 
 
+def fit(net, Xtr, Ytr, ntr, epochs, lr0, seed=0, log=print):
+    """Trains net on runs 0 .. ntr-1 of (Xtr, Ytr) in shuffled batches of
+    net.B: per step forward, loss and its gradient, backward, Adam, with a
+    linear warm-up over the first 5% of the steps and a cosine decay to 5%
+    of lr0.  Returns the mean loss of each epoch; fails if a tensor-core wait
+    gave up."""
+    import torch
+    from .surrogate import check_timeouts, timeouts
+    rng = np.random.default_rng(seed)
+    B = net.B
+    steps_per_epoch = ntr // B
+    total = steps_per_epoch * epochs
+    warm = max(1, total // 20)
+    hist = []
+    it = 0
+    tmo = timeouts()
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(ntr)).to(Xtr.device)
+        ep_loss = torch.zeros((), dtype=torch.float32, device=Xtr.device)
+        for s in range(steps_per_epoch):
+            idx = perm[s * B:(s + 1) * B]
+            net.x8.copy_(Xtr.index_select(0, idx).reshape(-1, 8))
+            tgt = Ytr.index_select(0, idx).reshape(-1)
+            lr = lr0 * min(1.0, (it + 1) / warm) * \
+                (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * it / max(1, total))))
+            net.forward()
+            loss = net.loss_and_grad(tgt)
+            net.backward()
+            net.adam_step(lr=lr)
+            ep_loss += loss.sum()
+            it += 1
+        hist.append(float(ep_loss.item()) / steps_per_epoch)
+        tmo = check_timeouts(tmo, f"training epoch {ep}")
+        log(f"epoch {ep}: loss {hist[-1]:.4f}")
+    return hist
+
+
+def evaluate(net, Xval, Yval, Xte, Yte):
+    """Chooses the logit threshold on the held-out runs (Xval, Yval) and
+    scores the test runs; returns a dict of the scores and the test logits."""
+    import torch
+    Zv = predict(net, Xval, net.B)
+    best_thr, best_j = 0.0, -1.0
+    for thr in np.linspace(-3, 3, 25):
+        j, _ = mean_jaccard(Zv, Yval, float(thr))
+        if j > best_j:
+            best_thr, best_j = float(thr), j
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    Zte = predict(net, Xte, net.B)
+    torch.cuda.synchronize()
+    infer_s = (time.perf_counter() - t2) / Xte.shape[0]
+    j_te, j_all = mean_jaccard(Zte, Yte, best_thr)
+    j_te0, _ = mean_jaccard(Zte, Yte, 0.0)
+    return {"threshold": best_thr, "val_jaccard": best_j, "test_mean_jaccard": j_te,
+            "test_mean_jaccard_thr0": j_te0,
+            "test_jaccard_p10_p50_p90": [float(np.percentile(j_all, q)) for q in (10, 50, 90)],
+            "network_seconds_per_run": infer_s}, Zte
+
+
 def bench_steps(B, n, chans=(32, 64, 128, 256, 512)):
     """Times forward, backward (loss included) and Adam of the surrogate on
     synthetic inputs (3 random channels, 7% cracked targets) after 3 warm-up
@@ -184,6 +244,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--dice", type=float, default=0.0,
+                    help="weight of the soft Dice term added to the weighted BCE")
     ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chans", default="32,64,128,256,512",
@@ -196,7 +258,7 @@ def main():
     args = ap.parse_args()
     import torch
     from . import build as _build
-    from .surrogate import UNet, check_timeouts, timeouts
+    from .surrogate import UNet
     _build.build()
     torch.cuda.set_device(0)
     log = lambda m: print(m, flush=True)
@@ -215,74 +277,34 @@ def main():
     pos_weight = float(min(20.0, (1.0 - frac) / max(frac, 1e-6)))
     chans = [int(c) for c in args.chans.split(",")]
     net = UNet(args.batch, H_EL, W_EL, chans=chans, pos_weight=pos_weight, lr=args.lr,
-               seed=args.seed)
-    rng = np.random.default_rng(args.seed)
-    steps_per_epoch = ntr // args.batch
-    total = steps_per_epoch * args.epochs
-    P = H_EL * W_EL
-    hist = []
+               seed=args.seed, dice=args.dice)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    it = 0
-    tmo = timeouts()
-    for ep in range(args.epochs):
-        perm = torch.from_numpy(rng.permutation(ntr)).to(Xtr.device)
-        ep_loss = torch.zeros((), dtype=torch.float32, device=Xtr.device)
-        for s in range(steps_per_epoch):
-            idx = perm[s * args.batch:(s + 1) * args.batch]
-            net.x8.copy_(Xtr.index_select(0, idx).reshape(-1, 8))
-            tgt = Ytr.index_select(0, idx).reshape(-1)
-            # linear warm-up over the first 5% of the steps, then cosine decay
-            warm = max(1, total // 20)
-            lr = args.lr * min(1.0, (it + 1) / warm) * \
-                (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * it / max(1, total))))
-            net.forward()
-            loss = net.loss_and_grad(tgt)
-            net.backward()
-            net.adam_step(lr=lr)
-            ep_loss += loss[0]
-            it += 1
-        hist.append(float(ep_loss.item()) / steps_per_epoch)
-        tmo = check_timeouts(tmo, f"training epoch {ep}")
-        log(f"epoch {ep}: loss {hist[-1]:.4f}")
+    hist = fit(net, Xtr, Ytr, ntr, args.epochs, args.lr, args.seed, log)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    # threshold on held-out training runs
-    Zv = predict(net, Xtr[ntr:], args.batch)
-    best_thr, best_j = 0.0, -1.0
-    for thr in np.linspace(-3, 3, 25):
-        j, _ = mean_jaccard(Zv, Ytr[ntr:], float(thr))
-        if j > best_j:
-            best_thr, best_j = float(thr), j
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    Zte = predict(net, Xte, args.batch)
-    torch.cuda.synchronize()
-    infer_s = (time.perf_counter() - t2) / args.test
-    j_te, j_all = mean_jaccard(Zte, Yte, best_thr)
-    j_te0, _ = mean_jaccard(Zte, Yte, 0.0)
+    scores, Zte = evaluate(net, Xtr[ntr:], Ytr[ntr:], Xte, Yte)
     out = {
         "workload": "surrogate_400x160", "train_runs": ntr, "val_runs": nval,
         "test_runs": args.test, "epochs": args.epochs, "batch": args.batch, "chans": chans,
+        "lr": args.lr, "dice": args.dice,
         "params": int(sum(p["w"].numel() + p["b"].numel() for p in net.convs.values())
                       + net.head["w"].numel() + 1),
         "cracked_fraction_train": frac, "pos_weight": pos_weight,
         "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
-        "threshold": best_thr, "val_jaccard": best_j,
-        "test_mean_jaccard": j_te, "test_mean_jaccard_thr0": j_te0,
-        "test_jaccard_p10_p50_p90": [float(np.percentile(j_all, q)) for q in (10, 50, 90)],
+        **scores,
         "straight_crack_floor_test": float(np.mean(floor_te)),
         "solver_seconds_per_run_batched": s_run,
-        "network_seconds_per_run": infer_s,
         "generation_s": gen_s, "training_s": train_s,
-        "train_steps": total,
+        "train_steps": (ntr // args.batch) * args.epochs,
     }
     if args.save:
         k = min(8, args.test)
         np.savez_compressed(args.save, **net.params_numpy(), chans=np.array(chans),
-                            threshold=np.array(best_thr),
+                            threshold=np.array(scores["threshold"]),
                             test_target=Yte[:k].cpu().numpy().reshape(k, H_EL, W_EL),
-                            test_pred=(Zte[:k] > best_thr).cpu().numpy().reshape(k, H_EL, W_EL))
+                            test_pred=(Zte[:k] > scores["threshold"]).cpu().numpy()
+                            .reshape(k, H_EL, W_EL))
     print(json.dumps(out))
 
 

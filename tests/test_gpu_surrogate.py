@@ -216,6 +216,38 @@ def test_bce_and_head():
     assert _rel(dx.float().cpu().numpy(), np.where(x > 0, dxr.reshape(P, C), 0.0)) < 1e-2
 
 
+@pytest.mark.parametrize("n_per", [9000, 4096, 1])
+def test_soft_dice_against_the_oracle(n_per):
+    """cem_sg_dice on 3 images (9000 elements: two whole 4096-element chunks
+    and a ragged one; exactly one chunk; one element): the loss and the
+    gradient it adds to an existing dz against the oracle's soft Dice, to
+    FP32 summation accuracy."""
+    import torch
+    from paper_2509_01827_gb300.surrogate import _p, sg
+    r = np.random.default_rng(11)
+    B = 3
+    z = (r.standard_normal((B, n_per)) * 3).astype(np.float32).astype(np.float64)
+    t = (r.random((B, n_per)) < 0.2).astype(np.uint8)
+    dz0 = r.standard_normal((B, n_per)).astype(np.float32).astype(np.float64) * 1e-3
+    L = sg()
+    wsb = int(L.cem_sg_dice_workspace(B, n_per))
+    assert wsb > 0
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    zd, td, dzd = _t(z, torch.float32), _t(t, torch.uint8), _t(dz0, torch.float32)
+    loss = torch.zeros(2, dtype=torch.float32, device="cuda")
+    assert L.cem_sg_dice(_p(zd), _p(td), B, n_per, 0.7, 1.0, _p(dzd), _p(loss, 1), _p(ws), wsb,
+                         0) == 0
+    torch.cuda.synchronize()
+    lr, dzr = so.soft_dice(z, t, eps=1.0)
+    assert loss[0].item() == 0.0
+    assert abs(loss[1].item() - 0.7 * lr) <= 1e-5 * max(1e-3, abs(lr))
+    assert _rel(dzd.cpu().numpy() - dz0, 0.7 * dzr) < 1e-4
+    # bad arguments
+    assert L.cem_sg_dice(_p(zd), _p(td), B, n_per, 0.7, 0.0, _p(dzd), _p(loss), _p(ws), wsb, 0) != 0
+    assert L.cem_sg_dice(_p(zd), _p(td), B, n_per, 0.7, 1.0, _p(dzd), _p(loss), _p(ws), wsb - 4,
+                         0) != 0
+
+
 def _unet_bf16_reference(p, x, t, chans, pw):
     """The oracle's layers composed with BF16 rounding wherever the GPU
     stores a tensor in BF16 (conv outputs, data gradients, pooled and

@@ -116,6 +116,35 @@ def test_bce_closed_form_and_gradient():
     _fd_check(lambda: so.bce_logits(z, t, 3.0)[0], z, dz, _coords(z.shape, 12, r), rtol=1e-7)
 
 
+def test_soft_dice_closed_forms_and_gradient():
+    # z = 0: p = 1/2 on all m elements of a sample with k cracked ones, so
+    # D = (k + eps) / (m/2 + k + eps)
+    z = np.zeros((2, 5, 4))
+    t = np.zeros((2, 5, 4))
+    t[0, 1, :3] = 1
+    t[1, 4, 0] = 1
+    loss, _ = so.soft_dice(z, t, eps=1.0)
+    d = [(3 + 1.0) / (10 + 3 + 1.0), (1 + 1.0) / (10 + 1 + 1.0)]
+    assert abs(loss - (1.0 - np.mean(d))) < 1e-15
+    # saturated logits: p is the 0/1 map, and with eps = 0 the Dice index of
+    # two sets is 2 J / (1 + J), J their Jaccard index
+    r = _rng(7)
+    for _ in range(4):
+        a = r.random((1, 6, 7)) < 0.4
+        b = r.random((1, 6, 7)) < 0.4
+        zz = np.where(a, 60.0, -60.0)
+        j = so.jaccard(a, b)
+        loss, _ = so.soft_dice(zz, b.astype(float), eps=0.0)
+        assert abs((1.0 - loss) - 2 * j / (1 + j)) < 1e-12
+    # samples are independent: the loss of a batch is the mean of its samples'
+    z = r.standard_normal((3, 4, 5))
+    t = (r.random((3, 4, 5)) < 0.3).astype(float)
+    per = [so.soft_dice(z[i:i + 1], t[i:i + 1])[0] for i in range(3)]
+    loss, dz = so.soft_dice(z, t)
+    assert abs(loss - np.mean(per)) < 1e-15
+    _fd_check(lambda: so.soft_dice(z, t)[0], z, dz, _coords(z.shape, 16, r), rtol=1e-7)
+
+
 def test_adam_first_step_moves_by_lr():
     w = np.array([1.0, -2.0, 0.5])
     g = np.array([0.3, -4.0, 1e-3])
