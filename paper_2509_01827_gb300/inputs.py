@@ -46,21 +46,19 @@ def philox4x32_10(counter: np.ndarray, key) -> np.ndarray:
 
     counter: (n, 4) uint32 array; key: two uint32 words.  Returns (n, 4) uint32.
     """
-    c = np.asarray(counter, dtype=np.uint64).reshape(-1, 4).copy()
+    c = np.asarray(counter, dtype=np.uint64).reshape(-1, 4)
+    c0, c1, c2, c3 = (np.ascontiguousarray(c[:, i]) for i in range(4))
     k0, k1 = np.uint64(int(key[0]) & _MASK), np.uint64(int(key[1]) & _MASK)
-    m0, m1, mask = np.uint64(_M0), np.uint64(_M1), np.uint64(_MASK)
+    m0, m1, mask, sh = np.uint64(_M0), np.uint64(_M1), np.uint64(_MASK), np.uint64(32)
     for r in range(10):
         if r:
             k0 = np.uint64((int(k0) + _W0) & _MASK)
             k1 = np.uint64((int(k1) + _W1) & _MASK)
-        p0 = m0 * c[:, 0]
-        p1 = m1 * c[:, 2]
-        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
-        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
-        n0 = hi1 ^ c[:, 1] ^ k0
-        n2 = hi0 ^ c[:, 3] ^ k1
-        c = np.stack([n0, lo1, n2, lo0], axis=1)
-    return c.astype(np.uint32)
+        p0 = m0 * c0
+        p1 = m1 * c2
+        # (hi(p1) ^ c1 ^ k0, lo(p1), hi(p0) ^ c3 ^ k1, lo(p0))
+        c0, c1, c2, c3 = (p1 >> sh) ^ c1 ^ k0, p1 & mask, (p0 >> sh) ^ c3 ^ k1, p0 & mask
+    return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
 
 
 def uniform01(n: int, seed: int, stream: int = 0) -> np.ndarray:

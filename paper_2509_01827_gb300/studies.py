@@ -3,6 +3,7 @@
     python -m paper_2509_01827_gb300.studies compact_tension [--n 100]
     python -m paper_2509_01827_gb300.studies kalthoff [--n 200,400]
     python -m paper_2509_01827_gb300.studies ceiling [--n 64]
+    python -m paper_2509_01827_gb300.studies sensitivity [--n 64]
     python -m paper_2509_01827_gb300.studies tri_throughput [--n 1024]
 
 compact_tension: the Dirichlet compact-tension plate (Sec. 4.3) at the three
@@ -19,6 +20,14 @@ On n runs of the surrogate's data set (test seeds 10^6 + q), the Jaccard
 index at 80 us of the FP32-mixed map (the training target) against the FP64
 map, and of the FP64 and FP32 maps against runs whose G_c field is raised by
 one FP32 ulp everywhere.
+
+sensitivity: how finely the crack map depends on the G_c field.  On n runs of
+the surrogate's data set, the Jaccard index at 80 us of the FP32-mixed map
+against the maps of the same run with G_c replaced by: the value the
+surrogate's BF16 input channel holds ((G_c - 3) / 0.36 rounded to BF16 and
+mapped back); the same in two BF16 words (the rounded value and its rounded
+remainder); G_c times 1 + r, r uniform in +-1e-4, +-1e-3, +-1e-2 (Philox
+stream 7); an independent field (another seed, same traction and notch).
 
 tri_throughput: FP64 and FP32-mixed element-updates/s of the unstructured
 constant-strain triangle path (cem_tri_mesh_create) on an n x n jittered plate of 2 n^2
@@ -124,6 +133,43 @@ def ceiling(n=64):
                                      p10=float(np.percentile(v, 10))) for k, v in J.items()})), flush=True)
 
 
+def bf16_round(a):
+    """Round-to-nearest-even of float32 values to BF16, returned as float32."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def sensitivity(n=64):
+    from .cem import CEM_FP32_MIXED
+    from .train_surrogate import GC_SD
+    keys = ["bf16_input", "bf16_two_words", "rel_1e-4", "rel_1e-3", "rel_1e-2", "other_field"]
+    J = {k: [] for k in keys}
+    for q in range(n):
+        seed = 10**6 + q
+        p, _ = inputs.surrogate_run(seed)
+        ref = _run(p, CEM_FP32_MIXED)["cracks"]["elem"]
+        gc = np.asarray(p.gc, np.float32)
+        v = ((gc.astype(np.float64) - 3.0) / GC_SD).astype(np.float32)
+        hi = bf16_round(v)
+        lo = bf16_round(v - hi)
+        r = 2.0 * inputs.uniform01(len(gc), seed, stream=7) - 1.0
+        other = inputs.weibull_gc(len(gc), 3.0, 10.0, seed + 10**7)
+        fields = {"bf16_input": 3.0 + GC_SD * hi.astype(np.float64),
+                  "bf16_two_words": 3.0 + GC_SD * (hi.astype(np.float64) + lo.astype(np.float64)),
+                  "rel_1e-4": gc * (1.0 + 1e-4 * r), "rel_1e-3": gc * (1.0 + 1e-3 * r),
+                  "rel_1e-2": gc * (1.0 + 1e-2 * r), "other_field": other}
+        line = dict(study="sensitivity", seed=seed, n32=len(ref))
+        for k in keys:
+            p.gc = np.asarray(fields[k], np.float32)
+            line[k] = metrics.jaccard(ref, _run(p, CEM_FP32_MIXED)["cracks"]["elem"])
+            J[k].append(line[k])
+        print(json.dumps(line), flush=True)
+    print(json.dumps(dict(study="sensitivity_summary", runs=n,
+                          **{k: dict(mean=float(np.mean(v)), min=float(np.min(v)),
+                                     p10=float(np.percentile(v, 10))) for k, v in J.items()})), flush=True)
+
+
 def tri_throughput(n=1024, steps=200, warmup=10):
     import torch
     from .cem import CEM_FP32_MIXED, CEM_FP64, TriSolver
@@ -151,7 +197,8 @@ def tri_throughput(n=1024, steps=200, warmup=10):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["compact_tension", "kalthoff", "ceiling", "tri_throughput"])
+    ap.add_argument("study", choices=["compact_tension", "kalthoff", "ceiling", "sensitivity",
+                                      "tri_throughput"])
     ap.add_argument("--n", default=None)
     a = ap.parse_args()
     from . import build
@@ -160,6 +207,8 @@ def main():
         compact_tension(int(a.n or 100))
     elif a.study == "ceiling":
         ceiling(int(a.n or 64))
+    elif a.study == "sensitivity":
+        sensitivity(int(a.n or 64))
     elif a.study == "tri_throughput":
         tri_throughput(int(a.n or 1024))
     else:

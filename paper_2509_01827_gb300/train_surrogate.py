@@ -13,7 +13,8 @@
    standard deviation).
 3. Training: the U-Net of surrogate.py (by default five levels, 32 .. 512
    channels), weighted binary cross-entropy (cracked elements weighted by
-   the training set's intact/cracked ratio, capped at 20), Adam (peak rate
+   the training set's intact/cracked ratio, capped at 20) plus, with
+   --dice w, w times one minus the mean soft Dice index of the batch, Adam (peak rate
    1e-3; the five-level net did not train at 2e-3) with a linear warm-up
    over 5% of the steps and a cosine learning-rate decay, batch 64.
 4. Evaluation: mean Jaccard index of the predicted cracked set (logit >
@@ -22,6 +23,7 @@
 Prints one JSON line.
 """
 import argparse
+import concurrent.futures as cf
 import json
 import math
 import time
@@ -74,9 +76,12 @@ def generate(seeds, chunk=256, device=0, log=print):
     floors = np.zeros(n)
     solve_s = 0.0
     config = None
+    # the next chunk's problems are drawn on host threads while a chunk runs
+    pool = cf.ThreadPoolExecutor(4)
+    ahead = [pool.submit(inputs.surrogate_run, s) for s in seeds[:chunk]]
     for c0 in range(0, n, chunk):
-        part = seeds[c0:c0 + chunk]
-        runs = [inputs.surrogate_run(s) for s in part]
+        runs = [f.result() for f in ahead]
+        ahead = [pool.submit(inputs.surrogate_run, s) for s in seeds[c0 + chunk:c0 + 2 * chunk]]
         members = [Solver(p, precision=CEM_FP32_MIXED, device=device) for p, _ in runs]
         b = Batch(members)
         if config is None:
@@ -100,6 +105,7 @@ def generate(seeds, chunk=256, device=0, log=print):
         for m in members:
             m.close()
         log(f"generated {min(n, c0 + chunk)}/{n} runs")
+    pool.shutdown()
     torch.cuda.synchronize()
     return X, Y, floors, solve_s / n
 

@@ -328,7 +328,7 @@ def test_unet_loss_gradients_vs_oracle():
     z_ref, _ = so.unet_forward(pr, x3, chans)
     assert _rel(net.z.cpu().numpy().reshape(B, H, W), z_ref[..., 0]) < 3e-2
     loss_ref, g_ref = so.unet_loss_and_grads(pr, x3, t, chans, 4.0)
-    assert abs(loss.item() - loss_ref) <= 1e-2 * abs(loss_ref)
+    assert abs(loss[0].item() - loss_ref) <= 1e-2 * abs(loss_ref)
     g = net.grads_numpy()
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
     loss_e, g_e = _unet_bf16_reference(pr, x3, t, chans, 4.0)
@@ -354,7 +354,7 @@ def test_training_reduces_loss():
     t = (x[..., 0] > 0.5).astype(np.uint8)  # a learnable map
     net.set_input(torch.tensor(x.reshape(-1, 8), device="cuda"))
     td = torch.tensor(t.reshape(-1), device="cuda")
-    losses = [float(net.train_step(td).item()) for _ in range(60)]
+    losses = [float(net.train_step(td)[0].item()) for _ in range(60)]
     assert losses[-1] < 0.5 * losses[0], losses[::10]
 
 
