@@ -261,7 +261,11 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
     if (e != cudaSuccess) return e;
     cudaEventRecord(marks[6], h->st);
   }
-  e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st);
+  // a programmatic dependent of the node update only in a captured graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool captured = !marks && cudaStreamIsCapturing(h->st, &cs) == cudaSuccess &&
+                        cs == cudaStreamCaptureStatusActive;
+  e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st, captured);
   if (marks) cudaEventRecord(marks[7], h->st);
   return e;
 }
@@ -302,6 +306,43 @@ cudaError_t create_aux_streams(StepStreams &ss) {
   return ce;
 }
 
+// A kernel launched as a programmatic dependent right after cross-stream
+// joins is captured with programmatic edges from every joined kernel, not
+// only from the kernel before it in its stream.  The split writes read the
+// selection's plan before their grid-dependency wait, so their edges from the
+// side branches' last kernels (the selection, the phantom update) are made
+// ordinary here: the split writes then start after those have completed,
+// while only the node update (or the energy epilogue) may still be running.
+cudaError_t ordinary_side_edges(cudaGraph_t g) {
+  auto func_of = [](cudaGraphNode_t nd) -> const void * {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) return nullptr;
+    cudaKernelNodeParams p;
+    return cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess ? p.func : nullptr;
+  };
+  const void *side[3] = {select_kernel(), phantom32_kernel(), phantom64_kernel()};
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    if (func_of(nodes[i]) != apply_kernel()) continue;
+    size_t m = 0;
+    e = cudaGraphNodeGetDependencies(nodes[i], nullptr, nullptr, &m);
+    std::vector<cudaGraphNode_t> from(m);
+    std::vector<cudaGraphEdgeData> ed(m);
+    if (e == cudaSuccess && m) e = cudaGraphNodeGetDependencies(nodes[i], from.data(), ed.data(), &m);
+    for (size_t k = 0; k < m && e == cudaSuccess; ++k) {
+      if (ed[k].type != cudaGraphDependencyTypeProgrammatic) continue;
+      const void *f = func_of(from[k]);
+      if (f != side[0] && f != side[1] && f != side[2]) continue;
+      e = cudaGraphRemoveDependencies(g, &from[k], &nodes[i], &ed[k], 1);
+      if (e == cudaSuccess) e = cudaGraphAddDependencies(g, &from[k], &nodes[i], nullptr, 1);
+    }
+  }
+  return e;
+}
+
 cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
   if (!h->graphs[cur][energy]) {
     cudaGraph_t g;
@@ -310,8 +351,9 @@ cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
-    cudaError_t e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g,
-                                          cudaGraphInstantiateFlagUseNodePriority);
+    cudaError_t e3 = ordinary_side_edges(g);
+    if (e3 == cudaSuccess)
+      e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
   }
@@ -349,7 +391,8 @@ cem_status multi_graph_for(cem_handle *h, int cur, unsigned mask, cudaGraphExec_
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
     cudaGraphExec_t x = nullptr;
-    cudaError_t e3 = cudaGraphInstantiate(&x, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaError_t e3 = ordinary_side_edges(g);
+    if (e3 == cudaSuccess) e3 = cudaGraphInstantiate(&x, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
     it = h->multi.emplace(key, x).first;

@@ -263,6 +263,12 @@ struct StepStreams {
   cudaStream_t main, aux1, aux2;
   cudaEvent_t fork, join1, join2;
 };
+// Kernel functions the step graphs' edges are checked against
+// (ordinary_side_edges in api.cpp).
+const void *apply_kernel();
+const void *select_kernel();
+const void *phantom32_kernel();
+const void *phantom64_kernel();
 constexpr int kStepKernels = 4;
 cudaError_t launch_step_fp64(const DevState &d, int cur, bool first, bool energy,
                              const StepStreams &ss, cudaEvent_t *marks = nullptr);
@@ -271,7 +277,10 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
 // Tracking: selection and planning (one CTA; may run concurrently with the
 // node updates) then the split writes (many CTAs; after the node updates).
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st);
-cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st);
+// programmatic: launched as a programmatic dependent of the kernel before it
+// (used in captured step graphs, whose edges ordinary_side_edges fixes)
+cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st,
+                         bool programmatic = false);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 // proposals one step can hold: the selection sorts (a power of two) that many
 // at most, in shared memory or in its global scratch of that size

@@ -750,7 +750,7 @@ __device__ __forceinline__ bool tile_clean(const DevState &d, int tile_x, int j0
   bool ok = true;
   for (int q = lane; q < TY + 3; q += 32) {
     const int r = j0 - 2 + q;
-    const int f = (r >= 0 && r <= d.g.ny) ? (int)d.mrow[(size_t)r * ntx + tile_x] : 0;
+    const int f = (r >= 0 && r <= d.g.ny) ? (int)__ldcg(d.mrow + (size_t)r * ntx + tile_x) : 0;
     ok = ok && (f & 0x100) && (r < j0 || r >= j0 + TY || (f & 1));
   }
   return __all_sync(0xffffffffu, ok);
@@ -765,10 +765,15 @@ __device__ __forceinline__ void march32_group(const DevState &d, int group, int 
   double *part = d.e_part + 2 * tix;
   if (tix < ntx * nty) {
     const int tile_x = tix % ntx, tile_y = tix / ntx;
-    if (tile_clean(d, tile_x, tile_y * ty, ty))
+    if (tile_clean(d, tile_x, tile_y * ty, ty)) {
       march32_tile<ENERGY, true>(d, tile_x, tile_y, ty, cur, first, part, rings[w]);
-    else
+    } else {
+      // the other tiles read the piece forces of the kernel before this one
+      // (when launched as its programmatic dependent): wait until it has
+      // completed and its writes are visible
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       march32_tile<ENERGY, false>(d, tile_x, tile_y, ty, cur, first, part, rings[w]);
+    }
   } else if (ENERGY && lane == 0) {
     part[0] = 0.0;
     part[1] = 0.0;
@@ -779,10 +784,12 @@ template <bool ENERGY>
 __global__ void __launch_bounds__(32 * kMarchWarps, 4) k_march32(DevState d, int cur, int first,
                                                                   int ty) {
   // launched as a programmatic dependent of the kernel before it (the piece
-  // forces): wait until that kernel has completed and its writes are
-  // visible; then let the kernels that follow be placed once every CTA of
-  // this kernel has started (they wait for it themselves)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // forces), which writes only the piece forces and its energy partials: a
+  // clean tile reads neither and starts at once, the others wait for that
+  // kernel (march32_group).  Everything else the tiles read was written by
+  // kernels that completed before the piece forces started.  The kernels
+  // that follow may be placed once every CTA of this kernel has started
+  // (they wait for it themselves).
   asm volatile("griddepcontrol.launch_dependents;");
   __shared__ MarchRing rings[kMarchWarps];
   march32_group<ENERGY>(d, blockIdx.x, ty, cur, first, rings);
@@ -1045,5 +1052,7 @@ cudaError_t launch_step_fp32_batch(const BatchDev &b, bool first, bool energy, i
   cudaStreamWaitEvent(st, ss.join2, 0);
   return cudaGetLastError();
 }
+
+const void *phantom32_kernel() { return reinterpret_cast<const void *>(&k_phantom32); }
 
 }  // namespace cem

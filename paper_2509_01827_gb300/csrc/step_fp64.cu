@@ -536,4 +536,6 @@ cudaError_t launch_step_fp64_batch(const BatchDev &b, bool first, bool energy, i
   return cudaGetLastError();
 }
 
+const void *phantom64_kernel() { return reinterpret_cast<const void *>(&k_phantom64); }
+
 }  // namespace cem

@@ -747,63 +747,87 @@ __device__ __forceinline__ void apply_tables(const DevState &d, VBlk vb, int mod
   }
 }
 
-__device__ __forceinline__ void apply_nodes(const DevState &d, VBlk vb, int cur_next, int mode) {
+// What the node writes need of winner w's local node a: the real node N,
+// its phantom P (new when reuse < 0, else shared), the masses before and
+// after the split and the mass moved.
+struct SplitNode {
+  int N, P, reuse;
+  double mold, mnew, mreal, dm, mireal, miph;
+};
+
+__device__ __forceinline__ SplitNode split_node(const DevState &d, int w, int a) {
+  SplitNode q;
+  q.N = elem_node(d.g, d.pl_e[w], a);
+  q.P = apply_phantom(d, w, a);
+  q.reuse = d.pl_reuse[w * 4 + a];
+  q.mold = d.pl_mold[w * 4 + a];
+  q.mnew = d.pl_mph[w * 4 + a];
+  q.mreal = d.pl_mreal[w * 4 + a];
+  q.dm = d.pl_dm[w * 4 + a];
+  q.mireal = d.pl_mireal[w * 4 + a];
+  q.miph = d.pl_miph[w * 4 + a];
+  return q;
+}
+
+// local node a: the new phantom's state, or the momentum-conserving merge
+// into a shared phantom; the masses after the split
+__device__ __forceinline__ void node_apply(const DevState &d, const SplitNode &q, int cur_next) {
+  const int N = q.N, P = q.P;
+  if (q.reuse < 0) {
+    if (d.precision == 1) {
+      d.u4[cur_next][P] = d.u4[cur_next][N];
+      d.v2[P] = d.v2[N];
+    } else {
+      d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
+      d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
+    }
+  } else if (q.mold >= 0.0) {
+    // merge: the phantom gains mass dm moving with its real node
+    if (d.precision == 1) {
+      const float2 vp = d.v2[P], vn = d.v2[N];
+      const double vx = ((q.mold * (double)vp.x) + q.dm * (double)vn.x) / q.mnew;
+      const double vy = ((q.mold * (double)vp.y) + q.dm * (double)vn.y) / q.mnew;
+      d.v2[P] = make_float2((float)vx, (float)vy);
+    } else {
+      d.vx[P] = (q.mold * d.vx[P] + q.dm * d.vx[N]) / q.mnew;
+      d.vy[P] = (q.mold * d.vy[P] + q.dm * d.vy[N]) / q.mnew;
+    }
+  }
+  set_mass(d, N, q.mreal, q.mireal);
+  set_mass(d, P, q.mnew, q.miph);
+}
+
+__device__ __forceinline__ void elem_split(const DevState &d, int e) {
+  d.estate[e] = ST_CRACKED;
+  march_rows_split(d, e);
+}
+
+// the commit changes no value that another block of this kernel reads
+__device__ __forceinline__ void apply_commit(const DevState &d, VBlk vb, int mode) {
   Counters *cnt = d.cnt;
-  const Geo &g = d.g;
-  const int nw = cnt->pend_nwin;
-  const int step = cnt->pend_step;
+  if (vb.x == 0 && threadIdx.x == 0) {
+    const int step = cnt->pend_step;
+    cnt->n_ph = cnt->pend_nph;
+    cnt->n_ck = cnt->pend_nck;
+    cnt->n_S = cnt->pend_nS;
+    cnt->n_dead += cnt->pend_dead;
+    cnt->n_win_last = cnt->pend_nwin;
+    if (mode == TRACK_STEP) cnt->step = step + 1;
+  }
+}
+
+__device__ __forceinline__ void apply_nodes(const DevState &d, VBlk vb, int cur_next, int mode) {
+  const int nw = d.cnt->pend_nwin;
   const int lane32 = threadIdx.x & 31, lane = lane32 & 7, grp = lane32 >> 3;
   const int warp = (vb.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (vb.gx * blockDim.x) >> 5;
   for (int wb = warp * 4; wb < nw; wb += nwarps * 4) {
     const int w = wb + grp;
     const bool act = w < nw;
-    const int a = lane & 3;
-    if (act && lane < 4) {
-      // local node a: the new phantom's state, or the momentum-conserving
-      // merge into a shared phantom; the masses after the split
-      const int e = d.pl_e[w];
-      const int N = elem_node(g, e, a);
-      const int P = apply_phantom(d, w, a);
-      const double mold = d.pl_mold[w * 4 + a], mnew = d.pl_mph[w * 4 + a];
-      const double mreal = d.pl_mreal[w * 4 + a], dm = d.pl_dm[w * 4 + a];
-      if (d.pl_reuse[w * 4 + a] < 0) {
-        if (d.precision == 1) {
-          d.u4[cur_next][P] = d.u4[cur_next][N];
-          d.v2[P] = d.v2[N];
-        } else {
-          d.ux[cur_next][P] = d.ux[cur_next][N]; d.uy[cur_next][P] = d.uy[cur_next][N];
-          d.vx[P] = d.vx[N]; d.vy[P] = d.vy[N];
-        }
-      } else if (mold >= 0.0) {
-        // merge: the phantom gains mass dm moving with its real node
-        if (d.precision == 1) {
-          const float2 vp = d.v2[P], vn = d.v2[N];
-          const double vx = ((mold * (double)vp.x) + dm * (double)vn.x) / mnew;
-          const double vy = ((mold * (double)vp.y) + dm * (double)vn.y) / mnew;
-          d.v2[P] = make_float2((float)vx, (float)vy);
-        } else {
-          d.vx[P] = (mold * d.vx[P] + dm * d.vx[N]) / mnew;
-          d.vy[P] = (mold * d.vy[P] + dm * d.vy[N]) / mnew;
-        }
-      }
-      set_mass(d, N, mreal, d.pl_mireal[w * 4 + a]);
-      set_mass(d, P, mnew, d.pl_miph[w * 4 + a]);
-    } else if (act && lane == 4) {
-      const int e = d.pl_e[w];
-      d.estate[e] = ST_CRACKED;
-      march_rows_split(d, e);
-    }
+    if (act && lane < 4) node_apply(d, split_node(d, w, lane & 3), cur_next);
+    else if (act && lane == 4) elem_split(d, d.pl_e[w]);
   }
-  // the commit changes no value that another block of this kernel reads
-  if (vb.x == 0 && threadIdx.x == 0) {
-    cnt->n_ph = cnt->pend_nph;
-    cnt->n_ck = cnt->pend_nck;
-    cnt->n_S = cnt->pend_nS;
-    cnt->n_dead += cnt->pend_dead;
-    cnt->n_win_last = nw;
-    if (mode == TRACK_STEP) cnt->step = step + 1;
-  }
+  apply_commit(d, vb, mode);
 }
 
 __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_next, int mode) {
@@ -811,16 +835,36 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
   apply_nodes(d, vb, cur_next, mode);
 }
 
-// Launched as a programmatic dependent of the kernel before it in the
-// stream: its CTAs may be placed while that kernel's last wave still runs,
-// and wait here until it has completed and its writes are visible.  It lets
-// the next step's tile update be placed in turn (that kernel waits for this
-// one the same way).
+// In a step graph, launched as a programmatic dependent of the node update
+// (the selection and the phantom update before it have completed): its CTAs
+// may be placed while the node update's last wave still runs, write phase 1
+// and read their plan, none of which the node update touches, and wait here
+// until the node update has completed and its writes are visible.
 __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
-  apply_tables(d, hw_vblk(), mode);
+  const VBlk vb = hw_vblk();
+  apply_tables(d, vb, mode);
+  // with at most four winners per warp each thread has at most one node
+  // write (or the element's): its plan is read before the wait, so that
+  // only the node update's own outputs are read after it
+  const int nw = d.cnt->pend_nwin;
+  const int lane32 = threadIdx.x & 31, lane = lane32 & 7;
+  const int w = ((vb.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane32 >> 3);
+  const bool one_pass = nw <= ((vb.gx * blockDim.x) >> 5) * 4;
+  SplitNode q;
+  int es = -1;
+  if (one_pass && w < nw) {
+    if (lane < 4) q = split_node(d, w, lane);
+    else if (lane == 4) es = d.pl_e[w];
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
-  apply_nodes(d, hw_vblk(), cur_next, mode);
+  if (!one_pass) {
+    apply_nodes(d, vb, cur_next, mode);
+    return;
+  }
+  if (w < nw && lane < 4) node_apply(d, q, cur_next);
+  if (es >= 0) elem_split(d, es);
+  apply_commit(d, vb, mode);
 }
 
 // APPLY_VB virtual CTAs per member of a batch; the last CTA to finish
@@ -940,7 +984,8 @@ cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st) {
+cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st,
+                         bool programmatic) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(64);
   cfg.blockDim = dim3(256);
@@ -950,7 +995,7 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = programmatic ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply, d, cur_next, mode);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -991,5 +1036,8 @@ cudaError_t launch_apply_batch(const BatchDev &b, cudaStream_t st) {
 }
 
 int track_sort_capacity() { return SORT_CAP; }
+
+const void *apply_kernel() { return reinterpret_cast<const void *>(&k_apply); }
+const void *select_kernel() { return reinterpret_cast<const void *>(&k_select); }
 
 }  // namespace cem

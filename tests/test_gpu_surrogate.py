@@ -332,7 +332,7 @@ def test_unet_loss_gradients_vs_oracle():
     g = net.grads_numpy()
     rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
     loss_e, g_e = _unet_bf16_reference(pr, x3, t, chans, 4.0)
-    assert abs(loss.item() - loss_e) <= 1e-4 * abs(loss_e)
+    assert abs(loss[0].item() - loss_e) <= 1e-4 * abs(loss_e)
     errs = {k: rel(g[k], g_e[k]) for k in g_e}
     print("relative gradient errors vs the BF16-storage reference:",
           {k: round(v, 5) for k, v in errs.items()})
