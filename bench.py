@@ -306,9 +306,9 @@ def run_ours(args, rank, world):
         traffic, traffic_window = args.traffic, "given on the command line"
 
     # end to end through the C ABI: one cem_step_async(1) per step from the
-    # host (each call reads back the previous step's status word while its
-    # own step runs), load factors uploaded from pinned host memory, and a
-    # final cem_sync for the last status
+    # host (each call reads back the previous step's status word, written to
+    # mapped pinned memory, while its own step runs), load factors uploaded
+    # from pinned host memory, and a final cem_sync for the last status
     ne2e = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -390,8 +390,9 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 76, "steps": ne2e,
                 "how": "one cem_step_async(1) call per step from the host: graph launch, "
-                       "the status word (76 B) copied to pinned memory and read back by the "
-                       "next call while that call's step runs, a final cem_sync; load "
+                       "the status word (76 B) written by a one-warp kernel into mapped "
+                       "pinned host memory and read back by the next call while that "
+                       "call's step runs, a final cem_sync; load "
                        "factors uploaded from pinned memory in 4096-step tables (16 B per "
                        "step)"},
         "gpu_launches": launches,

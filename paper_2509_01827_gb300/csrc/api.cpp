@@ -67,7 +67,8 @@ struct cem_handle {
   cem_handle *in_batch = nullptr;  // set on a member of a batch
   TriMesh *tri = nullptr;          // set on an unstructured triangle mesh (tri.cu)
   // cem_step_async: two pinned status slots, their events, which are pending
-  Counters *h_async = nullptr;
+  Counters *h_async = nullptr;  // two status slots, mapped pinned memory
+  Counters *d_async = nullptr;  // their device alias
   cudaEvent_t async_ev[2] = {nullptr, nullptr};
   int async_next = 0;
   unsigned async_pending = 0;
@@ -925,7 +926,8 @@ cem_status cem_step_async(cem_handle *h, int n) {
   if (rc != CEM_OK) return rc;
   CUDA_TRY(h, cudaSetDevice(h->device));
   if (!h->h_async) {
-    CUDA_TRY(h, cudaHostAlloc((void **)&h->h_async, 2 * sizeof(Counters), cudaHostAllocDefault));
+    CUDA_TRY(h, cudaHostAlloc((void **)&h->h_async, 2 * sizeof(Counters), cudaHostAllocMapped));
+    CUDA_TRY(h, cudaHostGetDevicePointer((void **)&h->d_async, h->h_async, 0));
     for (auto &ev : h->async_ev) CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   }
   // a slot still pending from two calls ago is collected first
@@ -938,7 +940,8 @@ cem_status cem_step_async(cem_handle *h, int n) {
     if (rc != CEM_OK) return rc;
   }
   const int slot = h->async_next;
-  CUDA_TRY(h, cudaMemcpyAsync(&h->h_async[slot], h->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, launch_status_copy(h->d.cnt, h->d_async + slot, h->st));
+  h->launches += 1;
   CUDA_TRY(h, cudaEventRecord(h->async_ev[slot], h->st));
   h->async_pending |= 1u << slot;
   h->async_next ^= 1;

@@ -282,6 +282,8 @@ cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st);
 cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st,
                          bool programmatic = false);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
+// copies the counters into host_mapped (a device alias of mapped pinned memory)
+cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st);
 // proposals one step can hold: the selection sorts (a power of two) that many
 // at most, in shared memory or in its global scratch of that size
 int track_sort_capacity();

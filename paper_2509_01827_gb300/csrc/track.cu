@@ -967,6 +967,14 @@ __global__ void k_surface_info(DevState d, int *out3) {
   }
 }
 
+// The status word of a pipelined step call, copied by a kernel into mapped
+// pinned host memory: no copy-engine operation between the calls' graphs.
+__global__ void k_status_copy(const Counters *cnt, Counters *out) {
+  constexpr int n = (int)(sizeof(Counters) / sizeof(int));
+  const int i = threadIdx.x;
+  if (i < n) reinterpret_cast<volatile int *>(out)[i] = reinterpret_cast<const int *>(cnt)[i];
+}
+
 }  // namespace
 
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
@@ -998,6 +1006,11 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
   cfg.numAttrs = programmatic ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply, d, cur_next, mode);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st) {
+  k_status_copy<<<1, 32, 0, st>>>(cnt, host_mapped);
   return cudaGetLastError();
 }
 
