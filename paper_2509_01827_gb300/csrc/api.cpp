@@ -72,6 +72,16 @@ struct cem_handle {
   cudaEvent_t async_ev[2] = {nullptr, nullptr};
   int async_next = 0;
   unsigned async_pending = 0;
+  long async_from[2] = {0, 0};  // steps taken before the call held by each slot
+  int async_steps[2] = {0, 0};  // and its step count (0: no per-step words)
+  // per-step status words of pipelined calls: kStatusRing slots of mapped
+  // pinned memory, each step's written by a one-warp kernel after its split
+  // writes (on aux2, so the next step does not wait for it)
+  Counters *h_ring = nullptr, *d_ring = nullptr;
+  bool ring_on = false;          // the steps being enqueued write their word
+  cudaEvent_t post = nullptr;    // after a step's split writes
+  cudaGraphExec_t rgraphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // with the words
+  std::map<unsigned, cudaGraphExec_t> rmulti;
 };
 
 namespace {
@@ -230,16 +240,21 @@ cem_status ensure_march_rows(cem_handle *h) {
 }
 
 void drop_graphs(cem_handle *h) {
-  for (auto &row : h->graphs)
-    for (auto &g : row)
-      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-  for (auto &kv : h->multi) cudaGraphExecDestroy(kv.second);
-  h->multi.clear();
+  for (auto *set : {&h->graphs, &h->rgraphs})
+    for (auto &row : *set)
+      for (auto &g : row)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (auto *m : {&h->multi, &h->rmulti}) {
+    for (auto &kv : *m) cudaGraphExecDestroy(kv.second);
+    m->clear();
+  }
 }
 
 // kernels one step launches: the step kernels, selection and split writes,
 // the energy prologue and epilogue on record steps
-int kernels_in_step(const cem_handle *, bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
+int kernels_in_step(const cem_handle *h, bool energy) {
+  return kStepKernels + 2 + (energy ? 2 : 0) + (h->ring_on ? 1 : 0);
+}
 
 // Enqueues one explicit step (buffers cur -> cur^1) on the stream.  With
 // marks (profiling) events are recorded after the energy prologue, after
@@ -268,6 +283,12 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
                         cs == cudaStreamCaptureStatusActive;
   e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st, captured);
   if (marks) cudaEventRecord(marks[7], h->st);
+  if (e == cudaSuccess && h->ring_on && !marks) {
+    // the step's status word into the ring, beside the next step
+    cudaEventRecord(h->post, h->st);
+    cudaStreamWaitEvent(h->ss.aux2, h->post, 0);
+    e = launch_status_ring(d.cnt, h->d_ring, kStatusRing, h->ss.aux2);
+  }
   return e;
 }
 
@@ -305,6 +326,14 @@ cudaError_t create_aux_streams(StepStreams &ss) {
   if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux1, cudaStreamNonBlocking, greatest);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux2, cudaStreamNonBlocking, greatest);
   return ce;
+}
+
+// The last status-word kernel on aux2 joins the main stream (a capture must
+// end on it; a call's event must follow it).
+void rejoin_ring(cem_handle *h) {
+  if (!h->ring_on) return;
+  cudaEventRecord(h->ss.join2, h->ss.aux2);
+  cudaStreamWaitEvent(h->st, h->ss.join2, 0);
 }
 
 // A kernel launched as a programmatic dependent right after cross-stream
@@ -345,20 +374,21 @@ cudaError_t ordinary_side_edges(cudaGraph_t g) {
 }
 
 cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
-  if (!h->graphs[cur][energy]) {
+  cudaGraphExec_t &slot = h->ring_on ? h->rgraphs[cur][energy] : h->graphs[cur][energy];
+  if (!slot) {
     cudaGraph_t g;
     CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_step(h, cur, false, energy != 0);
+    rejoin_ring(h);
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
     cudaError_t e3 = ordinary_side_edges(g);
-    if (e3 == cudaSuccess)
-      e3 = cudaGraphInstantiate(&h->graphs[cur][energy], g, cudaGraphInstantiateFlagUseNodePriority);
+    if (e3 == cudaSuccess) e3 = cudaGraphInstantiate(&slot, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
   }
-  *out = h->graphs[cur][energy];
+  *out = slot;
   return CEM_OK;
 }
 
@@ -381,13 +411,15 @@ int group_mask(long step, int energy_every) {
 
 cem_status multi_graph_for(cem_handle *h, int cur, unsigned mask, cudaGraphExec_t *out) {
   const unsigned key = (unsigned)cur | (mask << 1);
-  auto it = h->multi.find(key);
-  if (it == h->multi.end()) {
+  auto &cache = h->ring_on ? h->rmulti : h->multi;
+  auto it = cache.find(key);
+  if (it == cache.end()) {
     cudaGraph_t g;
     CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < kGraphSteps && e == cudaSuccess; ++q)
       e = enqueue_step(h, cur ^ (q & 1), false, ((mask >> q) & 1) != 0);
+    rejoin_ring(h);
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
@@ -396,7 +428,7 @@ cem_status multi_graph_for(cem_handle *h, int cur, unsigned mask, cudaGraphExec_
     if (e3 == cudaSuccess) e3 = cudaGraphInstantiate(&x, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e3));
-    it = h->multi.emplace(key, x).first;
+    it = cache.emplace(key, x).first;
   }
   *out = it->second;
   return CEM_OK;
@@ -628,6 +660,8 @@ void cem_mesh_destroy(cem_handle *h) {
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->h_lam) cudaFreeHost(h->h_lam);
   if (h->h_async) cudaFreeHost(h->h_async);
+  if (h->h_ring) cudaFreeHost(h->h_ring);
+  if (h->post) cudaEventDestroy(h->post);
   for (cudaEvent_t ev : h->async_ev)
     if (ev) cudaEventDestroy(ev);
   if (h->ss.aux1) cudaStreamDestroy(h->ss.aux1);
@@ -857,6 +891,7 @@ cem_status enqueue_steps(cem_handle *h, int n) {
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
         CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
+        rejoin_ring(h);
       } else {
         cudaGraphExec_t gx;
         rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
@@ -873,13 +908,23 @@ cem_status enqueue_steps(cem_handle *h, int n) {
   return CEM_OK;
 }
 
-// The status of the oldest pending cem_step_async call, after waiting for it.
+// The status of the oldest pending cem_step_async call, after waiting for it:
+// every step's status word in the ring (a call of at most kStatusRing / 2
+// steps), then the word copied after the call.
 cem_status async_collect(cem_handle *h) {
   const int slot = h->async_next ^ 1;
   int first = (h->async_pending & (1u << h->async_next)) ? h->async_next : slot;
   if (!(h->async_pending & (1u << first))) return CEM_OK;
   CUDA_TRY(h, cudaEventSynchronize(h->async_ev[first]));
   h->async_pending &= ~(1u << first);
+  for (int q = 0; q < h->async_steps[first]; ++q) {
+    const long taken = h->async_from[first] + q + 1;  // steps taken after step q of the call
+    const Counters c = h->h_ring[taken % kStatusRing];
+    if (c.step != (int)taken)
+      return fail(h, CEM_ERR_CUDA, "status word of step %ld missing from the ring", taken - 1);
+    cem_status rc = check_counters(h, c);
+    if (rc != CEM_OK) return rc;
+  }
   return check_counters(h, h->h_async[first]);
 }
 
@@ -928,18 +973,28 @@ cem_status cem_step_async(cem_handle *h, int n) {
   if (!h->h_async) {
     CUDA_TRY(h, cudaHostAlloc((void **)&h->h_async, 2 * sizeof(Counters), cudaHostAllocMapped));
     CUDA_TRY(h, cudaHostGetDevicePointer((void **)&h->d_async, h->h_async, 0));
+    CUDA_TRY(h, cudaHostAlloc((void **)&h->h_ring, kStatusRing * sizeof(Counters),
+                              cudaHostAllocMapped));
+    CUDA_TRY(h, cudaHostGetDevicePointer((void **)&h->d_ring, h->h_ring, 0));
     for (auto &ev : h->async_ev) CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventCreateWithFlags(&h->post, cudaEventDisableTiming));
   }
   // a slot still pending from two calls ago is collected first
   if (h->async_pending & (1u << h->async_next)) {
     rc = async_collect(h);
     if (rc != CEM_OK) return rc;
   }
+  const int slot = h->async_next;
+  // every step writes its status word when the call is short enough that
+  // the next call cannot overwrite them before they are read
+  h->async_from[slot] = h->step;
+  h->async_steps[slot] = n <= kStatusRing / 2 ? n : 0;
   if (n > 0) {
+    h->ring_on = n <= kStatusRing / 2;
     rc = enqueue_steps(h, n);
+    h->ring_on = false;
     if (rc != CEM_OK) return rc;
   }
-  const int slot = h->async_next;
   CUDA_TRY(h, launch_status_copy(h->d.cnt, h->d_async + slot, h->st));
   h->launches += 1;
   CUDA_TRY(h, cudaEventRecord(h->async_ev[slot], h->st));

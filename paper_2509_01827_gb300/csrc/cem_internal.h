@@ -284,6 +284,11 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 // copies the counters into host_mapped (a device alias of mapped pinned memory)
 cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st);
+// copies the counters into ring[cnt->step % R] (mapped pinned memory)
+cudaError_t launch_status_ring(const Counters *cnt, Counters *ring, int R, cudaStream_t st);
+// slots of the per-step status ring of pipelined step calls; a call of at
+// most kStatusRing / 2 steps has every step's status word read back
+constexpr int kStatusRing = 64;
 // proposals one step can hold: the selection sorts (a power of two) that many
 // at most, in shared memory or in its global scratch of that size
 int track_sort_capacity();

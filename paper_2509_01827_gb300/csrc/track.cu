@@ -975,6 +975,16 @@ __global__ void k_status_copy(const Counters *cnt, Counters *out) {
   if (i < n) reinterpret_cast<volatile int *>(out)[i] = reinterpret_cast<const int *>(cnt)[i];
 }
 
+// One step's status word, after its split writes, into slot (steps taken)
+// mod R of a ring in mapped pinned host memory.
+__global__ void k_status_ring(const Counters *cnt, Counters *ring, int R) {
+  constexpr int n = (int)(sizeof(Counters) / sizeof(int));
+  const int i = threadIdx.x;
+  const int slot = cnt->step % R;
+  if (i < n)
+    reinterpret_cast<volatile int *>(ring + slot)[i] = reinterpret_cast<const int *>(cnt)[i];
+}
+
 }  // namespace
 
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
@@ -1011,6 +1021,11 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
 
 cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st) {
   k_status_copy<<<1, 32, 0, st>>>(cnt, host_mapped);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status_ring(const Counters *cnt, Counters *ring, int R, cudaStream_t st) {
+  k_status_ring<<<1, 32, 0, st>>>(cnt, ring, R);
   return cudaGetLastError();
 }
 

@@ -44,18 +44,26 @@ def test_one_call_equals_single_steps(precision):
     b.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_async_steps_equal_blocking_steps(precision):
-    """cem_step_async, one step per call with each call collecting the
-    previous call's status, then cem_sync, ends bit-identical to cem_step."""
+@pytest.mark.parametrize("precision,calls", [(0, "ones"), (1, "ones"), (0, "mixed"), (1, "mixed")])
+def test_async_steps_equal_blocking_steps(precision, calls):
+    """cem_step_async, each call collecting the previous call's status (and,
+    for calls of at most 32 steps, every step's status word from the ring),
+    then cem_sync, ends bit-identical to cem_step: one step per call, or a
+    mix of 1-, 3-, 8-, 16- and 40-step calls (eight-step graphs with and
+    without the per-step words, energy records inside them)."""
     from paper_2509_01827_gb300.cem import Solver
     p = inputs.notched_plate(100, 40, traction=3e6, steps=0, phantom_cap=20000, crack_cap=4000)
     p.energy_every = 10
     a, b = Solver(p, precision=precision), Solver(p, precision=precision)
     n = 237
     a.step(n)
-    for _ in range(n):
-        b.step_async(1)
+    pattern = [1] if calls == "ones" else [1, 1, 8, 8, 3, 40, 8, 16, 1, 8]
+    done, q = 0, 0
+    while done < n:
+        k = min(pattern[q % len(pattern)], n - done)
+        b.step_async(k)
+        done += k
+        q += 1
     b.sync()
     na, nb = a.nodes(), b.nodes()
     for k in ("ux", "uy", "vx", "vy", "m"):
