@@ -16,13 +16,18 @@ Metric: element-updates/s = active elements * steps / time.
   (FP32-mixed) over its average launch time.  Beside it: the whole run from
   t = 0 to 60 us in both precisions (throughput of each, and the FP32 crack
   pattern against the FP64 one: Jaccard over time, fragments, branching
-  time), one-call-per-step end-to-end throughput, and the CPU oracle on a
-  bounded sample.
+  time), end-to-end throughput through pipelined eight-step calls, and the
+  CPU oracle on a bounded sample.
 --impl reference: the CPU oracle as it stands (the only reference this
   method has), timed on a bounded sample on this host.
 Multi-GPU (torchrun): one independent replica per GPU (the path does not
 shard across GPUs); value = all ranks' element-updates / max rank time.
 
+--workload notched_plate_100x40 / notched_plate_400x160: the single notched
+  plates (1 mm and 0.25 mm elements, 1 MPa traction), L2-resident, so their
+  throughput is latency- and L2-bound; use --min-tips 0.
+--workload fragmentation_2048_dirichlet: the same plate under a 2 m/s
+  outward edge velocity.
 --workload specimens_64: 64 notched plates from 100 x 40 to 400 x 160 (seed
   1827), each run to 80 us with its own time step, stepped together as one
   batch (one launch per kernel kind for all specimens); the launch
@@ -61,8 +66,12 @@ def make_problem(workload):
         p = inputs.fragmentation(2048, mode="neumann", p0=50e6, seed=2509)
     elif workload == "fragmentation_2048_dirichlet":
         p = inputs.fragmentation(2048, mode="dirichlet", v0=2.0, seed=2509)
-    elif workload == "notched_plate_400x160":
-        p = inputs.CONFIGS["notched_plate_400x160"]()
+    elif workload in ("notched_plate_100x40", "notched_plate_400x160"):
+        p = inputs.CONFIGS[workload]()
+        # room for the cracks of the timed, profiled and end-to-end steps
+        # beyond the configuration's own end time
+        p.phantom_cap = max(p.phantom_cap, 4 * p.nx * p.ny)
+        p.crack_cap = max(p.crack_cap, p.nx * p.ny)
     else:
         raise SystemExit(f"unknown workload {workload}")
     p.energy_every = 50

@@ -75,11 +75,9 @@ struct cem_handle {
   long async_from[2] = {0, 0};  // steps taken before the call held by each slot
   int async_steps[2] = {0, 0};  // and its step count (0: no per-step words)
   // per-step status words of pipelined calls: kStatusRing slots of mapped
-  // pinned memory, each step's written by a one-warp kernel after its split
-  // writes (on aux2, so the next step does not wait for it)
+  // pinned memory, each step's written by the last block of its split writes
   Counters *h_ring = nullptr, *d_ring = nullptr;
   bool ring_on = false;          // the steps being enqueued write their word
-  cudaEvent_t post = nullptr;    // after a step's split writes
   cudaGraphExec_t rgraphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // with the words
   std::map<unsigned, cudaGraphExec_t> rmulti;
 };
@@ -252,9 +250,7 @@ void drop_graphs(cem_handle *h) {
 
 // kernels one step launches: the step kernels, selection and split writes,
 // the energy prologue and epilogue on record steps
-int kernels_in_step(const cem_handle *h, bool energy) {
-  return kStepKernels + 2 + (energy ? 2 : 0) + (h->ring_on ? 1 : 0);
-}
+int kernels_in_step(const cem_handle *, bool energy) { return kStepKernels + 2 + (energy ? 2 : 0); }
 
 // Enqueues one explicit step (buffers cur -> cur^1) on the stream.  With
 // marks (profiling) events are recorded after the energy prologue, after
@@ -281,14 +277,9 @@ cudaError_t enqueue_step(cem_handle *h, int cur, bool first, bool energy,
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool captured = !marks && cudaStreamIsCapturing(h->st, &cs) == cudaSuccess &&
                         cs == cudaStreamCaptureStatusActive;
-  e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st, captured);
+  e = launch_apply(d, cur ^ 1, TRACK_STEP, h->st, captured,
+                   h->ring_on && !marks ? h->d_ring : nullptr);
   if (marks) cudaEventRecord(marks[7], h->st);
-  if (e == cudaSuccess && h->ring_on && !marks) {
-    // the step's status word into the ring, beside the next step
-    cudaEventRecord(h->post, h->st);
-    cudaStreamWaitEvent(h->ss.aux2, h->post, 0);
-    e = launch_status_ring(d.cnt, h->d_ring, kStatusRing, h->ss.aux2);
-  }
   return e;
 }
 
@@ -326,14 +317,6 @@ cudaError_t create_aux_streams(StepStreams &ss) {
   if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux1, cudaStreamNonBlocking, greatest);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ss.aux2, cudaStreamNonBlocking, greatest);
   return ce;
-}
-
-// The last status-word kernel on aux2 joins the main stream (a capture must
-// end on it; a call's event must follow it).
-void rejoin_ring(cem_handle *h) {
-  if (!h->ring_on) return;
-  cudaEventRecord(h->ss.join2, h->ss.aux2);
-  cudaStreamWaitEvent(h->st, h->ss.join2, 0);
 }
 
 // A kernel launched as a programmatic dependent right after cross-stream
@@ -379,7 +362,6 @@ cem_status graph_for(cem_handle *h, int cur, int energy, cudaGraphExec_t *out) {
     cudaGraph_t g;
     CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_step(h, cur, false, energy != 0);
-    rejoin_ring(h);
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
@@ -419,7 +401,6 @@ cem_status multi_graph_for(cem_handle *h, int cur, unsigned mask, cudaGraphExec_
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < kGraphSteps && e == cudaSuccess; ++q)
       e = enqueue_step(h, cur ^ (q & 1), false, ((mask >> q) & 1) != 0);
-    rejoin_ring(h);
     cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
     if (e != cudaSuccess) return fail(h, CEM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(h, CEM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e2));
@@ -661,7 +642,6 @@ void cem_mesh_destroy(cem_handle *h) {
   if (h->h_lam) cudaFreeHost(h->h_lam);
   if (h->h_async) cudaFreeHost(h->h_async);
   if (h->h_ring) cudaFreeHost(h->h_ring);
-  if (h->post) cudaEventDestroy(h->post);
   for (cudaEvent_t ev : h->async_ev)
     if (ev) cudaEventDestroy(ev);
   if (h->ss.aux1) cudaStreamDestroy(h->ss.aux1);
@@ -891,8 +871,7 @@ cem_status enqueue_steps(cem_handle *h, int n) {
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
         CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
-        rejoin_ring(h);
-      } else {
+          } else {
         cudaGraphExec_t gx;
         rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
         if (rc != CEM_OK) return rc;
@@ -977,7 +956,6 @@ cem_status cem_step_async(cem_handle *h, int n) {
                               cudaHostAllocMapped));
     CUDA_TRY(h, cudaHostGetDevicePointer((void **)&h->d_ring, h->h_ring, 0));
     for (auto &ev : h->async_ev) CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CUDA_TRY(h, cudaEventCreateWithFlags(&h->post, cudaEventDisableTiming));
   }
   // a slot still pending from two calls ago is collected first
   if (h->async_pending & (1u << h->async_next)) {

@@ -37,7 +37,8 @@ struct Counters {
   // planned by the selection kernel, committed by the apply kernel
   int pend_nwin, pend_nph, pend_nck, pend_nS, pend_dead;
   int pend_step;  // step of the planned splits (read by the apply kernel)
-  int pad[2];
+  int pad[1];
+  int apply_done;  // blocks of the split writes finished this step (status ring)
 };
 
 struct Geo {
@@ -278,14 +279,14 @@ cudaError_t launch_step_fp32(const DevState &d, int cur, bool first, bool energy
 // node updates) then the split writes (many CTAs; after the node updates).
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st);
 // programmatic: launched as a programmatic dependent of the kernel before it
-// (used in captured step graphs, whose edges ordinary_side_edges fixes)
+// (used in captured step graphs, whose edges ordinary_side_edges fixes);
+// ring: when given, the last block to finish copies the counters into
+// ring[steps taken % kStatusRing] (mapped pinned memory)
 cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st,
-                         bool programmatic = false);
+                         bool programmatic = false, Counters *ring = nullptr);
 cudaError_t launch_build_surface(const DevState &d, cudaStream_t st);
 // copies the counters into host_mapped (a device alias of mapped pinned memory)
 cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st);
-// copies the counters into ring[cnt->step % R] (mapped pinned memory)
-cudaError_t launch_status_ring(const Counters *cnt, Counters *ring, int R, cudaStream_t st);
 // slots of the per-step status ring of pipelined step calls; a call of at
 // most kStatusRing / 2 steps has every step's status word read back
 constexpr int kStatusRing = 64;

@@ -840,7 +840,27 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
 // may be placed while the node update's last wave still runs, write phase 1
 // and read their plan, none of which the node update touches, and wait here
 // until the node update has completed and its writes are visible.
-__global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode) {
+// With a status ring, the last block of the split writes to finish copies
+// the counters (committed by block 0) into ring[steps taken % kStatusRing].
+__device__ __forceinline__ void ring_status(const DevState &d, Counters *ring) {
+  __shared__ bool last;
+  __syncthreads();  // every write of this block is issued
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&d.cnt->apply_done, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  constexpr int n = (int)(sizeof(Counters) / sizeof(int));
+  volatile int *c = reinterpret_cast<volatile int *>(d.cnt);
+  if (threadIdx.x == 0) c[offsetof(Counters, apply_done) / sizeof(int)] = 0;
+  __syncthreads();
+  const int slot = c[offsetof(Counters, step) / sizeof(int)] % kStatusRing;
+  if (threadIdx.x < n) reinterpret_cast<volatile int *>(ring + slot)[threadIdx.x] = c[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode, Counters *ring) {
   const VBlk vb = hw_vblk();
   apply_tables(d, vb, mode);
   // with at most four winners per warp each thread has at most one node
@@ -860,11 +880,12 @@ __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mod
   asm volatile("griddepcontrol.launch_dependents;");
   if (!one_pass) {
     apply_nodes(d, vb, cur_next, mode);
-    return;
+  } else {
+    if (w < nw && lane < 4) node_apply(d, q, cur_next);
+    if (es >= 0) elem_split(d, es);
+    apply_commit(d, vb, mode);
   }
-  if (w < nw && lane < 4) node_apply(d, q, cur_next);
-  if (es >= 0) elem_split(d, es);
-  apply_commit(d, vb, mode);
+  if (ring) ring_status(d, ring);
 }
 
 // APPLY_VB virtual CTAs per member of a batch; the last CTA to finish
@@ -975,16 +996,6 @@ __global__ void k_status_copy(const Counters *cnt, Counters *out) {
   if (i < n) reinterpret_cast<volatile int *>(out)[i] = reinterpret_cast<const int *>(cnt)[i];
 }
 
-// One step's status word, after its split writes, into slot (steps taken)
-// mod R of a ring in mapped pinned host memory.
-__global__ void k_status_ring(const Counters *cnt, Counters *ring, int R) {
-  constexpr int n = (int)(sizeof(Counters) / sizeof(int));
-  const int i = threadIdx.x;
-  const int slot = cnt->step % R;
-  if (i < n)
-    reinterpret_cast<volatile int *>(ring + slot)[i] = reinterpret_cast<const int *>(cnt)[i];
-}
-
 }  // namespace
 
 cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
@@ -1003,7 +1014,7 @@ cudaError_t launch_select(const DevState &d, int mode, cudaStream_t st) {
 }
 
 cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t st,
-                         bool programmatic) {
+                         bool programmatic, Counters *ring) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(64);
   cfg.blockDim = dim3(256);
@@ -1014,18 +1025,13 @@ cudaError_t launch_apply(const DevState &d, int cur_next, int mode, cudaStream_t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = programmatic ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply, d, cur_next, mode);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_apply, d, cur_next, mode, ring);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_status_copy(const Counters *cnt, Counters *host_mapped, cudaStream_t st) {
   k_status_copy<<<1, 32, 0, st>>>(cnt, host_mapped);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_status_ring(const Counters *cnt, Counters *ring, int R, cudaStream_t st) {
-  k_status_ring<<<1, 32, 0, st>>>(cnt, ring, R);
   return cudaGetLastError();
 }
 
