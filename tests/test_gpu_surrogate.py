@@ -72,6 +72,40 @@ def test_conv3x3_forward(relu):
     assert np.all(yg[..., :yoff] == 0)  # other channels untouched
 
 
+@pytest.mark.parametrize("cin,cout", [(32, 32), (16, 136)])
+def test_conv3x3_many_tiles(cin, cout):
+    """64,000 pixels: several waves of 128-pixel tiles on the tcgen05 path
+    (with a ragged channel tile for 136 outputs).  Against the oracle, with
+    bias and ReLU, and as a data gradient with the ReLU mask of a layer
+    input."""
+    import ctypes
+    import torch
+    from oracle import surrogate_oracle as so
+    from paper_2509_01827_gb300.surrogate import _p, sg
+    x, w, b = _conv_case(B=8, H=80, W=100, Cin=cin, Cout=cout, seed=cin + cout)
+    B, H, W, _ = x.shape
+    P = B * H * W
+    L = sg()
+    xd, wd, bd = _t(x, torch.bfloat16), _t(w, torch.bfloat16), _t(b, torch.float32)
+    y = torch.zeros((P, cout), dtype=torch.bfloat16, device="cuda")
+    assert L.cem_sg_conv3x3(_p(xd), B, H, W, cin, cin, _p(wd), _p(bd), cout, 1, None, 0, _p(y),
+                            cout, 0, 0) == 0
+    mask = _t(bf16_round(np.random.default_rng(5).standard_normal((P, cout))), torch.bfloat16)
+    ym = torch.zeros_like(y)
+    assert L.cem_sg_conv3x3(_p(xd), B, H, W, cin, cin, _p(wd), None, cout, 0, _p(mask), cout,
+                            _p(ym), cout, 0, 0) == 0
+    torch.cuda.synchronize()
+    ref = so.conv2d(x, w, b, 1)
+    assert _rel(y.float().cpu().numpy().reshape(B, H, W, cout), so.relu(ref)) < 1e-2
+    ref0 = (ref - b).reshape(P, cout)
+    got = ym.float().cpu().numpy()
+    keep = mask.float().cpu().numpy() > 0
+    assert np.all(got[~keep] == 0)
+    assert _rel(np.where(keep, got, 0.0), np.where(keep, ref0, 0.0)) < 1e-2
+    n = ctypes.c_int(-1)
+    assert L.cem_sg_timeouts(ctypes.byref(n)) == 0 and n.value == 0
+
+
 def test_conv3x3_weight_gradient_and_data_gradient():
     import torch
     from oracle import surrogate_oracle as so
