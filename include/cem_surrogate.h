@@ -132,8 +132,8 @@ int cem_sg_adam(float *w, const float *g, float *m, float *v, long n, float lr, 
                 void *stream);
 
 /* Selects the tensor-core path of cem_sg_conv3x3 for later calls: 1 (the
- * default) = tcgen05 MMAs with a TMEM accumulator and a 4-stage
- * shared-memory ring (one CTA per SM, 128 threads), 0 = warp-level mma.sync
+ * default) = tcgen05 MMAs with a TMEM accumulator and a 2-stage
+ * shared-memory ring (CTAs of 128 threads, two to five per SM), 0 = warp-level mma.sync
  * m16n8k16 with register accumulators.  Both compute the same sums (FP32
  * accumulation in a different order).  Process-wide; not synchronised with
  * work in flight. */
