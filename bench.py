@@ -398,12 +398,12 @@ def run_ours(args, rank, world):
                      "avg_launch_ms": main_ms, "share_of_step": share,
                      "profiled_steps": nprof, "per_kernel_ms": prof},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 16,
-                "d2h_bytes_per_step": 76 + 76 / per_call, "steps": ne2e,
+                "d2h_bytes_per_step": 76, "steps": ne2e,
                 "how": "one cem_step_async(8) call per 8 steps from the host (an "
                        "eight-step graph): every step's status word (76 B) is written by "
-                       "a one-warp kernel into a ring in mapped pinned host memory, and "
-                       "the call's own word after it; the next call reads them back "
-                       "while its steps run, a final cem_sync; load "
+                       "the last block of its split writes into a ring in mapped pinned "
+                       "host memory; the next call reads them back while its steps run, "
+                       "a final cem_sync; load "
                        "factors uploaded from pinned memory in 4096-step tables (16 B per "
                        "step)"},
         "gpu_launches": launches,
@@ -469,6 +469,8 @@ def run_batch(args, rank, world):
     clocks.start()
     time.sleep(0.3)
     nrun = max(steps) - args.warmup
+    if args.batch_steps > 0:
+        nrun = min(nrun, args.batch_steps)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
@@ -482,7 +484,7 @@ def run_batch(args, rank, world):
     ms = e0.elapsed_time(e1)
     c1 = b.counts()
     launches = c1["kernel_launches"] - c0["kernel_launches"]
-    timed_updates = sum(p.n_active * max(0, n - args.warmup) for p, n in zip(probs, steps))
+    timed_updates = sum(p.n_active * max(0, min(n - args.warmup, nrun)) for p, n in zip(probs, steps))
     value, ms = replica_throughput(timed_updates, ms, world)
     cracked = c1["n_cracked"]
     b.close()
@@ -602,6 +604,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune-steps", type=int, default=5)
     ap.add_argument("--solo-sample", type=int, default=8)
+    ap.add_argument("--batch-steps", type=int, default=0,
+                    help="specimens_64: time only this many batch steps (0: the whole run)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the node update, overriding the "
                          "committed summary")

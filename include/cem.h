@@ -221,12 +221,13 @@ cem_status cem_set_fields(cem_handle *h, int which, const void *data,
 cem_status cem_step(cem_handle *h, int n);
 
 /* Pipelined stepping of a structured mesh handle: enqueues n steps like
- * cem_step (eight-step graphs where they fit) and a one-warp kernel that
- * copies the status word into mapped pinned host memory (no copy-engine
- * operation between graphs); with n <= 32 every step also writes its own
- * status word into a 64-slot ring there.  Then waits for the previous
- * cem_step_async call's steps to finish and returns that call's status,
- * checking each of its steps' words (the first call returns CEM_OK).  The
+ * cem_step (eight-step graphs where they fit).  With 1 <= n <= 32 every step
+ * writes its status word into a 64-slot ring in mapped pinned host memory
+ * (the last block of its split writes does); otherwise a one-warp kernel
+ * copies the status word there after the call (no copy-engine operation
+ * between graphs either way).  Then waits for the previous cem_step_async
+ * call's steps to finish and returns that call's status, checking each of
+ * its steps' words (the first call returns CEM_OK).  The
  * host's wait overlaps the steps just enqueued, so back-to-back calls keep
  * the GPU busy; each call's errors (CEM_ERR_NONFINITE, CEM_ERR_CAPACITY)
  * are reported by the call after it, or by cem_sync.  cem_step drains

@@ -888,8 +888,9 @@ cem_status enqueue_steps(cem_handle *h, int n) {
 }
 
 // The status of the oldest pending cem_step_async call, after waiting for it:
-// every step's status word in the ring (a call of at most kStatusRing / 2
-// steps), then the word copied after the call.
+// every step's status word in the ring (a call of 1 .. kStatusRing / 2
+// steps; the last one is the call's status), else the word copied after
+// the call.
 cem_status async_collect(cem_handle *h) {
   const int slot = h->async_next ^ 1;
   int first = (h->async_pending & (1u << h->async_next)) ? h->async_next : slot;
@@ -904,7 +905,7 @@ cem_status async_collect(cem_handle *h) {
     cem_status rc = check_counters(h, c);
     if (rc != CEM_OK) return rc;
   }
-  return check_counters(h, h->h_async[first]);
+  return h->async_steps[first] > 0 ? CEM_OK : check_counters(h, h->h_async[first]);
 }
 
 // waits for every pending cem_step_async call; the first error
@@ -973,8 +974,11 @@ cem_status cem_step_async(cem_handle *h, int n) {
     h->ring_on = false;
     if (rc != CEM_OK) return rc;
   }
-  CUDA_TRY(h, launch_status_copy(h->d.cnt, h->d_async + slot, h->st));
-  h->launches += 1;
+  if (h->async_steps[slot] == 0) {
+    // no per-step words: the status word after the call
+    CUDA_TRY(h, launch_status_copy(h->d.cnt, h->d_async + slot, h->st));
+    h->launches += 1;
+  }
   CUDA_TRY(h, cudaEventRecord(h->async_ev[slot], h->st));
   h->async_pending |= 1u << slot;
   h->async_next ^= 1;

@@ -1251,7 +1251,7 @@ int cem_sg_conv3x3(const void *x, int B, int H, int W, int Cin, int ldx, const v
 long cem_sg_wgrad_workspace(int B, int H, int W, int Cin, int Cout) {
   const long P = (long)B * H * W;
   long splits = (P + 4095) / 4096;
-  if (splits > 256) splits = 256;
+  if (splits > 512) splits = 512;
   return splits * (long)Cout * 9 * Cin * 4 + (long)Cout * 4 * 1024;
 }
 
@@ -1270,7 +1270,7 @@ int cem_sg_conv3x3_wgrad(const void *x, int ldx, const void *dy, int lddy, int B
   a.B = B; a.H = H; a.W = W; a.Cin = Cin; a.ldx = ldx; a.lddy = lddy; a.N = Cout;
   a.K = 9 * Cin; a.P = B * H * W;
   int splits = (a.P + 4095) / 4096;
-  if (splits > 256) splits = 256;
+  if (splits > 512) splits = 512;
   a.chunk = ((a.P + splits - 1) / splits + GBK - 1) / GBK * GBK;
   splits = (a.P + a.chunk - 1) / a.chunk;
   const long nw = (long)Cout * a.K;
