@@ -250,8 +250,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--dice", type=float, default=0.0,
-                    help="weight of the soft Dice term added to the weighted BCE")
+    ap.add_argument("--dice", type=float, default=1.0,
+                    help="weight of the soft Dice term added to the weighted BCE (0: BCE only)")
     ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chans", default="32,64,128,256,512",
