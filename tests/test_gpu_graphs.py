@@ -82,7 +82,9 @@ def test_async_steps_equal_blocking_steps(precision, calls):
 
 def test_async_errors_come_one_call_late():
     """A non-finite state makes the steps of one cem_step_async call fail:
-    that call returns, and the next call (or cem_sync) reports the error."""
+    that call returns, and the next call (or cem_sync) reports the error,
+    from the per-step status words (3-step calls) or from the word copied
+    after the call (40-step calls)."""
     from paper_2509_01827_gb300.cem import CEM_ERR_NONFINITE, CemError, Solver
     p = inputs.notched_plate(37, 19, steps=0)
     s = Solver(p, precision=1)
@@ -99,5 +101,12 @@ def test_async_errors_come_one_call_late():
     s.step_async(3)
     with pytest.raises(CemError) as ei:
         s.step_async(1)
+    assert ei.value.code == CEM_ERR_NONFINITE
+    s.close()
+    s = Solver(p, precision=1)
+    s.set_state(vx=vx)
+    s.step_async(40)
+    with pytest.raises(CemError) as ei:
+        s.step_async(40)
     assert ei.value.code == CEM_ERR_NONFINITE
     s.close()
