@@ -228,7 +228,8 @@ def advance_to_tips(sol, min_tips, max_steps, chunk=100):
 
 def accuracy_block(c32, c64, prob, dt, series_us=(5, 10, 20, 30, 40, 50, 60)):
     """FP32-mixed against FP64 crack patterns of the same run (Jaccard of the
-    cracked-element sets over time, fragments, branching step)."""
+    cracked-element sets over time, fragments, branching time and branch
+    angle)."""
     from paper_2509_01827_gb300 import metrics
     out = {"jaccard_end": metrics.jaccard(c32["elem"], c64["elem"]),
            "cracked_fp32": int(len(c32["elem"])), "cracked_fp64": int(len(c64["elem"]))}
@@ -242,6 +243,8 @@ def accuracy_block(c32, c64, prob, dt, series_us=(5, 10, 20, 30, 40, 50, 60)):
     for tag, c in (("fp32", c32), ("fp64", c64)):
         s_ = metrics.branching_step(c, prob.nx, prob.ny, prob.hx, prob.hy, prob.active)
         out[f"branching_t_us_{tag}"] = None if s_ is None else round(s_ * dt * 1e6, 3)
+        ang, _ = metrics.branch_angle(c, prob.nx, prob.ny, prob.hx, prob.hy, prob.active)
+        out[f"branch_angle_deg_{tag}"] = None if ang is None else round(ang, 2)
     return out
 
 
