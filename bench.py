@@ -11,9 +11,10 @@ Metric: element-updates/s = active elements * steps / time.
 --impl ours (default): the CUDA library.  After --warmup steps the run is
   advanced, untimed, past crack initiation until the tip list holds
   --min-tips tips; the --steps steps that follow are timed with CUDA events
-  (graph replays).  The roofline of the node update comes from a profiled
-  window right after (per-kernel CUDA events), 53 B per element-update
-  (FP32-mixed) over its average launch time.  Beside it: the whole run from
+  (graph replays).  The roofline of the node update comes from the same
+  steps replayed from the timed window's saved start state with per-kernel
+  CUDA events, 53 B per element-update (FP32-mixed) over its average launch
+  time.  Beside it: the whole run from
   t = 0 to 60 us in both precisions (throughput of each, and the FP32 crack
   pattern against the FP64 one: Jaccard over time, fragments, branching
   time), end-to-end throughput through pipelined eight-step calls, and the
@@ -269,6 +270,9 @@ def run_ours(args, rank, world):
     sol.step(args.warmup)
     adv = advance_to_tips(sol, args.min_tips, args.max_advance) if args.min_tips > 0 else 0
     torch.cuda.synchronize()
+    # the state at the start of the timed window: its steps are replayed for
+    # the per-kernel profile below
+    start_blob = sol.save_state()
     c0 = sol.counts()
     uuid = None
     try:
@@ -297,10 +301,14 @@ def run_ours(args, rank, world):
     c1 = sol.counts()
     launches = c1["kernel_launches"] - c0["kernel_launches"]
 
-    # per-kernel device time over a profiled window right after the timed one
-    # (kernels one after another, CUDA events on the launching stream)
-    nprof = max(1, min(args.profile_steps, 4000))
+    # per-kernel device time over the timed window's own steps, replayed from
+    # its saved start state (kernels one after another, CUDA events on the
+    # launching stream); the run then continues from the timed window's end
+    nprof = max(1, min(args.profile_steps, args.steps, 4000))
+    end_blob = sol.save_state()
+    sol.load_state(start_blob)
     prof = sol.profile_steps(nprof)
+    sol.load_state(end_blob)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
@@ -399,7 +407,10 @@ def run_ours(args, rank, world):
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "bytes_per_element_update": bpu,
                      "avg_launch_ms": main_ms, "share_of_step": share,
-                     "profiled_steps": nprof, "per_kernel_ms": prof},
+                     "profiled_steps": nprof,
+                     "profiled_window": "the timed window's first profiled_steps steps, replayed "
+                                        "from its saved start state, kernels one after another",
+                     "per_kernel_ms": prof},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 76, "steps": ne2e,
                 "how": "one cem_step_async(8) call per 8 steps from the host (an "
@@ -595,7 +606,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="fragmentation_2048_neumann")
-    ap.add_argument("--profile-steps", type=int, default=300)
+    ap.add_argument("--profile-steps", type=int, default=1000,
+                    help="steps of the timed window replayed with per-kernel timing (at most --steps)")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--whole-run", type=int, default=1,
                     help="also time the whole run in both precisions and compare crack patterns")
