@@ -410,7 +410,11 @@ def run_ours(args, rank, world):
                      "profiled_steps": nprof,
                      "profiled_window": "the timed window's first profiled_steps steps, replayed "
                                         "from its saved start state, kernels one after another",
-                     "per_kernel_ms": prof},
+                     "per_kernel_ms": prof,
+                     **({} if args.precision == "fp32" else {
+                         "note": "the FP64 mode is bound by the FP64 pipe, not by HBM: 0.96 of "
+                                 "its measured instruction rate (ncu summary of k_main64); this "
+                                 "line states its HBM fraction only"})},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 76, "steps": ne2e,
                 "how": "one cem_step_async(8) call per 8 steps from the host (an "
