@@ -871,7 +871,7 @@ cem_status enqueue_steps(cem_handle *h, int n) {
       bool energy = h->energy_every > 0 && (h->step % h->energy_every) == 0;
       if (h->step == 0) {
         CUDA_TRY(h, enqueue_step(h, h->cur, true, energy));
-          } else {
+      } else {
         cudaGraphExec_t gx;
         rc = graph_for(h, h->cur, energy ? 1 : 0, &gx);
         if (rc != CEM_OK) return rc;
