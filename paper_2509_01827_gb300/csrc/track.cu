@@ -835,11 +835,6 @@ __device__ __forceinline__ void apply_plan(const DevState &d, VBlk vb, int cur_n
   apply_nodes(d, vb, cur_next, mode);
 }
 
-// In a step graph, launched as a programmatic dependent of the node update
-// (the selection and the phantom update before it have completed): its CTAs
-// may be placed while the node update's last wave still runs, write phase 1
-// and read their plan, none of which the node update touches, and wait here
-// until the node update has completed and its writes are visible.
 // With a status ring, the last block of the split writes to finish copies
 // the counters (committed by block 0) into ring[steps taken % kStatusRing].
 __device__ __forceinline__ void ring_status(const DevState &d, Counters *ring) {
@@ -860,6 +855,11 @@ __device__ __forceinline__ void ring_status(const DevState &d, Counters *ring) {
   if (threadIdx.x < n) reinterpret_cast<volatile int *>(ring + slot)[threadIdx.x] = c[threadIdx.x];
 }
 
+// In a step graph, launched as a programmatic dependent of the node update
+// (the selection and the phantom update before it have completed): its CTAs
+// may be placed while the node update's last wave still runs, write phase 1
+// and read their plan, none of which the node update touches, and wait here
+// until the node update has completed and its writes are visible.
 __global__ void __launch_bounds__(256) k_apply(DevState d, int cur_next, int mode, Counters *ring) {
   const VBlk vb = hw_vblk();
   apply_tables(d, vb, mode);
